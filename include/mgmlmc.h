@@ -1,0 +1,240 @@
+/*
+ * mgmlmc.h -- C ABI of the GB300 (sm_103a) library for orthogonal-projector
+ * multigrid multilevel Monte Carlo trace estimation in lattice QCD
+ * (Frommer, Jimenez-Merchan, Knechtli, Korzec, Ramirez-Hidalgo,
+ * arXiv:2509.11424).
+ *
+ * The library computes, on one GPU, the estimators of the paper:
+ *   tr(D^-1) = sum_{l<L} tr(O_l) + sum_{l<L} tr(F_l) + tr(D_L^-1)      (Sec. 3)
+ *   O_l = (I - P_l P_l^H) D_l^-1 (I - P_l P_l^H),
+ *   F_l = P_l^H D_l^-1 P_l - D_{l+1}^-1                   (Eq. OandF_def)
+ * each term by Hutchinson's method with Z4 noise (Sec. 1, Eq. Hutchinson and
+ * Eq. z4), with every level solve D_l z = y driven to a relative residual
+ * (1e-12 in the paper, Sec. 4) by FGMRES preconditioned with a multigrid
+ * cycle that starts at level l.  It also estimates the connected
+ * pseudoscalar correlator G(t) (Eq. connected-G) through the orthogonal split
+ * of Eq. full_ops_orth / Eq. G-split, and the disconnected loops
+ * tr(Gamma5 D^-1(t,t)) (Eq. trace_equality_disconnected).
+ *
+ * Conventions
+ *   Levels are 0-based here: level 0 is the fine lattice (the paper's l = 1).
+ *   Complex numbers are interleaved (re, im) pairs of double (FP64) or
+ *   float (FP32).
+ *   Canonical layouts (host and device buffers passed to this API):
+ *     site s = x + Lx (y + Ly (z + Lz t)), dims = {Lx, Ly, Lz, Lt};
+ *     fine vector: index (s * 4 + spin) * 3 + colour (12 per site);
+ *     coarse vector at level l >= 1: index (X * 2 N_tv + c * N_tv + k) for
+ *       coarse site X (same ordering as s on the coarse lattice), chirality
+ *       c in {0, 1} and test vector k;
+ *     links: U[s][mu][a][b], mu = 0..3 = x, y, z, t (4 * 9 complex per site);
+ *     multi-vectors (nrhs right-hand sides): nrhs vectors stored one after
+ *       the other, each in the canonical vector layout.
+ *   The Wilson operator (the paper uses only its Gamma5-hermiticity, Sec. 2):
+ *     (D psi)(x) = (4 + m0) psi(x) - 1/2 sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                                   + (1 + gamma_mu) U_mu(x-mu)^H psi(x-mu) ]
+ *   in the chiral basis (gamma_5 = diag(1, 1, -1, -1)), periodic in space,
+ *   antiperiodic in time.
+ *   Z4 noise (Eq. z4): entry i of a noise vector for (seed, sample, term, aux)
+ *     takes word (i & 3) of Philox4x64-10 with counter
+ *     (i >> 2, sample, term, aux) and key (seed, 0), r = word >> 62 and
+ *     x_i = i^r.  term = 0 plain Hutchinson, 16 + l for O_l, 32 + l for F_l,
+ *     48 for the coarsest level, 64 for connected-correlator sources
+ *     (aux = source slice), 80 for disconnected loops (aux = slice).
+ *
+ * Ownership and streams
+ *   The context owns every device buffer it allocates; caller buffers are
+ *   only read or written during the call.  Every kernel is launched on the
+ *   stream given to mgmlmc_create (0 = legacy default stream).  Calls that
+ *   return host results synchronise that stream.  A context is not
+ *   thread-safe; use one context per host thread.
+ *
+ * Errors
+ *   Every call returns an mgmlmc_status and never aborts the process.
+ *   mgmlmc_last_error() returns a description of the last failure of that
+ *   context.  A solve that hits its iteration cap or meets a NaN/Inf returns
+ *   MGMLMC_ERR_NOT_CONVERGED / MGMLMC_ERR_NUMERIC; the context stays usable.
+ */
+#ifndef MGMLMC_H
+#define MGMLMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MGMLMC_MAX_LEVELS 4
+
+typedef struct mgmlmc_ctx mgmlmc_ctx;
+
+typedef enum {
+  MGMLMC_OK = 0,
+  MGMLMC_ERR_ARG = 1,            /* invalid argument */
+  MGMLMC_ERR_STATE = 2,          /* call out of order (e.g. no hierarchy yet) */
+  MGMLMC_ERR_OOM = 3,            /* device allocation failed */
+  MGMLMC_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+  MGMLMC_ERR_NOT_CONVERGED = 5,  /* iteration cap reached */
+  MGMLMC_ERR_NUMERIC = 6         /* NaN / Inf / breakdown */
+} mgmlmc_status;
+
+typedef enum { MGMLMC_FP64 = 0, MGMLMC_FP32 = 1 } mgmlmc_precision;
+
+/* Multigrid hierarchy (Sec. 2.2: aggregation-based P_l with P_l^H P_l = I,
+ * Galerkin D_{l+1} = P_l^H D_l P_l; Sec. 4: test vectors are rough
+ * approximations, residual ~1e-1, to low modes). */
+typedef struct {
+  int n_levels;                        /* L, 1 .. MGMLMC_MAX_LEVELS */
+  int block[MGMLMC_MAX_LEVELS - 1][4]; /* aggregate extents for level l -> l+1 */
+  int n_tv[MGMLMC_MAX_LEVELS - 1];     /* test vectors for level l -> l+1 */
+  int setup_rounds;   /* rounds of approximate inverse iteration */
+  int setup_iters;    /* Krylov iterations per round (rough solves) */
+  uint64_t seed;      /* seed of the initial random test vectors */
+} mgmlmc_mg_params;
+
+/* Level solver: FGMRES(restart) preconditioned by a multigrid K-cycle that
+ * starts at the level being solved (Sec. 4: all levels to 1e-12). */
+typedef struct {
+  double tol;          /* relative residual target ||b - D x|| / ||b|| */
+  int max_iter;        /* cap on outer FGMRES iterations per solve */
+  int restart;         /* FGMRES restart length, 1 .. 64 */
+  int smoother_steps;  /* minimal-residual smoothing steps per cycle */
+  int coarse_iters;    /* FGMRES iterations on intermediate levels */
+  int precision;       /* MGMLMC_FP64: all FP64.  MGMLMC_FP32: FP32 inner
+                          solves inside FP64 defect correction */
+  double inner_tol;    /* FP32 inner relative tolerance (defect correction) */
+} mgmlmc_solver_params;
+
+typedef enum { MGMLMC_EST_PLAIN = 0, MGMLMC_EST_ORTHOGONAL = 1 } mgmlmc_estimator;
+
+/* Term codes of the results (same numbers as the noise term ids). */
+#define MGMLMC_TERM_PLAIN 0
+#define MGMLMC_TERM_O 16        /* + level */
+#define MGMLMC_TERM_F 32        /* + level */
+#define MGMLMC_TERM_COARSEST 48
+
+typedef struct {
+  int kind;          /* mgmlmc_estimator */
+  int n_samples[2 * MGMLMC_MAX_LEVELS]; /* per term in the order
+                       O_0..O_{L-2}, F_0..F_{L-2}, coarsest; plain: [0] */
+  int batch;         /* right-hand sides solved together, >= 1 */
+  uint64_t seed;     /* noise seed */
+  uint64_t first_sample; /* sample counter of the first sample */
+} mgmlmc_est_params;
+
+typedef struct {
+  int term;            /* MGMLMC_TERM_* code */
+  int n;               /* samples taken */
+  double mean_re, mean_im;
+  double var;          /* 1/(N-1) sum |X_i - mean|^2 (Sec. 4) */
+  double sum_re, sum_im, sum_abs2; /* raw accumulators (resume / merge) */
+  double seconds;      /* device time spent on this term */
+  double iters_mean;   /* mean outer iterations per level solve */
+  double max_residual; /* largest true relative residual of its solves */
+} mgmlmc_term_result;
+
+/* ---- context -------------------------------------------------------------- */
+
+/* Create a context for a lattice of extents dims[4] (each >= 2 and even
+ * extents are not required; aggregation needs divisibility).  stream is a
+ * cudaStream_t (NULL = legacy default stream).  Uses the current device. */
+mgmlmc_status mgmlmc_create(const int dims[4], void *stream, mgmlmc_ctx **out);
+/* Release every device buffer of the context.  NULL is accepted. */
+void mgmlmc_destroy(mgmlmc_ctx *ctx);
+/* Description of the last failure (never NULL). */
+const char *mgmlmc_last_error(const mgmlmc_ctx *ctx);
+
+/* Gauge field (Sec. 1: 4-D lattice, 12 dof per site): 4 * V * 9 complex
+ * double in the canonical link layout; host pointer (on_device = 0) or
+ * device pointer (on_device = 1).  Invalidates the hierarchy. */
+mgmlmc_status mgmlmc_set_gauge(mgmlmc_ctx *ctx, const double *U, int on_device);
+/* Bare mass m0 of the Wilson operator.  Invalidates the hierarchy. */
+mgmlmc_status mgmlmc_set_mass(mgmlmc_ctx *ctx, double m0);
+/* Solver parameters (defaults: tol 1e-12, max_iter 2000, restart 16,
+ * smoother_steps 4, coarse_iters 8, FP64). */
+mgmlmc_status mgmlmc_set_solver(mgmlmc_ctx *ctx, const mgmlmc_solver_params *p);
+/* Import the N_tv test vectors of level `level` (0 .. L-2): n_tv vectors of
+ * length n (the level's vector length), one after the other (canonical
+ * layout, complex double), host or device.  The library keeps a copy; a later
+ * mgmlmc_build_hierarchy uses them for that level instead of its own setup
+ * (the parity hook: P and D_{l+1} become deterministic functions of the given
+ * vectors) and fails with MGMLMC_ERR_ARG if n or n_tv do not match. */
+mgmlmc_status mgmlmc_set_test_vectors(mgmlmc_ctx *ctx, int level, const double *V,
+                                      int n_tv, int64_t n, int on_device);
+/* Build P_l (per-aggregate, per-chirality modified Gram-Schmidt run twice),
+ * D_{l+1} = P_l^H D_l P_l for every level and the dense inverse of the
+ * coarsest operator. */
+mgmlmc_status mgmlmc_build_hierarchy(mgmlmc_ctx *ctx, const mgmlmc_mg_params *p);
+/* Size information of a level: dims[4] of its lattice, dofs per site and
+ * vector length (complex entries). */
+mgmlmc_status mgmlmc_level_info(const mgmlmc_ctx *ctx, int level, int dims[4],
+                                int *dof, int64_t *n);
+
+/* ---- estimators ----------------------------------------------------------- */
+
+/* tr(D^-1) by plain Hutchinson (kind 0) or by the orthogonal multilevel
+ * split (kind 1).  Writes one mgmlmc_term_result per term (plain: 1;
+ * orthogonal: 2(L-1)+1 in the order O_0.., F_0.., coarsest) into out[max_terms]
+ * and their count into *n_terms. */
+mgmlmc_status mgmlmc_estimate_trace(mgmlmc_ctx *ctx, const mgmlmc_est_params *p,
+                                    mgmlmc_term_result *out, int max_terms, int *n_terms);
+/* Exact trace of the coarsest-level inverse, tr(D_L^-1), from its dense
+ * inverse (Sec. 3 allows a direct computation of this term). */
+mgmlmc_status mgmlmc_coarsest_trace(mgmlmc_ctx *ctx, double *re, double *im);
+
+/* Connected correlator split (Eq. G-split), orthogonal operators of Eq.
+ * full_ops_orth with R = 2L-1 terms.  For samples k = first .. first+n-1 and
+ * every source slice t' in [0, T) (all slices), with Z4 noise x on slice t':
+ *   X_rs(t) = (1/T) sum_t' (Btil_s x)|_{t+t'}^H (B_r x)|_{t+t'},
+ *   Btil = Gamma5 B^H Gamma5.
+ * kind 0 (plain) uses the single operator D^-1 (R = 1).  Output (host):
+ * mean[R][R][T] and var[R][R][T] complex mean / real variance over samples. */
+mgmlmc_status mgmlmc_connected_correlator(mgmlmc_ctx *ctx, int kind, int n_samples,
+                                          uint64_t seed, uint64_t first_sample,
+                                          double *mean, double *var, int *R);
+/* Disconnected loop tr(Gamma5 D^-1(t,t)) = sum_r tr(Gamma5 B_r(t,t)): samples
+ * X_r = x^H Gamma5 B_r x with Z4 noise x on slice t.  Output mean[R] complex,
+ * var[R] real. */
+mgmlmc_status mgmlmc_disconnected_loop(mgmlmc_ctx *ctx, int kind, int t, int n_samples,
+                                       uint64_t seed, uint64_t first_sample,
+                                       double *mean, double *var, int *R);
+
+/* ---- operator hooks (device buffers, canonical layouts) ------------------ */
+
+typedef enum {
+  MGMLMC_OP_D = 0,        /* out = D_l in                      (level l)       */
+  MGMLMC_OP_RESTRICT = 1, /* out = P_l^H in      (level l -> level l+1)         */
+  MGMLMC_OP_PROLONG = 2,  /* out = P_l in        (level l+1 -> level l)         */
+  MGMLMC_OP_PROJECT = 3,  /* out = (I - P_l P_l^H) in            (level l)      */
+  MGMLMC_OP_SOLVE = 4,    /* out = D_l^-1 in by the MG-preconditioned solver   */
+  MGMLMC_OP_GAMMA5 = 5    /* out = Gamma5 in (level l)                         */
+} mgmlmc_op;
+
+/* Apply an operator to nrhs device vectors.  precision selects the storage
+ * type of in/out (complex double for MGMLMC_FP64, complex float for
+ * MGMLMC_FP32; MGMLMC_OP_SOLVE accepts MGMLMC_FP64 only, its internal
+ * precision is the solver's).  in and out must not overlap. */
+mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op, int level, int precision,
+                           const void *in, void *out, int nrhs);
+/* Z4 noise (Eq. z4) of `level` for samples first_sample .. + nrhs - 1 into a
+ * device multi-vector (complex double).  slice < 0: full support; otherwise
+ * supported on time slice `slice` of that level's lattice. */
+mgmlmc_status mgmlmc_noise(mgmlmc_ctx *ctx, int level, uint64_t seed, uint64_t first_sample,
+                           uint64_t term, uint64_t aux, int slice, double *out, int nrhs);
+/* Copy P_l to host as [aggregate][chirality][row][k] complex double, row =
+ * site_in_aggregate * dof/2 + (dof within chirality); site_in_aggregate
+ * ordered like s inside the block. */
+mgmlmc_status mgmlmc_get_prolongator(mgmlmc_ctx *ctx, int level, double *out);
+/* Copy the stencil blocks of D_l (level >= 1) to host as
+ * [X][d][i][j] complex double, d = 0 self, 1 + 2 mu (+mu), 2 + 2 mu (-mu);
+ * block d of X collects the fine hops of direction d leaving aggregate X,
+ * block 0 the diagonal and the hops staying inside X. */
+mgmlmc_status mgmlmc_get_coarse_op(mgmlmc_ctx *ctx, int level, double *out);
+/* Statistics of the last solve: outer iterations (max over rhs) and true
+ * relative residual (max over rhs). */
+mgmlmc_status mgmlmc_last_solve_stats(const mgmlmc_ctx *ctx, int *iters, double *residual);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MGMLMC_H */

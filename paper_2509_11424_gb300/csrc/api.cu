@@ -1,0 +1,257 @@
+// extern "C" boundary of libmgmlmc.so (declared in include/mgmlmc.h).  Every
+// entry point catches the engine's exceptions and turns them into a status
+// code plus a message retrievable with mgmlmc_last_error().
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "engine.h"
+
+struct mgmlmc_ctx {
+  mg::Engine *eng = nullptr;
+  std::string err;
+};
+
+namespace {
+thread_local std::string g_create_error;
+
+template <typename F> mgmlmc_status guard(mgmlmc_ctx *ctx, F &&f) {
+  if (!ctx) return MGMLMC_ERR_ARG;
+  try {
+    f();
+    return MGMLMC_OK;
+  } catch (const mg::Error &e) {
+    ctx->err = e.what();
+    // a failed kernel launch may leave a sticky error state; surface it
+    return (mgmlmc_status)e.code;
+  } catch (const std::bad_alloc &) {
+    ctx->err = "host allocation failed";
+    return MGMLMC_ERR_OOM;
+  } catch (const std::exception &e) {
+    ctx->err = e.what();
+    return MGMLMC_ERR_ARG;
+  }
+}
+
+mg::Engine &E(mgmlmc_ctx *ctx) { return *ctx->eng; }
+}  // namespace
+
+extern "C" {
+
+mgmlmc_status mgmlmc_create(const int dims[4], void *stream, mgmlmc_ctx **out) {
+  if (!dims || !out) return MGMLMC_ERR_ARG;
+  *out = nullptr;
+  mgmlmc_ctx *ctx = new (std::nothrow) mgmlmc_ctx();
+  if (!ctx) return MGMLMC_ERR_OOM;
+  try {
+    ctx->eng = new mg::Engine(dims, static_cast<cudaStream_t>(stream));
+  } catch (const mg::Error &e) {
+    g_create_error = e.what();
+    delete ctx;
+    return (mgmlmc_status)e.code;
+  } catch (const std::exception &e) {
+    g_create_error = e.what();
+    delete ctx;
+    return MGMLMC_ERR_OOM;
+  }
+  *out = ctx;
+  return MGMLMC_OK;
+}
+
+void mgmlmc_destroy(mgmlmc_ctx *ctx) {
+  if (!ctx) return;
+  delete ctx->eng;
+  delete ctx;
+}
+
+const char *mgmlmc_last_error(const mgmlmc_ctx *ctx) {
+  if (!ctx) return g_create_error.c_str();
+  return ctx->err.c_str();
+}
+
+mgmlmc_status mgmlmc_set_gauge(mgmlmc_ctx *ctx, const double *U, int on_device) {
+  return guard(ctx, [&] {
+    if (!U) throw mg::Error(MGMLMC_ERR_ARG, "U is NULL");
+    E(ctx).set_gauge(U, on_device != 0);
+  });
+}
+
+mgmlmc_status mgmlmc_set_mass(mgmlmc_ctx *ctx, double m0) {
+  return guard(ctx, [&] { E(ctx).set_mass(m0); });
+}
+
+mgmlmc_status mgmlmc_set_solver(mgmlmc_ctx *ctx, const mgmlmc_solver_params *p) {
+  return guard(ctx, [&] {
+    if (!p) throw mg::Error(MGMLMC_ERR_ARG, "params is NULL");
+    E(ctx).set_solver(*p);
+  });
+}
+
+mgmlmc_status mgmlmc_set_test_vectors(mgmlmc_ctx *ctx, int level, const double *V, int n_tv,
+                                      int64_t n, int on_device) {
+  return guard(ctx, [&] { E(ctx).set_test_vectors(level, V, n_tv, n, on_device != 0); });
+}
+
+mgmlmc_status mgmlmc_build_hierarchy(mgmlmc_ctx *ctx, const mgmlmc_mg_params *p) {
+  return guard(ctx, [&] {
+    if (!p) throw mg::Error(MGMLMC_ERR_ARG, "params is NULL");
+    E(ctx).build_hierarchy(*p);
+  });
+}
+
+mgmlmc_status mgmlmc_level_info(const mgmlmc_ctx *cctx, int level, int dims[4], int *dof,
+                                int64_t *n) {
+  mgmlmc_ctx *ctx = const_cast<mgmlmc_ctx *>(cctx);
+  return guard(ctx, [&] {
+    if (level < 0 || level >= E(ctx).n_levels()) throw mg::Error(MGMLMC_ERR_ARG, "level out of range");
+    const mg::Geom &g = E(ctx).level(level).g;
+    if (dims)
+      for (int i = 0; i < 4; ++i) dims[i] = g.L[i];
+    if (dof) *dof = g.dof;
+    if (n) *n = g.n();
+  });
+}
+
+mgmlmc_status mgmlmc_estimate_trace(mgmlmc_ctx *ctx, const mgmlmc_est_params *p,
+                                    mgmlmc_term_result *out, int max_terms, int *n_terms) {
+  return guard(ctx, [&] {
+    if (!p || !out || !n_terms) throw mg::Error(MGMLMC_ERR_ARG, "NULL argument");
+    std::vector<mg::TermAcc> acc;
+    E(ctx).estimate_trace(*p, acc);
+    if ((int)acc.size() > max_terms) throw mg::Error(MGMLMC_ERR_ARG, "max_terms too small");
+    *n_terms = (int)acc.size();
+    for (size_t i = 0; i < acc.size(); ++i) {
+      const mg::TermAcc &a = acc[i];
+      mgmlmc_term_result &r = out[i];
+      std::memset(&r, 0, sizeof(r));
+      r.term = a.term;
+      r.n = a.n;
+      r.sum_re = a.sre;
+      r.sum_im = a.sim;
+      r.sum_abs2 = a.sabs2;
+      r.seconds = a.seconds;
+      r.iters_mean = a.solves > 0 ? a.iters_sum / a.solves : 0.0;
+      r.max_residual = a.max_res;
+      if (a.n > 0) {
+        r.mean_re = a.sre / a.n;
+        r.mean_im = a.sim / a.n;
+        double v = 0.0;
+        for (const auto &x : a.samples) v += std::norm(x - std::complex<double>(r.mean_re, r.mean_im));
+        r.var = a.n > 1 ? v / (a.n - 1) : 0.0;
+      }
+    }
+  });
+}
+
+mgmlmc_status mgmlmc_coarsest_trace(mgmlmc_ctx *ctx, double *re, double *im) {
+  return guard(ctx, [&] {
+    if (!re || !im) throw mg::Error(MGMLMC_ERR_ARG, "NULL argument");
+    E(ctx).coarsest_trace(re, im);
+  });
+}
+
+mgmlmc_status mgmlmc_connected_correlator(mgmlmc_ctx *ctx, int kind, int n_samples, uint64_t seed,
+                                          uint64_t first_sample, double *mean, double *var, int *R) {
+  return guard(ctx, [&] {
+    if (!mean || !var || !R) throw mg::Error(MGMLMC_ERR_ARG, "NULL argument");
+    std::vector<double> m, v;
+    int r = 0;
+    E(ctx).connected(kind, n_samples, seed, first_sample, m, v, r);
+    std::memcpy(mean, m.data(), m.size() * sizeof(double));
+    std::memcpy(var, v.data(), v.size() * sizeof(double));
+    *R = r;
+  });
+}
+
+mgmlmc_status mgmlmc_disconnected_loop(mgmlmc_ctx *ctx, int kind, int t, int n_samples, uint64_t seed,
+                                       uint64_t first_sample, double *mean, double *var, int *R) {
+  return guard(ctx, [&] {
+    if (!mean || !var || !R) throw mg::Error(MGMLMC_ERR_ARG, "NULL argument");
+    std::vector<double> m, v;
+    int r = 0;
+    E(ctx).disconnected(kind, t, n_samples, seed, first_sample, m, v, r);
+    std::memcpy(mean, m.data(), m.size() * sizeof(double));
+    std::memcpy(var, v.data(), v.size() * sizeof(double));
+    *R = r;
+  });
+}
+
+mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op, int level, int precision, const void *in,
+                           void *out, int nrhs) {
+  return guard(ctx, [&] {
+    mg::Engine &e = E(ctx);
+    if (!in || !out || nrhs < 1) throw mg::Error(MGMLMC_ERR_ARG, "bad buffers or nrhs");
+    if (precision != MGMLMC_FP64 && precision != MGMLMC_FP32) throw mg::Error(MGMLMC_ERR_ARG, "bad precision");
+    if (level < 0 || level >= e.n_levels()) throw mg::Error(MGMLMC_ERR_ARG, "level out of range");
+    const bool dp = precision == MGMLMC_FP64;
+    const bool needs_next = op == MGMLMC_OP_RESTRICT || op == MGMLMC_OP_PROLONG || op == MGMLMC_OP_PROJECT;
+    if (needs_next && (!e.ready() || level + 1 >= e.n_levels()))
+      throw mg::Error(MGMLMC_ERR_STATE, "no transfer operator at that level");
+    if (level > 0 && !e.ready()) throw mg::Error(MGMLMC_ERR_STATE, "hierarchy not built");
+    switch (op) {
+      case MGMLMC_OP_D:
+        if (dp) e.apply_D<double>(level, (const double2 *)in, (double2 *)out, nrhs);
+        else e.apply_D<float>(level, (const float2 *)in, (float2 *)out, nrhs);
+        break;
+      case MGMLMC_OP_RESTRICT:
+        if (dp) e.restrict_to<double>(level, (const double2 *)in, (double2 *)out, nrhs);
+        else e.restrict_to<float>(level, (const float2 *)in, (float2 *)out, nrhs);
+        break;
+      case MGMLMC_OP_PROLONG:
+        if (dp) e.prolong_from<double>(level, (const double2 *)in, (double2 *)out, nrhs, 0.0);
+        else e.prolong_from<float>(level, (const float2 *)in, (float2 *)out, nrhs, 0.0);
+        break;
+      case MGMLMC_OP_PROJECT:
+        if (dp) e.project_out<double>(level, (const double2 *)in, (double2 *)out, nrhs);
+        else e.project_out<float>(level, (const float2 *)in, (float2 *)out, nrhs);
+        break;
+      case MGMLMC_OP_SOLVE:
+        if (!dp) throw mg::Error(MGMLMC_ERR_ARG, "solve takes FP64 buffers");
+        e.solve(level, (const double2 *)in, (double2 *)out, nrhs);
+        break;
+      case MGMLMC_OP_GAMMA5: {
+        const mg::Geom &g = e.level(level).g;
+        if (dp) mg::gamma5_apply<double>((const double2 *)in, (double2 *)out, g.V, g.dof, nrhs, e.stream);
+        else mg::gamma5_apply<float>((const float2 *)in, (float2 *)out, g.V, g.dof, nrhs, e.stream);
+        break;
+      }
+      default:
+        throw mg::Error(MGMLMC_ERR_ARG, "unknown op");
+    }
+    MG_CUDA(cudaGetLastError());
+  });
+}
+
+mgmlmc_status mgmlmc_noise(mgmlmc_ctx *ctx, int level, uint64_t seed, uint64_t first_sample,
+                           uint64_t term, uint64_t aux, int slice, double *out, int nrhs) {
+  return guard(ctx, [&] {
+    mg::Engine &e = E(ctx);
+    if (!out || nrhs < 1) throw mg::Error(MGMLMC_ERR_ARG, "bad buffer or nrhs");
+    if (level < 0 || level >= e.n_levels()) throw mg::Error(MGMLMC_ERR_ARG, "level out of range");
+    e.noise(level, seed, first_sample, term, aux, slice, (double2 *)out, nrhs);
+  });
+}
+
+mgmlmc_status mgmlmc_get_prolongator(mgmlmc_ctx *ctx, int level, double *out) {
+  return guard(ctx, [&] {
+    if (!out) throw mg::Error(MGMLMC_ERR_ARG, "NULL argument");
+    E(ctx).get_prolongator(level, out);
+  });
+}
+
+mgmlmc_status mgmlmc_get_coarse_op(mgmlmc_ctx *ctx, int level, double *out) {
+  return guard(ctx, [&] {
+    if (!out) throw mg::Error(MGMLMC_ERR_ARG, "NULL argument");
+    E(ctx).get_coarse_op(level, out);
+  });
+}
+
+mgmlmc_status mgmlmc_last_solve_stats(const mgmlmc_ctx *cctx, int *iters, double *residual) {
+  mgmlmc_ctx *ctx = const_cast<mgmlmc_ctx *>(cctx);
+  return guard(ctx, [&] {
+    if (iters) *iters = E(ctx).last_solve.iters;
+    if (residual) *residual = E(ctx).last_solve.residual;
+  });
+}
+
+}  // extern "C"

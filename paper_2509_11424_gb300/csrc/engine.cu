@@ -1,0 +1,717 @@
+// Host orchestration: hierarchy construction (Sec. 2.2 and Sec. 4: test
+// vectors, aggregation-based P_l with P_l^H P_l = I, Galerkin D_{l+1}),
+// the batched MG-preconditioned FGMRES level solves (the role DD-alpha-AMG
+// plays in Sec. 4: every level solved to a relative residual), and the
+// estimators of Sec. 3 / Sec. 4.
+#include "engine.h"
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+
+namespace mg {
+
+namespace {
+template <typename T> T *dalloc(size_t count) {
+  void *p = nullptr;
+  MG_CUDA(cudaMalloc(&p, count * sizeof(T) + 64));
+  return static_cast<T *>(p);
+}
+template <typename T> void dfree(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+__global__ void target_kernel(double *target, const double2 *nrm, double tol, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrhs) target[r] = tol * sqrt(fmax(nrm[r].x, 0.0));
+}
+__global__ void inv_norm_kernel(double *out, double *nrm_out, const double2 *nrm, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nrhs) {
+    const double v = sqrt(fmax(nrm[r].x, 0.0));
+    out[r] = v > 0.0 ? 1.0 / v : 0.0;
+    nrm_out[r] = v;
+  }
+}
+}  // namespace
+
+Engine::Engine(const int dims[4], cudaStream_t s) : stream(s) {
+  for (int i = 0; i < 4; ++i) {
+    if (dims[i] < 2) throw Error(MGMLMC_ERR_ARG, "lattice extents must be >= 2");
+    dims_[i] = dims[i];
+    fine_.L[i] = dims[i];
+  }
+  const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+  if (V * 12 * 9 > ((int64_t)1 << 40)) throw Error(MGMLMC_ERR_ARG, "lattice too large");
+  fine_.V = (int)V;
+  fine_.dof = 12;
+  sp_.tol = 1e-12;
+  sp_.max_iter = 2000;
+  sp_.restart = 16;
+  sp_.smoother_steps = 4;
+  sp_.coarse_iters = 8;
+  sp_.precision = MGMLMC_FP64;
+  sp_.inner_tol = 1e-6;
+  levels_.resize(1);
+  levels_[0].g = fine_;
+  levels_[0].fine = true;
+  levels_[0].U64 = dalloc<double2>((size_t)V * 36);
+  levels_[0].U32 = dalloc<float2>((size_t)V * 36);
+  scal_ = dalloc<double2>(4096);
+  flag_dev_ = dalloc<int>(16);
+}
+
+Engine::~Engine() {
+  free_hierarchy();
+  dfree(levels_[0].U64);
+  dfree(levels_[0].U32);
+  for (auto &kv : ws_) cudaFree(kv.second.first);
+  dfree(scal_);
+  dfree(partial_);
+  dfree(flag_dev_);
+  if (pinned_) cudaFreeHost(pinned_);
+}
+
+void Engine::sync() { MG_CUDA(cudaStreamSynchronize(stream)); }
+
+void *Engine::pinned(size_t bytes) {
+  if (bytes > pinned_cap_) {
+    if (pinned_) cudaFreeHost(pinned_);
+    pinned_ = nullptr;
+    MG_CUDA(cudaMallocHost(&pinned_, bytes));
+    pinned_cap_ = bytes;
+  }
+  return pinned_;
+}
+
+double2 *Engine::partials(size_t count) {
+  if (count > partial_cap_) {
+    sync();
+    dfree(partial_);
+    partial_ = dalloc<double2>(count);
+    partial_cap_ = count;
+  }
+  return partial_;
+}
+
+template <typename T> C<T> *Engine::ws(const std::string &name, int l, size_t count) {
+  const std::string key = name + "#" + std::to_string(l) + (sizeof(T) == 8 ? "d" : "f");
+  const size_t bytes = count * sizeof(C<T>);
+  auto it = ws_.find(key);
+  if (it != ws_.end() && it->second.second >= bytes) return static_cast<C<T> *>(it->second.first);
+  if (it != ws_.end()) {
+    sync();
+    cudaFree(it->second.first);
+    ws_.erase(it);
+  }
+  void *p = nullptr;
+  MG_CUDA(cudaMalloc(&p, bytes + 256));
+  ws_[key] = {p, bytes};
+  return static_cast<C<T> *>(p);
+}
+
+template <> const C<double> *Engine::Pmat<double>(int l) const { return levels_[l].P64; }
+template <> const C<float> *Engine::Pmat<float>(int l) const { return levels_[l].P32; }
+template <> const C<double> *Engine::Dinv<double>(int l) const { return levels_[l].Dinv64; }
+template <> const C<float> *Engine::Dinv<float>(int l) const { return levels_[l].Dinv32; }
+
+// ------------------------------------------------------------------ inputs
+void Engine::set_gauge(const double *U, bool on_device) {
+  const size_t cnt = (size_t)fine_.V * 36;
+  MG_CUDA(cudaMemcpyAsync(levels_[0].U64, U, cnt * sizeof(double2),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, stream));
+  MG_CUDA(cudaMemsetAsync(flag_dev_, 0, sizeof(int), stream));
+  check_finite<double>(levels_[0].U64, (int64_t)cnt, flag_dev_, stream);
+  int flag = 0;
+  MG_CUDA(cudaMemcpyAsync(&flag, flag_dev_, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  sync();
+  if (flag) {
+    have_gauge_ = false;
+    throw Error(MGMLMC_ERR_NUMERIC, "gauge field contains NaN or Inf");
+  }
+  convert<float, double>(levels_[0].U64, levels_[0].U32, (int64_t)cnt, stream);
+  have_gauge_ = true;
+  free_hierarchy();
+}
+
+void Engine::set_mass(double m0) {
+  if (!std::isfinite(m0)) throw Error(MGMLMC_ERR_ARG, "mass must be finite");
+  m0_ = m0;
+  free_hierarchy();
+}
+
+void Engine::set_solver(const mgmlmc_solver_params &p) {
+  if (!(p.tol > 0.0) || p.max_iter < 1 || p.restart < 1 || p.restart > 64 || p.smoother_steps < 0 ||
+      p.coarse_iters < 1 || p.coarse_iters > 64 ||
+      (p.precision != MGMLMC_FP64 && p.precision != MGMLMC_FP32) ||
+      (p.precision == MGMLMC_FP32 && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)))
+    throw Error(MGMLMC_ERR_ARG, "invalid solver parameters");
+  sp_ = p;
+}
+
+void Engine::set_test_vectors(int level, const double *V, int ntv, int64_t n, bool on_device) {
+  if (level < 0 || level >= MGMLMC_MAX_LEVELS - 1 || ntv < 1 || ntv > 64 || n < 1 || !V)
+    throw Error(MGMLMC_ERR_ARG, "set_test_vectors: bad level, count, length or pointer");
+  std::vector<double> &h = imported_host_[level];
+  h.assign((size_t)ntv * n * 2, 0.0);
+  MG_CUDA(cudaMemcpyAsync(h.data(), V, h.size() * sizeof(double),
+                          on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost, stream));
+  sync();
+  free_hierarchy();
+}
+
+void Engine::free_hierarchy() {
+  for (size_t l = 0; l < levels_.size(); ++l) {
+    Level &L = levels_[l];
+    dfree(L.P64);
+    dfree(L.P32);
+    dfree(L.Dinv64);
+    dfree(L.Dinv32);
+    if (l > 0) {
+      dfree(L.A64);
+      dfree(L.A32);
+    }
+    L.has_next = false;
+  }
+  levels_.resize(1);
+  ready_ = false;
+}
+
+// ------------------------------------------------------------------ operators
+template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int nrhs) {
+  const Level &L = levels_.at(l);
+  if (L.fine) {
+    const C<T> *U;
+    if constexpr (sizeof(T) == 8) U = L.U64; else U = L.U32;
+    wilson_apply<T>(in, out, U, L.g, m0_, nrhs, stream);
+  } else {
+    const C<T> *A;
+    if constexpr (sizeof(T) == 8) A = L.A64; else A = L.A32;
+    stencil_apply<T>(in, out, A, L.g, nrhs, stream);
+  }
+}
+
+template <typename T> void Engine::restrict_to(int l, const C<T> *in, C<T> *out, int nrhs) {
+  restrict_op<T>(in, out, Pmat<T>(l), levels_.at(l).agg, nrhs, stream);
+}
+template <typename T>
+void Engine::prolong_from(int l, const C<T> *in, C<T> *out, int nrhs, double beta) {
+  prolong_op<T>(in, out, Pmat<T>(l), levels_.at(l).agg, nrhs, beta, stream);
+}
+template <typename T> void Engine::project_out(int l, const C<T> *in, C<T> *out, int nrhs) {
+  const int64_t n = levels_[l].g.n(), nc = levels_[l + 1].g.n();
+  C<T> *xc = ws<T>("proj_c", l + 1, (size_t)nc * nrhs);
+  restrict_op<T>(in, xc, Pmat<T>(l), levels_[l].agg, nrhs, stream);
+  prolong_op<T>(xc, out, Pmat<T>(l), levels_[l].agg, nrhs, 0.0, stream);
+  axpby<T>(1.0, in, -1.0, out, n, nrhs, stream);
+}
+
+void Engine::noise(int l, uint64_t seed, uint64_t sample0, uint64_t term, uint64_t aux, int slice,
+                   double2 *out, int nrhs) {
+  const Level &L = levels_.at(l);
+  if (slice >= L.g.L[3]) throw Error(MGMLMC_ERR_ARG, "slice out of range");
+  z4_noise<double>(out, L.g, seed, sample0, term, aux, slice, nrhs, stream);
+}
+
+// ------------------------------------------------------------------ MG cycle
+// minimal-residual smoothing: res holds r - D z on entry and exit
+template <typename T> void Engine::smooth(int l, C<T> *z, C<T> *res, int nrhs) {
+  const int64_t n = levels_[l].g.n();
+  C<T> *q = ws<T>("smq", l, (size_t)n * nrhs);
+  double2 *d = ws<double>("smd", l, 2 * (size_t)nrhs);
+  for (int s = 0; s < sp_.smoother_steps; ++s) {
+    apply_D<T>(l, res, q, nrhs);
+    dot<T>(q, res, n, nrhs, d, partials((size_t)reduce_blocks(n) * nrhs), stream);
+    dot<T>(q, q, n, nrhs, d + nrhs, partials((size_t)reduce_blocks(n) * nrhs), stream);
+    mr_update<T>(z, res, q, d, d + nrhs, n, nrhs, stream);
+  }
+}
+
+// z = M r: pre-smoothing, coarse-grid correction (recursive K-cycle: a few
+// FGMRES iterations on the next level, exact dense solve on the coarsest),
+// post-smoothing.
+template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nrhs) {
+  const Level &L = levels_[l];
+  const int64_t n = L.g.n();
+  if (l == n_levels() - 1) {
+    dense_apply<T>(Dinv<T>(l), r, z, (int)n, nrhs, stream);
+    return;
+  }
+  const int64_t nc = levels_[l + 1].g.n();
+  C<T> *res = ws<T>("mgres", l, (size_t)n * nrhs);
+  C<T> *q = ws<T>("mgq", l, (size_t)n * nrhs);
+  C<T> *rc = ws<T>("mgrc", l + 1, (size_t)nc * nrhs);
+  C<T> *ec = ws<T>("mgec", l + 1, (size_t)nc * nrhs);
+  MG_CUDA(cudaMemsetAsync(z, 0, sizeof(C<T>) * n * nrhs, stream));
+  MG_CUDA(cudaMemcpyAsync(res, r, sizeof(C<T>) * n * nrhs, cudaMemcpyDeviceToDevice, stream));
+  smooth<T>(l, z, res, nrhs);
+  restrict_op<T>(res, rc, Pmat<T>(l), L.agg, nrhs, stream);
+  if (l + 1 == n_levels() - 1)
+    dense_apply<T>(Dinv<T>(l + 1), rc, ec, (int)nc, nrhs, stream);
+  else
+    fgmres<T>(l + 1, rc, ec, nrhs, 0.0, sp_.coarse_iters, sp_.coarse_iters, true, true);
+  prolong_op<T>(ec, z, Pmat<T>(l), L.agg, nrhs, 1.0, stream);
+  if (sp_.smoother_steps > 0) {
+    apply_D<T>(l, z, q, nrhs);
+    MG_CUDA(cudaMemcpyAsync(res, r, sizeof(C<T>) * n * nrhs, cudaMemcpyDeviceToDevice, stream));
+    axpby<T>(-1.0, q, 1.0, res, n, nrhs, stream);
+    smooth<T>(l, z, res, nrhs);
+  }
+}
+
+// ------------------------------------------------------------------ FGMRES
+template <typename T>
+SolveInfo Engine::fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, int max_iter, int m,
+                         bool use_precond, bool fixed) {
+  const Level &L = levels_[l];
+  const int64_t n = L.g.n();
+  const int64_t vs = n * nrhs;
+  const std::string tag = fixed ? "k" : "t";
+  C<T> *V = ws<T>("gmV" + tag, l, (size_t)(m + 1) * vs);
+  C<T> *Z = use_precond ? ws<T>("gmZ" + tag, l, (size_t)m * vs) : nullptr;
+  C<T> *w = ws<T>("gmw" + tag, l, (size_t)vs);
+  GmresState st;
+  st.m = m;
+  st.nrhs = nrhs;
+  st.H = ws<double>("gsH" + tag, l, (size_t)nrhs * (m + 1) * m);
+  st.h1 = ws<double>("gsh1" + tag, l, (size_t)nrhs * (m + 1));
+  st.h2 = ws<double>("gsh2" + tag, l, (size_t)nrhs * (m + 1));
+  st.sn = ws<double>("gssn" + tag, l, (size_t)nrhs * m);
+  st.g = ws<double>("gsg" + tag, l, (size_t)nrhs * (m + 1));
+  st.y = ws<double>("gsy" + tag, l, (size_t)nrhs * m);
+  st.nrm = ws<double>("gsnrm" + tag, l, (size_t)nrhs);
+  double2 *sc = ws<double>("gssc" + tag, l, (size_t)nrhs * 3 + (size_t)nrhs * m / 2 + 8);
+  st.cs = reinterpret_cast<double *>(sc);
+  st.inv = st.cs + (size_t)nrhs * m;
+  st.res = st.inv + nrhs;
+  st.target = st.res + nrhs;
+  int *iw = reinterpret_cast<int *>(ws<double>("gsi" + tag, l, (size_t)nrhs + 4));
+  st.active = iw;
+  st.nit = iw + nrhs;
+  double2 *part_k = nullptr;
+  auto part = [&](int k) { return partials((size_t)reduce_blocks(n) * nrhs * k); };
+  (void)part_k;
+
+  dot<T>(b, b, n, nrhs, st.nrm, part(1), stream);
+  target_kernel<<<(nrhs + 63) / 64, 64, 0, stream>>>(st.target, st.nrm, tol, nrhs);
+  double *bn_host = nullptr;
+  if (!fixed) {
+    double2 *h = static_cast<double2 *>(pinned(sizeof(double2) * 2 * nrhs + sizeof(int) * nrhs));
+    MG_CUDA(cudaMemcpyAsync(h, st.nrm, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, stream));
+    sync();
+    static thread_local std::vector<double> bn;
+    bn.assign(nrhs, 0.0);
+    for (int r = 0; r < nrhs; ++r) bn[r] = std::sqrt(std::max(h[r].x, 0.0));
+    bn_host = bn.data();
+  }
+  MG_CUDA(cudaMemsetAsync(x, 0, sizeof(C<T>) * vs, stream));
+  MG_CUDA(cudaMemcpyAsync(V, b, sizeof(C<T>) * vs, cudaMemcpyDeviceToDevice, stream));
+
+  SolveInfo info;
+  int total = 0;
+  for (;;) {
+    dot<T>(V, V, n, nrhs, st.nrm, part(1), stream);
+    gmres_start(st, stream);
+    scale_rhs<T>(V, V, st.inv, n, nrhs, stream);
+    int it = 0;
+    for (int i = 0; i < m; ++i) {
+      C<T> *vi = V + i * vs;
+      C<T> *zi = use_precond ? Z + i * vs : vi;
+      if (use_precond) precond<T>(l, vi, zi, nrhs);
+      apply_D<T>(l, zi, w, nrhs);
+      multi_dot<T>(V, vs, i + 1, w, n, nrhs, st.h1, m + 1, part(i + 1), stream);
+      multi_axpy<T>(V, vs, i + 1, w, n, nrhs, st.h1, m + 1, -1.0, stream);
+      multi_dot<T>(V, vs, i + 1, w, n, nrhs, st.h2, m + 1, part(i + 1), stream);
+      multi_axpy<T>(V, vs, i + 1, w, n, nrhs, st.h2, m + 1, -1.0, stream);
+      dot<T>(w, w, n, nrhs, st.nrm, part(1), stream);
+      gmres_arnoldi(st, i, stream);
+      scale_rhs<T>(w, V + (i + 1) * vs, st.inv, n, nrhs, stream);
+      ++it;
+      ++total;
+      if (total >= max_iter) break;
+      if (!fixed) {
+        int *ah = static_cast<int *>(pinned(sizeof(int) * nrhs));
+        MG_CUDA(cudaMemcpyAsync(ah, st.active, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, stream));
+        sync();
+        bool any = false;
+        for (int r = 0; r < nrhs; ++r) any |= ah[r] != 0;
+        if (!any) break;
+      }
+    }
+    gmres_solve(st, stream);
+    multi_axpy<T>(use_precond ? Z : V, vs, it, x, n, nrhs, st.y, m, 1.0, stream);
+    if (fixed && total >= max_iter) break;
+    // true residual
+    apply_D<T>(l, x, w, nrhs);
+    MG_CUDA(cudaMemcpyAsync(V, b, sizeof(C<T>) * vs, cudaMemcpyDeviceToDevice, stream));
+    axpby<T>(-1.0, w, 1.0, V, n, nrhs, stream);
+    if (fixed) continue;
+    dot<T>(V, V, n, nrhs, st.nrm, part(1), stream);
+    double2 *h = static_cast<double2 *>(pinned(sizeof(double2) * nrhs));
+    MG_CUDA(cudaMemcpyAsync(h, st.nrm, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, stream));
+    sync();
+    double worst = 0.0;
+    bool bad = false;
+    for (int r = 0; r < nrhs; ++r) {
+      const double rn = std::sqrt(std::max(h[r].x, 0.0));
+      if (!std::isfinite(h[r].x)) bad = true;
+      const double rel = bn_host[r] > 0.0 ? rn / bn_host[r] : 0.0;
+      worst = std::max(worst, rel);
+    }
+    info.residual = worst;
+    if (bad) {
+      info.converged = false;
+      info.iters = total;
+      throw Error(MGMLMC_ERR_NUMERIC, "solver produced NaN/Inf (level " + std::to_string(l) + ")");
+    }
+    if (worst <= tol) break;
+    if (total >= max_iter) {
+      info.converged = false;
+      break;
+    }
+  }
+  info.iters = total;
+  return info;
+}
+
+SolveInfo Engine::solve_mixed(int l, const double2 *b, double2 *x, int nrhs) {
+  const int64_t n = levels_[l].g.n();
+  const int64_t vs = n * nrhs;
+  double2 *r = ws<double>("dcr", l, (size_t)vs);
+  double2 *t = ws<double>("dct", l, (size_t)vs);
+  float2 *r32 = ws<float>("dcr32", l, (size_t)vs);
+  float2 *e32 = ws<float>("dce32", l, (size_t)vs);
+  double2 *nr = ws<double>("dcn", l, (size_t)nrhs * 2);
+  double *inv = reinterpret_cast<double *>(ws<double>("dcinv", l, (size_t)nrhs));
+  double *rn = reinterpret_cast<double *>(ws<double>("dcrn", l, (size_t)nrhs));
+  dot<double>(b, b, n, nrhs, nr, partials((size_t)reduce_blocks(n) * nrhs), stream);
+  double2 *h = static_cast<double2 *>(pinned(sizeof(double2) * nrhs));
+  MG_CUDA(cudaMemcpyAsync(h, nr, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, stream));
+  sync();
+  std::vector<double> bn(nrhs);
+  for (int q = 0; q < nrhs; ++q) bn[q] = std::sqrt(std::max(h[q].x, 0.0));
+  MG_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * vs, stream));
+  MG_CUDA(cudaMemcpyAsync(r, b, sizeof(double2) * vs, cudaMemcpyDeviceToDevice, stream));
+  SolveInfo info;
+  int total = 0;
+  for (int outer = 0;; ++outer) {
+    dot<double>(r, r, n, nrhs, nr, partials((size_t)reduce_blocks(n) * nrhs), stream);
+    MG_CUDA(cudaMemcpyAsync(h, nr, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, stream));
+    sync();
+    double worst = 0.0;
+    for (int q = 0; q < nrhs; ++q) {
+      if (!std::isfinite(h[q].x)) throw Error(MGMLMC_ERR_NUMERIC, "defect correction: NaN/Inf");
+      worst = std::max(worst, bn[q] > 0 ? std::sqrt(std::max(h[q].x, 0.0)) / bn[q] : 0.0);
+    }
+    info.residual = worst;
+    if (worst <= sp_.tol) break;
+    if (total >= sp_.max_iter || outer >= 100) {
+      info.converged = false;
+      break;
+    }
+    inv_norm_kernel<<<(nrhs + 63) / 64, 64, 0, stream>>>(inv, rn, nr, nrhs);
+    convert_scale<float, double>(r, r32, inv, n, nrhs, stream);
+    SolveInfo in = fgmres<float>(l, r32, e32, nrhs, sp_.inner_tol, sp_.max_iter - total,
+                                 sp_.restart, true, false);
+    total += in.iters;
+    convert_scale<double, float>(e32, t, rn, n, nrhs, stream);
+    axpby<double>(1.0, t, 1.0, x, n, nrhs, stream);
+    apply_D<double>(l, x, t, nrhs);
+    MG_CUDA(cudaMemcpyAsync(r, b, sizeof(double2) * vs, cudaMemcpyDeviceToDevice, stream));
+    axpby<double>(-1.0, t, 1.0, r, n, nrhs, stream);
+  }
+  info.iters = total;
+  return info;
+}
+
+SolveInfo Engine::solve(int l, const double2 *b, double2 *x, int nrhs) {
+  if (!ready_) throw Error(MGMLMC_ERR_STATE, "hierarchy not built");
+  const int64_t n = levels_.at(l).g.n();
+  SolveInfo info;
+  if (l == n_levels() - 1) {
+    dense_apply<double>(levels_[l].Dinv64, b, x, (int)n, nrhs, stream);
+    info.iters = 0;
+    info.residual = 0.0;
+  } else if (sp_.precision == MGMLMC_FP32) {
+    info = solve_mixed(l, b, x, nrhs);
+  } else {
+    info = fgmres<double>(l, b, x, nrhs, sp_.tol, sp_.max_iter, sp_.restart, true, false);
+  }
+  last_solve = info;
+  if (!info.converged)
+    throw Error(MGMLMC_ERR_NOT_CONVERGED,
+                "level " + std::to_string(l) + " solve stopped after " + std::to_string(info.iters) +
+                    " iterations at relative residual " + std::to_string(info.residual));
+  return info;
+}
+
+// ------------------------------------------------------------------ setup
+void Engine::galerkin(int l) {
+  Level &f = levels_[l];
+  Level &c = levels_[l + 1];
+  const AggMap &m = f.agg;
+  const int64_t nf = f.g.n(), nc = c.g.n();
+  const int dofc = c.g.dof;
+  double2 *probe = ws<double>("galp", l, (size_t)nf);
+  double2 *out9 = ws<double>("gal9", l, (size_t)9 * nf);
+  double2 *cols = ws<double>("galc", l, (size_t)9 * nc);
+  const size_t acnt = (size_t)c.g.V * 9 * dofc * dofc;
+  c.A64 = dalloc<double2>(acnt);
+  c.A32 = dalloc<float2>(acnt);
+  for (int col = 0; col < dofc; ++col) {
+    probe_column(probe, f.P64, m, col, stream);
+    if (f.fine) wilson_split<double>(probe, out9, f.U64, f.g, m0_, m.b, stream);
+    else stencil_split<double>(probe, out9, f.A64, f.g, m.b, stream);
+    restrict_op<double>(out9, cols, f.P64, m, 9, stream);
+    galerkin_scatter(cols, c.A64, c.g, col, stream);
+  }
+  convert<float, double>(c.A64, c.A32, (int64_t)acnt, stream);
+}
+
+void Engine::build_hierarchy(const mgmlmc_mg_params &p) {
+  if (!have_gauge_) throw Error(MGMLMC_ERR_STATE, "set the gauge field first");
+  if (p.n_levels < 1 || p.n_levels > MGMLMC_MAX_LEVELS) throw Error(MGMLMC_ERR_ARG, "n_levels out of range");
+  free_hierarchy();
+  // geometry of every level first (argument checks before any allocation)
+  std::vector<Geom> geo(p.n_levels);
+  std::vector<AggMap> maps(p.n_levels);
+  geo[0] = fine_;
+  for (int l = 0; l + 1 < p.n_levels; ++l) {
+    AggMap &m = maps[l];
+    m.fine = geo[l];
+    const int ntv = p.n_tv[l];
+    if (ntv < 1 || ntv > 64) throw Error(MGMLMC_ERR_ARG, "n_tv must be in 1..64");
+    Geom cg{};
+    int64_t cv = 1;
+    int sites = 1;
+    for (int i = 0; i < 4; ++i) {
+      const int b = p.block[l][i];
+      if (b < 1 || geo[l].L[i] % b) throw Error(MGMLMC_ERR_ARG, "block must divide the lattice");
+      m.b[i] = b;
+      cg.L[i] = geo[l].L[i] / b;
+      cv *= cg.L[i];
+      sites *= b;
+    }
+    cg.V = (int)cv;
+    cg.dof = 2 * ntv;
+    m.coarse = cg;
+    m.ntv = ntv;
+    m.half = geo[l].dof / 2;
+    m.sites = sites;
+    m.rows = sites * m.half;
+    if (ntv > m.rows) throw Error(MGMLMC_ERR_ARG, "more test vectors than rows per aggregate");
+    if ((size_t)m.rows * sizeof(double2) > 48 * 1024)
+      throw Error(MGMLMC_ERR_ARG, "aggregate too large (rows * 16 B must fit 48 KB)");
+    geo[l + 1] = cg;
+  }
+  const int64_t ncoarsest = geo[p.n_levels - 1].n();
+  if (ncoarsest > 20000) throw Error(MGMLMC_ERR_ARG, "coarsest level too large for the dense inverse");
+
+  levels_.resize(p.n_levels);
+  for (int l = 1; l < p.n_levels; ++l) {
+    levels_[l] = Level{};
+    levels_[l].g = geo[l];
+  }
+  for (int l = 0; l + 1 < p.n_levels; ++l) {
+    Level &f = levels_[l];
+    f.agg = maps[l];
+    f.has_next = true;
+    const int64_t n = f.g.n();
+    const int ntv = maps[l].ntv;
+    double2 *V = ws<double>("tv", l, (size_t)ntv * n);
+    auto imp = imported_host_.find(l);
+    if (imp != imported_host_.end()) {
+      if ((int64_t)imp->second.size() != (int64_t)ntv * n * 2)
+        throw Error(MGMLMC_ERR_ARG, "imported test vectors have the wrong size for level " + std::to_string(l));
+      MG_CUDA(cudaMemcpyAsync(V, imp->second.data(), sizeof(double2) * ntv * n, cudaMemcpyHostToDevice, stream));
+    } else {
+      z4_noise<double>(V, f.g, p.seed, 0, 96 + l, 0, -1, ntv, stream);
+      if (p.setup_rounds > 0) {
+        double2 *X = ws<double>("tvx", l, (size_t)ntv * n);
+        double *inv = reinterpret_cast<double *>(ws<double>("tvinv", l, (size_t)ntv));
+        double *nr = reinterpret_cast<double *>(ws<double>("tvnr", l, (size_t)ntv));
+        double2 *d = ws<double>("tvd", l, (size_t)ntv);
+        for (int round = 0; round < p.setup_rounds; ++round) {
+          const int it = std::max(1, p.setup_iters);
+          fgmres<double>(l, V, X, ntv, 0.0, it, std::min(it, 64), false, true);
+          dot<double>(X, X, n, ntv, d, partials((size_t)reduce_blocks(n) * ntv), stream);
+          inv_norm_kernel<<<(ntv + 63) / 64, 64, 0, stream>>>(inv, nr, d, ntv);
+          scale_rhs<double>(X, V, inv, n, ntv, stream);
+        }
+      }
+    }
+    f.P64 = dalloc<double2>((size_t)ntv * n);
+    f.P32 = dalloc<float2>((size_t)ntv * n);
+    MG_CUDA(cudaMemsetAsync(flag_dev_, 0, sizeof(int), stream));
+    build_prolongator(V, f.P64, f.agg, flag_dev_, stream);
+    convert<float, double>(f.P64, f.P32, (int64_t)ntv * n, stream);
+    int flag = 0;
+    MG_CUDA(cudaMemcpyAsync(&flag, flag_dev_, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    sync();
+    if (flag) throw Error(MGMLMC_ERR_NUMERIC, "test vectors are linearly dependent on an aggregate");
+    galerkin(l);
+  }
+  // coarsest level: dense inverse (FP64 Gauss-Jordan with partial pivoting)
+  Level &c = levels_.back();
+  const int n = (int)c.g.n();
+  if (c.fine) {
+    // one level only: the coarsest operator is the Wilson operator itself
+    throw Error(MGMLMC_ERR_ARG, "n_levels must be >= 2");
+  }
+  c.Dinv64 = dalloc<double2>((size_t)n * n);
+  c.Dinv32 = dalloc<float2>((size_t)n * n);
+  double2 *work = ws<double>("gj", 0, (size_t)2 * n * n + n + 8);
+  dense_from_stencil(c.A64, c.Dinv64, c.g, stream);
+  MG_CUDA(cudaMemsetAsync(flag_dev_, 0, sizeof(int), stream));
+  dense_invert(c.Dinv64, work, n, flag_dev_, stream);
+  convert<float, double>(c.Dinv64, c.Dinv32, (int64_t)n * n, stream);
+  int flag = 0;
+  MG_CUDA(cudaMemcpyAsync(&flag, flag_dev_, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  sync();
+  if (flag) throw Error(MGMLMC_ERR_NUMERIC, "coarsest operator is singular");
+  ready_ = true;
+}
+
+// ------------------------------------------------------------------ estimators
+namespace {
+struct TermDef {
+  int code, level, kind, N;  // kind 0 plain, 1 O, 2 F, 3 coarsest
+};
+}  // namespace
+
+void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &out) {
+  if (!ready_) throw Error(MGMLMC_ERR_STATE, "hierarchy not built");
+  const int L = n_levels();
+  std::vector<TermDef> terms;
+  if (p.kind == MGMLMC_EST_PLAIN) {
+    terms.push_back({MGMLMC_TERM_PLAIN, 0, 0, p.n_samples[0]});
+  } else if (p.kind == MGMLMC_EST_ORTHOGONAL) {
+    int idx = 0;
+    for (int l = 0; l + 1 < L; ++l) terms.push_back({MGMLMC_TERM_O + l, l, 1, p.n_samples[idx++]});
+    for (int l = 0; l + 1 < L; ++l) terms.push_back({MGMLMC_TERM_F + l, l, 2, p.n_samples[idx++]});
+    terms.push_back({MGMLMC_TERM_COARSEST, L - 1, 3, p.n_samples[idx++]});
+  } else {
+    throw Error(MGMLMC_ERR_ARG, "unknown estimator kind");
+  }
+  const int B = std::max(1, p.batch);
+  cudaEvent_t e0, e1;
+  MG_CUDA(cudaEventCreate(&e0));
+  MG_CUDA(cudaEventCreate(&e1));
+  out.clear();
+  for (const TermDef &td : terms) {
+    if (td.N < 0) throw Error(MGMLMC_ERR_ARG, "negative sample count");
+    TermAcc acc;
+    acc.term = td.code;
+    std::vector<std::complex<double>> X;
+    for (int k0 = 0; k0 < td.N; k0 += B) {
+      const int nb = std::min(B, td.N - k0);
+      const uint64_t s0 = p.first_sample + (uint64_t)k0;
+      double2 *res = ws<double>("est_res", 0, 2 * (size_t)nb);
+      MG_CUDA(cudaEventRecord(e0, stream));
+      const int l = td.level;
+      const int64_t n = levels_[l].g.n();
+      if (td.kind == 0) {
+        double2 *x = ws<double>("estx", l, (size_t)nb * n), *z = ws<double>("estz", l, (size_t)nb * n);
+        noise(l, p.seed, s0, MGMLMC_TERM_PLAIN, 0, -1, x, nb);
+        SolveInfo si = solve(l, x, z, nb);
+        acc.iters_sum += si.iters;
+        acc.solves += 1;
+        acc.max_res = std::max(acc.max_res, si.residual);
+        dot<double>(x, z, n, nb, res, partials((size_t)reduce_blocks(n) * nb), stream);
+      } else if (td.kind == 1) {
+        double2 *x = ws<double>("estx", l, (size_t)nb * n), *y = ws<double>("esty", l, (size_t)nb * n);
+        double2 *z = ws<double>("estz", l, (size_t)nb * n);
+        noise(l, p.seed, s0, MGMLMC_TERM_O + l, 0, -1, x, nb);
+        project_out<double>(l, x, y, nb);
+        SolveInfo si = solve(l, y, z, nb);
+        acc.iters_sum += si.iters;
+        acc.solves += 1;
+        acc.max_res = std::max(acc.max_res, si.residual);
+        dot<double>(y, z, n, nb, res, partials((size_t)reduce_blocks(n) * nb), stream);
+      } else if (td.kind == 2) {
+        const int64_t nc = levels_[l + 1].g.n();
+        double2 *x = ws<double>("estxc", l + 1, (size_t)nb * nc), *y = ws<double>("esty", l, (size_t)nb * n);
+        double2 *z1 = ws<double>("estz", l, (size_t)nb * n), *z2 = ws<double>("estzc", l + 1, (size_t)nb * nc);
+        noise(l + 1, p.seed, s0, MGMLMC_TERM_F + l, 0, -1, x, nb);
+        prolong_from<double>(l, x, y, nb, 0.0);
+        SolveInfo s1 = solve(l, y, z1, nb);
+        SolveInfo s2 = solve(l + 1, x, z2, nb);
+        acc.iters_sum += s1.iters + s2.iters;
+        acc.solves += 2;
+        acc.max_res = std::max(acc.max_res, std::max(s1.residual, s2.residual));
+        dot<double>(y, z1, n, nb, res, partials((size_t)reduce_blocks(n) * nb), stream);
+        dot<double>(x, z2, nc, nb, res + nb, partials((size_t)reduce_blocks(nc) * nb), stream);
+      } else {
+        double2 *x = ws<double>("estx", l, (size_t)nb * n), *z = ws<double>("estz", l, (size_t)nb * n);
+        noise(l, p.seed, s0, MGMLMC_TERM_COARSEST, 0, -1, x, nb);
+        dense_apply<double>(levels_[l].Dinv64, x, z, (int)n, nb, stream);
+        dot<double>(x, z, n, nb, res, partials((size_t)reduce_blocks(n) * nb), stream);
+      }
+      MG_CUDA(cudaEventRecord(e1, stream));
+      double2 *h = static_cast<double2 *>(pinned(sizeof(double2) * 2 * nb));
+      MG_CUDA(cudaMemcpyAsync(h, res, sizeof(double2) * 2 * nb, cudaMemcpyDeviceToHost, stream));
+      sync();
+      float ms = 0.f;
+      MG_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      acc.seconds += ms * 1e-3;
+      for (int q = 0; q < nb; ++q) {
+        std::complex<double> v(h[q].x, h[q].y);
+        if (td.kind == 2) v -= std::complex<double>(h[nb + q].x, h[nb + q].y);
+        X.push_back(v);
+      }
+    }
+    acc.n = (int)X.size();
+    for (auto &v : X) {
+      acc.sre += v.real();
+      acc.sim += v.imag();
+      acc.sabs2 += std::norm(v);
+    }
+    acc.samples = X;
+    out.push_back(acc);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+}
+
+void Engine::coarsest_trace(double *re, double *im) {
+  if (!ready_) throw Error(MGMLMC_ERR_STATE, "hierarchy not built");
+  const Level &c = levels_.back();
+  double2 *d = ws<double>("ctr", 0, 1);
+  dense_trace(c.Dinv64, (int)c.g.n(), d, stream);
+  double2 h;
+  MG_CUDA(cudaMemcpyAsync(&h, d, sizeof(double2), cudaMemcpyDeviceToHost, stream));
+  sync();
+  *re = h.x;
+  *im = h.y;
+}
+
+void Engine::get_prolongator(int l, double *host) {
+  if (!ready_ || l < 0 || l + 1 >= n_levels()) throw Error(MGMLMC_ERR_ARG, "no prolongator at that level");
+  const Level &f = levels_[l];
+  const size_t cnt = (size_t)f.agg.coarse.V * 2 * f.agg.ntv * f.agg.rows;
+  double2 *tmp = ws<double>("pcan", l, cnt);
+  prolongator_to_canonical(f.P64, tmp, f.agg, stream);
+  MG_CUDA(cudaMemcpyAsync(host, tmp, cnt * sizeof(double2), cudaMemcpyDeviceToHost, stream));
+  sync();
+}
+
+void Engine::get_coarse_op(int l, double *host) {
+  if (!ready_ || l < 1 || l >= n_levels()) throw Error(MGMLMC_ERR_ARG, "no coarse operator at that level");
+  const Level &c = levels_[l];
+  const size_t cnt = (size_t)c.g.V * 9 * c.g.dof * c.g.dof;
+  MG_CUDA(cudaMemcpyAsync(host, c.A64, cnt * sizeof(double2), cudaMemcpyDeviceToHost, stream));
+  sync();
+}
+
+template void Engine::apply_D<double>(int, const C<double> *, C<double> *, int);
+template void Engine::apply_D<float>(int, const C<float> *, C<float> *, int);
+template void Engine::restrict_to<double>(int, const C<double> *, C<double> *, int);
+template void Engine::restrict_to<float>(int, const C<float> *, C<float> *, int);
+template void Engine::prolong_from<double>(int, const C<double> *, C<double> *, int, double);
+template void Engine::prolong_from<float>(int, const C<float> *, C<float> *, int, double);
+template void Engine::project_out<double>(int, const C<double> *, C<double> *, int);
+template void Engine::project_out<float>(int, const C<float> *, C<float> *, int);
+
+}  // namespace mg

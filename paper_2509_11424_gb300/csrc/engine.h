@@ -1,0 +1,122 @@
+// Host orchestration of the multigrid hierarchy, the batched MG-preconditioned
+// FGMRES level solves and the MG-MLMC estimators.  Everything numeric runs in
+// the kernels of kernels.h on one stream; the host holds scalars only.
+#pragma once
+
+#include <complex>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mgmlmc.h"
+#include "kernels.h"
+
+namespace mg {
+
+struct Level {
+  Geom g{};
+  bool fine = false;
+  double2 *U64 = nullptr;  // fine links [V][4][3][3]
+  float2 *U32 = nullptr;
+  double2 *A64 = nullptr;  // coarse stencil [V][9][dof][dof]
+  float2 *A32 = nullptr;
+  bool has_next = false;
+  AggMap agg{};            // to level + 1
+  double2 *P64 = nullptr;  // [X][c][k][row]
+  float2 *P32 = nullptr;
+  double2 *Dinv64 = nullptr;  // coarsest: dense inverse, row-major
+  float2 *Dinv32 = nullptr;
+};
+
+struct SolveInfo {
+  int iters = 0;          // outer iterations (max over rhs)
+  double residual = 0.0;  // true relative residual (max over rhs)
+  bool converged = true;
+};
+
+struct TermAcc {
+  int term = 0;
+  int n = 0;
+  double sre = 0, sim = 0, sabs2 = 0;
+  double seconds = 0;
+  double iters_sum = 0;
+  int solves = 0;
+  double max_res = 0;
+  std::vector<std::complex<double>> samples;
+};
+
+class Engine {
+ public:
+  Engine(const int dims[4], cudaStream_t s);
+  ~Engine();
+
+  void set_gauge(const double *U, bool on_device);
+  void set_mass(double m0);
+  void set_solver(const mgmlmc_solver_params &p);
+  void set_test_vectors(int level, const double *V, int ntv, int64_t n, bool on_device);
+  void build_hierarchy(const mgmlmc_mg_params &p);
+
+  int n_levels() const { return (int)levels_.size(); }
+  const Level &level(int l) const { return levels_.at(l); }
+  bool ready() const { return ready_; }
+
+  // operator hooks (device buffers)
+  template <typename T> void apply_D(int l, const C<T> *in, C<T> *out, int nrhs);
+  template <typename T> void restrict_to(int l, const C<T> *in, C<T> *out, int nrhs);
+  template <typename T> void prolong_from(int l, const C<T> *in, C<T> *out, int nrhs, double beta);
+  template <typename T> void project_out(int l, const C<T> *in, C<T> *out, int nrhs);
+  // z = D_l^-1 b (FP64 interface; the solver precision is set by set_solver)
+  SolveInfo solve(int l, const double2 *b, double2 *x, int nrhs);
+  void noise(int l, uint64_t seed, uint64_t sample0, uint64_t term, uint64_t aux, int slice,
+             double2 *out, int nrhs);
+
+  void estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &out);
+  void coarsest_trace(double *re, double *im);
+  void connected(int kind, int n_samples, uint64_t seed, uint64_t first, std::vector<double> &mean,
+                 std::vector<double> &var, int &R);
+  void disconnected(int kind, int t, int n_samples, uint64_t seed, uint64_t first,
+                    std::vector<double> &mean, std::vector<double> &var, int &R);
+
+  void get_prolongator(int l, double *host);
+  void get_coarse_op(int l, double *host);
+
+  SolveInfo last_solve;
+  cudaStream_t stream;
+
+ private:
+  template <typename T> C<T> *ws(const std::string &name, int l, size_t count);
+  void contraction_vectors(int kind, int nb, double2 *x, double2 *B, double2 *Bt);
+  template <typename T> const C<T> *Pmat(int l) const;
+  template <typename T> const C<T> *Dinv(int l) const;
+
+  template <typename T> void smooth(int l, C<T> *z, C<T> *res, int nrhs);
+  template <typename T> void precond(int l, const C<T> *r, C<T> *z, int nrhs);
+  // batched FGMRES; fixed = run exactly max_iter iterations with no host check
+  template <typename T>
+  SolveInfo fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, int max_iter, int m,
+                   bool use_precond, bool fixed);
+  SolveInfo solve_mixed(int l, const double2 *b, double2 *x, int nrhs);
+  void galerkin(int l);
+  void free_hierarchy();
+  void sync();
+
+  int dims_[4];
+  Geom fine_{};
+  double m0_ = 0.0;
+  bool have_gauge_ = false;
+  bool ready_ = false;
+  mgmlmc_solver_params sp_{};
+  std::vector<Level> levels_;
+  std::map<int, std::vector<double>> imported_host_;  // level -> ntv * n complex
+  std::map<std::string, std::pair<void *, size_t>> ws_;
+  double2 *scal_ = nullptr;     // small scalar scratch
+  double2 *partial_ = nullptr;  // reduction partials
+  size_t partial_cap_ = 0;
+  int *flag_dev_ = nullptr;
+  void *pinned_ = nullptr;
+  size_t pinned_cap_ = 0;
+  void *pinned(size_t bytes);
+  double2 *partials(size_t count);
+};
+
+}  // namespace mg

@@ -1,0 +1,136 @@
+// Host-side launchers of the mgmlmc kernels.  Every launcher enqueues on the
+// given stream and returns immediately; buffers are device pointers.
+// Multi-vectors hold nrhs vectors of length n one after the other; a Krylov
+// basis holds k multi-vectors one after the other (stride nrhs * n).
+#pragma once
+
+#include "common.cuh"
+
+namespace mg {
+
+// Fixed two-stage reduction width (deterministic: depends on n only).
+int reduce_blocks(int64_t n);
+
+// ------------------------------------------------------------------ BLAS-1
+// out[r] = sum_i conj(x_r[i]) y_r[i]   (double2 results on the device)
+template <typename T>
+void dot(const C<T> *x, const C<T> *y, int64_t n, int nrhs, double2 *out, double2 *partial,
+         cudaStream_t s);
+// h[r * ldh + j] = <V_j,r , w_r> for j < k (basis stride vstride)
+template <typename T>
+void multi_dot(const C<T> *V, int64_t vstride, int k, const C<T> *w, int64_t n, int nrhs,
+               double2 *h, int ldh, double2 *partial, cudaStream_t s);
+// w_r += sign * sum_{j<k} h[r * ldh + j] V_j,r
+template <typename T>
+void multi_axpy(const C<T> *V, int64_t vstride, int k, C<T> *w, int64_t n, int nrhs,
+                const double2 *h, int ldh, double sign, cudaStream_t s);
+// y = a x + b y   (host scalars, all rhs)
+template <typename T>
+void axpby(double a, const C<T> *x, double b, C<T> *y, int64_t n, int nrhs, cudaStream_t s);
+// y_r = x_r * scal[r]  (real per-rhs factors on the device)
+template <typename T>
+void scale_rhs(const C<T> *x, C<T> *y, const double *scal, int64_t n, int nrhs, cudaStream_t s);
+// minimal-residual step for every rhs: alpha = <q, r> / <q, q>;
+// z += alpha r; r -= alpha q.  dots[r] = <q, r>, nq[r].x = <q, q>
+template <typename T>
+void mr_update(C<T> *z, C<T> *r, const C<T> *q, const double2 *dqr, const double2 *nq,
+               int64_t n, int nrhs, cudaStream_t s);
+// out = in converted between precisions
+template <typename To, typename From>
+void convert(const C<From> *in, C<To> *out, int64_t n, cudaStream_t s);
+// y += x (x in lower precision, y in higher)
+template <typename T, typename Tlo>
+void add_lo(const C<Tlo> *x, C<T> *y, int64_t n, cudaStream_t s);
+// y_r = x_r * scal[r] converting precision (scal real, device)
+template <typename To, typename From>
+void convert_scale(const C<From> *x, C<To> *y, const double *scal, int64_t n, int nrhs,
+                   cudaStream_t s);
+
+// ------------------------------------------------------------------ FGMRES
+// Small per-rhs state of a batched FGMRES cycle (device arrays).
+struct GmresState {
+  int m;          // restart length
+  int nrhs;
+  double2 *H;     // [nrhs][(m+1) * m]  column-major: H[r][j * (m+1) + i]
+  double2 *h1;    // [nrhs][m+1] first Gram-Schmidt coefficients
+  double2 *h2;    // [nrhs][m+1] second (re-orthogonalisation) coefficients
+  double *cs;     // [nrhs][m]
+  double2 *sn;    // [nrhs][m]
+  double2 *g;     // [nrhs][m+1]
+  double2 *y;     // [nrhs][m]
+  double2 *nrm;   // [nrhs] ||w||^2 in .x
+  double *inv;    // [nrhs] scale factor for the next basis vector
+  double *res;    // [nrhs] residual estimate |g_{i+1}|
+  double *target; // [nrhs] absolute tolerance per rhs
+  int *active;    // [nrhs] 1 while the rhs iterates in this cycle
+  int *nit;       // [nrhs] iterations done in this cycle
+};
+// initial: beta = sqrt(nrm.x); g = (beta, 0...); inv = 1/beta; active per
+// beta > target
+void gmres_start(GmresState st, cudaStream_t s);
+// fold the Gram-Schmidt coefficients and ||w||^2 of iteration i
+void gmres_arnoldi(GmresState st, int i, cudaStream_t s);
+// y = H^-1 g per rhs (upper triangular of size nit[r])
+void gmres_solve(GmresState st, cudaStream_t s);
+
+// ------------------------------------------------------------------ operators
+template <typename T>
+void wilson_apply(const C<T> *in, C<T> *out, const C<T> *U, Geom g, double m0, int nrhs,
+                  cudaStream_t s);
+// the 9 hop-class parts of D (Galerkin): out9[h] for h = 0..8, single rhs.
+template <typename T>
+void wilson_split(const C<T> *in, C<T> *out9, const C<T> *U, Geom g, double m0, const int b[4],
+                  cudaStream_t s);
+template <typename T>
+void stencil_apply(const C<T> *in, C<T> *out, const C<T> *A, Geom g, int nrhs, cudaStream_t s);
+template <typename T>
+void stencil_split(const C<T> *in, C<T> *out9, const C<T> *A, Geom g, const int b[4],
+                   cudaStream_t s);
+template <typename T>
+void gamma5_apply(const C<T> *in, C<T> *out, int64_t nsites, int dof, int nrhs, cudaStream_t s);
+
+// ------------------------------------------------------------------ transfer
+// P is stored [X][c][k][row] (row fastest).
+template <typename T>
+void restrict_op(const C<T> *in, C<T> *out, const C<T> *P, const AggMap &m, int nrhs,
+                 cudaStream_t s);
+// out = P in (beta = 0) or out = beta * out + P in
+template <typename T>
+void prolong_op(const C<T> *in, C<T> *out, const C<T> *P, const AggMap &m, int nrhs, double beta,
+                cudaStream_t s);
+// out = P e_col: column `col` of every aggregate's block (col = c * ntv + k)
+void probe_column(double2 *out, const double2 *P, const AggMap &m, int col, cudaStream_t s);
+// P from ntv test vectors V[k][n]: per (aggregate, chirality) modified
+// Gram-Schmidt run twice in k order.  status[0] set to 1 on a zero norm.
+void build_prolongator(const double2 *V, double2 *P, const AggMap &m, int *status,
+                       cudaStream_t s);
+// A[X][h][i][col] = cols[h][X * dof + i] for h = 0..8
+void galerkin_scatter(const double2 *cols, double2 *A, Geom coarse, int col, cudaStream_t s);
+// convert / transpose P to the canonical host order [X][c][row][k]
+void prolongator_to_canonical(const double2 *P, double2 *out, const AggMap &m, cudaStream_t s);
+
+// ------------------------------------------------------------------ noise
+// Z4 noise, samples sample0 .. sample0 + nrhs - 1 (Philox4x64-10).  When
+// slice >= 0 only entries of time slice `slice` are non-zero.
+template <typename T>
+void z4_noise(C<T> *out, Geom g, uint64_t seed, uint64_t sample0, uint64_t term, uint64_t aux,
+              int slice, int nrhs, cudaStream_t s);
+// per-slice dots: out[r][t] = sum_{i in slice t} conj(a_r[i]) b_r[i]
+template <typename T>
+void slice_dot(const C<T> *a, const C<T> *b, Geom g, int nrhs, double2 *out, cudaStream_t s);
+
+// ------------------------------------------------------------------ dense
+void dense_from_stencil(const double2 *A, double2 *M, Geom g, cudaStream_t s);
+// in-place Gauss-Jordan inverse with partial pivoting of the n x n row-major
+// M (work: 2 n^2 complex + n); status[0] = 1 on a zero pivot
+void dense_invert(double2 *M, double2 *work, int n, int *status, cudaStream_t s);
+template <typename T>
+void dense_apply(const C<T> *Minv, const C<T> *in, C<T> *out, int n, int nrhs, cudaStream_t s);
+void dense_trace(const double2 *M, int n, double2 *out, cudaStream_t s);
+
+// ------------------------------------------------------------------ checks
+// flag[0] = 1 when any entry of x is NaN / Inf
+template <typename T>
+void check_finite(const C<T> *x, int64_t n, int *flag, cudaStream_t s);
+
+}  // namespace mg

@@ -1,0 +1,400 @@
+// Level-1 vector kernels (batched over right-hand sides) and the per-rhs
+// small-matrix kernels of batched FGMRES.
+//
+// Reductions are deterministic: a fixed number of blocks (a function of n
+// only) writes partial sums that a second kernel adds in a fixed order, so a
+// result never depends on scheduling.  Sums are accumulated in FP64 for both
+// storage precisions.
+#include "kernels.h"
+
+namespace mg {
+
+namespace {
+constexpr int RB = 256;  // reduction block size
+
+__device__ __forceinline__ double2 warp_sum(double2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+// block-wide sum; valid in thread 0
+__device__ __forceinline__ double2 block_sum(double2 v) {
+  __shared__ double2 sh[RB / 32];
+  v = warp_sum(v);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = (l < (int)(blockDim.x >> 5)) ? sh[l] : make_double2(0.0, 0.0);
+    v = warp_sum(v);
+  }
+  __syncthreads();
+  return v;
+}
+
+// partial[(j * nrhs + r) * NB + b] = sum over block b's chunk of conj(x) y
+template <typename T>
+__global__ void dot_stage1(const C<T> *__restrict__ x, int64_t xstride, const C<T> *__restrict__ y,
+                           int64_t n, int64_t chunk, double2 *__restrict__ partial) {
+  const int b = blockIdx.x, r = blockIdx.y, j = blockIdx.z;
+  const C<T> *xr = x + j * xstride + r * n;
+  const C<T> *yr = y + r * n;
+  const int64_t beg = (int64_t)b * chunk;
+  const int64_t end = beg + chunk < n ? beg + chunk : n;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    C<T> a = xr[i], c = yr[i];
+    acc.x += (double)a.x * c.x + (double)a.y * c.y;
+    acc.y += (double)a.x * c.y - (double)a.y * c.x;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[((int64_t)j * gridDim.y + r) * gridDim.x + b] = acc;
+}
+
+// out[r * ldh + j] = sum_b partial[(j * nrhs + r) * NB + b]
+__global__ void dot_stage2(const double2 *__restrict__ partial, int NB, int nrhs,
+                           double2 *__restrict__ out, int ldh) {
+  const int idx = blockIdx.x;  // j * nrhs + r
+  const int j = idx / nrhs, r = idx - j * nrhs;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int b = threadIdx.x; b < NB; b += blockDim.x) {
+    double2 p = partial[(int64_t)idx * NB + b];
+    acc.x += p.x;
+    acc.y += p.y;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[r * ldh + j] = acc;
+}
+
+template <typename T>
+__global__ void multi_axpy_kernel(const C<T> *__restrict__ V, int64_t vstride, int k,
+                                  C<T> *__restrict__ w, int64_t n, const double2 *__restrict__ h,
+                                  int ldh, double sign) {
+  __shared__ C<T> coef[128];
+  const int r = blockIdx.y;
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double2 c = h[r * ldh + j];
+    coef[j] = mk<T>((T)(sign * c.x), (T)(sign * c.y));
+  }
+  __syncthreads();
+  C<T> *wr = w + r * n;
+  const C<T> *Vr = V + r * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    C<T> acc = wr[i];
+    for (int j = 0; j < k; ++j) acc = cfma(coef[j], Vr[j * vstride + i], acc);
+    wr[i] = acc;
+  }
+}
+
+template <typename T>
+__global__ void axpby_kernel(T a, const C<T> *__restrict__ x, T b, C<T> *__restrict__ y,
+                             int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    C<T> xv = x[i], yv = y[i];
+    yv.x = a * xv.x + b * yv.x;
+    yv.y = a * xv.y + b * yv.y;
+    y[i] = yv;
+  }
+}
+
+template <typename T>
+__global__ void scale_rhs_kernel(const C<T> *__restrict__ x, C<T> *__restrict__ y,
+                                 const double *__restrict__ scal, int64_t n) {
+  const int r = blockIdx.y;
+  const T f = (T)scal[r];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[r * n + i] = cscale(x[r * n + i], f);
+}
+
+template <typename T>
+__global__ void mr_update_kernel(C<T> *__restrict__ z, C<T> *__restrict__ res,
+                                 const C<T> *__restrict__ q, const double2 *__restrict__ dqr,
+                                 const double2 *__restrict__ nq, int64_t n) {
+  const int r = blockIdx.y;
+  const double qq = nq[r].x;
+  const double2 d = dqr[r];
+  const C<T> al = qq > 0.0 ? mk<T>((T)(d.x / qq), (T)(d.y / qq)) : mk<T>((T)0, (T)0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = r * n + i;
+    C<T> rv = res[o];
+    z[o] = cfma(al, rv, z[o]);
+    res[o] = cfma(cneg(al), q[o], rv);
+  }
+}
+
+template <typename To, typename From>
+__global__ void convert_kernel(const C<From> *__restrict__ in, C<To> *__restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = cvt<To>(in[i]);
+}
+
+template <typename To, typename From>
+__global__ void convert_scale_kernel(const C<From> *__restrict__ in, C<To> *__restrict__ out,
+                                     const double *__restrict__ scal, int64_t n) {
+  const int r = blockIdx.y;
+  const double f = scal[r];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    C<From> v = in[r * n + i];
+    out[r * n + i] = mk<To>((To)(v.x * f), (To)(v.y * f));
+  }
+}
+
+template <typename T, typename Tlo>
+__global__ void add_lo_kernel(const C<Tlo> *__restrict__ x, C<T> *__restrict__ y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    C<T> v = y[i];
+    C<Tlo> a = x[i];
+    v.x += (T)a.x;
+    v.y += (T)a.y;
+    y[i] = v;
+  }
+}
+
+template <typename T>
+__global__ void finite_kernel(const C<T> *__restrict__ x, int64_t n, int *flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    C<T> v = x[i];
+    if (!isfinite(v.x) || !isfinite(v.y)) {
+      *flag = 1;
+      return;
+    }
+  }
+}
+
+inline int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+// ----------------------------------------------------------------- FGMRES
+__device__ __forceinline__ double2 dcmul(double2 a, double2 b) { return cmul(a, b); }
+
+__global__ void gmres_start_kernel(GmresState st) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= st.nrhs) return;
+  const int m = st.m;
+  const double beta = sqrt(fmax(st.nrm[r].x, 0.0));
+  for (int i = 0; i <= m; ++i) st.g[r * (m + 1) + i] = make_double2(0.0, 0.0);
+  st.g[r * (m + 1)] = make_double2(beta, 0.0);
+  for (int i = 0; i < m; ++i) st.y[r * m + i] = make_double2(0.0, 0.0);
+  st.res[r] = beta;
+  st.nit[r] = 0;
+  const int act = (beta > st.target[r]) && isfinite(beta);
+  st.active[r] = act;
+  st.inv[r] = (act && beta > 0.0) ? 1.0 / beta : 0.0;
+}
+
+__global__ void gmres_arnoldi_kernel(GmresState st, int i) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= st.nrhs || !st.active[r]) return;
+  const int m = st.m;
+  double2 *H = st.H + (int64_t)r * (m + 1) * m;
+  double2 *col = H + i * (m + 1);
+  for (int j = 0; j <= i; ++j) {
+    double2 a = st.h1[r * (m + 1) + j], b = st.h2[r * (m + 1) + j];
+    col[j] = make_double2(a.x + b.x, a.y + b.y);
+  }
+  const double hn = sqrt(fmax(st.nrm[r].x, 0.0));
+  col[i + 1] = make_double2(hn, 0.0);
+  // previous rotations
+  for (int j = 0; j < i; ++j) {
+    const double c = st.cs[r * m + j];
+    const double2 s = st.sn[r * m + j];
+    const double2 a = col[j], b = col[j + 1];
+    col[j] = cadd(cscale(a, c), dcmul(s, b));
+    col[j + 1] = csub(cscale(b, c), dcmul(cconj(s), a));
+  }
+  // new rotation zeroing col[i+1] (real, >= 0)
+  const double2 a = col[i];
+  const double b = col[i + 1].x;
+  const double aa = sqrt(cabs2(a));
+  const double rr = sqrt(aa * aa + b * b);
+  double c;
+  double2 s;
+  if (rr == 0.0) {
+    c = 1.0;
+    s = make_double2(0.0, 0.0);
+  } else if (aa == 0.0) {
+    c = 0.0;
+    s = make_double2(1.0, 0.0);
+    col[i] = make_double2(rr, 0.0);
+  } else {
+    c = aa / rr;
+    const double2 ph = make_double2(a.x / aa, a.y / aa);
+    s = cscale(ph, b / rr);
+    col[i] = cscale(ph, rr);
+  }
+  col[i + 1] = make_double2(0.0, 0.0);
+  st.cs[r * m + i] = c;
+  st.sn[r * m + i] = s;
+  double2 *g = st.g + r * (m + 1);
+  const double2 gi = g[i];
+  g[i + 1] = cneg(dcmul(cconj(s), gi));
+  g[i] = cscale(gi, c);
+  const double res = sqrt(cabs2(g[i + 1]));
+  st.res[r] = res;
+  st.nit[r] = i + 1;
+  const bool done = !(res > st.target[r]) || hn == 0.0 || !isfinite(res) || rr == 0.0;
+  if (done) {
+    st.active[r] = 0;
+    st.inv[r] = 0.0;
+  } else {
+    st.inv[r] = 1.0 / hn;
+  }
+}
+
+__global__ void gmres_solve_kernel(GmresState st) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= st.nrhs) return;
+  const int m = st.m;
+  const int k = st.nit[r];
+  const double2 *H = st.H + (int64_t)r * (m + 1) * m;
+  const double2 *g = st.g + r * (m + 1);
+  double2 *y = st.y + r * m;
+  for (int j = k; j < m; ++j) y[j] = make_double2(0.0, 0.0);
+  for (int j = k - 1; j >= 0; --j) {
+    double2 acc = g[j];
+    for (int l = j + 1; l < k; ++l) acc = csub(acc, dcmul(H[l * (m + 1) + j], y[l]));
+    const double2 d = H[j * (m + 1) + j];
+    const double dd = cabs2(d);
+    y[j] = dd > 0.0 ? make_double2((acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd)
+                    : make_double2(0.0, 0.0);
+  }
+}
+}  // namespace
+
+int reduce_blocks(int64_t n) {
+  int64_t b = (n + 4095) / 4096;
+  if (b < 1) b = 1;
+  if (b > 512) b = 512;
+  return (int)b;
+}
+
+template <typename T>
+void dot(const C<T> *x, const C<T> *y, int64_t n, int nrhs, double2 *out, double2 *partial,
+         cudaStream_t s) {
+  const int NB = reduce_blocks(n);
+  const int64_t chunk = (n + NB - 1) / NB;
+  dot_stage1<T><<<dim3(NB, nrhs, 1), RB, 0, s>>>(x, 0, y, n, chunk, partial);
+  dot_stage2<<<nrhs, RB, 0, s>>>(partial, NB, nrhs, out, 1);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void multi_dot(const C<T> *V, int64_t vstride, int k, const C<T> *w, int64_t n, int nrhs,
+               double2 *h, int ldh, double2 *partial, cudaStream_t s) {
+  const int NB = reduce_blocks(n);
+  const int64_t chunk = (n + NB - 1) / NB;
+  dot_stage1<T><<<dim3(NB, nrhs, k), RB, 0, s>>>(V, vstride, w, n, chunk, partial);
+  dot_stage2<<<k * nrhs, RB, 0, s>>>(partial, NB, nrhs, h, ldh);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void multi_axpy(const C<T> *V, int64_t vstride, int k, C<T> *w, int64_t n, int nrhs,
+                const double2 *h, int ldh, double sign, cudaStream_t s) {
+  if (k <= 0) return;
+  if (k > 128) throw Error(1, "multi_axpy: k > 128");
+  const int gx = (grid_for(n) + nrhs - 1) / nrhs + 1;
+  multi_axpy_kernel<T><<<dim3(gx, nrhs), 256, 0, s>>>(V, vstride, k, w, n, h, ldh, sign);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void axpby(double a, const C<T> *x, double b, C<T> *y, int64_t n, int nrhs, cudaStream_t s) {
+  axpby_kernel<T><<<grid_for(n * nrhs), 256, 0, s>>>((T)a, x, (T)b, y, n * nrhs);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void scale_rhs(const C<T> *x, C<T> *y, const double *scal, int64_t n, int nrhs, cudaStream_t s) {
+  const int gx = (grid_for(n) + nrhs - 1) / nrhs + 1;
+  scale_rhs_kernel<T><<<dim3(gx, nrhs), 256, 0, s>>>(x, y, scal, n);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void mr_update(C<T> *z, C<T> *r, const C<T> *q, const double2 *dqr, const double2 *nq, int64_t n,
+               int nrhs, cudaStream_t s) {
+  const int gx = (grid_for(n) + nrhs - 1) / nrhs + 1;
+  mr_update_kernel<T><<<dim3(gx, nrhs), 256, 0, s>>>(z, r, q, dqr, nq, n);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename To, typename From>
+void convert(const C<From> *in, C<To> *out, int64_t n, cudaStream_t s) {
+  convert_kernel<To, From><<<grid_for(n), 256, 0, s>>>(in, out, n);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename To, typename From>
+void convert_scale(const C<From> *x, C<To> *y, const double *scal, int64_t n, int nrhs,
+                   cudaStream_t s) {
+  const int gx = (grid_for(n) + nrhs - 1) / nrhs + 1;
+  convert_scale_kernel<To, From><<<dim3(gx, nrhs), 256, 0, s>>>(x, y, scal, n);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T, typename Tlo>
+void add_lo(const C<Tlo> *x, C<T> *y, int64_t n, cudaStream_t s) {
+  add_lo_kernel<T, Tlo><<<grid_for(n), 256, 0, s>>>(x, y, n);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void check_finite(const C<T> *x, int64_t n, int *flag, cudaStream_t s) {
+  finite_kernel<T><<<grid_for(n), 256, 0, s>>>(x, n, flag);
+  MG_LAUNCH_CHECK();
+}
+
+void gmres_start(GmresState st, cudaStream_t s) {
+  gmres_start_kernel<<<(st.nrhs + 63) / 64, 64, 0, s>>>(st);
+  MG_LAUNCH_CHECK();
+}
+void gmres_arnoldi(GmresState st, int i, cudaStream_t s) {
+  gmres_arnoldi_kernel<<<(st.nrhs + 63) / 64, 64, 0, s>>>(st, i);
+  MG_LAUNCH_CHECK();
+}
+void gmres_solve(GmresState st, cudaStream_t s) {
+  gmres_solve_kernel<<<(st.nrhs + 63) / 64, 64, 0, s>>>(st);
+  MG_LAUNCH_CHECK();
+}
+
+#define INST(T)                                                                                  \
+  template void dot<T>(const C<T> *, const C<T> *, int64_t, int, double2 *, double2 *,           \
+                       cudaStream_t);                                                            \
+  template void multi_dot<T>(const C<T> *, int64_t, int, const C<T> *, int64_t, int, double2 *,  \
+                             int, double2 *, cudaStream_t);                                      \
+  template void multi_axpy<T>(const C<T> *, int64_t, int, C<T> *, int64_t, int, const double2 *, \
+                              int, double, cudaStream_t);                                        \
+  template void axpby<T>(double, const C<T> *, double, C<T> *, int64_t, int, cudaStream_t);      \
+  template void scale_rhs<T>(const C<T> *, C<T> *, const double *, int64_t, int, cudaStream_t);  \
+  template void mr_update<T>(C<T> *, C<T> *, const C<T> *, const double2 *, const double2 *,     \
+                             int64_t, int, cudaStream_t);                                        \
+  template void check_finite<T>(const C<T> *, int64_t, int *, cudaStream_t);
+INST(double)
+INST(float)
+template void convert<float, double>(const C<double> *, C<float> *, int64_t, cudaStream_t);
+template void convert<double, float>(const C<float> *, C<double> *, int64_t, cudaStream_t);
+template void convert_scale<float, double>(const C<double> *, C<float> *, const double *, int64_t,
+                                           int, cudaStream_t);
+template void convert_scale<double, double>(const C<double> *, C<double> *, const double *,
+                                            int64_t, int, cudaStream_t);
+template void convert_scale<double, float>(const C<float> *, C<double> *, const double *, int64_t,
+                                           int, cudaStream_t);
+template void add_lo<double, float>(const C<float> *, C<double> *, int64_t, cudaStream_t);
+template void add_lo<double, double>(const C<double> *, C<double> *, int64_t, cudaStream_t);
+
+}  // namespace mg

@@ -1,0 +1,478 @@
+// Coarse-level kernels: the Galerkin stencil D_{l+1} = P_l^H D_l P_l (Sec.
+// 2.2) stored as 9 dense (2 N_tv)^2 blocks per coarse site, the transfer
+// operators P_l / P_l^H built per aggregate and chirality, the Galerkin
+// construction, and the dense coarsest-level inverse.
+#include "kernels.h"
+
+namespace mg {
+
+namespace {
+
+inline int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+template <typename V> __device__ __forceinline__ V warp_csum(V v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+
+constexpr int RG = 4;  // right-hand sides per pass of the stencil kernel
+
+// y(X) = sum_d A[X][d] x(nbr(X, d)).  One block per coarse site; warp w
+// handles rows i = w, w + 8, ...; lanes stride over columns j; each A row
+// segment is loaded once and used for RG right-hand sides.
+template <typename T>
+__global__ void __launch_bounds__(256) stencil_kernel(const C<T> *__restrict__ in,
+                                                      C<T> *__restrict__ out,
+                                                      const C<T> *__restrict__ A, Geom g,
+                                                      int nrhs) {
+  extern __shared__ unsigned char smem_raw[];
+  C<T> *xs = reinterpret_cast<C<T> *>(smem_raw);  // [RG][9][m]
+  const int X = blockIdx.x;
+  const int m = g.dof;
+  const int64_t n = g.n();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int nb[9];
+#pragma unroll
+  for (int d = 0; d < 9; ++d) nb[d] = g.neighbor(X, d);
+  const C<T> *AX = A + (int64_t)X * 9 * m * m;
+  for (int r0 = 0; r0 < nrhs; r0 += RG) {
+    const int rg = nrhs - r0 < RG ? nrhs - r0 : RG;
+    __syncthreads();
+    for (int e = threadIdx.x; e < rg * 9 * m; e += blockDim.x) {
+      const int r = e / (9 * m), rem = e - r * 9 * m, d = rem / m, j = rem - d * m;
+      xs[e] = in[(r0 + r) * n + (int64_t)nb[d] * m + j];
+    }
+    __syncthreads();
+    for (int i = warp; i < m; i += (blockDim.x >> 5)) {
+      C<T> acc[RG];
+#pragma unroll
+      for (int r = 0; r < RG; ++r) acc[r] = mk<T>((T)0, (T)0);
+      for (int d = 0; d < 9; ++d) {
+        const C<T> *Ar = AX + ((int64_t)d * m + i) * m;
+        for (int j = lane; j < m; j += 32) {
+          const C<T> a = Ar[j];
+#pragma unroll
+          for (int r = 0; r < RG; ++r)
+            if (r < rg) acc[r] = cfma(a, xs[(r * 9 + d) * m + j], acc[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RG; ++r) {
+        if (r < rg) {
+          C<T> v = warp_csum(acc[r]);
+          if (lane == 0) out[(r0 + r) * n + (int64_t)X * m + i] = v;
+        }
+      }
+    }
+  }
+}
+
+// the 9 hop-class parts of a coarse stencil (Galerkin on the next level):
+// out9[h] row i of X = sum over d of class h of A[X][d] x(nbr(X, d)).
+template <typename T>
+__global__ void stencil_split_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ out9,
+                                     const C<T> *__restrict__ A, Geom g, int b0, int b1, int b2,
+                                     int b3) {
+  const int X = blockIdx.x;
+  const int m = g.dof;
+  const int64_t n = g.n();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b[4] = {b0, b1, b2, b3};
+  int c[4];
+  g.coords(X, c);
+  int cls[9], nb[9];
+  cls[0] = 0;
+  nb[0] = X;
+  for (int d = 1; d < 9; ++d) {
+    const int mu = (d - 1) >> 1;
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    if (d & 1) cn[mu] = (c[mu] + 1 == g.L[mu]) ? 0 : c[mu] + 1;
+    else cn[mu] = (c[mu] == 0) ? g.L[mu] - 1 : c[mu] - 1;
+    nb[d] = g.index(cn);
+    cls[d] = (c[mu] / b[mu]) != (cn[mu] / b[mu]) ? d : 0;
+  }
+  const C<T> *AX = A + (int64_t)X * 9 * m * m;
+  for (int i = warp; i < m; i += (blockDim.x >> 5)) {
+    C<T> acc[9];
+#pragma unroll
+    for (int h = 0; h < 9; ++h) acc[h] = mk<T>((T)0, (T)0);
+#pragma unroll
+    for (int d = 0; d < 9; ++d) {
+      const C<T> *Ar = AX + ((int64_t)d * m + i) * m;
+      C<T> v = mk<T>((T)0, (T)0);
+      for (int j = lane; j < m; j += 32) v = cfma(Ar[j], in[(int64_t)nb[d] * m + j], v);
+      v = warp_csum(v);
+      acc[cls[d]] = cadd(acc[cls[d]], v);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int h = 0; h < 9; ++h) out9[h * n + (int64_t)X * m + i] = acc[h];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ transfer
+// out[r][X][c*ntv + k] = sum_row conj(P[X][c][k][row]) in_r[fine(X, c, row)]
+template <typename T>
+__global__ void restrict_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ out,
+                                const C<T> *__restrict__ P, AggMap m, int nrhs) {
+  extern __shared__ unsigned char smem_raw[];
+  C<T> *xs = reinterpret_cast<C<T> *>(smem_raw);  // [rows]
+  const int X = blockIdx.x >> 1, c = blockIdx.x & 1;
+  const int64_t nf = m.fine.n(), nc = m.coarse.n();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const C<T> *PX = P + ((int64_t)(X * 2 + c) * m.ntv) * m.rows;
+  for (int r = 0; r < nrhs; ++r) {
+    __syncthreads();
+    for (int row = threadIdx.x; row < m.rows; row += blockDim.x)
+      xs[row] = in[r * nf + m.fine_index(X, c, row)];
+    __syncthreads();
+    for (int k = warp; k < m.ntv; k += nw) {
+      const C<T> *Pk = PX + (int64_t)k * m.rows;
+      C<T> acc = mk<T>((T)0, (T)0);
+      for (int row = lane; row < m.rows; row += 32) acc = cfmac(Pk[row], xs[row], acc);
+      acc = warp_csum(acc);
+      if (lane == 0) out[r * nc + (int64_t)X * m.coarse.dof + c * m.ntv + k] = acc;
+    }
+  }
+}
+
+// out_r[fine(X, c, row)] = beta out + sum_k P[X][c][k][row] in_r[X][c*ntv + k]
+template <typename T>
+__global__ void prolong_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ out,
+                               const C<T> *__restrict__ P, AggMap m, int nrhs, T beta) {
+  extern __shared__ unsigned char smem_raw[];
+  C<T> *cs = reinterpret_cast<C<T> *>(smem_raw);  // [nrhs][ntv]
+  const int X = blockIdx.x >> 1, c = blockIdx.x & 1;
+  const int64_t nf = m.fine.n(), nc = m.coarse.n();
+  for (int e = threadIdx.x; e < nrhs * m.ntv; e += blockDim.x) {
+    const int r = e / m.ntv, k = e - r * m.ntv;
+    cs[e] = in[r * nc + (int64_t)X * m.coarse.dof + c * m.ntv + k];
+  }
+  __syncthreads();
+  const C<T> *PX = P + ((int64_t)(X * 2 + c) * m.ntv) * m.rows;
+  for (int row = threadIdx.x; row < m.rows; row += blockDim.x) {
+    const int64_t fi = m.fine_index(X, c, row);
+    for (int r = 0; r < nrhs; ++r) {
+      C<T> acc = beta == (T)0 ? mk<T>((T)0, (T)0) : cscale(out[r * nf + fi], beta);
+      for (int k = 0; k < m.ntv; ++k) acc = cfma(PX[(int64_t)k * m.rows + row], cs[r * m.ntv + k], acc);
+      out[r * nf + fi] = acc;
+    }
+  }
+}
+
+__global__ void probe_kernel(double2 *__restrict__ out, const double2 *__restrict__ P, AggMap m,
+                             int col) {
+  const int cc = col / m.ntv, k = col - cc * m.ntv;
+  const int64_t nf = m.fine.n();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nf;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int X, c, row;
+    m.locate(i, X, c, row);
+    out[i] = (c == cc) ? P[((int64_t)(X * 2 + c) * m.ntv + k) * m.rows + row] : make_double2(0.0, 0.0);
+  }
+}
+
+__device__ __forceinline__ double2 block_csum(double2 v, double2 *sh) {
+  v = warp_csum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = make_double2(0.0, 0.0);
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { t.x += sh[i].x; t.y += sh[i].y; }
+    sh[32] = t;
+  }
+  __syncthreads();
+  double2 r = sh[32];
+  __syncthreads();
+  return r;
+}
+
+// P[X][c][k][:] = MGS-orthonormalised (twice, in k order) restriction of the
+// test vectors V[k] to aggregate X, chirality c.
+__global__ void mgs_kernel(const double2 *__restrict__ V, double2 *__restrict__ P, AggMap m,
+                           int *status) {
+  __shared__ double2 sh[33];
+  const int X = blockIdx.x >> 1, c = blockIdx.x & 1;
+  const int64_t nf = m.fine.n();
+  double2 *PX = P + ((int64_t)(X * 2 + c) * m.ntv) * m.rows;
+  for (int k = 0; k < m.ntv; ++k) {
+    double2 *w = PX + (int64_t)k * m.rows;
+    for (int row = threadIdx.x; row < m.rows; row += blockDim.x)
+      w[row] = V[k * nf + m.fine_index(X, c, row)];
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int j = 0; j < k; ++j) {
+        const double2 *q = PX + (int64_t)j * m.rows;
+        double2 acc = make_double2(0.0, 0.0);
+        for (int row = threadIdx.x; row < m.rows; row += blockDim.x) acc = cfmac(q[row], w[row], acc);
+        const double2 h = block_csum(acc, sh);
+        for (int row = threadIdx.x; row < m.rows; row += blockDim.x) w[row] = csub(w[row], cmul(h, q[row]));
+        __syncthreads();
+      }
+    }
+    double2 acc = make_double2(0.0, 0.0);
+    for (int row = threadIdx.x; row < m.rows; row += blockDim.x) acc.x += cabs2(w[row]);
+    const double nrm = sqrt(block_csum(acc, sh).x);
+    if (!(nrm > 0.0) && threadIdx.x == 0) *status = 1;
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int row = threadIdx.x; row < m.rows; row += blockDim.x) w[row] = cscale(w[row], inv);
+    __syncthreads();
+  }
+}
+
+__global__ void galerkin_scatter_kernel(const double2 *__restrict__ cols, double2 *__restrict__ A,
+                                        Geom g, int col) {
+  const int m = g.dof;
+  const int64_t nc = g.n();
+  const int64_t total = 9 * nc;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int h = (int)(e / nc);
+    const int64_t rem = e - h * nc;
+    const int X = (int)(rem / m), i = (int)(rem - (int64_t)X * m);
+    A[(((int64_t)X * 9 + h) * m + i) * m + col] = cols[e];
+  }
+}
+
+__global__ void p_canonical_kernel(const double2 *__restrict__ P, double2 *__restrict__ out, AggMap m) {
+  const int64_t total = (int64_t)m.coarse.V * 2 * m.ntv * m.rows;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    // e over [X][c][row][k]
+    const int k = (int)(e % m.ntv);
+    const int64_t t = e / m.ntv;
+    const int row = (int)(t % m.rows);
+    const int64_t xc = t / m.rows;
+    out[e] = P[(xc * m.ntv + k) * m.rows + row];
+  }
+}
+
+// ------------------------------------------------------------------ dense
+__global__ void dense_build_kernel(const double2 *__restrict__ A, double2 *__restrict__ M, Geom g) {
+  const int m = g.dof;
+  const int64_t n = g.n();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = e / n, col = e - row * n;
+    const int X = (int)(row / m), i = (int)(row - (int64_t)X * m);
+    const int Y = (int)(col / m), j = (int)(col - (int64_t)Y * m);
+    double2 v = make_double2(0.0, 0.0);
+    for (int d = 0; d < 9; ++d)
+      if (g.neighbor(X, d) == Y) v = cadd(v, A[(((int64_t)X * 9 + d) * m + i) * m + j]);
+    M[e] = v;
+  }
+}
+
+__global__ void gj_pivot_kernel(const double2 *__restrict__ M, int n, int k, int *piv,
+                                double2 *pivval, int *status) {
+  __shared__ double bv[1024];
+  __shared__ int bi[1024];
+  double best = -1.0;
+  int idx = k;
+  for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+    const double a = cabs2(M[(int64_t)i * n + k]);
+    if (a > best) { best = a; idx = i; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = idx;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double b2 = bv[threadIdx.x + o];
+      const int i2 = bi[threadIdx.x + o];
+      if (b2 > bv[threadIdx.x] || (b2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
+        bv[threadIdx.x] = b2;
+        bi[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *piv = bi[0];
+    *pivval = M[(int64_t)bi[0] * n + k];
+    if (!(bv[0] > 0.0)) *status = 1;
+  }
+}
+
+// column k of M after the row swap k <-> piv, with f[k] = 0 (read only).
+__global__ void gj_factor_kernel(const double2 *__restrict__ M, int n, int k, const int *piv,
+                                 double2 *__restrict__ f) {
+  const int p = *piv;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int src = (i == p) ? k : i;
+    f[i] = (i == k) ? make_double2(0.0, 0.0) : M[(int64_t)src * n + k];
+  }
+}
+
+// swap rows k and piv of M and Inv and divide row k by the pivot.
+__global__ void gj_swap_kernel(double2 *__restrict__ M, double2 *__restrict__ Inv, int n, int k,
+                               const int *piv, const double2 *pivval) {
+  const int p = *piv;
+  const double2 pv = *pivval;
+  const double d = cabs2(pv);
+  const double2 ip = d > 0.0 ? make_double2(pv.x / d, -pv.y / d) : make_double2(0.0, 0.0);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < 2 * n; j += gridDim.x * blockDim.x) {
+    double2 *B = j < n ? M : Inv;
+    const int jj = j < n ? j : j - n;
+    const double2 a = B[(int64_t)k * n + jj];
+    const double2 b = B[(int64_t)p * n + jj];
+    B[(int64_t)k * n + jj] = cmul(b, ip);
+    if (p != k) B[(int64_t)p * n + jj] = a;
+  }
+}
+
+__global__ void gj_elim_kernel(double2 *__restrict__ M, double2 *__restrict__ Inv, int n, int k,
+                               const double2 *__restrict__ f) {
+  const int64_t total = (int64_t)n * 2 * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / (2 * n));
+    const int j = (int)(e - (int64_t)i * 2 * n);
+    if (i == k) continue;
+    const double2 fi = f[i];
+    if (fi.x == 0.0 && fi.y == 0.0) continue;
+    double2 *B = j < n ? M : Inv;
+    const int jj = j < n ? j : j - n;
+    B[(int64_t)i * n + jj] = csub(B[(int64_t)i * n + jj], cmul(fi, B[(int64_t)k * n + jj]));
+  }
+}
+
+__global__ void eye_kernel(double2 *__restrict__ M, int n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / n, j = e - i * n;
+    M[e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// out_r = Minv in_r: warp per row, lanes over columns.
+template <typename T>
+__global__ void dense_apply_kernel(const C<T> *__restrict__ Minv, const C<T> *__restrict__ in,
+                                   C<T> *__restrict__ out, int n, int nrhs) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const C<T> *row = Minv + (int64_t)warp * n;
+  for (int r = 0; r < nrhs; ++r) {
+    C<T> acc = mk<T>((T)0, (T)0);
+    for (int j = lane; j < n; j += 32) acc = cfma(row[j], in[(int64_t)r * n + j], acc);
+    acc = warp_csum(acc);
+    if (lane == 0) out[(int64_t)r * n + warp] = acc;
+  }
+}
+
+__global__ void dense_trace_kernel(const double2 *__restrict__ M, int n, double2 *out) {
+  __shared__ double2 sh[33];
+  double2 acc = make_double2(0.0, 0.0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) acc = cadd(acc, M[(int64_t)i * n + i]);
+  acc = block_csum(acc, sh);
+  if (threadIdx.x == 0) *out = acc;
+}
+
+}  // namespace
+
+template <typename T>
+void stencil_apply(const C<T> *in, C<T> *out, const C<T> *A, Geom g, int nrhs, cudaStream_t s) {
+  const size_t sm = (size_t)RG * 9 * g.dof * sizeof(C<T>);
+  stencil_kernel<T><<<g.V, 256, sm, s>>>(in, out, A, g, nrhs);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void stencil_split(const C<T> *in, C<T> *out9, const C<T> *A, Geom g, const int b[4],
+                   cudaStream_t s) {
+  stencil_split_kernel<T><<<g.V, 256, 0, s>>>(in, out9, A, g, b[0], b[1], b[2], b[3]);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void restrict_op(const C<T> *in, C<T> *out, const C<T> *P, const AggMap &m, int nrhs,
+                 cudaStream_t s) {
+  const size_t sm = (size_t)m.rows * sizeof(C<T>);
+  if (sm > 48 * 1024) throw Error(1, "restrict: aggregate too large for shared memory");
+  restrict_kernel<T><<<m.coarse.V * 2, 256, sm, s>>>(in, out, P, m, nrhs);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void prolong_op(const C<T> *in, C<T> *out, const C<T> *P, const AggMap &m, int nrhs, double beta,
+                cudaStream_t s) {
+  const size_t sm = (size_t)nrhs * m.ntv * sizeof(C<T>);
+  if (sm > 48 * 1024) throw Error(1, "prolong: too many right-hand sides");
+  prolong_kernel<T><<<m.coarse.V * 2, 256, sm, s>>>(in, out, P, m, nrhs, (T)beta);
+  MG_LAUNCH_CHECK();
+}
+
+void probe_column(double2 *out, const double2 *P, const AggMap &m, int col, cudaStream_t s) {
+  probe_kernel<<<grid_for(m.fine.n()), 256, 0, s>>>(out, P, m, col);
+  MG_LAUNCH_CHECK();
+}
+
+void build_prolongator(const double2 *V, double2 *P, const AggMap &m, int *status, cudaStream_t s) {
+  mgs_kernel<<<m.coarse.V * 2, 256, 0, s>>>(V, P, m, status);
+  MG_LAUNCH_CHECK();
+}
+
+void galerkin_scatter(const double2 *cols, double2 *A, Geom coarse, int col, cudaStream_t s) {
+  galerkin_scatter_kernel<<<grid_for(9 * coarse.n()), 256, 0, s>>>(cols, A, coarse, col);
+  MG_LAUNCH_CHECK();
+}
+
+void prolongator_to_canonical(const double2 *P, double2 *out, const AggMap &m, cudaStream_t s) {
+  p_canonical_kernel<<<grid_for((int64_t)m.coarse.V * 2 * m.ntv * m.rows), 256, 0, s>>>(P, out, m);
+  MG_LAUNCH_CHECK();
+}
+
+void dense_from_stencil(const double2 *A, double2 *M, Geom g, cudaStream_t s) {
+  dense_build_kernel<<<grid_for(g.n() * g.n()), 256, 0, s>>>(A, M, g);
+  MG_LAUNCH_CHECK();
+}
+
+void dense_invert(double2 *M, double2 *work, int n, int *status, cudaStream_t s) {
+  double2 *Inv = work;
+  double2 *f = work + (int64_t)n * n;
+  double2 *pivval = f + n;
+  int *piv = reinterpret_cast<int *>(pivval + 1);
+  eye_kernel<<<grid_for((int64_t)n * n), 256, 0, s>>>(Inv, n);
+  for (int k = 0; k < n; ++k) {
+    gj_pivot_kernel<<<1, 1024, 0, s>>>(M, n, k, piv, pivval, status);
+    gj_factor_kernel<<<grid_for(n), 256, 0, s>>>(M, n, k, piv, f);
+    gj_swap_kernel<<<grid_for(2 * n), 256, 0, s>>>(M, Inv, n, k, piv, pivval);
+    gj_elim_kernel<<<grid_for((int64_t)n * 2 * n), 256, 0, s>>>(M, Inv, n, k, f);
+  }
+  MG_CUDA(cudaMemcpyAsync(M, Inv, sizeof(double2) * n * n, cudaMemcpyDeviceToDevice, s));
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void dense_apply(const C<T> *Minv, const C<T> *in, C<T> *out, int n, int nrhs, cudaStream_t s) {
+  dense_apply_kernel<T><<<div_up((int64_t)n * 32, 256), 256, 0, s>>>(Minv, in, out, n, nrhs);
+  MG_LAUNCH_CHECK();
+}
+
+void dense_trace(const double2 *M, int n, double2 *out, cudaStream_t s) {
+  dense_trace_kernel<<<1, 256, 0, s>>>(M, n, out);
+  MG_LAUNCH_CHECK();
+}
+
+#define INST(T)                                                                                 \
+  template void stencil_apply<T>(const C<T> *, C<T> *, const C<T> *, Geom, int, cudaStream_t);  \
+  template void stencil_split<T>(const C<T> *, C<T> *, const C<T> *, Geom, const int *,         \
+                                 cudaStream_t);                                                 \
+  template void restrict_op<T>(const C<T> *, C<T> *, const C<T> *, const AggMap &, int,         \
+                               cudaStream_t);                                                   \
+  template void prolong_op<T>(const C<T> *, C<T> *, const C<T> *, const AggMap &, int, double,  \
+                              cudaStream_t);                                                    \
+  template void dense_apply<T>(const C<T> *, const C<T> *, C<T> *, int, int, cudaStream_t);
+INST(double)
+INST(float)
+
+}  // namespace mg

@@ -1,0 +1,299 @@
+// Wilson-Dirac operator on the fine lattice (the paper's D; Sec. 1 and the
+// Gamma5-hermiticity of Sec. 2), Gamma5, and the Z4 noise generator.
+//
+//   (D psi)(x) = (4 + m0) psi(x) - 1/2 sum_mu [ (1 - gamma_mu) U_mu(x) psi(x+mu)
+//                                 + (1 + gamma_mu) U_mu(x-mu)^H psi(x-mu) ]
+//
+// Chiral basis: gamma_mu = [[0, B_mu], [B_mu^H, 0]] with B_k = -i sigma_k and
+// B_4 = 1, so (1 -+ gamma_mu) has rank 2 per colour: with the upper/lower
+// spin halves u, l of psi,
+//   (1 - gamma) psi = ( h, -B^H h ),  h = u - B l,
+//   (1 + gamma) psi = ( h,  B^H h ),  h = u + B l.
+// Each hop therefore multiplies two colour vectors by the link instead of
+// four.  Time is antiperiodic for the fermion field.
+#include "kernels.h"
+
+namespace mg {
+
+namespace {
+
+// (B_mu l)_a for a = 0, 1 given the lower spins l0 = psi_2, l1 = psi_3
+template <int MU, typename V> __device__ __forceinline__ V Bl(int a, V l0, V l1) {
+  if (MU == 0) return a == 0 ? cmulmi(l1) : cmulmi(l0);   // -i sigma_1
+  if (MU == 1) return a == 0 ? cneg(l1) : l0;              // -i sigma_2
+  if (MU == 2) return a == 0 ? cmulmi(l0) : cmuli(l1);     // -i sigma_3
+  return a == 0 ? l0 : l1;                                 // 1
+}
+// (B_mu^H v)_a
+template <int MU, typename V> __device__ __forceinline__ V Bh(int a, V v0, V v1) {
+  if (MU == 0) return a == 0 ? cmuli(v1) : cmuli(v0);
+  if (MU == 1) return a == 0 ? v1 : cneg(v0);
+  if (MU == 2) return a == 0 ? cmuli(v0) : cmulmi(v1);
+  return a == 0 ? v0 : v1;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_spinor(const C<T> *__restrict__ p, C<T> (&s)[12]) {
+#pragma unroll
+  for (int i = 0; i < 12; ++i) s[i] = p[i];
+}
+template <typename T>
+__device__ __forceinline__ void load_link(const C<T> *__restrict__ p, C<T> (&u)[9]) {
+#pragma unroll
+  for (int i = 0; i < 9; ++i) u[i] = p[i];
+}
+
+// contribution of one hop in direction MU (FWD: from x+mu through U_mu(x);
+// otherwise from x-mu through U_mu(x-mu)^H), scaled by k = -1/2 * boundary
+// sign, added to acc.
+template <int MU, bool FWD, typename T>
+__device__ __forceinline__ void hop(const C<T> (&p)[12], const C<T> (&u)[9], T k, C<T> (&acc)[12]) {
+  const T sg = FWD ? (T)-1 : (T)1;
+  C<T> h[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      C<T> b = Bl<MU>(a, p[6 + c], p[9 + c]);
+      h[a][c] = cadd(p[3 * a + c], cscale(b, sg));
+    }
+  C<T> v[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      C<T> z = mk<T>((T)0, (T)0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        if (FWD) z = cfma(u[3 * c + b], h[a][b], z);   // U h
+        else z = cfmac(u[3 * b + c], h[a][b], z);      // U^H h
+      }
+      v[a][c] = z;
+    }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[3 * a + c] = cfma(mk<T>(k, (T)0), v[a][c], acc[3 * a + c]);
+      C<T> w = Bh<MU>(a, v[0][c], v[1][c]);
+      acc[6 + 3 * a + c] = cfma(mk<T>(sg * k, (T)0), w, acc[6 + 3 * a + c]);
+    }
+}
+
+template <int MU, typename T, bool SPLIT>
+__device__ __forceinline__ void dir_pair(const C<T> *__restrict__ in, const C<T> *__restrict__ U,
+                                         const Geom &g, int s, const int (&c)[4], const int *b,
+                                         C<T> (&acc)[12], C<T> *__restrict__ out9,
+                                         int64_t nstride) {
+  // forward
+  {
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    cn[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
+    const int sn = g.index(cn);
+    const T k = (MU == 3 && cn[3] == 0) ? (T)0.5 : (T)-0.5;
+    C<T> p[12], u[9];
+    load_spinor<T>(in + (int64_t)sn * 12, p);
+    load_link<T>(U + ((int64_t)s * 4 + MU) * 9, u);
+    if (!SPLIT) {
+      hop<MU, true, T>(p, u, k, acc);
+    } else {
+      const bool cross = (c[MU] / b[MU]) != (cn[MU] / b[MU]);
+      if (cross) {
+        C<T> t[12];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) t[i] = mk<T>((T)0, (T)0);
+        hop<MU, true, T>(p, u, k, t);
+        C<T> *o = out9 + (1 + 2 * MU) * nstride + (int64_t)s * 12;
+#pragma unroll
+        for (int i = 0; i < 12; ++i) o[i] = t[i];
+      } else {
+        hop<MU, true, T>(p, u, k, acc);
+        C<T> *o = out9 + (1 + 2 * MU) * nstride + (int64_t)s * 12;
+#pragma unroll
+        for (int i = 0; i < 12; ++i) o[i] = mk<T>((T)0, (T)0);
+      }
+    }
+  }
+  // backward
+  {
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    cn[MU] = (c[MU] == 0) ? g.L[MU] - 1 : c[MU] - 1;
+    const int sn = g.index(cn);
+    const T k = (MU == 3 && c[3] == 0) ? (T)0.5 : (T)-0.5;
+    C<T> p[12], u[9];
+    load_spinor<T>(in + (int64_t)sn * 12, p);
+    load_link<T>(U + ((int64_t)sn * 4 + MU) * 9, u);
+    if (!SPLIT) {
+      hop<MU, false, T>(p, u, k, acc);
+    } else {
+      const bool cross = (c[MU] / b[MU]) != (cn[MU] / b[MU]);
+      C<T> *o = out9 + (2 + 2 * MU) * nstride + (int64_t)s * 12;
+      if (cross) {
+        C<T> t[12];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) t[i] = mk<T>((T)0, (T)0);
+        hop<MU, false, T>(p, u, k, t);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) o[i] = t[i];
+      } else {
+        hop<MU, false, T>(p, u, k, acc);
+#pragma unroll
+        for (int i = 0; i < 12; ++i) o[i] = mk<T>((T)0, (T)0);
+      }
+    }
+  }
+}
+
+template <typename T, bool SPLIT>
+__global__ void __launch_bounds__(128) wilson_kernel(const C<T> *__restrict__ in,
+                                                     C<T> *__restrict__ out,
+                                                     const C<T> *__restrict__ U, Geom g, T diag,
+                                                     int b0, int b1, int b2, int b3) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const int64_t n = (int64_t)g.V * 12;
+  const C<T> *inr = in + blockIdx.y * n;
+  C<T> *outr = out + (SPLIT ? 0 : blockIdx.y * n);
+  const int b[4] = {b0, b1, b2, b3};
+  int c[4];
+  g.coords(s, c);
+  C<T> acc[12];
+  {
+    const C<T> *ps = inr + (int64_t)s * 12;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[i] = cscale(ps[i], diag);
+  }
+  dir_pair<0, T, SPLIT>(inr, U, g, s, c, b, acc, outr, n);
+  dir_pair<1, T, SPLIT>(inr, U, g, s, c, b, acc, outr, n);
+  dir_pair<2, T, SPLIT>(inr, U, g, s, c, b, acc, outr, n);
+  dir_pair<3, T, SPLIT>(inr, U, g, s, c, b, acc, outr, n);
+  C<T> *o = outr + (int64_t)s * 12;
+#pragma unroll
+  for (int i = 0; i < 12; ++i) o[i] = acc[i];
+}
+
+template <typename T>
+__global__ void gamma5_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ out, int64_t total,
+                              int dof) {
+  const int half = dof / 2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int d = (int)(i % dof);
+    out[i] = d < half ? in[i] : cneg(in[i]);
+  }
+}
+
+// ------------------------------------------------------------------ Philox
+// Philox4x64-10 (Salmon et al., SC'11): 10 rounds of
+//   (hi0, lo0) = M0 c0, (hi1, lo1) = M1 c2,
+//   c = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0),
+// the key bumped by the Weyl constants between rounds.
+struct U64x4 { uint64_t v[4]; };
+__device__ __forceinline__ U64x4 philox4x64_10(U64x4 c, uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    const uint64_t lo0 = M0 * c.v[0], hi0 = __umul64hi(M0, c.v[0]);
+    const uint64_t lo1 = M1 * c.v[2], hi1 = __umul64hi(M1, c.v[2]);
+    U64x4 o;
+    o.v[0] = hi1 ^ c.v[1] ^ k0;
+    o.v[1] = lo1;
+    o.v[2] = hi0 ^ c.v[3] ^ k1;
+    o.v[3] = lo0;
+    c = o;
+  }
+  return c;
+}
+
+template <typename T>
+__global__ void z4_kernel(C<T> *__restrict__ out, int64_t n, uint64_t seed, uint64_t sample0,
+                          uint64_t term, uint64_t aux, int64_t lo, int64_t hi) {
+  const int r = blockIdx.y;
+  C<T> *o = out + r * n;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q * 4 < n;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i0 = q * 4;
+    const bool any = (i0 + 4 > lo) && (i0 < hi);
+    U64x4 w;
+    if (any) {
+      U64x4 c;
+      c.v[0] = (uint64_t)q;
+      c.v[1] = sample0 + (uint64_t)r;
+      c.v[2] = term;
+      c.v[3] = aux;
+      w = philox4x64_10(c, seed, 0ull);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t i = i0 + j;
+      if (i >= n) break;
+      C<T> x = mk<T>((T)0, (T)0);
+      if (any && i >= lo && i < hi) {
+        const int code = (int)(w.v[j] >> 62);
+        x = code == 0 ? mk<T>((T)1, (T)0)
+                      : code == 1 ? mk<T>((T)0, (T)1) : code == 2 ? mk<T>((T)-1, (T)0) : mk<T>((T)0, (T)-1);
+      }
+      o[i] = x;
+    }
+  }
+}
+
+inline int grid_for(int64_t n) {
+  int64_t b = (n + 255) / 256;
+  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+}  // namespace
+
+template <typename T>
+void wilson_apply(const C<T> *in, C<T> *out, const C<T> *U, Geom g, double m0, int nrhs,
+                  cudaStream_t s) {
+  dim3 grid(div_up(g.V, 128), nrhs);
+  wilson_kernel<T, false><<<grid, 128, 0, s>>>(in, out, U, g, (T)(4.0 + m0), 1, 1, 1, 1);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void wilson_split(const C<T> *in, C<T> *out9, const C<T> *U, Geom g, double m0, const int b[4],
+                  cudaStream_t s) {
+  dim3 grid(div_up(g.V, 128), 1);
+  wilson_kernel<T, true><<<grid, 128, 0, s>>>(in, out9, U, g, (T)(4.0 + m0), b[0], b[1], b[2], b[3]);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void gamma5_apply(const C<T> *in, C<T> *out, int64_t nsites, int dof, int nrhs, cudaStream_t s) {
+  const int64_t total = nsites * dof * nrhs;
+  gamma5_kernel<T><<<grid_for(total), 256, 0, s>>>(in, out, total, dof);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void z4_noise(C<T> *out, Geom g, uint64_t seed, uint64_t sample0, uint64_t term, uint64_t aux,
+              int slice, int nrhs, cudaStream_t s) {
+  const int64_t n = g.n();
+  int64_t lo = 0, hi = n;
+  if (slice >= 0) {
+    const int64_t per = n / g.L[3];
+    lo = per * slice;
+    hi = lo + per;
+  }
+  const int gx = grid_for((n + 3) / 4);
+  z4_kernel<T><<<dim3(gx, nrhs), 256, 0, s>>>(out, n, seed, sample0, term, aux, lo, hi);
+  MG_LAUNCH_CHECK();
+}
+
+#define INST(T)                                                                               \
+  template void wilson_apply<T>(const C<T> *, C<T> *, const C<T> *, Geom, double, int,        \
+                                cudaStream_t);                                                \
+  template void wilson_split<T>(const C<T> *, C<T> *, const C<T> *, Geom, double, const int *, \
+                                cudaStream_t);                                                \
+  template void gamma5_apply<T>(const C<T> *, C<T> *, int64_t, int, int, cudaStream_t);       \
+  template void z4_noise<T>(C<T> *, Geom, uint64_t, uint64_t, uint64_t, uint64_t, int, int,   \
+                            cudaStream_t);
+INST(double)
+INST(float)
+
+}  // namespace mg

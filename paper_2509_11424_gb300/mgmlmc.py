@@ -1,0 +1,283 @@
+"""ctypes binding of libmgmlmc.so (include/mgmlmc.h): the same entry points
+under the same names, argument marshalling only.
+
+Buffers may be torch tensors (host or CUDA; their data_ptr() is passed),
+numpy arrays (host) or raw integer addresses.  Every call raises
+MgmlmcError carrying the library's status and last error message when the
+status is not MGMLMC_OK.  There is no fallback: if the shared library is not
+built the first call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, 'libmgmlmc.so')
+
+MAX_LEVELS = 4
+FP64, FP32 = 0, 1
+EST_PLAIN, EST_ORTHOGONAL = 0, 1
+OP_D, OP_RESTRICT, OP_PROLONG, OP_PROJECT, OP_SOLVE, OP_GAMMA5 = range(6)
+TERM_PLAIN, TERM_O, TERM_F, TERM_COARSEST = 0, 16, 32, 48
+STATUS = {0: 'OK', 1: 'ERR_ARG', 2: 'ERR_STATE', 3: 'ERR_OOM', 4: 'ERR_CUDA',
+          5: 'ERR_NOT_CONVERGED', 6: 'ERR_NUMERIC'}
+
+
+class MgParams(ctypes.Structure):
+    _fields_ = [('n_levels', ctypes.c_int),
+                ('block', (ctypes.c_int * 4) * (MAX_LEVELS - 1)),
+                ('n_tv', ctypes.c_int * (MAX_LEVELS - 1)),
+                ('setup_rounds', ctypes.c_int),
+                ('setup_iters', ctypes.c_int),
+                ('seed', ctypes.c_uint64)]
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [('tol', ctypes.c_double),
+                ('max_iter', ctypes.c_int),
+                ('restart', ctypes.c_int),
+                ('smoother_steps', ctypes.c_int),
+                ('coarse_iters', ctypes.c_int),
+                ('precision', ctypes.c_int),
+                ('inner_tol', ctypes.c_double)]
+
+
+class EstParams(ctypes.Structure):
+    _fields_ = [('kind', ctypes.c_int),
+                ('n_samples', ctypes.c_int * (2 * MAX_LEVELS)),
+                ('batch', ctypes.c_int),
+                ('seed', ctypes.c_uint64),
+                ('first_sample', ctypes.c_uint64)]
+
+
+class TermResult(ctypes.Structure):
+    _fields_ = [('term', ctypes.c_int), ('n', ctypes.c_int),
+                ('mean_re', ctypes.c_double), ('mean_im', ctypes.c_double),
+                ('var', ctypes.c_double),
+                ('sum_re', ctypes.c_double), ('sum_im', ctypes.c_double),
+                ('sum_abs2', ctypes.c_double),
+                ('seconds', ctypes.c_double), ('iters_mean', ctypes.c_double),
+                ('max_residual', ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class MgmlmcError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__('%s: %s' % (STATUS.get(status, status), message))
+        self.status = status
+
+
+_lib = None
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_U64 = ctypes.c_uint64
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+_SIGNATURES = {
+    'mgmlmc_create': [ctypes.POINTER(_I), _P, ctypes.POINTER(_P)],
+    'mgmlmc_destroy': [_P],
+    'mgmlmc_last_error': [_P],
+    'mgmlmc_set_gauge': [_P, _P, _I],
+    'mgmlmc_set_mass': [_P, _D],
+    'mgmlmc_set_solver': [_P, ctypes.POINTER(SolverParams)],
+    'mgmlmc_set_test_vectors': [_P, _I, _P, _I, _I64, _I],
+    'mgmlmc_build_hierarchy': [_P, ctypes.POINTER(MgParams)],
+    'mgmlmc_level_info': [_P, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I64)],
+    'mgmlmc_estimate_trace': [_P, ctypes.POINTER(EstParams), ctypes.POINTER(TermResult), _I,
+                              ctypes.POINTER(_I)],
+    'mgmlmc_coarsest_trace': [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    'mgmlmc_connected_correlator': [_P, _I, _I, _U64, _U64, _P, _P, ctypes.POINTER(_I)],
+    'mgmlmc_disconnected_loop': [_P, _I, _I, _I, _U64, _U64, _P, _P, ctypes.POINTER(_I)],
+    'mgmlmc_apply': [_P, _I, _I, _I, _P, _P, _I],
+    'mgmlmc_noise': [_P, _I, _U64, _U64, _U64, _U64, _I, _P, _I],
+    'mgmlmc_get_prolongator': [_P, _I, _P],
+    'mgmlmc_get_coarse_op': [_P, _I, _P],
+    'mgmlmc_last_solve_stats': [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)],
+}
+
+
+def lib():
+    """The loaded shared library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError('libmgmlmc.so is not built (run paper_2509_11424_gb300.build.build())')
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = None if name == 'mgmlmc_destroy' else (
+                ctypes.c_char_p if name == 'mgmlmc_last_error' else ctypes.c_int)
+        _lib = L
+    return _lib
+
+
+def ptr(buf):
+    """Address of a torch tensor, numpy array or integer."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if hasattr(buf, 'data_ptr'):
+        return buf.data_ptr()
+    if isinstance(buf, np.ndarray):
+        if not buf.flags['C_CONTIGUOUS']:
+            raise ValueError('numpy buffers must be C-contiguous')
+        return buf.ctypes.data
+    raise TypeError('unsupported buffer type %r' % type(buf))
+
+
+def _check(ctx, status):
+    if status != 0:
+        msg = lib().mgmlmc_last_error(ctx)
+        raise MgmlmcError(status, msg.decode() if msg else '')
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+# ---------------------------------------------------------------- entry points
+def mgmlmc_create(dims, stream=None):
+    d = (_I * 4)(*[int(v) for v in dims])
+    out = _P()
+    st = lib().mgmlmc_create(d, _stream_handle(stream), ctypes.byref(out))
+    if st != 0:
+        raise MgmlmcError(st, lib().mgmlmc_last_error(None).decode())
+    return out.value
+
+
+def mgmlmc_destroy(ctx):
+    lib().mgmlmc_destroy(ctx)
+
+
+def mgmlmc_last_error(ctx):
+    return lib().mgmlmc_last_error(ctx).decode()
+
+
+def mgmlmc_set_gauge(ctx, U, on_device=None):
+    if on_device is None:
+        on_device = bool(getattr(U, 'is_cuda', False))
+    _check(ctx, lib().mgmlmc_set_gauge(ctx, ptr(U), int(on_device)))
+
+
+def mgmlmc_set_mass(ctx, m0):
+    _check(ctx, lib().mgmlmc_set_mass(ctx, float(m0)))
+
+
+def solver_params(tol=1e-12, max_iter=2000, restart=16, smoother_steps=4, coarse_iters=8,
+                  precision=FP64, inner_tol=1e-6):
+    return SolverParams(tol, max_iter, restart, smoother_steps, coarse_iters, precision, inner_tol)
+
+
+def mgmlmc_set_solver(ctx, params=None, **kw):
+    p = params if params is not None else solver_params(**kw)
+    _check(ctx, lib().mgmlmc_set_solver(ctx, ctypes.byref(p)))
+
+
+def mgmlmc_set_test_vectors(ctx, level, V, n_tv, n, on_device=None):
+    if on_device is None:
+        on_device = bool(getattr(V, 'is_cuda', False))
+    _check(ctx, lib().mgmlmc_set_test_vectors(ctx, level, ptr(V), n_tv, n, int(on_device)))
+
+
+def mg_params(blocks, n_tv, setup_rounds=3, setup_iters=20, seed=3000):
+    p = MgParams()
+    p.n_levels = len(blocks) + 1
+    for l, b in enumerate(blocks):
+        for i in range(4):
+            p.block[l][i] = int(b[i])
+        p.n_tv[l] = int(n_tv[l])
+    p.setup_rounds = setup_rounds
+    p.setup_iters = setup_iters
+    p.seed = seed
+    return p
+
+
+def mgmlmc_build_hierarchy(ctx, params):
+    _check(ctx, lib().mgmlmc_build_hierarchy(ctx, ctypes.byref(params)))
+
+
+def mgmlmc_level_info(ctx, level):
+    d = (_I * 4)()
+    dof = _I()
+    n = _I64()
+    _check(ctx, lib().mgmlmc_level_info(ctx, level, d, ctypes.byref(dof), ctypes.byref(n)))
+    return tuple(d), dof.value, n.value
+
+
+def est_params(kind, n_samples, batch=8, seed=2000, first_sample=0):
+    p = EstParams()
+    p.kind = kind
+    for i, v in enumerate(n_samples):
+        p.n_samples[i] = int(v)
+    p.batch = batch
+    p.seed = seed
+    p.first_sample = first_sample
+    return p
+
+
+def mgmlmc_estimate_trace(ctx, params):
+    out = (TermResult * (2 * MAX_LEVELS))()
+    nt = _I()
+    _check(ctx, lib().mgmlmc_estimate_trace(ctx, ctypes.byref(params), out, 2 * MAX_LEVELS,
+                                            ctypes.byref(nt)))
+    return [out[i].as_dict() for i in range(nt.value)]
+
+
+def mgmlmc_coarsest_trace(ctx):
+    re, im = _D(), _D()
+    _check(ctx, lib().mgmlmc_coarsest_trace(ctx, ctypes.byref(re), ctypes.byref(im)))
+    return complex(re.value, im.value)
+
+
+def mgmlmc_connected_correlator(ctx, kind, n_samples, seed, first_sample, T, R_max):
+    mean = np.zeros(2 * R_max * R_max * T)
+    var = np.zeros(R_max * R_max * T)
+    R = _I()
+    _check(ctx, lib().mgmlmc_connected_correlator(ctx, kind, n_samples, seed, first_sample,
+                                                  ptr(mean), ptr(var), ctypes.byref(R)))
+    r = R.value
+    m = mean[:2 * r * r * T].view(np.complex128).reshape(r, r, T)
+    return m, var[:r * r * T].reshape(r, r, T)
+
+
+def mgmlmc_disconnected_loop(ctx, kind, t, n_samples, seed, first_sample, R_max):
+    mean = np.zeros(2 * R_max)
+    var = np.zeros(R_max)
+    R = _I()
+    _check(ctx, lib().mgmlmc_disconnected_loop(ctx, kind, t, n_samples, seed, first_sample,
+                                               ptr(mean), ptr(var), ctypes.byref(R)))
+    r = R.value
+    return mean[:2 * r].view(np.complex128), var[:r]
+
+
+def mgmlmc_apply(ctx, op, level, precision, inp, out, nrhs=1):
+    _check(ctx, lib().mgmlmc_apply(ctx, op, level, precision, ptr(inp), ptr(out), nrhs))
+
+
+def mgmlmc_noise(ctx, level, seed, first_sample, term, aux, slice_, out, nrhs=1):
+    _check(ctx, lib().mgmlmc_noise(ctx, level, seed, first_sample, term, aux, slice_, ptr(out), nrhs))
+
+
+def mgmlmc_get_prolongator(ctx, level, out):
+    _check(ctx, lib().mgmlmc_get_prolongator(ctx, level, ptr(out)))
+
+
+def mgmlmc_get_coarse_op(ctx, level, out):
+    _check(ctx, lib().mgmlmc_get_coarse_op(ctx, level, ptr(out)))
+
+
+def mgmlmc_last_solve_stats(ctx):
+    it = _I()
+    res = _D()
+    _check(ctx, lib().mgmlmc_last_solve_stats(ctx, ctypes.byref(it), ctypes.byref(res)))
+    return it.value, res.value

