@@ -715,3 +715,8 @@ template void Engine::project_out<double>(int, const C<double> *, C<double> *, i
 template void Engine::project_out<float>(int, const C<float> *, C<float> *, int);
 
 }  // namespace mg
+
+namespace mg {
+template C<double> *Engine::ws<double>(const std::string &, int, size_t);
+template C<float> *Engine::ws<float>(const std::string &, int, size_t);
+}  // namespace mg
