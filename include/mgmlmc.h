@@ -234,6 +234,30 @@ mgmlmc_status mgmlmc_get_coarse_op(mgmlmc_ctx *ctx, int level, double *out);
  * relative residual (max over rhs). */
 mgmlmc_status mgmlmc_last_solve_stats(const mgmlmc_ctx *ctx, int *iters, double *residual);
 
+/* ---- measurement --------------------------------------------------------- */
+
+/* Kernel classes timed by mgmlmc_profile. */
+#define MGMLMC_KERNEL_WILSON_FP64 0
+#define MGMLMC_KERNEL_WILSON_FP32 1
+#define MGMLMC_KERNEL_STENCIL_FP64 2
+#define MGMLMC_KERNEL_STENCIL_FP32 3
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * contexts), for counting the launches of a timed region. */
+int64_t mgmlmc_kernel_launches(void);
+/* Enable (1) or disable (0) per-launch timing of the operator kernels with
+ * CUDA events on the context's stream, and reset the counters. */
+mgmlmc_status mgmlmc_profile(mgmlmc_ctx *ctx, int enable);
+/* Counters of one kernel class since the last mgmlmc_profile: launches,
+ * summed device milliseconds, summed algorithmic bytes (unique data: for the
+ * Wilson operator nrhs input and output spinors plus 4 links per site; for a
+ * coarse stencil the 9 blocks plus input and output per site) and summed
+ * algorithmic flops (1368 per site and rhs for Wilson; 72 m^2 per coarse
+ * site and rhs for a stencil with m dofs per site).  Synchronises the
+ * stream. */
+mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *launches,
+                                   double *ms, double *bytes, double *flops);
+
 #ifdef __cplusplus
 }
 #endif

@@ -254,4 +254,21 @@ mgmlmc_status mgmlmc_last_solve_stats(const mgmlmc_ctx *cctx, int *iters, double
   });
 }
 
+int64_t mgmlmc_kernel_launches(void) { return mg::launch_counter().load(); }
+
+mgmlmc_status mgmlmc_profile(mgmlmc_ctx *ctx, int enable) {
+  return guard(ctx, [&] { E(ctx).profile(enable != 0); });
+}
+
+mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *launches,
+                                   double *ms, double *bytes, double *flops) {
+  return guard(ctx, [&] {
+    const mg::KStat k = E(ctx).kstat(kernel_class);
+    if (launches) *launches = k.launches;
+    if (ms) *ms = k.ms;
+    if (bytes) *bytes = k.bytes;
+    if (flops) *flops = k.flops;
+  });
+}
+
 }  // extern "C"

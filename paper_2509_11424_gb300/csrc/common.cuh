@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <stdexcept>
@@ -136,7 +138,14 @@ struct Error : std::runtime_error {
                         std::string(#call) + ": " + cudaGetErrorString(e_));           \
   } while (0)
 
-#define MG_LAUNCH_CHECK() MG_CUDA(cudaGetLastError())
+// process-wide count of kernel launches issued by this library
+std::atomic<int64_t> &launch_counter();
+#define MG_COUNT(k) ::mg::launch_counter().fetch_add((k), std::memory_order_relaxed)
+#define MG_LAUNCH_CHECK()          \
+  do {                             \
+    MG_COUNT(1);                   \
+    MG_CUDA(cudaGetLastError());   \
+  } while (0)
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 

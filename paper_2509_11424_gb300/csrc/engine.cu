@@ -68,21 +68,69 @@ Engine::~Engine() {
   dfree(levels_[0].U64);
   dfree(levels_[0].U32);
   for (auto &kv : ws_) cudaFree(kv.second.first);
+  for (auto &p : pending_) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : events_) cudaEventDestroy(e);
   dfree(scal_);
   dfree(partial_);
   dfree(flag_dev_);
   if (pinned_) cudaFreeHost(pinned_);
 }
 
-void Engine::sync() { MG_CUDA(cudaStreamSynchronize(stream)); }
+void Engine::sync() {
+  MG_CUDA(cudaStreamSynchronize(stream));
+  if (!pending_.empty()) prof_resolve();
+}
 
-void *Engine::pinned(size_t bytes) {
-  if (bytes > pinned_cap_) {
-    if (pinned_) cudaFreeHost(pinned_);
-    pinned_ = nullptr;
-    MG_CUDA(cudaMallocHost(&pinned_, bytes));
-    pinned_cap_ = bytes;
+cudaEvent_t Engine::take_event() {
+  if (events_.empty()) {
+    cudaEvent_t e;
+    MG_CUDA(cudaEventCreate(&e));
+    return e;
   }
+  cudaEvent_t e = events_.back();
+  events_.pop_back();
+  return e;
+}
+
+void Engine::prof_resolve() {
+  for (const Pending &p : pending_) {
+    float ms = 0.f;
+    MG_CUDA(cudaEventElapsedTime(&ms, p.a, p.b));
+    KStat &k = kst_[p.cls];
+    k.launches += 1;
+    k.ms += ms;
+    k.bytes += p.bytes;
+    k.flops += p.flops;
+    events_.push_back(p.a);
+    events_.push_back(p.b);
+  }
+  pending_.clear();
+}
+
+void Engine::profile(bool on) {
+  sync();
+  prof_ = on;
+  for (auto &k : kst_) k = KStat{};
+}
+
+KStat Engine::kstat(int cls) {
+  if (cls < 0 || cls >= K_NCLASS) throw Error(MGMLMC_ERR_ARG, "kernel class out of range");
+  sync();
+  return kst_[cls];
+}
+
+// One pinned staging buffer of fixed size, allocated once: callers may keep
+// the pointer across nested solver calls (it is never reallocated).  Every
+// use copies, synchronises and consumes before the next use.
+void *Engine::pinned(size_t bytes) {
+  if (!pinned_) {
+    MG_CUDA(cudaMallocHost(&pinned_, kPinnedBytes));
+    pinned_cap_ = kPinnedBytes;
+  }
+  if (bytes > pinned_cap_) throw Error(MGMLMC_ERR_ARG, "too many right-hand sides for the staging buffer");
   return pinned_;
 }
 
@@ -182,14 +230,35 @@ void Engine::free_hierarchy() {
 // ------------------------------------------------------------------ operators
 template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int nrhs) {
   const Level &L = levels_.at(l);
+  cudaEvent_t a = nullptr;
+  if (prof_) {
+    a = take_event();
+    MG_CUDA(cudaEventRecord(a, stream));
+  }
+  const double cs = (double)sizeof(C<T>);
+  double bytes, flops;
+  int cls;
   if (L.fine) {
     const C<T> *U;
     if constexpr (sizeof(T) == 8) U = L.U64; else U = L.U32;
     wilson_apply<T>(in, out, U, L.g, m0_, nrhs, stream);
+    // unique data: nrhs spinors in and out, 4 links per site; 1368 flop per site
+    bytes = (double)L.g.V * (24.0 * nrhs + 36.0) * cs;
+    flops = 1368.0 * L.g.V * nrhs;
+    cls = sizeof(T) == 8 ? K_WILSON64 : K_WILSON32;
   } else {
     const C<T> *A;
     if constexpr (sizeof(T) == 8) A = L.A64; else A = L.A32;
     stencil_apply<T>(in, out, A, L.g, nrhs, stream);
+    const double m = L.g.dof;
+    bytes = (double)L.g.V * (9.0 * m * m + 2.0 * m * nrhs) * cs;
+    flops = 8.0 * 9.0 * m * m * L.g.V * nrhs;
+    cls = sizeof(T) == 8 ? K_STENCIL64 : K_STENCIL32;
+  }
+  if (prof_) {
+    cudaEvent_t b = take_event();
+    MG_CUDA(cudaEventRecord(b, stream));
+    pending_.push_back({cls, a, b, bytes, flops});
   }
 }
 
@@ -296,12 +365,13 @@ SolveInfo Engine::fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, in
 
   dot<T>(b, b, n, nrhs, st.nrm, part(1), stream);
   target_kernel<<<(nrhs + 63) / 64, 64, 0, stream>>>(st.target, st.nrm, tol, nrhs);
-  double *bn_host = nullptr;
+  MG_LAUNCH_CHECK();
+  std::vector<double> bn;
+  const double *bn_host = nullptr;
   if (!fixed) {
-    double2 *h = static_cast<double2 *>(pinned(sizeof(double2) * 2 * nrhs + sizeof(int) * nrhs));
+    double2 *h = static_cast<double2 *>(pinned(sizeof(double2) * nrhs));
     MG_CUDA(cudaMemcpyAsync(h, st.nrm, sizeof(double2) * nrhs, cudaMemcpyDeviceToHost, stream));
     sync();
-    static thread_local std::vector<double> bn;
     bn.assign(nrhs, 0.0);
     for (int r = 0; r < nrhs; ++r) bn[r] = std::sqrt(std::max(h[r].x, 0.0));
     bn_host = bn.data();
@@ -412,6 +482,7 @@ SolveInfo Engine::solve_mixed(int l, const double2 *b, double2 *x, int nrhs) {
       break;
     }
     inv_norm_kernel<<<(nrhs + 63) / 64, 64, 0, stream>>>(inv, rn, nr, nrhs);
+    MG_LAUNCH_CHECK();
     convert_scale<float, double>(r, r32, inv, n, nrhs, stream);
     SolveInfo in = fgmres<float>(l, r32, e32, nrhs, sp_.inner_tol, sp_.max_iter - total,
                                  sp_.restart, true, false);
@@ -538,6 +609,7 @@ void Engine::build_hierarchy(const mgmlmc_mg_params &p) {
           fgmres<double>(l, V, X, ntv, 0.0, it, std::min(it, 64), false, true);
           dot<double>(X, X, n, ntv, d, partials((size_t)reduce_blocks(n) * ntv), stream);
           inv_norm_kernel<<<(ntv + 63) / 64, 64, 0, stream>>>(inv, nr, d, ntv);
+          MG_LAUNCH_CHECK();
           scale_rhs<double>(X, V, inv, n, ntv, stream);
         }
       }

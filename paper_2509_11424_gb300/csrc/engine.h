@@ -45,6 +45,16 @@ struct TermAcc {
   std::vector<std::complex<double>> samples;
 };
 
+// Per-kernel-class timing collected with CUDA events on the engine's stream
+// while profiling is enabled (mgmlmc_profile).
+enum KClass { K_WILSON64 = 0, K_WILSON32 = 1, K_STENCIL64 = 2, K_STENCIL32 = 3, K_NCLASS = 8 };
+struct KStat {
+  int64_t launches = 0;
+  double ms = 0.0;
+  double bytes = 0.0;  // algorithmic bytes
+  double flops = 0.0;  // algorithmic flops
+};
+
 class Engine {
  public:
   Engine(const int dims[4], cudaStream_t s);
@@ -83,6 +93,9 @@ class Engine {
   SolveInfo last_solve;
   cudaStream_t stream;
 
+  void profile(bool on);
+  KStat kstat(int cls);
+
  private:
   template <typename T> C<T> *ws(const std::string &name, int l, size_t count);
   void contraction_vectors(int kind, int nb, double2 *x, double2 *B, double2 *Bt);
@@ -113,9 +126,17 @@ class Engine {
   double2 *partial_ = nullptr;  // reduction partials
   size_t partial_cap_ = 0;
   int *flag_dev_ = nullptr;
+  static constexpr size_t kPinnedBytes = 1 << 20;
   void *pinned_ = nullptr;
   size_t pinned_cap_ = 0;
   void *pinned(size_t bytes);
+  bool prof_ = false;
+  struct Pending { int cls; cudaEvent_t a, b; double bytes, flops; };
+  std::vector<Pending> pending_;
+  std::vector<cudaEvent_t> events_;
+  KStat kst_[K_NCLASS];
+  cudaEvent_t take_event();
+  void prof_resolve();
   double2 *partials(size_t count);
 };
 

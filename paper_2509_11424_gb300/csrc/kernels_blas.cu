@@ -275,6 +275,11 @@ __global__ void gmres_solve_kernel(GmresState st) {
 }
 }  // namespace
 
+std::atomic<int64_t> &launch_counter() {
+  static std::atomic<int64_t> c{0};
+  return c;
+}
+
 int reduce_blocks(int64_t n) {
   int64_t b = (n + 4095) / 4096;
   if (b < 1) b = 1;
@@ -289,6 +294,7 @@ void dot(const C<T> *x, const C<T> *y, int64_t n, int nrhs, double2 *out, double
   const int64_t chunk = (n + NB - 1) / NB;
   dot_stage1<T><<<dim3(NB, nrhs, 1), RB, 0, s>>>(x, 0, y, n, chunk, partial);
   dot_stage2<<<nrhs, RB, 0, s>>>(partial, NB, nrhs, out, 1);
+  MG_COUNT(1);
   MG_LAUNCH_CHECK();
 }
 
@@ -299,6 +305,7 @@ void multi_dot(const C<T> *V, int64_t vstride, int k, const C<T> *w, int64_t n, 
   const int64_t chunk = (n + NB - 1) / NB;
   dot_stage1<T><<<dim3(NB, nrhs, k), RB, 0, s>>>(V, vstride, w, n, chunk, partial);
   dot_stage2<<<k * nrhs, RB, 0, s>>>(partial, NB, nrhs, h, ldh);
+  MG_COUNT(1);
   MG_LAUNCH_CHECK();
 }
 

@@ -449,6 +449,7 @@ void dense_invert(double2 *M, double2 *work, int n, int *status, cudaStream_t s)
     gj_elim_kernel<<<grid_for((int64_t)n * 2 * n), 256, 0, s>>>(M, Inv, n, k, f);
   }
   MG_CUDA(cudaMemcpyAsync(M, Inv, sizeof(double2) * n * n, cudaMemcpyDeviceToDevice, s));
+  MG_COUNT(4 * (int64_t)n);
   MG_LAUNCH_CHECK();
 }
 

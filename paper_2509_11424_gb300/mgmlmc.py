@@ -97,6 +97,10 @@ _SIGNATURES = {
     'mgmlmc_get_prolongator': [_P, _I, _P],
     'mgmlmc_get_coarse_op': [_P, _I, _P],
     'mgmlmc_last_solve_stats': [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)],
+    'mgmlmc_profile': [_P, _I],
+    'mgmlmc_kernel_launches': [],
+    'mgmlmc_profile_stats': [_P, _I, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_D),
+                             ctypes.POINTER(_D)],
 }
 
 
@@ -111,7 +115,8 @@ def lib():
             f = getattr(L, name)
             f.argtypes = args
             f.restype = None if name == 'mgmlmc_destroy' else (
-                ctypes.c_char_p if name == 'mgmlmc_last_error' else ctypes.c_int)
+                ctypes.c_char_p if name == 'mgmlmc_last_error' else (
+                    ctypes.c_int64 if name == 'mgmlmc_kernel_launches' else ctypes.c_int))
         _lib = L
     return _lib
 
@@ -281,3 +286,22 @@ def mgmlmc_last_solve_stats(ctx):
     res = _D()
     _check(ctx, lib().mgmlmc_last_solve_stats(ctx, ctypes.byref(it), ctypes.byref(res)))
     return it.value, res.value
+
+
+KERNEL_WILSON_FP64, KERNEL_WILSON_FP32, KERNEL_STENCIL_FP64, KERNEL_STENCIL_FP32 = 0, 1, 2, 3
+
+
+def mgmlmc_profile(ctx, enable):
+    _check(ctx, lib().mgmlmc_profile(ctx, int(bool(enable))))
+
+
+def mgmlmc_profile_stats(ctx, kernel_class):
+    n = _I64()
+    ms, by, fl = _D(), _D(), _D()
+    _check(ctx, lib().mgmlmc_profile_stats(ctx, kernel_class, ctypes.byref(n), ctypes.byref(ms),
+                                           ctypes.byref(by), ctypes.byref(fl)))
+    return {'launches': n.value, 'ms': ms.value, 'bytes': by.value, 'flops': fl.value}
+
+
+def mgmlmc_kernel_launches():
+    return int(lib().mgmlmc_kernel_launches())
