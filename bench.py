@@ -250,7 +250,6 @@ def main():
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    M.mgmlmc_profile(ctx, 1)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     total_ms = 0.0
@@ -264,6 +263,17 @@ def main():
         total_ms += e0.elapsed_time(e1)
     clk = clocks.stop()
     launches = M.mgmlmc_kernel_launches() - n_launch0
+    # profile pass: the first timed step again with CUDA events around every
+    # operator launch (the preconditioner runs eagerly, outside its graph,
+    # while events are on; kernel durations are those of the timed launches)
+    flush.zero_()
+    torch.cuda.synchronize()
+    M.mgmlmc_profile(ctx, 1)
+    e0.record(stream)
+    step(args.warmup)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = e0.elapsed_time(e1)
     kst = {c: M.mgmlmc_profile_stats(ctx, c) for c in range(4)}
     M.mgmlmc_profile(ctx, 0)
     if dist:
@@ -328,7 +338,8 @@ def main():
         roof['kernel'] = names[dom]
         roof['launches'] = ks['launches']
         roof['avg_launch_us'] = ks['ms'] * 1e3 / ks['launches']
-        roof['share_of_step'] = ks['ms'] / total_ms
+        roof['share_of_profiled_step'] = ks['ms'] / prof_ms
+        roof['profiled_step_ms'] = prof_ms
         roof['algorithmic_bytes_per_launch'] = ks['bytes'] / ks['launches']
         roof['algorithmic_flops_per_launch'] = ks['flops'] / ks['launches']
 

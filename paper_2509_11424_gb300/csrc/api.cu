@@ -18,6 +18,13 @@ thread_local std::string g_create_error;
 template <typename F> mgmlmc_status guard(mgmlmc_ctx *ctx, F &&f) {
   if (!ctx) return MGMLMC_ERR_ARG;
   try {
+    ctx->eng->enter();
+    struct Leave {
+      mg::Engine *e;
+      ~Leave() {
+        try { e->leave(); } catch (...) {}
+      }
+    } leave{ctx->eng};
     f();
     return MGMLMC_OK;
   } catch (const mg::Error &e) {

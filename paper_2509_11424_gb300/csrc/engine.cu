@@ -37,7 +37,10 @@ __global__ void inv_norm_kernel(double *out, double *nrm_out, const double2 *nrm
 }
 }  // namespace
 
-Engine::Engine(const int dims[4], cudaStream_t s) : stream(s) {
+Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
+  MG_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+  MG_CUDA(cudaEventCreateWithFlags(&ev_enter_, cudaEventDisableTiming));
+  MG_CUDA(cudaEventCreateWithFlags(&ev_leave_, cudaEventDisableTiming));
   for (int i = 0; i < 4; ++i) {
     if (dims[i] < 2) throw Error(MGMLMC_ERR_ARG, "lattice extents must be >= 2");
     dims_[i] = dims[i];
@@ -64,6 +67,7 @@ Engine::Engine(const int dims[4], cudaStream_t s) : stream(s) {
 }
 
 Engine::~Engine() {
+  cudaStreamSynchronize(stream);
   free_hierarchy();
   dfree(levels_[0].U64);
   dfree(levels_[0].U32);
@@ -77,6 +81,26 @@ Engine::~Engine() {
   dfree(partial_);
   dfree(flag_dev_);
   if (pinned_) cudaFreeHost(pinned_);
+  if (ev_enter_) cudaEventDestroy(ev_enter_);
+  if (ev_leave_) cudaEventDestroy(ev_leave_);
+  if (stream) cudaStreamDestroy(stream);
+}
+
+void Engine::enter() {
+  MG_CUDA(cudaEventRecord(ev_enter_, user_stream));
+  MG_CUDA(cudaStreamWaitEvent(stream, ev_enter_, 0));
+}
+
+void Engine::leave() {
+  MG_CUDA(cudaEventRecord(ev_leave_, stream));
+  MG_CUDA(cudaStreamWaitEvent(user_stream, ev_leave_, 0));
+}
+
+void Engine::drop_graphs() {
+  if (graphs_.empty()) return;
+  cudaStreamSynchronize(stream);
+  for (auto &kv : graphs_) cudaGraphExecDestroy(kv.second.exec);
+  graphs_.clear();
 }
 
 void Engine::sync() {
@@ -136,6 +160,8 @@ void *Engine::pinned(size_t bytes) {
 
 double2 *Engine::partials(size_t count) {
   if (count > partial_cap_) {
+    if (capturing_) throw Error(MGMLMC_ERR_STATE, "reduction scratch growth during graph capture");
+    drop_graphs();
     sync();
     dfree(partial_);
     partial_ = dalloc<double2>(count);
@@ -150,6 +176,8 @@ template <typename T> C<T> *Engine::ws(const std::string &name, int l, size_t co
   auto it = ws_.find(key);
   if (it != ws_.end() && it->second.second >= bytes) return static_cast<C<T> *>(it->second.first);
   if (it != ws_.end()) {
+    if (capturing_) throw Error(MGMLMC_ERR_STATE, "workspace growth during graph capture");
+    drop_graphs();  // captured graphs may reference the old buffer
     sync();
     cudaFree(it->second.first);
     ws_.erase(it);
@@ -196,6 +224,7 @@ void Engine::set_solver(const mgmlmc_solver_params &p) {
       (p.precision != MGMLMC_FP64 && p.precision != MGMLMC_FP32) ||
       (p.precision == MGMLMC_FP32 && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)))
     throw Error(MGMLMC_ERR_ARG, "invalid solver parameters");
+  drop_graphs();  // captured preconditioners bake in smoother / inner iteration counts
   sp_ = p;
 }
 
@@ -211,6 +240,7 @@ void Engine::set_test_vectors(int level, const double *V, int ntv, int64_t n, bo
 }
 
 void Engine::free_hierarchy() {
+  drop_graphs();
   for (size_t l = 0; l < levels_.size(); ++l) {
     Level &L = levels_[l];
     dfree(L.P64);
@@ -219,7 +249,8 @@ void Engine::free_hierarchy() {
     dfree(L.Dinv32);
     if (l > 0) {
       dfree(L.A64);
-      dfree(L.A32);
+      dfree(L.AT64);
+      dfree(L.AT32);
     }
     L.has_next = false;
   }
@@ -231,7 +262,8 @@ void Engine::free_hierarchy() {
 template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int nrhs) {
   const Level &L = levels_.at(l);
   cudaEvent_t a = nullptr;
-  if (prof_) {
+  const bool prof = prof_ && !capturing_;
+  if (prof) {
     a = take_event();
     MG_CUDA(cudaEventRecord(a, stream));
   }
@@ -248,14 +280,14 @@ template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int
     cls = sizeof(T) == 8 ? K_WILSON64 : K_WILSON32;
   } else {
     const C<T> *A;
-    if constexpr (sizeof(T) == 8) A = L.A64; else A = L.A32;
+    if constexpr (sizeof(T) == 8) A = L.AT64; else A = L.AT32;
     stencil_apply<T>(in, out, A, L.g, nrhs, stream);
     const double m = L.g.dof;
     bytes = (double)L.g.V * (9.0 * m * m + 2.0 * m * nrhs) * cs;
     flops = 8.0 * 9.0 * m * m * L.g.V * nrhs;
     cls = sizeof(T) == 8 ? K_STENCIL64 : K_STENCIL32;
   }
-  if (prof_) {
+  if (prof) {
     cudaEvent_t b = take_event();
     MG_CUDA(cudaEventRecord(b, stream));
     pending_.push_back({cls, a, b, bytes, flops});
@@ -292,8 +324,7 @@ template <typename T> void Engine::smooth(int l, C<T> *z, C<T> *res, int nrhs) {
   double2 *d = ws<double>("smd", l, 2 * (size_t)nrhs);
   for (int s = 0; s < sp_.smoother_steps; ++s) {
     apply_D<T>(l, res, q, nrhs);
-    dot<T>(q, res, n, nrhs, d, partials((size_t)reduce_blocks(n) * nrhs), stream);
-    dot<T>(q, q, n, nrhs, d + nrhs, partials((size_t)reduce_blocks(n) * nrhs), stream);
+    dot_qr<T>(q, res, n, nrhs, d, d + nrhs, partials((size_t)reduce_blocks(n) * nrhs * 2), stream);
     mr_update<T>(z, res, q, d, d + nrhs, n, nrhs, stream);
   }
 }
@@ -328,6 +359,50 @@ template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nr
     axpby<T>(-1.0, q, 1.0, res, n, nrhs, stream);
     smooth<T>(l, z, res, nrhs);
   }
+}
+
+template <typename T> void Engine::precond_top(int l, const C<T> *r, C<T> *z, int nrhs) {
+  if (!graphs_on_ || prof_ || l == n_levels() - 1) {
+    precond<T>(l, r, z, nrhs);
+    return;
+  }
+  const int64_t n = levels_[l].g.n();
+  const size_t bytes = sizeof(C<T>) * n * nrhs;
+  const auto key = std::make_tuple(l, nrhs, (int)sizeof(T));
+  auto it = graphs_.find(key);
+  if (it == graphs_.end()) {
+    C<T> *in = ws<T>("gin", l, (size_t)n * nrhs);
+    C<T> *out = ws<T>("gout", l, (size_t)n * nrhs);
+    // eager run: sizes every workspace the captured sequence touches
+    MG_CUDA(cudaMemcpyAsync(in, r, bytes, cudaMemcpyDeviceToDevice, stream));
+    precond<T>(l, in, out, nrhs);
+    MG_CUDA(cudaMemcpyAsync(z, out, bytes, cudaMemcpyDeviceToDevice, stream));
+    sync();
+    cudaGraph_t graph = nullptr;
+    MG_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+    capturing_ = true;
+    const int64_t launches_before = launch_counter().load();
+    try {
+      precond<T>(l, in, out, nrhs);
+    } catch (...) {
+      capturing_ = false;
+      cudaStreamEndCapture(stream, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      throw;
+    }
+    capturing_ = false;
+    MG_CUDA(cudaStreamEndCapture(stream, &graph));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    MG_CUDA(e);
+    graphs_[key] = GraphEntry{exec, in, out, launch_counter().load() - launches_before};
+    return;  // z already holds the eager result
+  }
+  MG_CUDA(cudaMemcpyAsync(it->second.in, r, bytes, cudaMemcpyDeviceToDevice, stream));
+  MG_CUDA(cudaGraphLaunch(it->second.exec, stream));
+  MG_COUNT(it->second.kernels);  // the kernels replayed by the graph
+  MG_CUDA(cudaMemcpyAsync(z, it->second.out, bytes, cudaMemcpyDeviceToDevice, stream));
 }
 
 // ------------------------------------------------------------------ FGMRES
@@ -389,7 +464,10 @@ SolveInfo Engine::fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, in
     for (int i = 0; i < m; ++i) {
       C<T> *vi = V + i * vs;
       C<T> *zi = use_precond ? Z + i * vs : vi;
-      if (use_precond) precond<T>(l, vi, zi, nrhs);
+      if (use_precond) {
+        if (fixed) precond<T>(l, vi, zi, nrhs);
+        else precond_top<T>(l, vi, zi, nrhs);
+      }
       apply_D<T>(l, zi, w, nrhs);
       multi_dot<T>(V, vs, i + 1, w, n, nrhs, st.h1, m + 1, part(i + 1), stream);
       multi_axpy<T>(V, vs, i + 1, w, n, nrhs, st.h1, m + 1, -1.0, stream);
@@ -530,7 +608,8 @@ void Engine::galerkin(int l) {
   double2 *cols = ws<double>("galc", l, (size_t)9 * nc);
   const size_t acnt = (size_t)c.g.V * 9 * dofc * dofc;
   c.A64 = dalloc<double2>(acnt);
-  c.A32 = dalloc<float2>(acnt);
+  c.AT64 = dalloc<double2>(acnt);
+  c.AT32 = dalloc<float2>(acnt);
   for (int col = 0; col < dofc; ++col) {
     probe_column(probe, f.P64, m, col, stream);
     if (f.fine) wilson_split<double>(probe, out9, f.U64, f.g, m0_, m.b, stream);
@@ -538,7 +617,8 @@ void Engine::galerkin(int l) {
     restrict_op<double>(out9, cols, f.P64, m, 9, stream);
     galerkin_scatter(cols, c.A64, c.g, col, stream);
   }
-  convert<float, double>(c.A64, c.A32, (int64_t)acnt, stream);
+  stencil_transpose<double>(c.A64, c.AT64, (int64_t)c.g.V * 9, dofc, stream);
+  stencil_transpose<float>(c.A64, c.AT32, (int64_t)c.g.V * 9, dofc, stream);
 }
 
 void Engine::build_hierarchy(const mgmlmc_mg_params &p) {

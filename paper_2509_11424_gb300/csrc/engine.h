@@ -5,6 +5,7 @@
 
 #include <complex>
 #include <map>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -18,8 +19,9 @@ struct Level {
   bool fine = false;
   double2 *U64 = nullptr;  // fine links [V][4][3][3]
   float2 *U32 = nullptr;
-  double2 *A64 = nullptr;  // coarse stencil [V][9][dof][dof]
-  float2 *A32 = nullptr;
+  double2 *A64 = nullptr;   // coarse stencil, canonical [V][9][dof][dof]
+  double2 *AT64 = nullptr;  // the same blocks transposed [V][9][j][i] (apply)
+  float2 *AT32 = nullptr;
   bool has_next = false;
   AggMap agg{};            // to level + 1
   double2 *P64 = nullptr;  // [X][c][k][row]
@@ -91,7 +93,13 @@ class Engine {
   void get_coarse_op(int l, double *host);
 
   SolveInfo last_solve;
-  cudaStream_t stream;
+  cudaStream_t stream = nullptr;       // internal non-blocking stream: all work runs here
+  cudaStream_t user_stream = nullptr;  // the caller's stream given at creation
+  // order the internal stream after the caller's earlier work / the caller's
+  // stream after ours (every API call is bracketed by these)
+  void enter();
+  void leave();
+  void set_graphs(bool on) { graphs_on_ = on; if (!on) drop_graphs(); }
 
   void profile(bool on);
   KStat kstat(int cls);
@@ -104,6 +112,9 @@ class Engine {
 
   template <typename T> void smooth(int l, C<T> *z, C<T> *res, int nrhs);
   template <typename T> void precond(int l, const C<T> *r, C<T> *z, int nrhs);
+  // the preconditioner of an outer solve: replayed from a CUDA graph captured
+  // once per (level, nrhs, precision) unless profiling or graphs are off
+  template <typename T> void precond_top(int l, const C<T> *r, C<T> *z, int nrhs);
   // batched FGMRES; fixed = run exactly max_iter iterations with no host check
   template <typename T>
   SolveInfo fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, int max_iter, int m,
@@ -138,6 +149,17 @@ class Engine {
   cudaEvent_t take_event();
   void prof_resolve();
   double2 *partials(size_t count);
+  bool graphs_on_ = true;
+  bool capturing_ = false;
+  struct GraphEntry {
+    cudaGraphExec_t exec;
+    void *in;
+    void *out;
+    int64_t kernels;  // kernel nodes in the graph
+  };
+  std::map<std::tuple<int, int, int>, GraphEntry> graphs_;
+  void drop_graphs();
+  cudaEvent_t ev_enter_ = nullptr, ev_leave_ = nullptr;
 };
 
 }  // namespace mg

@@ -81,8 +81,16 @@ void wilson_apply(const C<T> *in, C<T> *out, const C<T> *U, Geom g, double m0, i
 template <typename T>
 void wilson_split(const C<T> *in, C<T> *out9, const C<T> *U, Geom g, double m0, const int b[4],
                   cudaStream_t s);
+// coarse stencil with transposed blocks AT[X][d][j][i]
 template <typename T>
-void stencil_apply(const C<T> *in, C<T> *out, const C<T> *A, Geom g, int nrhs, cudaStream_t s);
+void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, cudaStream_t s);
+// AT = blockwise transpose of the canonical A[X][d][i][j] (nblocks = 9 V)
+template <typename To>
+void stencil_transpose(const double2 *A, C<To> *AT, int64_t nblocks, int m, cudaStream_t s);
+// (<q, r>, <q, q>) for every rhs in one pass: out_qr[r], out_qq[r]
+template <typename T>
+void dot_qr(const C<T> *q, const C<T> *r, int64_t n, int nrhs, double2 *out_qr, double2 *out_qq,
+            double2 *partial, cudaStream_t s);
 template <typename T>
 void stencil_split(const C<T> *in, C<T> *out9, const C<T> *A, Geom g, const int b[4],
                    cudaStream_t s);

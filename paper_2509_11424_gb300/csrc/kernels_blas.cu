@@ -45,14 +45,16 @@ __global__ void dot_stage1(const C<T> *__restrict__ x, int64_t xstride, const C<
   const C<T> *yr = y + r * n;
   const int64_t beg = (int64_t)b * chunk;
   const int64_t end = beg + chunk < n ? beg + chunk : n;
-  double2 acc = make_double2(0.0, 0.0);
+  // per-thread partial in the storage precision over the few elements a
+  // thread visits (reduce_blocks keeps that short; FP32 FMAs run ~58x faster
+  // than FP64 ones on this part), then FP64 across threads and blocks
+  C<T> acc = mk<T>((T)0, (T)0);
   for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
-    C<T> a = xr[i], c = yr[i];
-    acc.x += (double)a.x * c.x + (double)a.y * c.y;
-    acc.y += (double)a.x * c.y - (double)a.y * c.x;
+    const C<T> a = xr[i], c = yr[i];
+    acc = cfmac(a, c, acc);
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) partial[((int64_t)j * gridDim.y + r) * gridDim.x + b] = acc;
+  double2 tot = block_sum(make_double2((double)acc.x, (double)acc.y));
+  if (threadIdx.x == 0) partial[((int64_t)j * gridDim.y + r) * gridDim.x + b] = tot;
 }
 
 // out[r * ldh + j] = sum_b partial[(j * nrhs + r) * NB + b]
@@ -68,6 +70,43 @@ __global__ void dot_stage2(const double2 *__restrict__ partial, int NB, int nrhs
   }
   acc = block_sum(acc);
   if (threadIdx.x == 0) out[r * ldh + j] = acc;
+}
+
+// partial[(r * 2 + o) * NB + b]: o = 0 <q, r>, o = 1 <q, q> over block b's chunk
+template <typename T>
+__global__ void dot_qr_stage1(const C<T> *__restrict__ q, const C<T> *__restrict__ rr, int64_t n,
+                              int64_t chunk, double2 *__restrict__ partial) {
+  const int b = blockIdx.x, r = blockIdx.y;
+  const C<T> *qr = q + r * n;
+  const C<T> *xr = rr + r * n;
+  const int64_t beg = (int64_t)b * chunk;
+  const int64_t end = beg + chunk < n ? beg + chunk : n;
+  C<T> ta = mk<T>((T)0, (T)0);
+  T tc = (T)0;
+  for (int64_t i = beg + threadIdx.x; i < end; i += blockDim.x) {
+    const C<T> u = qr[i], v = xr[i];
+    ta = cfmac(u, v, ta);
+    tc = fma(u.x, u.x, fma(u.y, u.y, tc));
+  }
+  const double2 a = block_sum(make_double2((double)ta.x, (double)ta.y));
+  const double2 c = block_sum(make_double2((double)tc, 0.0));
+  if (threadIdx.x == 0) {
+    partial[((int64_t)r * 2 + 0) * gridDim.x + b] = a;
+    partial[((int64_t)r * 2 + 1) * gridDim.x + b] = c;
+  }
+}
+
+__global__ void dot_qr_stage2(const double2 *__restrict__ partial, int NB, double2 *__restrict__ oqr,
+                              double2 *__restrict__ oqq) {
+  const int idx = blockIdx.x;  // r * 2 + o
+  double2 acc = make_double2(0.0, 0.0);
+  for (int b = threadIdx.x; b < NB; b += blockDim.x) {
+    const double2 p = partial[(int64_t)idx * NB + b];
+    acc.x += p.x;
+    acc.y += p.y;
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) (idx & 1 ? oqq : oqr)[idx >> 1] = acc;
 }
 
 template <typename T>
@@ -280,10 +319,13 @@ std::atomic<int64_t> &launch_counter() {
   return c;
 }
 
+// blocks of the first reduction stage: chunks of >= 4096 elements, at most
+// 4096 blocks, so a thread of a 256-wide block sums at most ~16 elements for
+// vectors up to 16.7 M entries (and proportionally more beyond)
 int reduce_blocks(int64_t n) {
   int64_t b = (n + 4095) / 4096;
   if (b < 1) b = 1;
-  if (b > 512) b = 512;
+  if (b > 4096) b = 4096;
   return (int)b;
 }
 
@@ -294,6 +336,17 @@ void dot(const C<T> *x, const C<T> *y, int64_t n, int nrhs, double2 *out, double
   const int64_t chunk = (n + NB - 1) / NB;
   dot_stage1<T><<<dim3(NB, nrhs, 1), RB, 0, s>>>(x, 0, y, n, chunk, partial);
   dot_stage2<<<nrhs, RB, 0, s>>>(partial, NB, nrhs, out, 1);
+  MG_COUNT(1);
+  MG_LAUNCH_CHECK();
+}
+
+template <typename T>
+void dot_qr(const C<T> *q, const C<T> *r, int64_t n, int nrhs, double2 *out_qr, double2 *out_qq,
+            double2 *partial, cudaStream_t s) {
+  const int NB = reduce_blocks(n);
+  const int64_t chunk = (n + NB - 1) / NB;
+  dot_qr_stage1<T><<<dim3(NB, nrhs), RB, 0, s>>>(q, r, n, chunk, partial);
+  dot_qr_stage2<<<2 * nrhs, RB, 0, s>>>(partial, NB, out_qr, out_qq);
   MG_COUNT(1);
   MG_LAUNCH_CHECK();
 }
@@ -390,7 +443,9 @@ void gmres_solve(GmresState st, cudaStream_t s) {
   template void scale_rhs<T>(const C<T> *, C<T> *, const double *, int64_t, int, cudaStream_t);  \
   template void mr_update<T>(C<T> *, C<T> *, const C<T> *, const double2 *, const double2 *,     \
                              int64_t, int, cudaStream_t);                                        \
-  template void check_finite<T>(const C<T> *, int64_t, int *, cudaStream_t);
+  template void check_finite<T>(const C<T> *, int64_t, int *, cudaStream_t);               \
+  template void dot_qr<T>(const C<T> *, const C<T> *, int64_t, int, double2 *, double2 *,        \
+                          double2 *, cudaStream_t);
 INST(double)
 INST(float)
 template void convert<float, double>(const C<double> *, C<float> *, int64_t, cudaStream_t);

@@ -22,55 +22,67 @@ template <typename V> __device__ __forceinline__ V warp_csum(V v) {
   return v;
 }
 
-constexpr int RG = 4;  // right-hand sides per pass of the stencil kernel
-
-// y(X) = sum_d A[X][d] x(nbr(X, d)).  One block per coarse site; warp w
-// handles rows i = w, w + 8, ...; lanes stride over columns j; each A row
-// segment is loaded once and used for RG right-hand sides.
-template <typename T>
-__global__ void __launch_bounds__(256) stencil_kernel(const C<T> *__restrict__ in,
-                                                      C<T> *__restrict__ out,
-                                                      const C<T> *__restrict__ A, Geom g,
-                                                      int nrhs) {
+// y(X) = sum_d A[X][d] x(nbr(X, d)) with the blocks stored transposed,
+// AT[X][d][j][i], so that the m threads of one direction read a block column
+// with one coalesced access.  Block = (m, 9) threads: thread (i, d) forms row
+// i of direction d for RG right-hand sides at a time from the neighbour
+// vectors staged in shared memory; the 9 partial rows are then summed in
+// shared memory by the d = 0 threads.  Each block entry is read once per RG
+// right-hand sides.
+template <typename T, int RG>
+__global__ void stencil_t_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ out,
+                                 const C<T> *__restrict__ AT, Geom g, int nrhs) {
   extern __shared__ unsigned char smem_raw[];
-  C<T> *xs = reinterpret_cast<C<T> *>(smem_raw);  // [RG][9][m]
-  const int X = blockIdx.x;
   const int m = g.dof;
+  C<T> *xs = reinterpret_cast<C<T> *>(smem_raw);  // [9][RG][m]
+  C<T> *part = xs + 9 * RG * m;                   // [9][RG][m]
+  const int X = blockIdx.x;
+  const int i = threadIdx.x, d = threadIdx.y;
   const int64_t n = g.n();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int nb[9];
-#pragma unroll
-  for (int d = 0; d < 9; ++d) nb[d] = g.neighbor(X, d);
-  const C<T> *AX = A + (int64_t)X * 9 * m * m;
+  const int nb = g.neighbor(X, d);
+  const C<T> *Ad = AT + ((int64_t)X * 9 + d) * m * m;
   for (int r0 = 0; r0 < nrhs; r0 += RG) {
     const int rg = nrhs - r0 < RG ? nrhs - r0 : RG;
+#pragma unroll
+    for (int r = 0; r < RG; ++r)
+      if (r < rg) xs[(d * RG + r) * m + i] = in[(int64_t)(r0 + r) * n + (int64_t)nb * m + i];
     __syncthreads();
-    for (int e = threadIdx.x; e < rg * 9 * m; e += blockDim.x) {
-      const int r = e / (9 * m), rem = e - r * 9 * m, d = rem / m, j = rem - d * m;
-      xs[e] = in[(r0 + r) * n + (int64_t)nb[d] * m + j];
+    C<T> acc[RG];
+#pragma unroll
+    for (int r = 0; r < RG; ++r) acc[r] = mk<T>((T)0, (T)0);
+    const C<T> *xd = xs + d * RG * m;
+#pragma unroll 4
+    for (int j = 0; j < m; ++j) {
+      const C<T> a = __ldg(Ad + (int64_t)j * m + i);
+#pragma unroll
+      for (int r = 0; r < RG; ++r) acc[r] = cfma(a, xd[r * m + j], acc[r]);
     }
+#pragma unroll
+    for (int r = 0; r < RG; ++r) part[(d * RG + r) * m + i] = acc[r];
     __syncthreads();
-    for (int i = warp; i < m; i += (blockDim.x >> 5)) {
-      C<T> acc[RG];
+    if (d == 0) {
+      for (int r = 0; r < rg; ++r) {
+        C<T> v = part[r * m + i];
 #pragma unroll
-      for (int r = 0; r < RG; ++r) acc[r] = mk<T>((T)0, (T)0);
-      for (int d = 0; d < 9; ++d) {
-        const C<T> *Ar = AX + ((int64_t)d * m + i) * m;
-        for (int j = lane; j < m; j += 32) {
-          const C<T> a = Ar[j];
-#pragma unroll
-          for (int r = 0; r < RG; ++r)
-            if (r < rg) acc[r] = cfma(a, xs[(r * 9 + d) * m + j], acc[r]);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < RG; ++r) {
-        if (r < rg) {
-          C<T> v = warp_csum(acc[r]);
-          if (lane == 0) out[(r0 + r) * n + (int64_t)X * m + i] = v;
-        }
+        for (int dd = 1; dd < 9; ++dd) v = cadd(v, part[(dd * RG + r) * m + i]);
+        out[(int64_t)(r0 + r) * n + (int64_t)X * m + i] = v;
       }
     }
+    __syncthreads();
+  }
+}
+
+// AT[X][d][j][i] = A[X][d][i][j], converted to the storage type To.
+template <typename To>
+__global__ void stencil_transpose_kernel(const double2 *__restrict__ A, C<To> *__restrict__ AT,
+                                         int64_t nblocks, int m) {
+  const int64_t total = nblocks * m * m;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t blk = e / ((int64_t)m * m);
+    const int rem = (int)(e - blk * m * m);
+    const int j = rem / m, i = rem - j * m;  // e indexes AT[blk][j][i]
+    AT[e] = cvt<To>(A[blk * m * m + (int64_t)i * m + j]);
   }
 }
 
@@ -120,32 +132,50 @@ __global__ void stencil_split_kernel(const C<T> *__restrict__ in, C<T> *__restri
 
 // ------------------------------------------------------------------ transfer
 // out[r][X][c*ntv + k] = sum_row conj(P[X][c][k][row]) in_r[fine(X, c, row)]
-template <typename T>
+// One block per (aggregate, chirality); RG right-hand sides are staged in
+// shared memory per pass so each P entry is read once per RG of them.
+template <typename T, int RG>
 __global__ void restrict_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ out,
                                 const C<T> *__restrict__ P, AggMap m, int nrhs) {
   extern __shared__ unsigned char smem_raw[];
-  C<T> *xs = reinterpret_cast<C<T> *>(smem_raw);  // [rows]
+  C<T> *xs = reinterpret_cast<C<T> *>(smem_raw);  // [RG][rows]
   const int X = blockIdx.x >> 1, c = blockIdx.x & 1;
   const int64_t nf = m.fine.n(), nc = m.coarse.n();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const C<T> *PX = P + ((int64_t)(X * 2 + c) * m.ntv) * m.rows;
-  for (int r = 0; r < nrhs; ++r) {
+  for (int r0 = 0; r0 < nrhs; r0 += RG) {
+    const int rg = nrhs - r0 < RG ? nrhs - r0 : RG;
     __syncthreads();
-    for (int row = threadIdx.x; row < m.rows; row += blockDim.x)
-      xs[row] = in[r * nf + m.fine_index(X, c, row)];
+    for (int row = threadIdx.x; row < m.rows; row += blockDim.x) {
+      const int64_t fi = m.fine_index(X, c, row);
+#pragma unroll
+      for (int r = 0; r < RG; ++r)
+        if (r < rg) xs[r * m.rows + row] = in[(int64_t)(r0 + r) * nf + fi];
+    }
     __syncthreads();
     for (int k = warp; k < m.ntv; k += nw) {
       const C<T> *Pk = PX + (int64_t)k * m.rows;
-      C<T> acc = mk<T>((T)0, (T)0);
-      for (int row = lane; row < m.rows; row += 32) acc = cfmac(Pk[row], xs[row], acc);
-      acc = warp_csum(acc);
-      if (lane == 0) out[r * nc + (int64_t)X * m.coarse.dof + c * m.ntv + k] = acc;
+      C<T> acc[RG];
+#pragma unroll
+      for (int r = 0; r < RG; ++r) acc[r] = mk<T>((T)0, (T)0);
+      for (int row = lane; row < m.rows; row += 32) {
+        const C<T> a = __ldg(Pk + row);
+#pragma unroll
+        for (int r = 0; r < RG; ++r) acc[r] = cfmac(a, xs[r * m.rows + row], acc[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < RG; ++r) {
+        const C<T> v = warp_csum(acc[r]);
+        if (lane == 0 && r < rg) out[(int64_t)(r0 + r) * nc + (int64_t)X * m.coarse.dof + c * m.ntv + k] = v;
+      }
     }
   }
 }
 
 // out_r[fine(X, c, row)] = beta out + sum_k P[X][c][k][row] in_r[X][c*ntv + k]
-template <typename T>
+// One block per (aggregate, chirality); each thread owns rows and applies the
+// column segment of P to RG right-hand sides at a time.
+template <typename T, int RG>
 __global__ void prolong_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ out,
                                const C<T> *__restrict__ P, AggMap m, int nrhs, T beta) {
   extern __shared__ unsigned char smem_raw[];
@@ -154,16 +184,30 @@ __global__ void prolong_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ o
   const int64_t nf = m.fine.n(), nc = m.coarse.n();
   for (int e = threadIdx.x; e < nrhs * m.ntv; e += blockDim.x) {
     const int r = e / m.ntv, k = e - r * m.ntv;
-    cs[e] = in[r * nc + (int64_t)X * m.coarse.dof + c * m.ntv + k];
+    cs[e] = in[(int64_t)r * nc + (int64_t)X * m.coarse.dof + c * m.ntv + k];
   }
   __syncthreads();
   const C<T> *PX = P + ((int64_t)(X * 2 + c) * m.ntv) * m.rows;
   for (int row = threadIdx.x; row < m.rows; row += blockDim.x) {
     const int64_t fi = m.fine_index(X, c, row);
-    for (int r = 0; r < nrhs; ++r) {
-      C<T> acc = beta == (T)0 ? mk<T>((T)0, (T)0) : cscale(out[r * nf + fi], beta);
-      for (int k = 0; k < m.ntv; ++k) acc = cfma(PX[(int64_t)k * m.rows + row], cs[r * m.ntv + k], acc);
-      out[r * nf + fi] = acc;
+    for (int r0 = 0; r0 < nrhs; r0 += RG) {
+      const int rg = nrhs - r0 < RG ? nrhs - r0 : RG;
+      C<T> acc[RG];
+#pragma unroll
+      for (int r = 0; r < RG; ++r) acc[r] = mk<T>((T)0, (T)0);
+      for (int k = 0; k < m.ntv; ++k) {
+        const C<T> a = __ldg(PX + (int64_t)k * m.rows + row);
+#pragma unroll
+        for (int r = 0; r < RG; ++r)
+          if (r < rg) acc[r] = cfma(a, cs[(r0 + r) * m.ntv + k], acc[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < RG; ++r) {
+        if (r < rg) {
+          C<T> *o = out + (int64_t)(r0 + r) * nf + fi;
+          *o = beta == (T)0 ? acc[r] : cadd(cscale(*o, beta), acc[r]);
+        }
+      }
     }
   }
 }
@@ -354,18 +398,30 @@ __global__ void eye_kernel(double2 *__restrict__ M, int n) {
   }
 }
 
-// out_r = Minv in_r: warp per row, lanes over columns.
-template <typename T>
+// out_r = Minv in_r: warp per row, lanes over columns, RG right-hand sides
+// per pass so each matrix entry is loaded once per RG of them.
+template <typename T, int RG>
 __global__ void dense_apply_kernel(const C<T> *__restrict__ Minv, const C<T> *__restrict__ in,
                                    C<T> *__restrict__ out, int n, int nrhs) {
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= n) return;
   const C<T> *row = Minv + (int64_t)warp * n;
-  for (int r = 0; r < nrhs; ++r) {
-    C<T> acc = mk<T>((T)0, (T)0);
-    for (int j = lane; j < n; j += 32) acc = cfma(row[j], in[(int64_t)r * n + j], acc);
-    acc = warp_csum(acc);
-    if (lane == 0) out[(int64_t)r * n + warp] = acc;
+  for (int r0 = 0; r0 < nrhs; r0 += RG) {
+    const int rg = nrhs - r0 < RG ? nrhs - r0 : RG;
+    C<T> acc[RG];
+#pragma unroll
+    for (int r = 0; r < RG; ++r) acc[r] = mk<T>((T)0, (T)0);
+    for (int j = lane; j < n; j += 32) {
+      const C<T> a = __ldg(row + j);
+#pragma unroll
+      for (int r = 0; r < RG; ++r)
+        if (r < rg) acc[r] = cfma(a, in[(int64_t)(r0 + r) * n + j], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < RG; ++r) {
+      const C<T> v = warp_csum(acc[r]);
+      if (lane == 0 && r < rg) out[(int64_t)(r0 + r) * n + warp] = v;
+    }
   }
 }
 
@@ -380,11 +436,28 @@ __global__ void dense_trace_kernel(const double2 *__restrict__ M, int n, double2
 }  // namespace
 
 template <typename T>
-void stencil_apply(const C<T> *in, C<T> *out, const C<T> *A, Geom g, int nrhs, cudaStream_t s) {
-  const size_t sm = (size_t)RG * 9 * g.dof * sizeof(C<T>);
-  stencil_kernel<T><<<g.V, 256, sm, s>>>(in, out, A, g, nrhs);
+void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, cudaStream_t s) {
+  constexpr int RG = sizeof(T) == 4 ? 8 : 4;
+  const int m = g.dof;
+  if (m > 112) throw Error(1, "coarse stencil: more than 112 dofs per site");
+  const size_t sm = (size_t)2 * 9 * RG * m * sizeof(C<T>);
+  static bool configured = false;
+  if (!configured) {
+    MG_CUDA(cudaFuncSetAttribute(stencil_t_kernel<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+    configured = true;
+  }
+  stencil_t_kernel<T, RG><<<g.V, dim3(m, 9), sm, s>>>(in, out, AT, g, nrhs);
   MG_LAUNCH_CHECK();
 }
+
+template <typename To>
+void stencil_transpose(const double2 *A, C<To> *AT, int64_t nblocks, int m, cudaStream_t s) {
+  stencil_transpose_kernel<To><<<grid_for(nblocks * m * m), 256, 0, s>>>(A, AT, nblocks, m);
+  MG_LAUNCH_CHECK();
+}
+template void stencil_transpose<double>(const double2 *, C<double> *, int64_t, int, cudaStream_t);
+template void stencil_transpose<float>(const double2 *, C<float> *, int64_t, int, cudaStream_t);
 
 template <typename T>
 void stencil_split(const C<T> *in, C<T> *out9, const C<T> *A, Geom g, const int b[4],
@@ -396,9 +469,16 @@ void stencil_split(const C<T> *in, C<T> *out9, const C<T> *A, Geom g, const int 
 template <typename T>
 void restrict_op(const C<T> *in, C<T> *out, const C<T> *P, const AggMap &m, int nrhs,
                  cudaStream_t s) {
-  const size_t sm = (size_t)m.rows * sizeof(C<T>);
-  if (sm > 48 * 1024) throw Error(1, "restrict: aggregate too large for shared memory");
-  restrict_kernel<T><<<m.coarse.V * 2, 256, sm, s>>>(in, out, P, m, nrhs);
+  constexpr int RG = 4;
+  const size_t sm = (size_t)RG * m.rows * sizeof(C<T>);
+  if (sm > 200 * 1024) throw Error(1, "restrict: aggregate too large for shared memory");
+  static bool configured = false;
+  if (!configured) {
+    MG_CUDA(cudaFuncSetAttribute(restrict_kernel<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+    configured = true;
+  }
+  restrict_kernel<T, RG><<<m.coarse.V * 2, 256, sm, s>>>(in, out, P, m, nrhs);
   MG_LAUNCH_CHECK();
 }
 
@@ -407,7 +487,7 @@ void prolong_op(const C<T> *in, C<T> *out, const C<T> *P, const AggMap &m, int n
                 cudaStream_t s) {
   const size_t sm = (size_t)nrhs * m.ntv * sizeof(C<T>);
   if (sm > 48 * 1024) throw Error(1, "prolong: too many right-hand sides");
-  prolong_kernel<T><<<m.coarse.V * 2, 256, sm, s>>>(in, out, P, m, nrhs, (T)beta);
+  prolong_kernel<T, 4><<<m.coarse.V * 2, 256, sm, s>>>(in, out, P, m, nrhs, (T)beta);
   MG_LAUNCH_CHECK();
 }
 
@@ -455,7 +535,7 @@ void dense_invert(double2 *M, double2 *work, int n, int *status, cudaStream_t s)
 
 template <typename T>
 void dense_apply(const C<T> *Minv, const C<T> *in, C<T> *out, int n, int nrhs, cudaStream_t s) {
-  dense_apply_kernel<T><<<div_up((int64_t)n * 32, 256), 256, 0, s>>>(Minv, in, out, n, nrhs);
+  dense_apply_kernel<T, 8><<<div_up((int64_t)n * 32, 256), 256, 0, s>>>(Minv, in, out, n, nrhs);
   MG_LAUNCH_CHECK();
 }
 
