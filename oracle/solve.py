@@ -4,9 +4,10 @@ Sec. 4 solves every level system D_l z = y to a relative residual of 1e-12
 (with DD-alpha-AMG).  What such a solve returns is D_l^{-1} y up to that
 tolerance, so the oracle takes the plain definition: a sparse direct LU
 factorisation (SuperLU via scipy) for the small lattices the parity tests use,
-and, for lattices too large to factor, scipy's BiCGStab driven to the same
-1e-12 relative residual.  Solves with D_l^H (needed by the literal Gamma_5
-adjoints of the correlator split) use the same factorisation transposed.
+and, for lattices too large to factor, scipy's restarted GMRES(64) driven to
+the same relative residual (BiCGStab stagnates on the indefinite Wilson
+operators near the most ill-conditioned masses, GMRES does not).  Solves with
+D_l^H use the same factorisation transposed, or GMRES on D_l^H.
 """
 import numpy as np
 import scipy.sparse.linalg as spla
@@ -15,17 +16,26 @@ LU_MAX_N = 40000
 
 
 class LevelSolver:
-    def __init__(self, M, tol=1e-12, maxiter=20000):
+    def __init__(self, M, tol=1e-12, maxiter=400, restart=64):
         self.M = M.tocsc()
         self.n = M.shape[0]
         self.tol = tol
         self.maxiter = maxiter
+        self.restart = restart
         self.lu = spla.splu(self.M) if self.n <= LU_MAX_N else None
+        self.last_iters = 0
 
     def _iterative(self, M, b):
-        x, info = spla.bicgstab(M, b, rtol=self.tol, atol=0.0, maxiter=self.maxiter)
+        it = [0]
+
+        def cb(_):
+            it[0] += 1
+
+        x, info = spla.gmres(M, b, rtol=self.tol, atol=0.0, restart=self.restart,
+                             maxiter=self.maxiter, callback=cb, callback_type='pr_norm')
+        self.last_iters = it[0]
         if info != 0:
-            raise RuntimeError('oracle BiCGStab did not converge (info=%d)' % info)
+            raise RuntimeError('oracle GMRES did not converge (info=%d)' % info)
         return x
 
     def solve(self, b):
@@ -33,14 +43,14 @@ class LevelSolver:
         b = np.asarray(b, dtype=np.complex128)
         if self.lu is not None:
             return self.lu.solve(b)
-        return self._iterative(self.M, b)
+        return self._iterative(self.M.tocsr(), b)
 
     def solve_adjoint(self, b):
         """z = D^{-H} b."""
         b = np.asarray(b, dtype=np.complex128)
         if self.lu is not None:
             return self.lu.solve(b, trans='H')
-        return self._iterative(self.M.conj().T.tocsc(), b)
+        return self._iterative(self.M.conj().T.tocsr(), b)
 
     def __call__(self, b):
         return self.solve(b)
