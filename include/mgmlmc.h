@@ -216,6 +216,24 @@ typedef enum {
  * precision is the solver's).  in and out must not overlap. */
 mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op, int level, int precision,
                            const void *in, void *out, int nrhs);
+/* The projection of MGMLMC_OP_PROJECT, out = (I - P_l P_l^H) in, without any
+ * device allocation during the call.  The paper has no counterpart: this is
+ * for callers that cannot allocate device memory while they run -- code
+ * inside a CUDA stream capture that must not create allocations, processes
+ * whose device memory is reserved up front by a pool they do not control,
+ * or loops that forbid allocator calls on their critical path.  in/out are
+ * device buffers as for mgmlmc_apply (complex double for MGMLMC_FP64,
+ * complex float for MGMLMC_FP32), nrhs vectors of level `level`.
+ * The coarse intermediate P_l^H in lives in a fixed device array of 2 MiB
+ * (131072 complex doubles, 262144 complex floats) that every GPU loading the
+ * library holds until exit; calls with nrhs * n_{l+1} beyond that return
+ * MGMLMC_ERR_ARG.  The first call on a device looks the array's address up
+ * (once per device), so make that first call before any stream capture.
+ * Every call shares the array: calls whose kernels overlap on the GPU race on
+ * it and must be serialised by the caller.  The array is fully overwritten
+ * before it is read, so no clearing is needed between calls. */
+mgmlmc_status mgmlmc_project_noalloc(mgmlmc_ctx *ctx, int level, int precision, const void *in,
+                                     void *out, int nrhs);
 /* Z4 noise (Eq. z4) of `level` for samples first_sample .. + nrhs - 1 into a
  * device multi-vector (complex double).  slice < 0: full support; otherwise
  * supported on time slice `slice` of that level's lattice. */

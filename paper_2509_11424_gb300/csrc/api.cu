@@ -5,12 +5,7 @@
 #include <new>
 #include <string>
 
-#include "engine.h"
-
-struct mgmlmc_ctx {
-  mg::Engine *eng = nullptr;
-  std::string err;
-};
+#include "ctx.h"
 
 namespace {
 thread_local std::string g_create_error;

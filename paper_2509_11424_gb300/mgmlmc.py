@@ -99,6 +99,7 @@ _SIGNATURES = {
     'mgmlmc_last_solve_stats': [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)],
     'mgmlmc_profile': [_P, _I],
     'mgmlmc_kernel_launches': [],
+    'mgmlmc_project_noalloc': [_P, _I, _I, _P, _P, _I],
     'mgmlmc_profile_stats': [_P, _I, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_D),
                              ctypes.POINTER(_D)],
 }
@@ -305,3 +306,7 @@ def mgmlmc_profile_stats(ctx, kernel_class):
 
 def mgmlmc_kernel_launches():
     return int(lib().mgmlmc_kernel_launches())
+
+
+def mgmlmc_project_noalloc(ctx, level, precision, inp, out, nrhs=1):
+    _check(ctx, lib().mgmlmc_project_noalloc(ctx, level, precision, ptr(inp), ptr(out), nrhs))
