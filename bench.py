@@ -1,27 +1,30 @@
 #!/usr/bin/env python
 """Benchmark of the orthogonal-projector MG-MLMC trace estimator on one GPU
-(or N ranks, one GPU each, sharding the noise samples).
+(or N ranks, one GPU each, sharding the noise samples; `--impl reference`
+times the FP64 CPU oracle instead).
 
-Metric: time to reach a fixed variance of the tr(D^-1) estimate
-(eps = 1e-5 |tr|), predicted from the measured per-sample device cost C_l and
-sample variance V_l of every term by the optimal allocation
+Metric: time to reach a fixed standard error eps = 1e-5 |tr| of the
+tr(D^-1) estimate, predicted from the measured per-sample device cost C_l
+and sample variance V_l of every term with the optimal allocation
 (sum_l sqrt(V_l C_l))^2 / eps^2 (Sec. 2.2, Eq. MLMC-Nl); lower is better.
 
 Workload: 16^4 lattice, synthetic SU(3) links U = exp(i 0.4 H) (seed 1002),
 Wilson mass m0 from tests/golden/mass_16x16x16x16.json (the most
-ill-conditioned point the oracle found on this field), three-level hierarchy
-(4^4 then 2^4 aggregates, 16 test vectors per level), noise seed 2002.
-A step is one batch of `--batch` Z4 noise vectors through every term of the
-orthogonal split (O_0, O_1, F_0, F_1, D_2^-1), each solve to a relative
-residual of 1e-12.  Inputs (gauge field, hierarchy, vectors) are resident in
-HBM; the 16^4 working set (~0.5 GB) is larger than the 129 MB L2, and an L2
-flush (a 256 MB write) separates timed steps.
+ill-conditioned point of an oracle scan on this field), three-level
+hierarchy (4^4 then 2^4 aggregates, 16 test vectors per level), noise seed
+2002.  A step is one batch of `--batch` Z4 noise vectors through every term
+of the orthogonal split (O_0, O_1, F_0, F_1, D_2^-1), every solve to a
+relative residual of 1e-12 (FP32 SAP/MG-preconditioned FGMRES inside FP64
+defect correction by default; `--precision fp64` for all-FP64).  Inputs
+(gauge field, hierarchy, vectors) are resident in HBM; a 256 MB write
+flushes the 129 MB L2 between timed steps.
 
-Also reported: the plain Hutchinson estimator on the same GPU, the roofline
-of the dominant kernel (CUDA events around its launches in the timed region),
-the clocks sampled during the timed region, an end-to-end figure through the
-C-ABI with the gauge field copied from pinned host memory every step, and
-the FP64 CPU oracle timed on the host on a bounded sample.
+Also reported: plain Hutchinson and all-FP64 MG-MLMC on the same GPU, the
+roofline of the dominant kernel (CUDA events around its launches in a
+profiled repeat of the first timed step), the clocks sampled during the
+timed region, an end-to-end figure through the C-ABI with the gauge field
+copied from pinned host memory and the hierarchy rebuilt every step, and the
+FP64 CPU oracle timed on the host on a bounded sample.
 """
 import argparse
 import hashlib
@@ -36,6 +39,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+METRIC = 'tr(D^-1) MLMC time to fixed variance, learned+mixed vs plain; Dslash GB/s'
 DIMS = (16, 16, 16, 16)
 EPS_GAUGE = 0.4
 GAUGE_SEED, NOISE_SEED, TV_SEED = 1002, 2002, 3002
@@ -44,22 +48,26 @@ NTV = [16, 16]
 REL_EPS = 1e-5
 MASS_FILE = os.path.join(ROOT, 'tests', 'golden', 'mass_16x16x16x16.json')
 PEAKS_FILE = os.path.join(ROOT, 'MEASURED_PEAKS.json')
-FP64_PEAK_TFLOPS = 1.25  # recipe table: GB300 FP64 rate (FMA pipe), see the design doc
-
-# dram bytes per launch of the dominant kernel from an ncu capture, keyed by
-# the sha1 of the kernel source it was measured on (stale -> null)
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate from the hardware table
+FP32_PEAK_TFLOPS = 80.0  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+SOLVER = dict(tol=1e-12, restart=24, max_iter=2000, smoother=1, smoother_steps=1, sap_iters=4,
+              coarse_iters=8, inner_tol=1e-6)
+KERNELS = {0: 'wilson_dslash_fp64', 1: 'wilson_dslash_fp32', 2: 'coarse_stencil_fp64',
+           3: 'coarse_stencil_fp32', 4: 'sap_sweep_fp64', 5: 'sap_sweep_fp32'}
+# dram bytes per launch of a kernel from an ncu capture, keyed by (kernel,
+# sha1 of the kernel sources it was measured on); a stale key gives null
 TRAFFIC = {}
 
 
-def workload_mass():
+def workload():
     with open(MASS_FILE) as f:
-        return float(json.load(f)['m0'])
+        return json.load(f)
 
 
 def kernel_source_hash():
     p = os.path.join(ROOT, 'paper_2509_11424_gb300', 'csrc')
     h = hashlib.sha1()
-    for f in ('kernels_dirac.cu', 'kernels_coarse.cu', 'common.cuh'):
+    for f in ('kernels_dirac.cu', 'kernels_coarse.cu', 'kernels_sap.cu', 'common.cuh'):
         h.update(open(os.path.join(p, f), 'rb').read())
     return h.hexdigest()[:12]
 
@@ -73,7 +81,7 @@ class Clocks:
     def __init__(self, device_index):
         self.idx = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, 'gpurun_out', 'clocks_bench.csv')
+        self.path = os.path.join(ROOT, 'gpurun_out', 'clocks_bench_%d.csv' % device_index)
 
     def start(self):
         try:
@@ -91,15 +99,13 @@ class Clocks:
         self.proc.terminate()
         self.proc.wait()
         self.f.close()
-        rows = []
-        for line in open(self.path):
-            parts = [p.strip() for p in line.split(',')]
-            if len(parts) >= 9:
-                rows.append(parts)
+        rows = [[p.strip() for p in line.split(',')] for line in open(self.path)]
+        rows = [r for r in rows if len(r) >= 9]
         if not rows:
             return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['no samples']}
-        sm = [float(r[1]) for r in rows if r[1].replace('.', '').isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace('.', '').isdigit()]
+        num = lambda v: v.replace('.', '', 1).isdigit()
+        sm = [float(r[1]) for r in rows if num(r[1])]
+        mx = [float(r[2]) for r in rows if num(r[2])]
         names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith('active')})
         return {'sm_mhz': float(np.median(sm)) if sm else None, 'sm_max_mhz': max(mx) if mx else None,
@@ -112,15 +118,15 @@ def dist_init():
     local = int(os.environ.get('LOCAL_RANK', '0'))
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group('nccl')
+        if not dist.is_initialized():
+            dist.init_process_group('nccl')
         return dist, rank, ws, local
     return None, 0, 1, local
 
 
-def merge_terms(terms_list):
-    """accumulate per-term results of several estimate_trace calls."""
+def merge_terms(results):
     acc = {}
-    for res in terms_list:
+    for res in results:
         for r in res:
             a = acc.setdefault(r['term'], dict(n=0, sre=0.0, sim=0.0, sab=0.0, sec=0.0, it=0.0, k=0, res=0.0))
             a['n'] += r['n']
@@ -142,14 +148,13 @@ def stats_of(a):
 
 
 def time_to_variance(acc, world, step_ms, steps, rel_eps=REL_EPS):
-    """(predicted seconds, details) with per-sample costs rescaled so the
-    terms add up to the measured step time and divided by the ranks."""
+    """(predicted seconds, details): per-sample costs from the library's
+    per-term device time, rescaled so the terms add up to the measured step
+    time (host gaps included), divided by the number of ranks."""
     terms = sorted(acc)
     dev_sec = sum(acc[t]['sec'] for t in terms)
     scale = (step_ms * 1e-3 * steps) / dev_sec if dev_sec > 0 else 1.0
-    tr = 0j
-    S = 0.0
-    det = {}
+    tr, S, det = 0j, 0.0, {}
     for t in terms:
         mu, var = stats_of(acc[t])
         C = acc[t]['sec'] * scale / acc[t]['n'] / world
@@ -161,39 +166,76 @@ def time_to_variance(acc, world, step_ms, steps, rel_eps=REL_EPS):
     return S ** 2 / eps ** 2, dict(trace=[tr.real, tr.imag], eps=eps, terms=det)
 
 
-def cpu_baseline(m0, budget_s=25.0):
-    """The FP64 oracle timed on the host on a bounded sample of the same
-    workload: per-sample cost of the plain Hutchinson term (one 16^4 solve
-    to 1e-12 with the oracle's BiCGStab) measured on the first BiCGStab
-    iterations inside `budget_s` and scaled by the iteration count the full
-    solve needs, which the oracle takes from a 1e-12 run on the coarse
-    operator's spectrum-equivalent residual history."""
+# ---------------------------------------------------------------- CPU oracle
+def oracle_gmres_cycle(m0):
+    """One bounded sample of the workload with the FP64 oracle on the host:
+    one restart cycle (64 iterations) of the oracle's GMRES(64) on the 16^4
+    plain-Hutchinson system D z = x, x the first Z4 sample.  Returns seconds
+    per GMRES iteration and the setup time."""
     import scipy.sparse.linalg as spla
-    from oracle import dirac
+    from oracle import dirac, noise
     from paper_2509_11424_gb300 import synth
     t0 = time.time()
     U = synth.gauge_field(DIMS, EPS_GAUGE, GAUGE_SEED)
-    Mx = dirac.wilson_matrix(U, m0, DIMS)
-    from oracle import noise as onz
-    x = onz.z4_vector(Mx.shape[0], NOISE_SEED, 0, onz.TERM_PLAIN)
+    M = dirac.wilson_matrix(U, m0, DIMS).tocsr()
+    x = noise.z4_vector(M.shape[0], NOISE_SEED, 0, noise.TERM_PLAIN)
     setup = time.time() - t0
     it = [0]
-    t1 = time.time()
 
     def cb(_):
         it[0] += 1
-        if time.time() - t1 > budget_s:
-            raise StopIteration
 
-    try:
-        spla.bicgstab(Mx, x, rtol=1e-12, atol=0.0, maxiter=100000, callback=cb)
-    except StopIteration:
-        pass
+    t1 = time.time()
+    spla.gmres(M, x, rtol=1e-12, atol=0.0, restart=64, maxiter=1, callback=cb, callback_type='pr_norm')
     el = time.time() - t1
-    per_iter = el / max(1, it[0])
-    return dict(per_iter_s=per_iter, iters_done=it[0], setup_s=setup, threads=os.cpu_count())
+    return dict(sec_per_iter=el / max(1, it[0]), iters=it[0], seconds=el, setup_s=setup)
 
 
+def oracle_time_to_variance(sample, wl):
+    """Time to the benchmark's eps for the oracle's plain Hutchinson estimator:
+    V and the iterations per 1e-12 solve from the oracle run stored in the
+    workload file (tests/golden/oracle_workload.py), seconds per iteration
+    measured now on this host."""
+    op = wl['oracle_plain']
+    C = sample['sec_per_iter'] * float(np.mean(op['gmres_iters']))
+    eps = REL_EPS * abs(complex(*op['mean']))
+    return op['var'] * C / eps ** 2, C
+
+
+def reference_arm(args, rank, world):
+    """The FP64 CPU oracle on this host's cores, same metric and workload:
+    each step one bounded sample (a 64-iteration GMRES cycle of the plain
+    Hutchinson solve), the value its time to the same variance."""
+    if rank != 0:
+        return
+    wl = workload()
+    for _ in range(args.warmup):
+        oracle_gmres_cycle(wl['m0'])
+    t = []
+    samples = []
+    for _ in range(args.steps):
+        s = oracle_gmres_cycle(wl['m0'])
+        samples.append(s)
+        t.append(s['seconds'])
+    spi = float(np.mean([s['sec_per_iter'] for s in samples]))
+    value, C = oracle_time_to_variance(dict(sec_per_iter=spi), wl)
+    sample = ('plain Hutchinson, 16^4 solve by the oracle GMRES(64): one 64-iteration restart cycle '
+              'per step timed, scaled by %.0f iterations per 1e-12 solve and the oracle variance %.4g '
+              '(tests/golden/mass_16x16x16x16.json)' % (np.mean(wl['oracle_plain']['gmres_iters']),
+                                                        wl['oracle_plain']['var']))
+    line = {'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': 's', 'n_gpus': world,
+            'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': 1e3 * float(np.mean(t)),
+            'higher_is_better': False, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
+            'data': 'synthetic',
+            'config': {'workload': '16^4 Wilson-Dirac, SU(3) exp(i 0.4 H) seed 1002, m0 %.4f, '
+                                   'plain Hutchinson with the FP64 CPU oracle' % wl['m0']},
+            'cpu_baseline': {'value': value, 'unit': 's', 'cores': 1, 'kind': 'oracle', 'sample': sample,
+                             'seconds_per_solve': C, 'threads_available': os.cpu_count()},
+            'e2e': {'value': value, 'unit': 's', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
@@ -201,17 +243,21 @@ def main():
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--batch', type=int, default=8)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
-    ap.add_argument('--precision', default='fp64', choices=['fp64', 'fp32'])
+    ap.add_argument('--precision', default='fp32', choices=['fp64', 'fp32'])
+    ap.add_argument('--compare-steps', type=int, default=2)
     ap.add_argument('--no-cpu', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
-    ap.add_argument('--plain-steps', type=int, default=2)
     ap.add_argument('--m0', type=float, default=None, help='override the tuned mass (exploration)')
     args = ap.parse_args()
 
     dist, rank, world, local = dist_init()
-    m0 = args.m0 if args.m0 is not None else workload_mass()
     if args.impl == 'reference':
-        return reference_arm(args, dist, rank, world, m0)
+        reference_arm(args, rank, world)
+        if dist:
+            dist.destroy_process_group()
+        return
+    wl = workload()
+    m0 = args.m0 if args.m0 is not None else wl['m0']
 
     import torch
     from paper_2509_11424_gb300 import mgmlmc as M, synth
@@ -222,60 +268,48 @@ def main():
     prec = M.FP64 if args.precision == 'fp64' else M.FP32
     M.mgmlmc_set_gauge(ctx, U)
     M.mgmlmc_set_mass(ctx, m0)
-    M.mgmlmc_set_solver(ctx, tol=1e-12, restart=24, max_iter=2000, precision=prec, inner_tol=1e-5)
-    mgp = M.mg_params(BLOCKS, NTV, setup_rounds=3, setup_iters=20, seed=TV_SEED)
+    M.mgmlmc_set_solver(ctx, precision=prec, **SOLVER)
+    mgp = M.mg_params(BLOCKS, NTV, setup_rounds=6, setup_iters=30, seed=TV_SEED)
     torch.cuda.synchronize()
     t_setup = time.time()
     M.mgmlmc_build_hierarchy(ctx, mgp)
     torch.cuda.synchronize()
     t_setup = time.time() - t_setup
     print('kernel launches after setup: %d' % M.mgmlmc_kernel_launches(), file=sys.stderr)
-    flush =torch.empty(64 * 1024 * 1024, dtype=torch.float32, device='cuda')  # 256 MB > L2
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device='cuda')  # 256 MB > L2
 
     B = args.batch
     nterm = 2 * len(BLOCKS) + 1
-    sample_base = rank * 1000000
+    base = rank * 1000000
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def step(k, kind=M.EST_ORTHOGONAL):
         n = [B] * nterm if kind == M.EST_ORTHOGONAL else [B]
         return M.mgmlmc_estimate_trace(ctx, M.est_params(kind, n, batch=B, seed=NOISE_SEED,
-                                                         first_sample=sample_base + k * B))
+                                                         first_sample=base + k * B))
+
+    def timed(k0, K, kind=M.EST_ORTHOGONAL):
+        res, ms = [], 0.0
+        for k in range(K):
+            flush.zero_()
+            e0.record(stream)
+            res.append(step(k0 + k, kind))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        return res, ms
 
     for k in range(args.warmup):
         step(k)
-    # timed region
-    results = []
-    step_ms = []
-    clocks = Clocks(local)
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
+    clocks = Clocks(local)
     clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    total_ms = 0.0
     n_launch0 = M.mgmlmc_kernel_launches()
-    for k in range(args.steps):
-        flush.zero_()
-        e0.record(stream)
-        results.append(step(args.warmup + k))
-        e1.record(stream)
-        torch.cuda.synchronize()
-        total_ms += e0.elapsed_time(e1)
-    clk = clocks.stop()
+    results, total_ms = timed(args.warmup, args.steps)
     launches = M.mgmlmc_kernel_launches() - n_launch0
-    # profile pass: the first timed step again with CUDA events around every
-    # operator launch (the preconditioner runs eagerly, outside its graph,
-    # while events are on; kernel durations are those of the timed launches)
-    flush.zero_()
-    torch.cuda.synchronize()
-    M.mgmlmc_profile(ctx, 1)
-    e0.record(stream)
-    step(args.warmup)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    prof_ms = e0.elapsed_time(e1)
-    kst = {c: M.mgmlmc_profile_stats(ctx, c) for c in range(4)}
-    M.mgmlmc_profile(ctx, 0)
+    clk = clocks.stop()
     if dist:
         t = torch.tensor([total_ms], device='cuda')
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -284,66 +318,76 @@ def main():
     acc = merge_terms(results)
     if dist:
         keys = sorted(acc)
-        vec = torch.tensor([[acc[k][f] for f in ('n', 'sre', 'sim', 'sab', 'sec')] for k in keys],
-                           dtype=torch.float64, device='cuda')
+        fields = ('n', 'sre', 'sim', 'sab', 'sec')
+        vec = torch.tensor([[acc[k][f] for f in fields] for k in keys], dtype=torch.float64, device='cuda')
         dist.all_reduce(vec)
         for i, k in enumerate(keys):
-            for j, f in enumerate(('n', 'sre', 'sim', 'sab', 'sec')):
+            for j, f in enumerate(fields):
                 acc[k][f] = vec[i, j].item()
-        for k in keys:
-            acc[k]['sec'] /= world  # per-rank device seconds
+            acc[k]['sec'] /= world
             acc[k]['n'] = int(round(acc[k]['n']))
     value, det = time_to_variance(acc, world, ms_per_step, args.steps)
 
-    # plain Hutchinson on the same GPU for comparison
-    plain = None
-    if args.plain_steps > 0:
-        pres = []
-        pms = 0.0
-        for k in range(args.plain_steps):
-            flush.zero_()
-            e0.record(stream)
-            pres.append(step(10000 + k, M.EST_PLAIN))
-            e1.record(stream)
-            torch.cuda.synchronize()
-            pms += e0.elapsed_time(e1)
-        pacc = merge_terms(pres)
-        # variance of the plain estimator relative to the same eps
-        pval, pdet = time_to_variance(pacc, world, pms / args.plain_steps, args.plain_steps)
-        # rescale to the MLMC eps (same tr, same relative target)
-        pval *= (pdet['eps'] / det['eps']) ** 2
-        plain = dict(value=pval, detail=pdet)
-
-    # roofline of the dominant kernel class
-    names = {0: 'wilson_dslash_fp64', 1: 'wilson_dslash_fp32', 2: 'coarse_stencil_fp64', 3: 'coarse_stencil_fp32'}
+    # profiled repeat of the first timed step: per-launch events
+    flush.zero_()
+    torch.cuda.synchronize()
+    M.mgmlmc_profile(ctx, 1)
+    e0.record(stream)
+    step(args.warmup)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof_ms = e0.elapsed_time(e1)
+    kst = {c: M.mgmlmc_profile_stats(ctx, c) for c in KERNELS}
+    M.mgmlmc_profile(ctx, 0)
     dom = max(kst, key=lambda c: kst[c]['ms'])
     ks = kst[dom]
     roof = None
     if ks['launches'] > 0:
         sec = ks['ms'] * 1e-3
-        fp64 = dom in (0, 2)
-        if fp64:
+        peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+        hbm = peaks.get('hbm_gbs')
+        if dom in (0, 2, 4):  # FP64 kernels are bound by the FP64 pipe on this part
             achieved = ks['flops'] / sec / 1e12
             roof = dict(bound='alu', achieved=achieved, peak=FP64_PEAK_TFLOPS, unit='TFLOP/s',
-                        frac=achieved / FP64_PEAK_TFLOPS, peak_source='recipe FP64 rate (1.25 TFLOP/s)')
+                        frac=achieved / FP64_PEAK_TFLOPS, peak_source='GB300 FP64 rate 1.25 TFLOP/s (table)')
         else:
-            peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-            hbm = peaks.get('hbm_gbs', 6800.0)
             achieved = ks['bytes'] / sec / 1e9
-            roof = dict(bound='hbm', achieved=achieved, peak=hbm, unit='GB/s', frac=achieved / hbm,
-                        peak_source='MEASURED_PEAKS.json hbm_gbs' if peaks else 'fallback 6.8 TB/s')
-        key = (names[dom], kernel_source_hash())
-        tr = TRAFFIC.get(key)
-        roof['traffic'] = tr
-        roof['kernel'] = names[dom]
-        roof['launches'] = ks['launches']
-        roof['avg_launch_us'] = ks['ms'] * 1e3 / ks['launches']
-        roof['share_of_profiled_step'] = ks['ms'] / prof_ms
-        roof['profiled_step_ms'] = prof_ms
-        roof['algorithmic_bytes_per_launch'] = ks['bytes'] / ks['launches']
-        roof['algorithmic_flops_per_launch'] = ks['flops'] / ks['launches']
+            peak = hbm if hbm else 6800.0
+            roof = dict(bound='hbm', achieved=achieved, peak=peak, unit='GB/s', frac=achieved / peak,
+                        peak_source='of measured (MEASURED_PEAKS.json hbm_gbs)' if hbm else 'of fallback 6.8 TB/s')
+        roof['traffic'] = TRAFFIC.get((KERNELS[dom], kernel_source_hash()))
+        roof.update(kernel=KERNELS[dom], launches=ks['launches'], avg_launch_us=ks['ms'] * 1e3 / ks['launches'],
+                    share_of_profiled_step=ks['ms'] / prof_ms, profiled_step_ms=prof_ms,
+                    algorithmic_bytes_per_launch=ks['bytes'] / ks['launches'],
+                    algorithmic_flops_per_launch=ks['flops'] / ks['launches'])
+    # FP32 Dslash on its own terms (the metric's 'Dslash GB/s')
+    dslash = None
+    ws = kst[1] if prec == M.FP32 else kst[0]
+    if ws['launches'] > 0:
+        peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+        gbs = ws['bytes'] / (ws['ms'] * 1e-3) / 1e9
+        dslash = dict(kernel=KERNELS[1 if prec == M.FP32 else 0], achieved_gbs=gbs,
+                      frac_of_measured_hbm=gbs / peaks['hbm_gbs'] if 'hbm_gbs' in peaks else None,
+                      avg_launch_us=ws['ms'] * 1e3 / ws['launches'], nrhs=B,
+                      note='16^4 x 8 rhs working set ~0.12 GB is L2-resident within a step')
 
-    # end to end through the C-ABI with host buffers: gauge H2D + setup + one batch + results D2H
+    compare = {}
+    if rank == 0 and args.compare_steps > 0:
+        pres, pms = timed(10000, args.compare_steps, M.EST_PLAIN)
+        pval, pdet = time_to_variance(merge_terms(pres), 1, pms / args.compare_steps, args.compare_steps)
+        compare['plain_hutchinson_same_solver'] = dict(value=pval * (pdet['eps'] / det['eps']) ** 2,
+                                                       ms_per_step=pms / args.compare_steps, detail=pdet)
+        if prec == M.FP32:
+            M.mgmlmc_set_solver(ctx, precision=M.FP64, **SOLVER)
+            step(20000)
+            fres, fms = timed(20001, args.compare_steps)
+            fval, fdet = time_to_variance(merge_terms(fres), 1, fms / args.compare_steps, args.compare_steps)
+            compare['mlmc_fp64'] = dict(value=fval, ms_per_step=fms / args.compare_steps, detail=fdet)
+            pres, pms = timed(30000, 1, M.EST_PLAIN)
+            p64, p64d = time_to_variance(merge_terms(pres), 1, pms, 1)
+            compare['plain_hutchinson_fp64'] = dict(value=p64 * (p64d['eps'] / det['eps']) ** 2, ms_per_step=pms)
+            M.mgmlmc_set_solver(ctx, precision=prec, **SOLVER)
+
     e2e = None
     if not args.no_e2e and rank == 0:
         Uh = torch.from_numpy(U.view(np.float64)).pin_memory()
@@ -352,54 +396,44 @@ def main():
         M.mgmlmc_set_gauge(ctx, Uh.numpy(), on_device=False)
         M.mgmlmc_set_mass(ctx, m0)
         M.mgmlmc_build_hierarchy(ctx, mgp)
-        r = step(20000)
+        t_build = time.time() - t0
+        r = step(40000)
         torch.cuda.synchronize()
         t_e2e = time.time() - t0
-        # setup part and the sampling part; time to variance = setup + sampling
-        eacc = merge_terms([r])
-        v_e2e, _ = time_to_variance(acc, world, ms_per_step, args.steps)
-        e2e = dict(value=(t_e2e - ms_per_step * 1e-3) + v_e2e, unit='s',
-                   h2d_bytes_per_step=int(U.nbytes), d2h_bytes_per_step=int(nterm * 88),
-                   setup_s=t_e2e - ms_per_step * 1e-3)
+        e2e = dict(value=t_build + value, unit='s', h2d_bytes_per_step=int(U.nbytes),
+                   d2h_bytes_per_step=int(nterm * 88), setup_s=t_build, step_s=t_e2e - t_build,
+                   note='gauge field from pinned host memory + hierarchy setup + sampling to the same eps')
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu:
-        cb = cpu_baseline(m0)
-        cpu = cb
+    if rank == 0 and world == 1 and not args.no_cpu and 'oracle_plain' in wl:
+        s = oracle_gmres_cycle(m0)
+        cval, C = oracle_time_to_variance(s, wl)
+        cpu = {'value': cval, 'unit': 's', 'cores': 1, 'kind': 'oracle',
+               'sample': 'plain Hutchinson, one 64-iteration GMRES(64) cycle of the oracle on the 16^4 system '
+                         '(%.1f s), scaled by %.0f iterations per 1e-12 solve and the oracle variance'
+                         % (s['seconds'], np.mean(wl['oracle_plain']['gmres_iters'])),
+               'seconds_per_solve': C, 'threads_available': os.cpu_count()}
 
     if rank == 0:
         line = {
-            'metric': 'tr(D^-1) MLMC time to fixed variance, learned+mixed vs plain; Dslash GB/s',
-            'value': value, 'unit': 's', 'n_gpus': world, 'steps': args.steps, 'warmup': args.warmup,
-            'ms_per_step': ms_per_step, 'higher_is_better': False, 'scaling': 'weak',
-            'vs_baseline': None, 'dtype': 'f64' if prec == M.FP64 else 'f32+f64',
+            'metric': METRIC, 'value': value, 'unit': 's', 'n_gpus': world, 'steps': args.steps,
+            'warmup': args.warmup, 'ms_per_step': ms_per_step, 'higher_is_better': False,
+            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64' if prec == M.FP64 else 'f32+f64',
             'data': 'synthetic',
-            'config': {'workload': '16^4 Wilson-Dirac, SU(3) exp(i 0.4 H) seed 1002, m0 %.4f, '
-                                   'orthogonal MG-MLMC 3 levels (4^4, 2^4 aggregates, 16 tv), '
-                                   'Z4 batch %d per term per step, solves to 1e-12' % (m0, B),
-                       'global_batch': B * nterm * world, 'lattice': list(DIMS),
-                       'l2': 'flushed between steps (256 MB write)', 'rel_eps': REL_EPS},
-            'setup_s': t_setup,
-            'detail': det,
-            'plain_hutchinson': plain,
-            'roofline': roof,
-            'clocks': clk,
-            'e2e': e2e,
-            'gpu_launches': launches,
-            'kernel_stats': {names[c]: kst[c] for c in kst},
-            'cpu_baseline': cpu,
+            'config': {'workload': '16^4 Wilson-Dirac, SU(3) exp(i 0.4 H) seed 1002, m0 %.4f, orthogonal '
+                                   'MG-MLMC 3 levels (4^4, 2^4 aggregates, 16 tv), SAP-MG FGMRES, Z4 batch %d '
+                                   'per term per step, solves to 1e-12' % (m0, B),
+                       'global_batch': B * nterm * world, 'lattice': list(DIMS), 'rel_eps': REL_EPS,
+                       'l2': 'flushed between steps (256 MB write)', 'parallelism': 'samples sharded, dp%d' % world},
+            'setup_s': t_setup, 'detail': det, 'compare': compare, 'roofline': roof, 'dslash': dslash,
+            'clocks': clk, 'e2e': e2e, 'gpu_launches': launches,
+            'kernel_stats': {KERNELS[c]: kst[c] for c in kst}, 'cpu_baseline': cpu,
         }
         print(json.dumps(line))
     M.mgmlmc_destroy(ctx)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
-
-
-def reference_arm(args, dist, rank, world, m0):
-    if rank != 0:
-        return
-    print(json.dumps({'impl': 'reference', 'unavailable': 'not implemented yet'}))
 
 
 if __name__ == '__main__':

@@ -103,7 +103,16 @@ typedef struct {
   int precision;       /* MGMLMC_FP64: all FP64.  MGMLMC_FP32: FP32 inner
                           solves inside FP64 defect correction */
   double inner_tol;    /* FP32 inner relative tolerance (defect correction) */
+  int smoother;        /* fine level: MGMLMC_SMOOTHER_SAP (red/black Schwarz
+                          blocks, MR inside each block) or MGMLMC_SMOOTHER_MR;
+                          coarse levels always use MR.  SAP needs an even
+                          number of blocks in every direction (blocks of 4^4,
+                          else 2^4); otherwise MR is used. */
+  int sap_iters;       /* MR iterations inside each SAP block */
 } mgmlmc_solver_params;
+
+#define MGMLMC_SMOOTHER_MR 0
+#define MGMLMC_SMOOTHER_SAP 1
 
 typedef enum { MGMLMC_EST_PLAIN = 0, MGMLMC_EST_ORTHOGONAL = 1 } mgmlmc_estimator;
 
@@ -151,7 +160,7 @@ mgmlmc_status mgmlmc_set_gauge(mgmlmc_ctx *ctx, const double *U, int on_device);
 /* Bare mass m0 of the Wilson operator.  Invalidates the hierarchy. */
 mgmlmc_status mgmlmc_set_mass(mgmlmc_ctx *ctx, double m0);
 /* Solver parameters (defaults: tol 1e-12, max_iter 2000, restart 16,
- * smoother_steps 4, coarse_iters 8, FP64). */
+ * smoother_steps 4, coarse_iters 8, FP64, MR smoother, sap_iters 4). */
 mgmlmc_status mgmlmc_set_solver(mgmlmc_ctx *ctx, const mgmlmc_solver_params *p);
 /* Import the N_tv test vectors of level `level` (0 .. L-2): n_tv vectors of
  * length n (the level's vector length), one after the other (canonical
@@ -207,7 +216,10 @@ typedef enum {
   MGMLMC_OP_PROLONG = 2,  /* out = P_l in        (level l+1 -> level l)         */
   MGMLMC_OP_PROJECT = 3,  /* out = (I - P_l P_l^H) in            (level l)      */
   MGMLMC_OP_SOLVE = 4,    /* out = D_l^-1 in by the MG-preconditioned solver   */
-  MGMLMC_OP_GAMMA5 = 5    /* out = Gamma5 in (level l)                         */
+  MGMLMC_OP_GAMMA5 = 5,   /* out = Gamma5 in (level l)                         */
+  MGMLMC_OP_SMOOTH = 6    /* out = z after the level's smoother (SAP on level 0
+                             when selected, else MR; smoother_steps sweeps)
+                             applied to D_l z = in from z = 0                 */
 } mgmlmc_op;
 
 /* Apply an operator to nrhs device vectors.  precision selects the storage
@@ -259,6 +271,8 @@ mgmlmc_status mgmlmc_last_solve_stats(const mgmlmc_ctx *ctx, int *iters, double 
 #define MGMLMC_KERNEL_WILSON_FP32 1
 #define MGMLMC_KERNEL_STENCIL_FP64 2
 #define MGMLMC_KERNEL_STENCIL_FP32 3
+#define MGMLMC_KERNEL_SAP_FP64 4 /* one SAP sweep (both colours) */
+#define MGMLMC_KERNEL_SAP_FP32 5
 
 /* Number of CUDA kernels this library has launched in this process (all
  * contexts), for counting the launches of a timed region. */

@@ -211,6 +211,10 @@ mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op, int level, int precision, co
         if (!dp) throw mg::Error(MGMLMC_ERR_ARG, "solve takes FP64 buffers");
         e.solve(level, (const double2 *)in, (double2 *)out, nrhs);
         break;
+      case MGMLMC_OP_SMOOTH:
+        if (dp) e.smooth_apply<double>(level, (const double2 *)in, (double2 *)out, nrhs);
+        else e.smooth_apply<float>(level, (const float2 *)in, (float2 *)out, nrhs);
+        break;
       case MGMLMC_OP_GAMMA5: {
         const mg::Geom &g = e.level(level).g;
         if (dp) mg::gamma5_apply<double>((const double2 *)in, (double2 *)out, g.V, g.dof, nrhs, e.stream);

@@ -57,6 +57,16 @@ Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
   sp_.coarse_iters = 8;
   sp_.precision = MGMLMC_FP64;
   sp_.inner_tol = 1e-6;
+  sp_.smoother = MGMLMC_SMOOTHER_MR;
+  sp_.sap_iters = 4;
+  // SAP blocks: 4^4 when every direction holds an even number of them, else 2^4
+  for (int bsz : {4, 2}) {
+    int b[4] = {bsz, bsz, bsz, bsz};
+    if (sap_feasible(fine_, b)) {
+      for (int i = 0; i < 4; ++i) sap_b_[i] = bsz;
+      break;
+    }
+  }
   levels_.resize(1);
   levels_[0].g = fine_;
   levels_[0].fine = true;
@@ -132,6 +142,20 @@ void Engine::prof_resolve() {
     events_.push_back(p.b);
   }
   pending_.clear();
+}
+
+cudaEvent_t Engine::prof_begin() {
+  if (!prof_ || capturing_) return nullptr;
+  cudaEvent_t a = take_event();
+  MG_CUDA(cudaEventRecord(a, stream));
+  return a;
+}
+
+void Engine::prof_end(cudaEvent_t a, int cls, double bytes, double flops) {
+  if (!a) return;
+  cudaEvent_t b = take_event();
+  MG_CUDA(cudaEventRecord(b, stream));
+  pending_.push_back({cls, a, b, bytes, flops});
 }
 
 void Engine::profile(bool on) {
@@ -222,7 +246,9 @@ void Engine::set_solver(const mgmlmc_solver_params &p) {
   if (!(p.tol > 0.0) || p.max_iter < 1 || p.restart < 1 || p.restart > 64 || p.smoother_steps < 0 ||
       p.coarse_iters < 1 || p.coarse_iters > 64 ||
       (p.precision != MGMLMC_FP64 && p.precision != MGMLMC_FP32) ||
-      (p.precision == MGMLMC_FP32 && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)))
+      (p.precision == MGMLMC_FP32 && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)) ||
+      (p.smoother != MGMLMC_SMOOTHER_MR && p.smoother != MGMLMC_SMOOTHER_SAP) || p.sap_iters < 1 ||
+      p.sap_iters > 64)
     throw Error(MGMLMC_ERR_ARG, "invalid solver parameters");
   drop_graphs();  // captured preconditioners bake in smoother / inner iteration counts
   sp_ = p;
@@ -320,6 +346,24 @@ void Engine::noise(int l, uint64_t seed, uint64_t sample0, uint64_t term, uint64
 // minimal-residual smoothing: res holds r - D z on entry and exit
 template <typename T> void Engine::smooth(int l, C<T> *z, C<T> *res, int nrhs) {
   const int64_t n = levels_[l].g.n();
+  if (l == 0 && sp_.smoother == MGMLMC_SMOOTHER_SAP && sap_b_[0] > 0) {
+    C<T> *e = ws<T>("sape", l, (size_t)n * nrhs);
+    const C<T> *U;
+    if constexpr (sizeof(T) == 8) U = levels_[0].U64; else U = levels_[0].U32;
+    const Geom &g = levels_[0].g;
+    // per sweep: both colours read links + residual, write z, e and the
+    // residual (block kernels), then the boundary pass reads e and the
+    // residual and writes the residual: 36 + 12 * (1 + 3 + 3) complex per site;
+    // flops: sap_iters block operators (1368 per site) + the boundary hops
+    const double bytes = (double)g.V * (36.0 + 84.0 * nrhs) * sizeof(C<T>);
+    const double flops = (double)g.V * nrhs * (1368.0 * sp_.sap_iters + 684.0);
+    for (int s = 0; s < sp_.smoother_steps; ++s) {
+      cudaEvent_t a = prof_begin();
+      sap_sweep<T>(res, z, e, U, g, sap_b_, m0_, sp_.sap_iters, nrhs, stream);
+      prof_end(a, sizeof(T) == 8 ? K_SAP64 : K_SAP32, bytes, flops);
+    }
+    return;
+  }
   C<T> *q = ws<T>("smq", l, (size_t)n * nrhs);
   double2 *d = ws<double>("smd", l, 2 * (size_t)nrhs);
   for (int s = 0; s < sp_.smoother_steps; ++s) {
@@ -328,6 +372,16 @@ template <typename T> void Engine::smooth(int l, C<T> *z, C<T> *res, int nrhs) {
     mr_update<T>(z, res, q, d, d + nrhs, n, nrhs, stream);
   }
 }
+
+template <typename T> void Engine::smooth_apply(int l, const C<T> *in, C<T> *out, int nrhs) {
+  const int64_t n = levels_.at(l).g.n();
+  C<T> *res = ws<T>("smres", l, (size_t)n * nrhs);
+  MG_CUDA(cudaMemcpyAsync(res, in, sizeof(C<T>) * n * nrhs, cudaMemcpyDeviceToDevice, stream));
+  MG_CUDA(cudaMemsetAsync(out, 0, sizeof(C<T>) * n * nrhs, stream));
+  smooth<T>(l, out, res, nrhs);
+}
+template void Engine::smooth_apply<double>(int, const C<double> *, C<double> *, int);
+template void Engine::smooth_apply<float>(int, const C<float> *, C<float> *, int);
 
 // z = M r: pre-smoothing, coarse-grid correction (recursive K-cycle: a few
 // FGMRES iterations on the next level, exact dense solve on the coarsest),

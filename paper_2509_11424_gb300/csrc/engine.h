@@ -49,7 +49,15 @@ struct TermAcc {
 
 // Per-kernel-class timing collected with CUDA events on the engine's stream
 // while profiling is enabled (mgmlmc_profile).
-enum KClass { K_WILSON64 = 0, K_WILSON32 = 1, K_STENCIL64 = 2, K_STENCIL32 = 3, K_NCLASS = 8 };
+enum KClass {
+  K_WILSON64 = 0,
+  K_WILSON32 = 1,
+  K_STENCIL64 = 2,
+  K_STENCIL32 = 3,
+  K_SAP64 = 4,
+  K_SAP32 = 5,
+  K_NCLASS = 8
+};
 struct KStat {
   int64_t launches = 0;
   double ms = 0.0;
@@ -77,6 +85,7 @@ class Engine {
   template <typename T> void restrict_to(int l, const C<T> *in, C<T> *out, int nrhs);
   template <typename T> void prolong_from(int l, const C<T> *in, C<T> *out, int nrhs, double beta);
   template <typename T> void project_out(int l, const C<T> *in, C<T> *out, int nrhs);
+  template <typename T> void smooth_apply(int l, const C<T> *in, C<T> *out, int nrhs);
   // z = D_l^-1 b (FP64 interface; the solver precision is set by set_solver)
   SolveInfo solve(int l, const double2 *b, double2 *x, int nrhs);
   void noise(int l, uint64_t seed, uint64_t sample0, uint64_t term, uint64_t aux, int slice,
@@ -126,6 +135,7 @@ class Engine {
 
   int dims_[4];
   Geom fine_{};
+  int sap_b_[4] = {0, 0, 0, 0};  // SAP block extents (0: SAP not possible)
   double m0_ = 0.0;
   bool have_gauge_ = false;
   bool ready_ = false;
@@ -148,6 +158,9 @@ class Engine {
   KStat kst_[K_NCLASS];
   cudaEvent_t take_event();
   void prof_resolve();
+  // event pair around a launch sequence of one kernel class (no-op unless profiling)
+  cudaEvent_t prof_begin();
+  void prof_end(cudaEvent_t a, int cls, double bytes, double flops);
   double2 *partials(size_t count);
   bool graphs_on_ = true;
   bool capturing_ = false;

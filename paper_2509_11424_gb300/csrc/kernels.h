@@ -97,6 +97,15 @@ void stencil_split(const C<T> *in, C<T> *out9, const C<T> *A, Geom g, const int 
 template <typename T>
 void gamma5_apply(const C<T> *in, C<T> *out, int64_t nsites, int dof, int nrhs, cudaStream_t s);
 
+// ------------------------------------------------------------------ SAP
+// blocks b tile the lattice with an even block count in every direction
+bool sap_feasible(const Geom &g, const int b[4]);
+template <typename T> size_t sap_smem_bytes(const int b[4]);
+// one red/black sweep: r (residual, exact on exit), z += correction, e scratch
+template <typename T>
+void sap_sweep(C<T> *r, C<T> *z, C<T> *e, const C<T> *U, Geom g, const int b[4], double m0,
+               int block_iters, int nrhs, cudaStream_t s);
+
 // ------------------------------------------------------------------ transfer
 // P is stored [X][c][k][row] (row fastest).
 template <typename T>

@@ -1,0 +1,334 @@
+// Schwarz alternating procedure (SAP) smoother on the fine lattice: the
+// domain-decomposition smoother of the paper's solver (DD-alpha-AMG, Sec. 4)
+// written for one GPU.
+//
+// The lattice is cut into blocks of extent b[4]; blocks are coloured red /
+// black by the parity of their block coordinates (every direction must hold
+// an even number of blocks, so neighbouring blocks always differ in colour).
+// One sweep visits red then black blocks.  For every block B of the active
+// colour, in parallel, a few minimal-residual iterations solve
+// D_BB e_B = r_B with the block-local Wilson operator (hops that leave B are
+// dropped); then z_B += e_B, the residual inside B becomes the block MR
+// residual, and the residual of the other colour loses the hops of e that
+// cross block faces.  The residual r = b - D z stays exact throughout.
+//
+// One CTA per (active block, rhs), one thread per site of the block.  The
+// block's links and its residual live in shared memory for all block
+// iterations (FP32: 256 sites x (36 + 12) complex = 98 KB), so the MR
+// iterations touch HBM once per sweep.
+#include "kernels.h"
+
+namespace mg {
+
+namespace {
+
+struct SapGeom {
+  Geom g;
+  int b[4];   // block extents
+  int nb[4];  // blocks per direction
+  int sites;  // sites per block
+};
+
+template <int MU, typename V> __device__ __forceinline__ V sBl(int a, V l0, V l1) {
+  if (MU == 0) return a == 0 ? cmulmi(l1) : cmulmi(l0);
+  if (MU == 1) return a == 0 ? cneg(l1) : l0;
+  if (MU == 2) return a == 0 ? cmulmi(l0) : cmuli(l1);
+  return a == 0 ? l0 : l1;
+}
+template <int MU, typename V> __device__ __forceinline__ V sBh(int a, V v0, V v1) {
+  if (MU == 0) return a == 0 ? cmuli(v1) : cmuli(v0);
+  if (MU == 1) return a == 0 ? v1 : cneg(v0);
+  if (MU == 2) return a == 0 ? cmuli(v0) : cmulmi(v1);
+  return a == 0 ? v0 : v1;
+}
+
+// acc += k * (1 -+ gamma_MU) (U or U^H) p   (same algebra as the full operator)
+template <int MU, bool FWD, typename T>
+__device__ __forceinline__ void shop(const C<T> *p, const C<T> *u, T k, C<T> (&acc)[12]) {
+  const T sg = FWD ? (T)-1 : (T)1;
+  C<T> h[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) h[a][c] = cadd(p[3 * a + c], cscale(sBl<MU>(a, p[6 + c], p[9 + c]), sg));
+  C<T> v[2][3];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      C<T> z = mk<T>((T)0, (T)0);
+#pragma unroll
+      for (int bb = 0; bb < 3; ++bb) {
+        if (FWD) z = cfma(u[3 * c + bb], h[a][bb], z);
+        else z = cfmac(u[3 * bb + c], h[a][bb], z);
+      }
+      v[a][c] = z;
+    }
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      acc[3 * a + c].x = fma(k, v[a][c].x, acc[3 * a + c].x);
+      acc[3 * a + c].y = fma(k, v[a][c].y, acc[3 * a + c].y);
+      const C<T> w = sBh<MU>(a, v[0][c], v[1][c]);
+      acc[6 + 3 * a + c].x = fma(sg * k, w.x, acc[6 + 3 * a + c].x);
+      acc[6 + 3 * a + c].y = fma(sg * k, w.y, acc[6 + 3 * a + c].y);
+    }
+}
+
+// block index (of all blocks) of the i-th block of colour `color`
+__device__ __forceinline__ void active_block(const SapGeom &sg, int i, int color, int (&bc)[4]) {
+  const int half = sg.nb[0] >> 1;
+  const int k = i % half;
+  int rest = i / half;
+  bc[1] = rest % sg.nb[1];
+  rest /= sg.nb[1];
+  bc[2] = rest % sg.nb[2];
+  bc[3] = rest / sg.nb[2];
+  bc[0] = 2 * k + ((color + bc[1] + bc[2] + bc[3]) & 1);
+}
+
+template <typename T>
+__device__ __forceinline__ double2 block_reduce2(double v0, double v1, double v2, double2 *sh,
+                                                 double *out3) {
+  // sum (v0, v1, v2) over the block; deterministic tree order
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_down_sync(0xffffffffu, v0, o);
+    v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    v2 += __shfl_down_sync(0xffffffffu, v2, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
+  double *s = reinterpret_cast<double *>(sh);
+  if (l == 0) {
+    s[3 * w] = v0;
+    s[3 * w + 1] = v1;
+    s[3 * w + 2] = v2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0;
+    for (int i = 0; i < nw; ++i) {
+      a += s[3 * i];
+      b += s[3 * i + 1];
+      c += s[3 * i + 2];
+    }
+    out3[0] = a;
+    out3[1] = b;
+    out3[2] = c;
+  }
+  __syncthreads();
+  return make_double2(out3[0], out3[1]);
+}
+
+template <typename T, int DIR>
+__device__ __forceinline__ void local_hops(const C<T> *rho, const C<T> *Us, const int (&lc)[4],
+                                           const int *b, int lsite, int sites_stride, T ksign_t,
+                                           C<T> (&acc)[12]) {
+  (void)sites_stride;
+  // forward
+  if (lc[DIR] + 1 < b[DIR]) {
+    int stride = 1;
+    for (int i = 0; i < DIR; ++i) stride *= b[i];
+    const int ln = lsite + stride;
+    // the time-boundary sign never applies inside a block unless the block
+    // wraps, which it cannot (blocks tile the lattice without wrapping)
+    shop<DIR, true, T>(rho + ln * 12, Us + (lsite * 4 + DIR) * 9, (T)-0.5, acc);
+  }
+  if (lc[DIR] > 0) {
+    int stride = 1;
+    for (int i = 0; i < DIR; ++i) stride *= b[i];
+    const int ln = lsite - stride;
+    shop<DIR, false, T>(rho + ln * 12, Us + (ln * 4 + DIR) * 9, (T)-0.5, acc);
+  }
+  (void)ksign_t;
+}
+
+// One colour of one SAP sweep.  r: residual (in/out), z: solution (+= e),
+// e: correction of this colour (written for the boundary update).
+template <typename T>
+__global__ void __launch_bounds__(256) sap_block_kernel(C<T> *__restrict__ r, C<T> *__restrict__ z,
+                                                        C<T> *__restrict__ e_out,
+                                                        const C<T> *__restrict__ U, SapGeom sg,
+                                                        T diag, int color, int iters) {
+  extern __shared__ unsigned char smem_raw[];
+  const int sites = sg.sites;
+  C<T> *Us = reinterpret_cast<C<T> *>(smem_raw);  // [sites][4][9]
+  C<T> *rho = Us + sites * 36;                      // [sites][12]
+  double2 *red = reinterpret_cast<double2 *>(rho + sites * 12);  // reduction scratch
+  double *out3 = reinterpret_cast<double *>(red + 64);
+  const int64_t n = sg.g.n();
+  const int rr = blockIdx.y;
+  C<T> *rv = r + rr * n;
+  C<T> *zv = z + rr * n;
+  C<T> *ev = e_out + rr * n;
+  int bc[4];
+  active_block(sg, blockIdx.x, color, bc);
+  const int ls = threadIdx.x;
+  int lc[4];
+  {
+    int t = ls;
+    lc[0] = t % sg.b[0]; t /= sg.b[0];
+    lc[1] = t % sg.b[1]; t /= sg.b[1];
+    lc[2] = t % sg.b[2];
+    lc[3] = t / sg.b[2];
+  }
+  int gc[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) gc[i] = bc[i] * sg.b[i] + lc[i];
+  const int s = sg.g.index(gc);
+  // stage links and the residual of the block
+  for (int i = 0; i < 36; ++i) Us[ls * 36 + i] = U[(int64_t)s * 36 + i];
+  for (int i = 0; i < 12; ++i) rho[ls * 12 + i] = rv[(int64_t)s * 12 + i];
+  C<T> e[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) e[i] = mk<T>((T)0, (T)0);
+  __syncthreads();
+  for (int it = 0; it < iters; ++it) {
+    C<T> q[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) q[i] = cscale(rho[ls * 12 + i], diag);
+    local_hops<T, 0>(rho, Us, lc, sg.b, ls, sites, (T)1, q);
+    local_hops<T, 1>(rho, Us, lc, sg.b, ls, sites, (T)1, q);
+    local_hops<T, 2>(rho, Us, lc, sg.b, ls, sites, (T)1, q);
+    local_hops<T, 3>(rho, Us, lc, sg.b, ls, sites, (T)1, q);
+    T qr_re = 0, qr_im = 0, qq = 0;
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      const C<T> p = rho[ls * 12 + i];
+      qr_re = fma(q[i].x, p.x, fma(q[i].y, p.y, qr_re));
+      qr_im = fma(q[i].x, p.y, fma(-q[i].y, p.x, qr_im));
+      qq = fma(q[i].x, q[i].x, fma(q[i].y, q[i].y, qq));
+    }
+    block_reduce2<T>((double)qr_re, (double)qr_im, (double)qq, red, out3);
+    const double den = out3[2];
+    const C<T> al = den > 1e-280 ? mk<T>((T)(out3[0] / den), (T)(out3[1] / den)) : mk<T>((T)0, (T)0);
+#pragma unroll
+    for (int i = 0; i < 12; ++i) {
+      const C<T> p = rho[ls * 12 + i];
+      e[i] = cfma(al, p, e[i]);
+      rho[ls * 12 + i] = cfma(cneg(al), q[i], p);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 12; ++i) {
+    const int64_t o = (int64_t)s * 12 + i;
+    zv[o] = cadd(zv[o], e[i]);
+    ev[o] = e[i];
+    rv[o] = rho[ls * 12 + i];
+  }
+}
+
+// residual of the inactive colour: r(x) -= hops of e that cross a block face
+// into x from a block of the active colour.
+template <int MU, typename T>
+__device__ __forceinline__ void cross_pair(const C<T> *__restrict__ ev, const C<T> *__restrict__ U,
+                                           const SapGeom &sg, int s, const int (&c)[4],
+                                           C<T> (&acc)[12]) {
+  const Geom &g = sg.g;
+  {
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    cn[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
+    if (c[MU] / sg.b[MU] != cn[MU] / sg.b[MU]) {
+      const int sn = g.index(cn);
+      const T k = (MU == 3 && cn[3] == 0) ? (T)0.5 : (T)-0.5;
+      C<T> p[12];
+#pragma unroll
+      for (int i = 0; i < 12; ++i) p[i] = ev[(int64_t)sn * 12 + i];
+      shop<MU, true, T>(p, U + ((int64_t)s * 4 + MU) * 9, k, acc);
+    }
+  }
+  {
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    cn[MU] = (c[MU] == 0) ? g.L[MU] - 1 : c[MU] - 1;
+    if (c[MU] / sg.b[MU] != cn[MU] / sg.b[MU]) {
+      const int sn = g.index(cn);
+      const T k = (MU == 3 && c[3] == 0) ? (T)0.5 : (T)-0.5;
+      C<T> p[12];
+#pragma unroll
+      for (int i = 0; i < 12; ++i) p[i] = ev[(int64_t)sn * 12 + i];
+      shop<MU, false, T>(p, U + ((int64_t)sn * 4 + MU) * 9, k, acc);
+    }
+  }
+}
+
+template <typename T>
+__global__ void sap_boundary_kernel(C<T> *__restrict__ r, const C<T> *__restrict__ e,
+                                    const C<T> *__restrict__ U, SapGeom sg, int color) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= sg.g.V) return;
+  int c[4];
+  sg.g.coords(s, c);
+  const int par = (c[0] / sg.b[0] + c[1] / sg.b[1] + c[2] / sg.b[2] + c[3] / sg.b[3]) & 1;
+  if (par == color) return;  // residual of active blocks was written by the block kernel
+  const int64_t n = sg.g.n();
+  const C<T> *ev = e + blockIdx.y * n;
+  C<T> *rv = r + blockIdx.y * n;
+  C<T> acc[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) acc[i] = mk<T>((T)0, (T)0);
+  cross_pair<0, T>(ev, U, sg, s, c, acc);
+  cross_pair<1, T>(ev, U, sg, s, c, acc);
+  cross_pair<2, T>(ev, U, sg, s, c, acc);
+  cross_pair<3, T>(ev, U, sg, s, c, acc);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) rv[(int64_t)s * 12 + i] = csub(rv[(int64_t)s * 12 + i], acc[i]);
+}
+
+}  // namespace
+
+bool sap_feasible(const Geom &g, const int b[4]) {
+  int sites = 1;
+  for (int i = 0; i < 4; ++i) {
+    if (b[i] < 1 || g.L[i] % b[i]) return false;
+    if ((g.L[i] / b[i]) % 2) return false;
+    sites *= b[i];
+  }
+  return sites <= 256 && sites >= 2;
+}
+
+template <typename T>
+size_t sap_smem_bytes(const int b[4]) {
+  const int sites = b[0] * b[1] * b[2] * b[3];
+  return (size_t)sites * 48 * sizeof(C<T>) + 64 * sizeof(double2) + 4 * sizeof(double);
+}
+
+template <typename T>
+void sap_sweep(C<T> *r, C<T> *z, C<T> *e, const C<T> *U, Geom g, const int b[4], double m0,
+               int block_iters, int nrhs, cudaStream_t s) {
+  SapGeom sg;
+  sg.g = g;
+  sg.sites = 1;
+  int nblocks = 1;
+  for (int i = 0; i < 4; ++i) {
+    sg.b[i] = b[i];
+    sg.nb[i] = g.L[i] / b[i];
+    sg.sites *= b[i];
+    nblocks *= sg.nb[i];
+  }
+  const size_t sm = sap_smem_bytes<T>(b);
+  static bool configured = false;
+  if (!configured) {
+    MG_CUDA(cudaFuncSetAttribute(sap_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(220 * 1024)));
+    configured = true;
+  }
+  if (sm > 220 * 1024) throw Error(1, "SAP block too large for shared memory");
+  for (int color = 0; color < 2; ++color) {
+    sap_block_kernel<T><<<dim3(nblocks / 2, nrhs), sg.sites, sm, s>>>(r, z, e, U, sg, (T)(4.0 + m0),
+                                                                      color, block_iters);
+    MG_LAUNCH_CHECK();
+    sap_boundary_kernel<T><<<dim3(div_up(g.V, 128), nrhs), 128, 0, s>>>(r, e, U, sg, color);
+    MG_LAUNCH_CHECK();
+  }
+}
+
+template void sap_sweep<double>(C<double> *, C<double> *, C<double> *, const C<double> *, Geom,
+                                const int *, double, int, int, cudaStream_t);
+template void sap_sweep<float>(C<float> *, C<float> *, C<float> *, const C<float> *, Geom,
+                               const int *, double, int, int, cudaStream_t);
+template size_t sap_smem_bytes<double>(const int *);
+template size_t sap_smem_bytes<float>(const int *);
+
+}  // namespace mg

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, 'libmgmlmc.so')
 MAX_LEVELS = 4
 FP64, FP32 = 0, 1
 EST_PLAIN, EST_ORTHOGONAL = 0, 1
-OP_D, OP_RESTRICT, OP_PROLONG, OP_PROJECT, OP_SOLVE, OP_GAMMA5 = range(6)
+OP_D, OP_RESTRICT, OP_PROLONG, OP_PROJECT, OP_SOLVE, OP_GAMMA5, OP_SMOOTH = range(7)
 TERM_PLAIN, TERM_O, TERM_F, TERM_COARSEST = 0, 16, 32, 48
 STATUS = {0: 'OK', 1: 'ERR_ARG', 2: 'ERR_STATE', 3: 'ERR_OOM', 4: 'ERR_CUDA',
           5: 'ERR_NOT_CONVERGED', 6: 'ERR_NUMERIC'}
@@ -40,7 +40,9 @@ class SolverParams(ctypes.Structure):
                 ('smoother_steps', ctypes.c_int),
                 ('coarse_iters', ctypes.c_int),
                 ('precision', ctypes.c_int),
-                ('inner_tol', ctypes.c_double)]
+                ('inner_tol', ctypes.c_double),
+                ('smoother', ctypes.c_int),
+                ('sap_iters', ctypes.c_int)]
 
 
 class EstParams(ctypes.Structure):
@@ -179,9 +181,13 @@ def mgmlmc_set_mass(ctx, m0):
     _check(ctx, lib().mgmlmc_set_mass(ctx, float(m0)))
 
 
+SMOOTHER_MR, SMOOTHER_SAP = 0, 1
+
+
 def solver_params(tol=1e-12, max_iter=2000, restart=16, smoother_steps=4, coarse_iters=8,
-                  precision=FP64, inner_tol=1e-6):
-    return SolverParams(tol, max_iter, restart, smoother_steps, coarse_iters, precision, inner_tol)
+                  precision=FP64, inner_tol=1e-6, smoother=SMOOTHER_MR, sap_iters=4):
+    return SolverParams(tol, max_iter, restart, smoother_steps, coarse_iters, precision, inner_tol,
+                        smoother, sap_iters)
 
 
 def mgmlmc_set_solver(ctx, params=None, **kw):
