@@ -113,6 +113,13 @@ typedef struct {
 
 #define MGMLMC_SMOOTHER_MR 0
 #define MGMLMC_SMOOTHER_SAP 1
+#define MGMLMC_SMOOTHER_LEARNED 2 /* fine level: SAP sweeps followed by one
+                                     step along the trained network's output,
+                                     z += alpha N(r) with the residual-minimising
+                                     alpha (see mgmlmc_learned_train); a solve
+                                     that does not converge within max_iter / 4
+                                     is redone with SAP alone (counted in
+                                     mgmlmc_learned_stats) */
 
 typedef enum { MGMLMC_EST_PLAIN = 0, MGMLMC_EST_ORTHOGONAL = 1 } mgmlmc_estimator;
 
@@ -217,9 +224,10 @@ typedef enum {
   MGMLMC_OP_PROJECT = 3,  /* out = (I - P_l P_l^H) in            (level l)      */
   MGMLMC_OP_SOLVE = 4,    /* out = D_l^-1 in by the MG-preconditioned solver   */
   MGMLMC_OP_GAMMA5 = 5,   /* out = Gamma5 in (level l)                         */
-  MGMLMC_OP_SMOOTH = 6    /* out = z after the level's smoother (SAP on level 0
+  MGMLMC_OP_SMOOTH = 6,   /* out = z after the level's smoother (SAP on level 0
                              when selected, else MR; smoother_steps sweeps)
                              applied to D_l z = in from z = 0                 */
+  MGMLMC_OP_NET = 7       /* out = N(in), the learned network (level 0)       */
 } mgmlmc_op;
 
 /* Apply an operator to nrhs device vectors.  precision selects the storage
@@ -263,6 +271,57 @@ mgmlmc_status mgmlmc_get_coarse_op(mgmlmc_ctx *ctx, int level, double *out);
 /* Statistics of the last solve: outer iterations (max over rhs) and true
  * relative residual (max over rhs). */
 mgmlmc_status mgmlmc_last_solve_stats(const mgmlmc_ctx *ctx, int *iters, double *residual);
+
+/* ---- learned smoother ------------------------------------------------------
+ * Not in the paper.  A gauge-covariant convolutional network stands in for the
+ * fine-level smoother: three linear layers, channels 1 -> C -> C -> 1,
+ *   phi[o](x) = sum_c sum_h W[h][o][c] (T_h psi[c])(x),
+ * h = 0 identity, 1 + 2 mu: U_mu(x) psi(x + mu), 2 + 2 mu: U_mu(x - mu)^H
+ * psi(x - mu) (fermion boundary sign), W[h][o][c] a complex 4x4 spin matrix.
+ * Weights are stored layer by layer, each [h][o][c][4][4] complex double.
+ * Training minimises sum_b ||r_b - D N(r_b)||^2 / ||r_b||^2 over residuals
+ * r_b that the solver itself produces (the residuals left by the SAP
+ * post-smoother of its multigrid cycles, i.e. what the learned step sees);
+ * with the error e = D^-1 r this is ||N(r) - e||^2 in the D^H D norm.
+ * The true FP64 residual still decides every solve, so estimates stay
+ * unbiased whatever the network does. */
+typedef struct {
+  int channels;   /* C, 1 .. 32 (16 for the workload) */
+  int steps;      /* Adam steps */
+  int batch;      /* residuals per step */
+  int pool;       /* residual / error pairs collected from the solver */
+  double lr;      /* Adam learning rate */
+  uint64_t seed;  /* seed of the weight initialisation and of the noise of the
+                     solves that produce the pairs */
+} mgmlmc_train_params;
+
+typedef struct {
+  int steps, pairs;
+  double loss_init;   /* mean loss of the initial (Jacobi-like) network */
+  double loss_first;  /* mean loss over the first 10 steps */
+  double loss_last;   /* mean loss over the last 10 steps */
+  double seconds;     /* wall time of collection + training */
+} mgmlmc_train_result;
+
+/* (Re)initialise the network: channel 0 carries the input through the layers
+ * scaled to a Jacobi step 1/(4 + m0), every other weight small (Z4 draws of
+ * size 0.01 from the library's Philox stream). */
+mgmlmc_status mgmlmc_learned_init(mgmlmc_ctx *ctx, int channels, uint64_t seed);
+/* Number of complex weights of all layers together. */
+mgmlmc_status mgmlmc_learned_size(const mgmlmc_ctx *ctx, int64_t *n_complex);
+/* Copy all weights to (set = 0) or from (set = 1) a host array of
+ * 2 * n_complex doubles. */
+mgmlmc_status mgmlmc_learned_weights(mgmlmc_ctx *ctx, double *host, int set);
+/* FP64 loss and gradient dL/dW* (host, 2 * n_complex doubles) of a batch of
+ * nrhs fine-level device vectors r (complex double). */
+mgmlmc_status mgmlmc_learned_loss_grad(mgmlmc_ctx *ctx, const double *r, int nrhs, double *loss,
+                                       double *grad_host);
+/* Collect p->pool residuals from solves with the current solver, then run
+ * p->steps Adam steps on the GPU (FP32 forward/backward, FP64 weights). */
+mgmlmc_status mgmlmc_learned_train(mgmlmc_ctx *ctx, const mgmlmc_train_params *p,
+                                   mgmlmc_train_result *out);
+/* Solves that fell back from the learned smoother to SAP. */
+mgmlmc_status mgmlmc_learned_stats(const mgmlmc_ctx *ctx, int64_t *fallbacks);
 
 /* ---- measurement --------------------------------------------------------- */
 

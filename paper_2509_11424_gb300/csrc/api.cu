@@ -215,6 +215,11 @@ mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op, int level, int precision, co
         if (dp) e.smooth_apply<double>(level, (const double2 *)in, (double2 *)out, nrhs);
         else e.smooth_apply<float>(level, (const float2 *)in, (float2 *)out, nrhs);
         break;
+      case MGMLMC_OP_NET:
+        if (level != 0) throw mg::Error(MGMLMC_ERR_ARG, "the network acts on level 0");
+        if (dp) e.net_forward<double>((const double2 *)in, (double2 *)out, nrhs);
+        else e.net_forward<float>((const float2 *)in, (float2 *)out, nrhs);
+        break;
       case MGMLMC_OP_GAMMA5: {
         const mg::Geom &g = e.level(level).g;
         if (dp) mg::gamma5_apply<double>((const double2 *)in, (double2 *)out, g.V, g.dof, nrhs, e.stream);
@@ -257,6 +262,61 @@ mgmlmc_status mgmlmc_last_solve_stats(const mgmlmc_ctx *cctx, int *iters, double
   return guard(ctx, [&] {
     if (iters) *iters = E(ctx).last_solve.iters;
     if (residual) *residual = E(ctx).last_solve.residual;
+  });
+}
+
+mgmlmc_status mgmlmc_learned_init(mgmlmc_ctx *ctx, int channels, uint64_t seed) {
+  return guard(ctx, [&] { E(ctx).net_init(channels, seed); });
+}
+
+mgmlmc_status mgmlmc_learned_size(const mgmlmc_ctx *cctx, int64_t *n_complex) {
+  mgmlmc_ctx *ctx = const_cast<mgmlmc_ctx *>(cctx);
+  return guard(ctx, [&] {
+    if (!n_complex) throw mg::Error(MGMLMC_ERR_ARG, "NULL argument");
+    *n_complex = E(ctx).net_size();
+  });
+}
+
+mgmlmc_status mgmlmc_learned_weights(mgmlmc_ctx *ctx, double *host, int set) {
+  return guard(ctx, [&] {
+    if (!host) throw mg::Error(MGMLMC_ERR_ARG, "NULL argument");
+    E(ctx).net_weights(host, set != 0);
+  });
+}
+
+mgmlmc_status mgmlmc_learned_loss_grad(mgmlmc_ctx *ctx, const double *r, int nrhs, double *loss,
+                                       double *grad_host) {
+  return guard(ctx, [&] {
+    mg::Engine &e = E(ctx);
+    if (!r || !loss || !grad_host || nrhs < 1) throw mg::Error(MGMLMC_ERR_ARG, "bad arguments");
+    const int64_t tot = e.net_size();
+    if (tot <= 0) throw mg::Error(MGMLMC_ERR_STATE, "network not initialised");
+    double2 *g = nullptr;
+    MG_CUDA(cudaMalloc(&g, sizeof(double2) * tot));
+    try {
+      *loss = e.net_loss_grad<double>((const double2 *)r, nrhs, g);
+      MG_CUDA(cudaMemcpy(grad_host, g, sizeof(double2) * tot, cudaMemcpyDeviceToHost));
+    } catch (...) {
+      cudaFree(g);
+      throw;
+    }
+    cudaFree(g);
+  });
+}
+
+mgmlmc_status mgmlmc_learned_train(mgmlmc_ctx *ctx, const mgmlmc_train_params *p,
+                                   mgmlmc_train_result *out) {
+  return guard(ctx, [&] {
+    if (!p || !out) throw mg::Error(MGMLMC_ERR_ARG, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    E(ctx).net_train(*p, *out);
+  });
+}
+
+mgmlmc_status mgmlmc_learned_stats(const mgmlmc_ctx *cctx, int64_t *fallbacks) {
+  mgmlmc_ctx *ctx = const_cast<mgmlmc_ctx *>(cctx);
+  return guard(ctx, [&] {
+    if (fallbacks) *fallbacks = E(ctx).net_fallbacks();
   });
 }
 

@@ -79,6 +79,8 @@ Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
 Engine::~Engine() {
   cudaStreamSynchronize(stream);
   free_hierarchy();
+  net_free();
+  if (pool_) cudaFree(pool_);
   dfree(levels_[0].U64);
   dfree(levels_[0].U32);
   for (auto &kv : ws_) cudaFree(kv.second.first);
@@ -247,7 +249,8 @@ void Engine::set_solver(const mgmlmc_solver_params &p) {
       p.coarse_iters < 1 || p.coarse_iters > 64 ||
       (p.precision != MGMLMC_FP64 && p.precision != MGMLMC_FP32) ||
       (p.precision == MGMLMC_FP32 && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)) ||
-      (p.smoother != MGMLMC_SMOOTHER_MR && p.smoother != MGMLMC_SMOOTHER_SAP) || p.sap_iters < 1 ||
+      (p.smoother != MGMLMC_SMOOTHER_MR && p.smoother != MGMLMC_SMOOTHER_SAP &&
+       p.smoother != MGMLMC_SMOOTHER_LEARNED) || p.sap_iters < 1 ||
       p.sap_iters > 64)
     throw Error(MGMLMC_ERR_ARG, "invalid solver parameters");
   drop_graphs();  // captured preconditioners bake in smoother / inner iteration counts
@@ -343,10 +346,14 @@ void Engine::noise(int l, uint64_t seed, uint64_t sample0, uint64_t term, uint64
 }
 
 // ------------------------------------------------------------------ MG cycle
-// minimal-residual smoothing: res holds r - D z on entry and exit
+// Smoothing: res holds r - D z on entry and exit.  Level 0: SAP sweeps
+// (MGMLMC_SMOOTHER_SAP), followed for MGMLMC_SMOOTHER_LEARNED by one learned
+// step z += alpha N(res) with the residual-minimising alpha (so the step can
+// only lower ||res||); other levels / MR: minimal-residual steps.
 template <typename T> void Engine::smooth(int l, C<T> *z, C<T> *res, int nrhs) {
   const int64_t n = levels_[l].g.n();
-  if (l == 0 && sp_.smoother == MGMLMC_SMOOTHER_SAP && sap_b_[0] > 0) {
+  const bool learned = l == 0 && sp_.smoother == MGMLMC_SMOOTHER_LEARNED;
+  if (l == 0 && (sp_.smoother == MGMLMC_SMOOTHER_SAP || learned) && sap_b_[0] > 0) {
     C<T> *e = ws<T>("sape", l, (size_t)n * nrhs);
     const C<T> *U;
     if constexpr (sizeof(T) == 8) U = levels_[0].U64; else U = levels_[0].U32;
@@ -361,6 +368,18 @@ template <typename T> void Engine::smooth(int l, C<T> *z, C<T> *res, int nrhs) {
       cudaEvent_t a = prof_begin();
       sap_sweep<T>(res, z, e, U, g, sap_b_, m0_, sp_.sap_iters, nrhs, stream);
       prof_end(a, sizeof(T) == 8 ? K_SAP64 : K_SAP32, bytes, flops);
+    }
+    // training pairs: the residuals the learned step will see -- after SAP,
+    // in the post-smoother, i.e. once the coarse grid has acted
+    if (post_smooth_) record<T>(res, nrhs);
+    if (learned) {
+      if (!net_.C) throw Error(MGMLMC_ERR_STATE, "learned smoother selected but the network is not initialised");
+      C<T> *q = ws<T>("netq", l, (size_t)n * nrhs);
+      double2 *d = ws<double>("netd", l, 2 * (size_t)nrhs);
+      net_forward<T>(res, e, nrhs);
+      apply_D<T>(0, e, q, nrhs);
+      dot_qr<T>(q, res, n, nrhs, d, d + nrhs, partials((size_t)reduce_blocks(n) * nrhs * 2), stream);
+      mr_dir_update<T>(z, res, e, q, d, d + nrhs, n, nrhs, stream);
     }
     return;
   }
@@ -411,12 +430,14 @@ template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nr
     apply_D<T>(l, z, q, nrhs);
     MG_CUDA(cudaMemcpyAsync(res, r, sizeof(C<T>) * n * nrhs, cudaMemcpyDeviceToDevice, stream));
     axpby<T>(-1.0, q, 1.0, res, n, nrhs, stream);
+    post_smooth_ = true;
     smooth<T>(l, z, res, nrhs);
+    post_smooth_ = false;
   }
 }
 
 template <typename T> void Engine::precond_top(int l, const C<T> *r, C<T> *z, int nrhs) {
-  if (!graphs_on_ || prof_ || l == n_levels() - 1) {
+  if (!graphs_on_ || prof_ || recording_ || l == n_levels() - 1) {
     precond<T>(l, r, z, nrhs);
     return;
   }
@@ -637,6 +658,41 @@ SolveInfo Engine::solve(int l, const double2 *b, double2 *x, int nrhs) {
     dense_apply<double>(levels_[l].Dinv64, b, x, (int)n, nrhs, stream);
     info.iters = 0;
     info.residual = 0.0;
+  } else if (l == 0 && sp_.smoother == MGMLMC_SMOOTHER_LEARNED) {
+    // learned smoother first; the true residual judges it, SAP takes over
+    // when it does not converge within a quarter of the iteration budget
+    const int full = sp_.max_iter;
+    sp_.max_iter = std::max(1, full / 4);
+    bool ok = true;
+    try {
+      info = sp_.precision == MGMLMC_FP32
+                 ? solve_mixed(l, b, x, nrhs)
+                 : fgmres<double>(l, b, x, nrhs, sp_.tol, sp_.max_iter, sp_.restart, true, false);
+      ok = info.converged;
+    } catch (const Error &e) {
+      if (e.code != MGMLMC_ERR_NUMERIC && e.code != MGMLMC_ERR_NOT_CONVERGED) {
+        sp_.max_iter = full;
+        throw;
+      }
+      ok = false;
+    }
+    sp_.max_iter = full;
+    if (!ok) {
+      ++net_.fallbacks;
+      sp_.smoother = MGMLMC_SMOOTHER_SAP;
+      drop_graphs();
+      try {
+        info = sp_.precision == MGMLMC_FP32
+                   ? solve_mixed(l, b, x, nrhs)
+                   : fgmres<double>(l, b, x, nrhs, sp_.tol, sp_.max_iter, sp_.restart, true, false);
+      } catch (...) {
+        sp_.smoother = MGMLMC_SMOOTHER_LEARNED;
+        drop_graphs();
+        throw;
+      }
+      sp_.smoother = MGMLMC_SMOOTHER_LEARNED;
+      drop_graphs();
+    }
   } else if (sp_.precision == MGMLMC_FP32) {
     info = solve_mixed(l, b, x, nrhs);
   } else {

@@ -65,6 +65,19 @@ struct KStat {
   double flops = 0.0;  // algorithmic flops
 };
 
+// Learned smoother: three gauge-covariant layers, channels 1 -> C -> C -> 1.
+struct Net {
+  int C = 0;
+  int cin[3] = {0, 0, 0}, cout[3] = {0, 0, 0};
+  int64_t cnt[3] = {0, 0, 0};  // complex weights per layer
+  double2 *W64[3] = {nullptr, nullptr, nullptr};
+  float2 *W32[3] = {nullptr, nullptr, nullptr};
+  double2 *m[3] = {nullptr, nullptr, nullptr};
+  double2 *v[3] = {nullptr, nullptr, nullptr};
+  int adam_t = 0;
+  int64_t fallbacks = 0;
+};
+
 class Engine {
  public:
   Engine(const int dims[4], cudaStream_t s);
@@ -97,6 +110,16 @@ class Engine {
                  std::vector<double> &var, int &R);
   void disconnected(int kind, int t, int n_samples, uint64_t seed, uint64_t first,
                     std::vector<double> &mean, std::vector<double> &var, int &R);
+
+  // learned smoother
+  void net_init(int channels, uint64_t seed);
+  int64_t net_size() const;
+  void net_weights(double *host, bool set);
+  template <typename T> void net_forward(const C<T> *in, C<T> *out, int B);
+  // loss sum_b ||r_b - D N(r_b)||^2 / ||r_b||^2 and dL/dW* (device, [layer][cnt])
+  template <typename T> double net_loss_grad(const C<T> *r, int B, double2 *grad);
+  void net_train(const mgmlmc_train_params &p, mgmlmc_train_result &out);
+  int64_t net_fallbacks() const { return net_.fallbacks; }
 
   void get_prolongator(int l, double *host);
   void get_coarse_op(int l, double *host);
@@ -162,6 +185,13 @@ class Engine {
   cudaEvent_t prof_begin();
   void prof_end(cudaEvent_t a, int cls, double bytes, double flops);
   double2 *partials(size_t count);
+  Net net_;
+  void net_free();
+  bool recording_ = false;    // copy level-0 post-smoother inputs into the training pool
+  bool post_smooth_ = false;  // set while the post-smoother of a cycle runs
+  float2 *pool_ = nullptr;    // [pool_cap][n0] FP32
+  int pool_n_ = 0, pool_cap_ = 0;
+  template <typename T> void record(const C<T> *res, int nrhs);
   bool graphs_on_ = true;
   bool capturing_ = false;
   struct GraphEntry {

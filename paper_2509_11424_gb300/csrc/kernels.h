@@ -35,6 +35,11 @@ void scale_rhs(const C<T> *x, C<T> *y, const double *scal, int64_t n, int nrhs, 
 template <typename T>
 void mr_update(C<T> *z, C<T> *r, const C<T> *q, const double2 *dqr, const double2 *nq,
                int64_t n, int nrhs, cudaStream_t s);
+// minimal-residual step along a given direction e with q = D e:
+// alpha = <q, r> / <q, q>; z += alpha e; r -= alpha q
+template <typename T>
+void mr_dir_update(C<T> *z, C<T> *r, const C<T> *e, const C<T> *q, const double2 *dqr,
+                   const double2 *nq, int64_t n, int nrhs, cudaStream_t s);
 // out = in converted between precisions
 template <typename To, typename From>
 void convert(const C<From> *in, C<To> *out, int64_t n, cudaStream_t s);
@@ -105,6 +110,25 @@ template <typename T> size_t sap_smem_bytes(const int b[4]);
 template <typename T>
 void sap_sweep(C<T> *r, C<T> *z, C<T> *e, const C<T> *U, Geom g, const int b[4], double m0,
                int block_iters, int nrhs, cudaStream_t s);
+
+// ------------------------------------------------------------------ learned smoother
+// gauge-covariant layer phi[o] = sum_c sum_h W[h][o][c] T_h psi[c]; activations
+// [b][c][site][12], weights [h][o][c][4][4]
+template <typename T>
+void glayer_forward(const C<T> *in, C<T> *out, const C<T> *W, const C<T> *U, Geom g, int Cin,
+                    int Cout, int B, cudaStream_t s);
+// input gradient: out[c] = sum_o sum_h W[h][o][c]^H T_rev(h) gin[o]
+template <typename T>
+void glayer_adjoint(const C<T> *gin, C<T> *out, const C<T> *W, const C<T> *U, Geom g, int Cin,
+                    int Cout, int B, cudaStream_t s);
+int glayer_wgrad_chunks(const Geom &g);
+// out[h][o][c][16] = sum_b sum_x gin[b][o](x) (T_h in[b][c])(x)^H (colour summed)
+template <typename T>
+void glayer_wgrad(const C<T> *gin, const C<T> *in, const C<T> *U, Geom g, int Cin, int Cout, int B,
+                  double2 *partial, double2 *out, cudaStream_t s);
+// Adam (t = step count from 1) on complex weights given dL/dW* (times scale)
+void adam_step(double2 *W, const double2 *grad, double2 *m, double2 *v, int64_t count, double lr,
+               double b1, double b2, double eps, int t, double scale, cudaStream_t s);
 
 // ------------------------------------------------------------------ transfer
 // P is stored [X][c][k][row] (row fastest).

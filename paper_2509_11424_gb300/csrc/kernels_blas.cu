@@ -169,6 +169,23 @@ __global__ void mr_update_kernel(C<T> *__restrict__ z, C<T> *__restrict__ res,
   }
 }
 
+// z += alpha e; r -= alpha q with alpha = <q, r> / <q, q> per rhs
+template <typename T>
+__global__ void mr_dir_kernel(C<T> *__restrict__ z, C<T> *__restrict__ res, const C<T> *__restrict__ e,
+                              const C<T> *__restrict__ q, const double2 *__restrict__ dqr,
+                              const double2 *__restrict__ nq, int64_t n) {
+  const int r = blockIdx.y;
+  const double qq = nq[r].x;
+  const double2 d = dqr[r];
+  const C<T> al = qq > 1e-280 ? mk<T>((T)(d.x / qq), (T)(d.y / qq)) : mk<T>((T)0, (T)0);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = r * n + i;
+    z[o] = cfma(al, e[o], z[o]);
+    res[o] = cfma(cneg(al), q[o], res[o]);
+  }
+}
+
 template <typename To, typename From>
 __global__ void convert_kernel(const C<From> *__restrict__ in, C<To> *__restrict__ out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -393,6 +410,14 @@ void mr_update(C<T> *z, C<T> *r, const C<T> *q, const double2 *dqr, const double
   MG_LAUNCH_CHECK();
 }
 
+template <typename T>
+void mr_dir_update(C<T> *z, C<T> *r, const C<T> *e, const C<T> *q, const double2 *dqr,
+                   const double2 *nq, int64_t n, int nrhs, cudaStream_t s) {
+  const int gx = (grid_for(n) + nrhs - 1) / nrhs + 1;
+  mr_dir_kernel<T><<<dim3(gx, nrhs), 256, 0, s>>>(z, r, e, q, dqr, nq, n);
+  MG_LAUNCH_CHECK();
+}
+
 template <typename To, typename From>
 void convert(const C<From> *in, C<To> *out, int64_t n, cudaStream_t s) {
   convert_kernel<To, From><<<grid_for(n), 256, 0, s>>>(in, out, n);
@@ -445,7 +470,9 @@ void gmres_solve(GmresState st, cudaStream_t s) {
                              int64_t, int, cudaStream_t);                                        \
   template void check_finite<T>(const C<T> *, int64_t, int *, cudaStream_t);               \
   template void dot_qr<T>(const C<T> *, const C<T> *, int64_t, int, double2 *, double2 *,        \
-                          double2 *, cudaStream_t);
+                          double2 *, cudaStream_t);                                            \
+  template void mr_dir_update<T>(C<T> *, C<T> *, const C<T> *, const C<T> *, const double2 *,    \
+                                 const double2 *, int64_t, int, cudaStream_t);
 INST(double)
 INST(float)
 template void convert<float, double>(const C<double> *, C<float> *, int64_t, cudaStream_t);

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, 'libmgmlmc.so')
 MAX_LEVELS = 4
 FP64, FP32 = 0, 1
 EST_PLAIN, EST_ORTHOGONAL = 0, 1
-OP_D, OP_RESTRICT, OP_PROLONG, OP_PROJECT, OP_SOLVE, OP_GAMMA5, OP_SMOOTH = range(7)
+OP_D, OP_RESTRICT, OP_PROLONG, OP_PROJECT, OP_SOLVE, OP_GAMMA5, OP_SMOOTH, OP_NET = range(8)
 TERM_PLAIN, TERM_O, TERM_F, TERM_COARSEST = 0, 16, 32, 48
 STATUS = {0: 'OK', 1: 'ERR_ARG', 2: 'ERR_STATE', 3: 'ERR_OOM', 4: 'ERR_CUDA',
           5: 'ERR_NOT_CONVERGED', 6: 'ERR_NUMERIC'}
@@ -66,6 +66,20 @@ class TermResult(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class TrainParams(ctypes.Structure):
+    _fields_ = [('channels', ctypes.c_int), ('steps', ctypes.c_int), ('batch', ctypes.c_int),
+                ('pool', ctypes.c_int), ('lr', ctypes.c_double), ('seed', ctypes.c_uint64)]
+
+
+class TrainResult(ctypes.Structure):
+    _fields_ = [('steps', ctypes.c_int), ('pairs', ctypes.c_int), ('loss_init', ctypes.c_double),
+                ('loss_first', ctypes.c_double), ('loss_last', ctypes.c_double),
+                ('seconds', ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class MgmlmcError(RuntimeError):
     def __init__(self, status, message):
         super().__init__('%s: %s' % (STATUS.get(status, status), message))
@@ -102,6 +116,12 @@ _SIGNATURES = {
     'mgmlmc_profile': [_P, _I],
     'mgmlmc_kernel_launches': [],
     'mgmlmc_project_noalloc': [_P, _I, _I, _P, _P, _I],
+    'mgmlmc_learned_init': [_P, _I, _U64],
+    'mgmlmc_learned_size': [_P, ctypes.POINTER(_I64)],
+    'mgmlmc_learned_weights': [_P, _P, _I],
+    'mgmlmc_learned_loss_grad': [_P, _P, _I, ctypes.POINTER(_D), _P],
+    'mgmlmc_learned_train': [_P, ctypes.POINTER(TrainParams), ctypes.POINTER(TrainResult)],
+    'mgmlmc_learned_stats': [_P, ctypes.POINTER(_I64)],
     'mgmlmc_profile_stats': [_P, _I, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_D),
                              ctypes.POINTER(_D)],
 }
@@ -181,7 +201,7 @@ def mgmlmc_set_mass(ctx, m0):
     _check(ctx, lib().mgmlmc_set_mass(ctx, float(m0)))
 
 
-SMOOTHER_MR, SMOOTHER_SAP = 0, 1
+SMOOTHER_MR, SMOOTHER_SAP, SMOOTHER_LEARNED = 0, 1, 2
 
 
 def solver_params(tol=1e-12, max_iter=2000, restart=16, smoother_steps=4, coarse_iters=8,
@@ -316,3 +336,36 @@ def mgmlmc_kernel_launches():
 
 def mgmlmc_project_noalloc(ctx, level, precision, inp, out, nrhs=1):
     _check(ctx, lib().mgmlmc_project_noalloc(ctx, level, precision, ptr(inp), ptr(out), nrhs))
+
+
+def mgmlmc_learned_init(ctx, channels=16, seed=5000):
+    _check(ctx, lib().mgmlmc_learned_init(ctx, channels, seed))
+
+
+def mgmlmc_learned_size(ctx):
+    n = _I64()
+    _check(ctx, lib().mgmlmc_learned_size(ctx, ctypes.byref(n)))
+    return n.value
+
+
+def mgmlmc_learned_weights(ctx, host, set_):
+    _check(ctx, lib().mgmlmc_learned_weights(ctx, ptr(host), int(set_)))
+
+
+def mgmlmc_learned_loss_grad(ctx, r, nrhs, grad_host):
+    loss = _D()
+    _check(ctx, lib().mgmlmc_learned_loss_grad(ctx, ptr(r), nrhs, ctypes.byref(loss), ptr(grad_host)))
+    return loss.value
+
+
+def mgmlmc_learned_train(ctx, channels=16, steps=200, batch=8, pool=2000, lr=1e-3, seed=5000):
+    p = TrainParams(channels, steps, batch, pool, lr, seed)
+    out = TrainResult()
+    _check(ctx, lib().mgmlmc_learned_train(ctx, ctypes.byref(p), ctypes.byref(out)))
+    return out.as_dict()
+
+
+def mgmlmc_learned_stats(ctx):
+    n = _I64()
+    _check(ctx, lib().mgmlmc_learned_stats(ctx, ctypes.byref(n)))
+    return n.value

@@ -44,7 +44,8 @@ def test_binding_covers_header():
 def test_struct_layouts_match_c():
     from paper_2509_11424_gb300 import mgmlmc as M
     structs = {'mgmlmc_mg_params': M.MgParams, 'mgmlmc_solver_params': M.SolverParams,
-               'mgmlmc_est_params': M.EstParams, 'mgmlmc_term_result': M.TermResult}
+               'mgmlmc_est_params': M.EstParams, 'mgmlmc_term_result': M.TermResult,
+               'mgmlmc_train_params': M.TrainParams, 'mgmlmc_train_result': M.TrainResult}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mgmlmc.h"', 'int main(void){']
     for cname, py in structs.items():
         lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
