@@ -51,7 +51,7 @@ PEAKS_FILE = os.path.join(ROOT, 'MEASURED_PEAKS.json')
 FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate from the hardware table
 FP32_PEAK_TFLOPS = 80.0  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 SOLVER = dict(tol=1e-12, restart=24, max_iter=2000, smoother=1, smoother_steps=1, sap_iters=4,
-              coarse_iters=8, inner_tol=1e-6)
+              coarse_iters=4, inner_tol=1e-6, coarse_smoother_steps=4)
 KERNELS = {0: 'wilson_dslash_fp64', 1: 'wilson_dslash_fp32', 2: 'coarse_stencil_fp64',
            3: 'coarse_stencil_fp32', 4: 'sap_sweep_fp64', 5: 'sap_sweep_fp32'}
 # dram bytes per launch of a kernel from an ncu capture, keyed by (kernel,
@@ -248,6 +248,8 @@ def main():
     ap.add_argument('--no-cpu', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--m0', type=float, default=None, help='override the tuned mass (exploration)')
+    ap.add_argument('--learned', type=int, default=2, help='channels of the learned smoother (0: off)')
+    ap.add_argument('--train-steps', type=int, default=200)
     args = ap.parse_args()
 
     dist, rank, world, local = dist_init()
@@ -256,7 +258,7 @@ def main():
         if dist:
             dist.destroy_process_group()
         return
-    wl = workload()
+    wl = workload() if (args.m0 is None or os.path.exists(MASS_FILE)) else {}
     m0 = args.m0 if args.m0 is not None else wl['m0']
 
     import torch
@@ -275,6 +277,14 @@ def main():
     M.mgmlmc_build_hierarchy(ctx, mgp)
     torch.cuda.synchronize()
     t_setup = time.time() - t_setup
+    train = None
+    main_solver = dict(SOLVER)
+    if args.learned > 0:
+        # gauge-covariant network trained on the solver's own post-SAP residuals
+        train = M.mgmlmc_learned_train(ctx, channels=args.learned, steps=args.train_steps, batch=8,
+                                       pool=2000, lr=1e-3, seed=5002)
+        main_solver['smoother'] = M.SMOOTHER_LEARNED
+        M.mgmlmc_set_solver(ctx, precision=prec, **main_solver)
     print('kernel launches after setup: %d' % M.mgmlmc_kernel_launches(), file=sys.stderr)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device='cuda')  # 256 MB > L2
 
@@ -377,6 +387,13 @@ def main():
         pval, pdet = time_to_variance(merge_terms(pres), 1, pms / args.compare_steps, args.compare_steps)
         compare['plain_hutchinson_same_solver'] = dict(value=pval * (pdet['eps'] / det['eps']) ** 2,
                                                        ms_per_step=pms / args.compare_steps, detail=pdet)
+        if args.learned > 0:
+            M.mgmlmc_set_solver(ctx, precision=prec, **SOLVER)
+            step(15000)
+            sres, sms = timed(15001, args.compare_steps)
+            sval, sdet = time_to_variance(merge_terms(sres), 1, sms / args.compare_steps, args.compare_steps)
+            compare['mlmc_same_precision_sap_only'] = dict(value=sval, ms_per_step=sms / args.compare_steps,
+                                                           detail=sdet)
         if prec == M.FP32:
             M.mgmlmc_set_solver(ctx, precision=M.FP64, **SOLVER)
             step(20000)
@@ -386,7 +403,7 @@ def main():
             pres, pms = timed(30000, 1, M.EST_PLAIN)
             p64, p64d = time_to_variance(merge_terms(pres), 1, pms, 1)
             compare['plain_hutchinson_fp64'] = dict(value=p64 * (p64d['eps'] / det['eps']) ** 2, ms_per_step=pms)
-            M.mgmlmc_set_solver(ctx, precision=prec, **SOLVER)
+        M.mgmlmc_set_solver(ctx, precision=prec, **main_solver)
 
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -421,11 +438,13 @@ def main():
             'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64' if prec == M.FP64 else 'f32+f64',
             'data': 'synthetic',
             'config': {'workload': '16^4 Wilson-Dirac, SU(3) exp(i 0.4 H) seed 1002, m0 %.4f, orthogonal '
-                                   'MG-MLMC 3 levels (4^4, 2^4 aggregates, 16 tv), SAP-MG FGMRES, Z4 batch %d '
-                                   'per term per step, solves to 1e-12' % (m0, B),
+                                   'MG-MLMC 3 levels (4^4, 2^4 aggregates, 16 tv), SAP%s-MG FGMRES, Z4 batch %d '
+                                   'per term per step, solves to 1e-12'
+                                   % (m0, ' + learned(%d ch)' % args.learned if args.learned else '', B),
                        'global_batch': B * nterm * world, 'lattice': list(DIMS), 'rel_eps': REL_EPS,
                        'l2': 'flushed between steps (256 MB write)', 'parallelism': 'samples sharded, dp%d' % world},
-            'setup_s': t_setup, 'detail': det, 'compare': compare, 'roofline': roof, 'dslash': dslash,
+            'setup_s': t_setup, 'learned': train, 'learned_fallbacks': M.mgmlmc_learned_stats(ctx),
+            'detail': det, 'compare': compare, 'roofline': roof, 'dslash': dslash,
             'clocks': clk, 'e2e': e2e, 'gpu_launches': launches,
             'kernel_stats': {KERNELS[c]: kst[c] for c in kst}, 'cpu_baseline': cpu,
         }

@@ -109,6 +109,7 @@ typedef struct {
                           number of blocks in every direction (blocks of 4^4,
                           else 2^4); otherwise MR is used. */
   int sap_iters;       /* MR iterations inside each SAP block */
+  int coarse_smoother_steps; /* MR steps of the smoother on levels >= 1 */
 } mgmlmc_solver_params;
 
 #define MGMLMC_SMOOTHER_MR 0
@@ -167,7 +168,10 @@ mgmlmc_status mgmlmc_set_gauge(mgmlmc_ctx *ctx, const double *U, int on_device);
 /* Bare mass m0 of the Wilson operator.  Invalidates the hierarchy. */
 mgmlmc_status mgmlmc_set_mass(mgmlmc_ctx *ctx, double m0);
 /* Solver parameters (defaults: tol 1e-12, max_iter 2000, restart 16,
- * smoother_steps 4, coarse_iters 8, FP64, MR smoother, sap_iters 4). */
+ * smoother_steps 4, coarse_iters 8, FP64, MR smoother, sap_iters 4,
+ * coarse_smoother_steps 4).  smoother_steps counts the fine-level smoother
+ * applications (SAP sweeps or MR steps) of each pre- and post-smoothing; the
+ * learned step, when selected, follows the SAP sweeps of the post-smoother. */
 mgmlmc_status mgmlmc_set_solver(mgmlmc_ctx *ctx, const mgmlmc_solver_params *p);
 /* Import the N_tv test vectors of level `level` (0 .. L-2): n_tv vectors of
  * length n (the level's vector length), one after the other (canonical

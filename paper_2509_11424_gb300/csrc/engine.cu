@@ -59,6 +59,7 @@ Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
   sp_.inner_tol = 1e-6;
   sp_.smoother = MGMLMC_SMOOTHER_MR;
   sp_.sap_iters = 4;
+  sp_.coarse_smoother_steps = 4;
   // SAP blocks: 4^4 when every direction holds an even number of them, else 2^4
   for (int bsz : {4, 2}) {
     int b[4] = {bsz, bsz, bsz, bsz};
@@ -250,7 +251,7 @@ void Engine::set_solver(const mgmlmc_solver_params &p) {
       (p.precision != MGMLMC_FP64 && p.precision != MGMLMC_FP32) ||
       (p.precision == MGMLMC_FP32 && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)) ||
       (p.smoother != MGMLMC_SMOOTHER_MR && p.smoother != MGMLMC_SMOOTHER_SAP &&
-       p.smoother != MGMLMC_SMOOTHER_LEARNED) || p.sap_iters < 1 ||
+       p.smoother != MGMLMC_SMOOTHER_LEARNED) || p.sap_iters < 1 || p.coarse_smoother_steps < 0 ||
       p.sap_iters > 64)
     throw Error(MGMLMC_ERR_ARG, "invalid solver parameters");
   drop_graphs();  // captured preconditioners bake in smoother / inner iteration counts
@@ -372,7 +373,7 @@ template <typename T> void Engine::smooth(int l, C<T> *z, C<T> *res, int nrhs) {
     // training pairs: the residuals the learned step will see -- after SAP,
     // in the post-smoother, i.e. once the coarse grid has acted
     if (post_smooth_) record<T>(res, nrhs);
-    if (learned) {
+    if (learned && post_smooth_) {
       if (!net_.C) throw Error(MGMLMC_ERR_STATE, "learned smoother selected but the network is not initialised");
       C<T> *q = ws<T>("netq", l, (size_t)n * nrhs);
       double2 *d = ws<double>("netd", l, 2 * (size_t)nrhs);
@@ -385,7 +386,8 @@ template <typename T> void Engine::smooth(int l, C<T> *z, C<T> *res, int nrhs) {
   }
   C<T> *q = ws<T>("smq", l, (size_t)n * nrhs);
   double2 *d = ws<double>("smd", l, 2 * (size_t)nrhs);
-  for (int s = 0; s < sp_.smoother_steps; ++s) {
+  const int steps = l == 0 ? sp_.smoother_steps : sp_.coarse_smoother_steps;
+  for (int s = 0; s < steps; ++s) {
     apply_D<T>(l, res, q, nrhs);
     dot_qr<T>(q, res, n, nrhs, d, d + nrhs, partials((size_t)reduce_blocks(n) * nrhs * 2), stream);
     mr_update<T>(z, res, q, d, d + nrhs, n, nrhs, stream);
@@ -426,7 +428,7 @@ template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nr
   else
     fgmres<T>(l + 1, rc, ec, nrhs, 0.0, sp_.coarse_iters, sp_.coarse_iters, true, true);
   prolong_op<T>(ec, z, Pmat<T>(l), L.agg, nrhs, 1.0, stream);
-  if (sp_.smoother_steps > 0) {
+  if ((l == 0 ? sp_.smoother_steps : sp_.coarse_smoother_steps) > 0) {
     apply_D<T>(l, z, q, nrhs);
     MG_CUDA(cudaMemcpyAsync(res, r, sizeof(C<T>) * n * nrhs, cudaMemcpyDeviceToDevice, stream));
     axpby<T>(-1.0, q, 1.0, res, n, nrhs, stream);

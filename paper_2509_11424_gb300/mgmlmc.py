@@ -42,7 +42,8 @@ class SolverParams(ctypes.Structure):
                 ('precision', ctypes.c_int),
                 ('inner_tol', ctypes.c_double),
                 ('smoother', ctypes.c_int),
-                ('sap_iters', ctypes.c_int)]
+                ('sap_iters', ctypes.c_int),
+                ('coarse_smoother_steps', ctypes.c_int)]
 
 
 class EstParams(ctypes.Structure):
@@ -205,9 +206,10 @@ SMOOTHER_MR, SMOOTHER_SAP, SMOOTHER_LEARNED = 0, 1, 2
 
 
 def solver_params(tol=1e-12, max_iter=2000, restart=16, smoother_steps=4, coarse_iters=8,
-                  precision=FP64, inner_tol=1e-6, smoother=SMOOTHER_MR, sap_iters=4):
+                  precision=FP64, inner_tol=1e-6, smoother=SMOOTHER_MR, sap_iters=4,
+                  coarse_smoother_steps=4):
     return SolverParams(tol, max_iter, restart, smoother_steps, coarse_iters, precision, inner_tol,
-                        smoother, sap_iters)
+                        smoother, sap_iters, coarse_smoother_steps)
 
 
 def mgmlmc_set_solver(ctx, params=None, **kw):

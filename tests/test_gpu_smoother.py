@@ -41,7 +41,7 @@ def test_sap_smoother_matches_oracle(dims, bsz, blocks, prec, tol):
 
 def test_mr_smoother_matches_oracle():
     dims = (4, 4, 4, 8)
-    s = Setup(dims, [(2, 2, 2, 2)], [4], eps=0.4, m0=0.1, gseed=93, solver=dict(smoother_steps=3))
+    s = Setup(dims, [(2, 2, 2, 2)], [4], eps=0.4, m0=0.1, gseed=93, solver=dict(smoother_steps=3, coarse_smoother_steps=3))
     try:
         M = s.M
         for level in (0, 1):
