@@ -54,6 +54,8 @@ SOLVER = dict(tol=1e-12, restart=24, max_iter=2000, smoother=1, smoother_steps=1
               coarse_iters=4, inner_tol=1e-6, coarse_smoother_steps=4)
 KERNELS = {0: 'wilson_dslash_fp64', 1: 'wilson_dslash_fp32', 2: 'coarse_stencil_fp64',
            3: 'coarse_stencil_fp32', 4: 'sap_sweep_fp64', 5: 'sap_sweep_fp32'}
+# further event-timed groups (breakdown only; no roofline)
+GROUPS = {6: 'transfer_in_cycle', 7: 'gram_schmidt', 8: 'learned_step', 9: 'coarsest_dense'}
 # dram bytes per launch of a kernel from an ncu capture, keyed by (kernel,
 # sha1 of the kernel sources it was measured on); a stale key gives null
 TRAFFIC = {}
@@ -235,6 +237,48 @@ def reference_arm(args, rank, world):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- Dslash
+def dslash_hbm(M, torch, U16, m0, reps=5):
+    """FP32 Wilson Dslash on a 32^4 lattice (the 16^4 field tiled 2x2x2x2, a
+    valid SU(3) field), 1 and 8 right-hand sides, each launch timed with CUDA
+    events after an L2 flush: the working set (>= 500 MB) is far above L2.
+    Algorithmic bytes per site: (24 nrhs + 36) x 8 B (spinors in and out, four
+    links)."""
+    dims = (32, 32, 32, 32)
+    V = int(np.prod(dims))
+    U = np.tile(U16.reshape(16, 16, 16, 16, 36), (2, 2, 2, 2, 1)).reshape(-1)
+    ctx = M.mgmlmc_create(dims, torch.cuda.current_stream())
+    out = {}
+    try:
+        M.mgmlmc_set_gauge(ctx, U)
+        M.mgmlmc_set_mass(ctx, m0)
+        flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device='cuda')
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+        for nrhs in (1, 8):
+            x = torch.randn((nrhs, V * 12), dtype=torch.complex64, device='cuda')
+            y = torch.empty_like(x)
+            for _ in range(3):
+                M.mgmlmc_apply(ctx, M.OP_D, 0, M.FP32, x, y, nrhs)
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                e0.record()
+                M.mgmlmc_apply(ctx, M.OP_D, 0, M.FP32, x, y, nrhs)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = float(np.median(ts))
+            by = V * (24.0 * nrhs + 36.0) * 8
+            gbs = by / (ms * 1e-3) / 1e9
+            out['nrhs%d' % nrhs] = dict(ms=ms, algorithmic_bytes=by, achieved_gbs=gbs,
+                                        frac_of_measured_hbm=gbs / peaks['hbm_gbs'] if 'hbm_gbs' in peaks else None)
+        out['lattice'] = list(dims)
+    finally:
+        M.mgmlmc_destroy(ctx)
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -250,6 +294,7 @@ def main():
     ap.add_argument('--m0', type=float, default=None, help='override the tuned mass (exploration)')
     ap.add_argument('--learned', type=int, default=2, help='channels of the learned smoother (0: off)')
     ap.add_argument('--train-steps', type=int, default=200)
+    ap.add_argument('--dslash-only', action='store_true', help='only the 32^4 FP32 Dslash measurement')
     args = ap.parse_args()
 
     dist, rank, world, local = dist_init()
@@ -266,6 +311,9 @@ def main():
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     U = synth.gauge_field(DIMS, EPS_GAUGE, GAUGE_SEED)
+    if args.dslash_only:
+        print(json.dumps({'dslash_hbm': dslash_hbm(M, torch, U, m0)}))
+        return
     ctx = M.mgmlmc_create(DIMS, stream)
     prec = M.FP64 if args.precision == 'fp64' else M.FP32
     M.mgmlmc_set_gauge(ctx, U)
@@ -348,6 +396,7 @@ def main():
     torch.cuda.synchronize()
     prof_ms = e0.elapsed_time(e1)
     kst = {c: M.mgmlmc_profile_stats(ctx, c) for c in KERNELS}
+    gst = {GROUPS[c]: M.mgmlmc_profile_stats(ctx, c) for c in GROUPS}
     M.mgmlmc_profile(ctx, 0)
     dom = max(kst, key=lambda c: kst[c]['ms'])
     ks = kst[dom]
@@ -381,26 +430,29 @@ def main():
                       avg_launch_us=ws['ms'] * 1e3 / ws['launches'], nrhs=B,
                       note='16^4 x 8 rhs working set ~0.12 GB is L2-resident within a step')
 
+    dslash_32 = dslash_hbm(M, torch, U, m0) if rank == 0 else None
+
     compare = {}
     if rank == 0 and args.compare_steps > 0:
-        pres, pms = timed(10000, args.compare_steps, M.EST_PLAIN)
+        k0 = args.warmup  # the timed run's first sample batch: identical noise
+        pres, pms = timed(k0, args.compare_steps, M.EST_PLAIN)
         pval, pdet = time_to_variance(merge_terms(pres), 1, pms / args.compare_steps, args.compare_steps)
         compare['plain_hutchinson_same_solver'] = dict(value=pval * (pdet['eps'] / det['eps']) ** 2,
                                                        ms_per_step=pms / args.compare_steps, detail=pdet)
         if args.learned > 0:
             M.mgmlmc_set_solver(ctx, precision=prec, **SOLVER)
-            step(15000)
-            sres, sms = timed(15001, args.compare_steps)
+            step(k0)
+            sres, sms = timed(k0, args.compare_steps)
             sval, sdet = time_to_variance(merge_terms(sres), 1, sms / args.compare_steps, args.compare_steps)
             compare['mlmc_same_precision_sap_only'] = dict(value=sval, ms_per_step=sms / args.compare_steps,
                                                            detail=sdet)
         if prec == M.FP32:
             M.mgmlmc_set_solver(ctx, precision=M.FP64, **SOLVER)
-            step(20000)
-            fres, fms = timed(20001, args.compare_steps)
+            step(k0)
+            fres, fms = timed(k0, args.compare_steps)
             fval, fdet = time_to_variance(merge_terms(fres), 1, fms / args.compare_steps, args.compare_steps)
             compare['mlmc_fp64'] = dict(value=fval, ms_per_step=fms / args.compare_steps, detail=fdet)
-            pres, pms = timed(30000, 1, M.EST_PLAIN)
+            pres, pms = timed(k0, 1, M.EST_PLAIN)
             p64, p64d = time_to_variance(merge_terms(pres), 1, pms, 1)
             compare['plain_hutchinson_fp64'] = dict(value=p64 * (p64d['eps'] / det['eps']) ** 2, ms_per_step=pms)
         M.mgmlmc_set_solver(ctx, precision=prec, **main_solver)
@@ -443,10 +495,10 @@ def main():
                                    % (m0, ' + learned(%d ch)' % args.learned if args.learned else '', B),
                        'global_batch': B * nterm * world, 'lattice': list(DIMS), 'rel_eps': REL_EPS,
                        'l2': 'flushed between steps (256 MB write)', 'parallelism': 'samples sharded, dp%d' % world},
-            'setup_s': t_setup, 'learned': train, 'learned_fallbacks': M.mgmlmc_learned_stats(ctx),
+            'dslash_hbm': dslash_32, 'setup_s': t_setup, 'learned': train, 'learned_fallbacks': M.mgmlmc_learned_stats(ctx),
             'detail': det, 'compare': compare, 'roofline': roof, 'dslash': dslash,
             'clocks': clk, 'e2e': e2e, 'gpu_launches': launches,
-            'kernel_stats': {KERNELS[c]: kst[c] for c in kst}, 'cpu_baseline': cpu,
+            'kernel_stats': {KERNELS[c]: kst[c] for c in kst}, 'group_stats': gst, 'cpu_baseline': cpu,
         }
         print(json.dumps(line))
     M.mgmlmc_destroy(ctx)

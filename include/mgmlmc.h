@@ -336,6 +336,10 @@ mgmlmc_status mgmlmc_learned_stats(const mgmlmc_ctx *ctx, int64_t *fallbacks);
 #define MGMLMC_KERNEL_STENCIL_FP32 3
 #define MGMLMC_KERNEL_SAP_FP64 4 /* one SAP sweep (both colours) */
 #define MGMLMC_KERNEL_SAP_FP32 5
+#define MGMLMC_KERNEL_TRANSFER 6 /* P^H and P inside the multigrid cycle */
+#define MGMLMC_KERNEL_ORTHO 7    /* Gram-Schmidt of the FGMRES basis */
+#define MGMLMC_KERNEL_NET 8      /* learned step: network forward */
+#define MGMLMC_KERNEL_COARSEST 9 /* dense coarsest apply inside the cycle */
 
 /* Number of CUDA kernels this library has launched in this process (all
  * contexts), for counting the launches of a timed region. */

@@ -75,6 +75,7 @@ Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
   levels_[0].U32 = dalloc<float2>((size_t)V * 36);
   scal_ = dalloc<double2>(4096);
   flag_dev_ = dalloc<int>(16);
+  MG_CUDA(cudaMemset(flag_dev_, 0, 16 * sizeof(int)));
 }
 
 Engine::~Engine() {
@@ -311,7 +312,7 @@ template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int
   } else {
     const C<T> *A;
     if constexpr (sizeof(T) == 8) A = L.AT64; else A = L.AT32;
-    stencil_apply<T>(in, out, A, L.g, nrhs, stream);
+    stencil_apply<T>(in, out, A, L.g, nrhs, flag_dev_ + 1, stream);
     const double m = L.g.dof;
     bytes = (double)L.g.V * (9.0 * m * m + 2.0 * m * nrhs) * cs;
     flops = 8.0 * 9.0 * m * m * L.g.V * nrhs;
@@ -377,7 +378,9 @@ template <typename T> void Engine::smooth(int l, C<T> *z, C<T> *res, int nrhs) {
       if (!net_.C) throw Error(MGMLMC_ERR_STATE, "learned smoother selected but the network is not initialised");
       C<T> *q = ws<T>("netq", l, (size_t)n * nrhs);
       double2 *d = ws<double>("netd", l, 2 * (size_t)nrhs);
+      cudaEvent_t pa = prof_begin();
       net_forward<T>(res, e, nrhs);
+      prof_end(pa, K_NET, 0.0, 0.0);
       apply_D<T>(0, e, q, nrhs);
       dot_qr<T>(q, res, n, nrhs, d, d + nrhs, partials((size_t)reduce_blocks(n) * nrhs * 2), stream);
       mr_dir_update<T>(z, res, e, q, d, d + nrhs, n, nrhs, stream);
@@ -422,12 +425,19 @@ template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nr
   MG_CUDA(cudaMemsetAsync(z, 0, sizeof(C<T>) * n * nrhs, stream));
   MG_CUDA(cudaMemcpyAsync(res, r, sizeof(C<T>) * n * nrhs, cudaMemcpyDeviceToDevice, stream));
   smooth<T>(l, z, res, nrhs);
+  cudaEvent_t pr = prof_begin();
   restrict_op<T>(res, rc, Pmat<T>(l), L.agg, nrhs, stream);
-  if (l + 1 == n_levels() - 1)
+  prof_end(pr, K_TRANSFER, 0.0, 0.0);
+  if (l + 1 == n_levels() - 1) {
+    cudaEvent_t pd = prof_begin();
     dense_apply<T>(Dinv<T>(l + 1), rc, ec, (int)nc, nrhs, stream);
-  else
+    prof_end(pd, K_COARSEST, 0.0, 0.0);
+  } else {
     fgmres<T>(l + 1, rc, ec, nrhs, 0.0, sp_.coarse_iters, sp_.coarse_iters, true, true);
+  }
+  cudaEvent_t pp = prof_begin();
   prolong_op<T>(ec, z, Pmat<T>(l), L.agg, nrhs, 1.0, stream);
+  prof_end(pp, K_TRANSFER, 0.0, 0.0);
   if ((l == 0 ? sp_.smoother_steps : sp_.coarse_smoother_steps) > 0) {
     apply_D<T>(l, z, q, nrhs);
     MG_CUDA(cudaMemcpyAsync(res, r, sizeof(C<T>) * n * nrhs, cudaMemcpyDeviceToDevice, stream));
@@ -546,11 +556,15 @@ SolveInfo Engine::fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, in
         else precond_top<T>(l, vi, zi, nrhs);
       }
       apply_D<T>(l, zi, w, nrhs);
+      cudaEvent_t po = prof_begin();
       multi_dot<T>(V, vs, i + 1, w, n, nrhs, st.h1, m + 1, part(i + 1), stream);
       multi_axpy<T>(V, vs, i + 1, w, n, nrhs, st.h1, m + 1, -1.0, stream);
       multi_dot<T>(V, vs, i + 1, w, n, nrhs, st.h2, m + 1, part(i + 1), stream);
       multi_axpy<T>(V, vs, i + 1, w, n, nrhs, st.h2, m + 1, -1.0, stream);
       dot<T>(w, w, n, nrhs, st.nrm, part(1), stream);
+      // unique data of CGS2: the i+1 basis vectors twice for the dots and
+      // twice for the updates, w read/written four times
+      prof_end(po, K_ORTHO, (double)vs * sizeof(C<T>) * (4.0 * (i + 1) + 9.0), 0.0);
       gmres_arnoldi(st, i, stream);
       scale_rhs<T>(w, V + (i + 1) * vs, st.inv, n, nrhs, stream);
       ++it;
@@ -701,6 +715,16 @@ SolveInfo Engine::solve(int l, const double2 *b, double2 *x, int nrhs) {
     info = fgmres<double>(l, b, x, nrhs, sp_.tol, sp_.max_iter, sp_.restart, true, false);
   }
   last_solve = info;
+  {
+    // a TMA staging wait that ran out of its bound sets flag_dev_[1]
+    int tma_err = 0;
+    MG_CUDA(cudaMemcpyAsync(&tma_err, flag_dev_ + 1, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    sync();
+    if (tma_err) {
+      MG_CUDA(cudaMemsetAsync(flag_dev_ + 1, 0, sizeof(int), stream));
+      throw Error(MGMLMC_ERR_CUDA, "a shared-memory staging copy did not complete within its bounded wait");
+    }
+  }
   if (!info.converged)
     throw Error(MGMLMC_ERR_NOT_CONVERGED,
                 "level " + std::to_string(l) + " solve stopped after " + std::to_string(info.iters) +

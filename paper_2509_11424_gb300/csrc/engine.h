@@ -56,7 +56,11 @@ enum KClass {
   K_STENCIL32 = 3,
   K_SAP64 = 4,
   K_SAP32 = 5,
-  K_NCLASS = 8
+  K_TRANSFER = 6,   // restriction + prolongation inside the cycle
+  K_ORTHO = 7,      // Gram-Schmidt of the FGMRES basis (all levels)
+  K_NET = 8,        // learned step (network forward)
+  K_COARSEST = 9,   // dense coarsest-level apply inside the cycle
+  K_NCLASS = 12
 };
 struct KStat {
   int64_t launches = 0;

@@ -86,9 +86,12 @@ void wilson_apply(const C<T> *in, C<T> *out, const C<T> *U, Geom g, double m0, i
 template <typename T>
 void wilson_split(const C<T> *in, C<T> *out9, const C<T> *U, Geom g, double m0, const int b[4],
                   cudaStream_t s);
-// coarse stencil with transposed blocks AT[X][d][j][i]
+// coarse stencil with transposed blocks AT[X][d][j][i]; when they fit, the 9
+// blocks of a site are staged by one TMA bulk copy; err[0] = 2 if a copy
+// does not complete within the bounded wait
 template <typename T>
-void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, cudaStream_t s);
+void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, int *err,
+                   cudaStream_t s);
 // AT = blockwise transpose of the canonical A[X][d][i][j] (nblocks = 9 V)
 template <typename To>
 void stencil_transpose(const double2 *A, C<To> *AT, int64_t nblocks, int m, cudaStream_t s);

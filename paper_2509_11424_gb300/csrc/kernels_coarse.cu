@@ -72,6 +72,111 @@ __global__ void stencil_t_kernel(const C<T> *__restrict__ in, C<T> *__restrict__
   }
 }
 
+// ---- TMA bulk staging (cp.async.bulk + mbarrier) --------------------------
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *mbar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *mbar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+               : "memory");
+}
+// one bulk copy global -> this CTA's shared memory; 16-byte aligned
+// addresses and a byte count that is a multiple of 16
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *mbar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(mbar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false (and *err set) if the copy did not land in time
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, unsigned parity, int *err) {
+  for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(mbar, parity)) return true;
+  if (err) atomicExch(err, 2);
+  return false;
+}
+
+// Same contraction as stencil_t_kernel, with the site's 9 transposed blocks
+// (9 m^2 complex, contiguous) brought into shared memory by one TMA bulk copy
+// issued by thread 0 while the others stage the neighbour vectors; every
+// block entry is then read from shared memory for all right-hand sides.
+template <typename T, int RG>
+__global__ void stencil_tma_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ out,
+                                   const C<T> *__restrict__ AT, Geom g, int nrhs, int *err) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t mbar;
+  const int m = g.dof;
+  C<T> *As = reinterpret_cast<C<T> *>(smem_raw);  // [9][j][i]
+  C<T> *xs = As + 9 * m * m;                        // [9][RG][m]
+  C<T> *part = xs + 9 * RG * m;                     // [9][RG][m]
+  const int X = blockIdx.x;
+  const int i = threadIdx.x, d = threadIdx.y;
+  const int tid = d * blockDim.x + i;
+  const int64_t n = g.n();
+  const unsigned bytes = (unsigned)(9u * m * m * sizeof(C<T>));
+  if (tid == 0) mbar_init(&mbar, 1);
+  __syncthreads();
+  if (tid == 0) {
+    mbar_expect_tx(&mbar, bytes);
+    bulk_g2s(As, AT + (int64_t)X * 9 * m * m, bytes, &mbar);
+  }
+  const int nb = g.neighbor(X, d);
+  bool ready = false;
+  for (int r0 = 0; r0 < nrhs; r0 += RG) {
+    const int rg = nrhs - r0 < RG ? nrhs - r0 : RG;
+#pragma unroll
+    for (int r = 0; r < RG; ++r)
+      if (r < rg) xs[(d * RG + r) * m + i] = in[(int64_t)(r0 + r) * n + (int64_t)nb * m + i];
+    if (!ready) {
+      ready = mbar_wait_bounded(&mbar, 0, err);
+      // the whole block gives up together (no thread may be left at a
+      // barrier); a copy still in flight gets a second bounded wait first
+      if (__syncthreads_or(ready ? 0 : 1)) {
+        if (!ready) mbar_wait_bounded(&mbar, 0, nullptr);
+        return;
+      }
+    }
+    __syncthreads();
+    C<T> acc[RG];
+#pragma unroll
+    for (int r = 0; r < RG; ++r) acc[r] = mk<T>((T)0, (T)0);
+    const C<T> *xd = xs + d * RG * m;
+    const C<T> *Ad = As + d * m * m;
+#pragma unroll 4
+    for (int j = 0; j < m; ++j) {
+      const C<T> a = Ad[j * m + i];
+#pragma unroll
+      for (int r = 0; r < RG; ++r) acc[r] = cfma(a, xd[r * m + j], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < RG; ++r) part[(d * RG + r) * m + i] = acc[r];
+    __syncthreads();
+    if (d == 0) {
+      for (int r = 0; r < rg; ++r) {
+        C<T> v = part[r * m + i];
+#pragma unroll
+        for (int dd = 1; dd < 9; ++dd) v = cadd(v, part[(dd * RG + r) * m + i]);
+        out[(int64_t)(r0 + r) * n + (int64_t)X * m + i] = v;
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // AT[X][d][j][i] = A[X][d][i][j], converted to the storage type To.
 template <typename To>
 __global__ void stencil_transpose_kernel(const double2 *__restrict__ A, C<To> *__restrict__ AT,
@@ -436,10 +541,23 @@ __global__ void dense_trace_kernel(const double2 *__restrict__ M, int n, double2
 }  // namespace
 
 template <typename T>
-void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, cudaStream_t s) {
+void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, int *err,
+                   cudaStream_t s) {
   constexpr int RG = sizeof(T) == 4 ? 8 : 4;
   const int m = g.dof;
   if (m > 112) throw Error(1, "coarse stencil: more than 112 dofs per site");
+  const size_t sm_tma = (size_t)(9 * m * m + 2 * 9 * RG * m) * sizeof(C<T>);
+  if (sm_tma <= 200 * 1024) {
+    static bool configured_tma = false;
+    if (!configured_tma) {
+      MG_CUDA(cudaFuncSetAttribute(stencil_tma_kernel<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   200 * 1024));
+      configured_tma = true;
+    }
+    stencil_tma_kernel<T, RG><<<g.V, dim3(m, 9), sm_tma, s>>>(in, out, AT, g, nrhs, err);
+    MG_LAUNCH_CHECK();
+    return;
+  }
   const size_t sm = (size_t)2 * 9 * RG * m * sizeof(C<T>);
   static bool configured = false;
   if (!configured) {
@@ -545,7 +663,8 @@ void dense_trace(const double2 *M, int n, double2 *out, cudaStream_t s) {
 }
 
 #define INST(T)                                                                                 \
-  template void stencil_apply<T>(const C<T> *, C<T> *, const C<T> *, Geom, int, cudaStream_t);  \
+  template void stencil_apply<T>(const C<T> *, C<T> *, const C<T> *, Geom, int, int *,         \
+                                 cudaStream_t);                                                 \
   template void stencil_split<T>(const C<T> *, C<T> *, const C<T> *, Geom, const int *,         \
                                  cudaStream_t);                                                 \
   template void restrict_op<T>(const C<T> *, C<T> *, const C<T> *, const AggMap &, int,         \

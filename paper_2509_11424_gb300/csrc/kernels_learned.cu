@@ -61,19 +61,23 @@ __device__ __forceinline__ void transported(const C<T> *__restrict__ psi, const 
   }
 }
 
-// forward: one thread per site, blockIdx.y = output channel, blockIdx.z = sample
-template <typename T>
+// forward: one thread per site computing OG output channels at once, so each
+// transported input T_h psi[c] is formed once for the whole group;
+// blockIdx.y = output group, blockIdx.z = sample
+template <typename T, int OG>
 __global__ void __launch_bounds__(128) glayer_forward_kernel(const C<T> *__restrict__ in,
                                                              C<T> *__restrict__ out,
                                                              const C<T> *__restrict__ W,
                                                              const C<T> *__restrict__ U, Geom g,
                                                              int Cin, int Cout) {
   extern __shared__ unsigned char smem_raw[];
-  C<T> *Ws = reinterpret_cast<C<T> *>(smem_raw);  // [h][c][16] for this o
-  const int o = blockIdx.y, b = blockIdx.z;
-  for (int e = threadIdx.x; e < 9 * Cin * 16; e += blockDim.x) {
-    const int h = e / (Cin * 16), rem = e - h * Cin * 16, c = rem / 16, k = rem % 16;
-    Ws[e] = W[(((int64_t)h * Cout + o) * Cin + c) * 16 + k];
+  C<T> *Ws = reinterpret_cast<C<T> *>(smem_raw);  // [h][c][og][16] for this group
+  const int o0 = blockIdx.y * OG, b = blockIdx.z;
+  const int og = Cout - o0 < OG ? Cout - o0 : OG;
+  for (int e = threadIdx.x; e < 9 * Cin * OG * 16; e += blockDim.x) {
+    const int h = e / (Cin * OG * 16), rem = e - h * Cin * OG * 16;
+    const int c = rem / (OG * 16), rem2 = rem - c * OG * 16, k = rem2 / 16, q = rem2 % 16;
+    Ws[e] = k < og ? W[(((int64_t)h * Cout + o0 + k) * Cin + c) * 16 + q] : mk<T>((T)0, (T)0);
   }
   __syncthreads();
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -81,28 +85,38 @@ __global__ void __launch_bounds__(128) glayer_forward_kernel(const C<T> *__restr
   const int64_t n = g.n();
   int cc[4];
   g.coords(s, cc);
-  C<T> acc[12];
+  C<T> acc[OG][12];
 #pragma unroll
-  for (int i = 0; i < 12; ++i) acc[i] = mk<T>((T)0, (T)0);
+  for (int k = 0; k < OG; ++k)
+#pragma unroll
+    for (int i = 0; i < 12; ++i) acc[k][i] = mk<T>((T)0, (T)0);
   for (int c = 0; c < Cin; ++c) {
     const C<T> *psi = in + ((int64_t)b * Cin + c) * n;
     for (int h = 0; h < 9; ++h) {
       C<T> t[12];
       transported<T>(psi, U, g, s, cc, h, t);
-      const C<T> *w = Ws + (h * Cin + c) * 16;
 #pragma unroll
-      for (int sp = 0; sp < 4; ++sp)
+      for (int k = 0; k < OG; ++k) {
+        const C<T> *w = Ws + ((h * Cin + c) * OG + k) * 16;
 #pragma unroll
-        for (int sq = 0; sq < 4; ++sq) {
-          const C<T> wv = w[sp * 4 + sq];
+        for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-          for (int a = 0; a < 3; ++a) acc[sp * 3 + a] = cfma(wv, t[sq * 3 + a], acc[sp * 3 + a]);
-        }
+          for (int sq = 0; sq < 4; ++sq) {
+            const C<T> wv = w[sp * 4 + sq];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) acc[k][sp * 3 + a] = cfma(wv, t[sq * 3 + a], acc[k][sp * 3 + a]);
+          }
+      }
     }
   }
-  C<T> *o_ = out + ((int64_t)b * Cout + o) * n + (int64_t)s * 12;
 #pragma unroll
-  for (int i = 0; i < 12; ++i) o_[i] = acc[i];
+  for (int k = 0; k < OG; ++k) {
+    if (k < og) {
+      C<T> *o_ = out + ((int64_t)b * Cout + o0 + k) * n + (int64_t)s * 12;
+#pragma unroll
+      for (int i = 0; i < 12; ++i) o_[i] = acc[k][i];
+    }
+  }
 }
 
 // adjoint: out[c](x) = sum_o sum_h W[h][o][c]^H (T_rev(h) gin[o])(x)
@@ -251,18 +265,27 @@ __global__ void adam_kernel(double2 *__restrict__ W, const double2 *__restrict__
 
 }  // namespace
 
+template <typename T, int OG>
+static void glayer_forward_og(const C<T> *in, C<T> *out, const C<T> *W, const C<T> *U, Geom g, int Cin,
+                              int Cout, int B, cudaStream_t s) {
+  const size_t sm = (size_t)9 * Cin * OG * 16 * sizeof(C<T>);
+  static bool configured = false;
+  if (!configured) {
+    MG_CUDA(cudaFuncSetAttribute(glayer_forward_kernel<T, OG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 160 * 1024));
+    configured = true;
+  }
+  glayer_forward_kernel<T, OG><<<dim3(div_up(g.V, 128), div_up(Cout, OG), B), 128, sm, s>>>(in, out, W, U,
+                                                                                          g, Cin, Cout);
+  MG_LAUNCH_CHECK();
+}
+
 template <typename T>
 void glayer_forward(const C<T> *in, C<T> *out, const C<T> *W, const C<T> *U, Geom g, int Cin,
                     int Cout, int B, cudaStream_t s) {
-  const size_t sm = (size_t)9 * Cin * 16 * sizeof(C<T>);
-  static bool configured = false;
-  if (!configured) {
-    MG_CUDA(cudaFuncSetAttribute(glayer_forward_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 100 * 1024));
-    configured = true;
-  }
-  glayer_forward_kernel<T><<<dim3(div_up(g.V, 128), Cout, B), 128, sm, s>>>(in, out, W, U, g, Cin, Cout);
-  MG_LAUNCH_CHECK();
+  if (Cout == 1) glayer_forward_og<T, 1>(in, out, W, U, g, Cin, Cout, B, s);
+  else if (Cout == 2) glayer_forward_og<T, 2>(in, out, W, U, g, Cin, Cout, B, s);
+  else glayer_forward_og<T, 4>(in, out, W, U, g, Cin, Cout, B, s);
 }
 
 template <typename T>

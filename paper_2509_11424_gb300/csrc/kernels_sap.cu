@@ -88,10 +88,11 @@ __device__ __forceinline__ void active_block(const SapGeom &sg, int i, int color
   bc[0] = 2 * k + ((color + bc[1] + bc[2] + bc[3]) & 1);
 }
 
+// sum (v0, v1, v2) over the block in the storage precision (warp shuffles,
+// then the per-warp sums in a fixed order), result in out3 for all threads;
+// FP32 sums here keep the block MR iterations off the slow FP64 pipe
 template <typename T>
-__device__ __forceinline__ double2 block_reduce2(double v0, double v1, double v2, double2 *sh,
-                                                 double *out3) {
-  // sum (v0, v1, v2) over the block; deterministic tree order
+__device__ __forceinline__ void block_reduce3(T v0, T v1, T v2, T *s, T *out3) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     v0 += __shfl_down_sync(0xffffffffu, v0, o);
@@ -99,7 +100,6 @@ __device__ __forceinline__ double2 block_reduce2(double v0, double v1, double v2
     v2 += __shfl_down_sync(0xffffffffu, v2, o);
   }
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = (blockDim.x + 31) >> 5;
-  double *s = reinterpret_cast<double *>(sh);
   if (l == 0) {
     s[3 * w] = v0;
     s[3 * w + 1] = v1;
@@ -107,7 +107,7 @@ __device__ __forceinline__ double2 block_reduce2(double v0, double v1, double v2
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double a = 0, b = 0, c = 0;
+    T a = 0, b = 0, c = 0;
     for (int i = 0; i < nw; ++i) {
       a += s[3 * i];
       b += s[3 * i + 1];
@@ -118,7 +118,6 @@ __device__ __forceinline__ double2 block_reduce2(double v0, double v1, double v2
     out3[2] = c;
   }
   __syncthreads();
-  return make_double2(out3[0], out3[1]);
 }
 
 template <typename T, int DIR>
@@ -155,8 +154,8 @@ __global__ void __launch_bounds__(256) sap_block_kernel(C<T> *__restrict__ r, C<
   const int sites = sg.sites;
   C<T> *Us = reinterpret_cast<C<T> *>(smem_raw);  // [sites][4][9]
   C<T> *rho = Us + sites * 36;                      // [sites][12]
-  double2 *red = reinterpret_cast<double2 *>(rho + sites * 12);  // reduction scratch
-  double *out3 = reinterpret_cast<double *>(red + 64);
+  T *red = reinterpret_cast<T *>(rho + sites * 12);  // reduction scratch [3 * warps]
+  T *out3 = red + 96;
   const int64_t n = sg.g.n();
   const int rr = blockIdx.y;
   C<T> *rv = r + rr * n;
@@ -200,9 +199,10 @@ __global__ void __launch_bounds__(256) sap_block_kernel(C<T> *__restrict__ r, C<
       qr_im = fma(q[i].x, p.y, fma(-q[i].y, p.x, qr_im));
       qq = fma(q[i].x, q[i].x, fma(q[i].y, q[i].y, qq));
     }
-    block_reduce2<T>((double)qr_re, (double)qr_im, (double)qq, red, out3);
-    const double den = out3[2];
-    const C<T> al = den > 1e-280 ? mk<T>((T)(out3[0] / den), (T)(out3[1] / den)) : mk<T>((T)0, (T)0);
+    block_reduce3<T>(qr_re, qr_im, qq, red, out3);
+    const T den = out3[2];
+    const T tiny = sizeof(T) == 4 ? (T)1e-30 : (T)1e-280;
+    const C<T> al = den > tiny ? mk<T>(out3[0] / den, out3[1] / den) : mk<T>((T)0, (T)0);
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
       const C<T> p = rho[ls * 12 + i];
@@ -291,7 +291,7 @@ bool sap_feasible(const Geom &g, const int b[4]) {
 template <typename T>
 size_t sap_smem_bytes(const int b[4]) {
   const int sites = b[0] * b[1] * b[2] * b[3];
-  return (size_t)sites * 48 * sizeof(C<T>) + 64 * sizeof(double2) + 4 * sizeof(double);
+  return (size_t)sites * 48 * sizeof(C<T>) + 100 * sizeof(T);
 }
 
 template <typename T>

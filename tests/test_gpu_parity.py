@@ -66,7 +66,7 @@ def test_dslash_fp64(dims):
         M.mgmlmc_destroy(ctx)
 
 
-@pytest.mark.parametrize('dims', [(4, 4, 4, 4), ODD])
+@pytest.mark.parametrize('dims', [(4, 4, 4, 4), ODD, (6, 2, 2, 3), (3, 2, 2, 2)])  # last two: V % 32 != 0
 def test_dslash_fp32(dims):
     U = synth.gauge_field(dims, 0.5, 7)
     ctx = M.mgmlmc_create(dims, torch.cuda.current_stream())
