@@ -255,9 +255,9 @@ def dslash_hbm(M, torch, U16, m0, reps=5):
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device='cuda')
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-        for nrhs in (1, 8):
-            x = torch.randn((nrhs, V * 12), dtype=torch.complex64, device='cuda')
-            y = torch.empty_like(x)
+        hbm = peaks.get('hbm_gbs')
+
+        def timed(x, y, nrhs):
             for _ in range(3):
                 M.mgmlmc_apply(ctx, M.OP_D, 0, M.FP32, x, y, nrhs)
             ts = []
@@ -268,11 +268,24 @@ def dslash_hbm(M, torch, U16, m0, reps=5):
                 e1.record()
                 torch.cuda.synchronize()
                 ts.append(e0.elapsed_time(e1))
-            ms = float(np.median(ts))
+            return float(np.median(ts))
+
+        for nrhs in (1, 8):
+            x = torch.randn((nrhs, V * 12), dtype=torch.complex64, device='cuda')
+            y = torch.empty_like(x)
             by = V * (24.0 * nrhs + 36.0) * 8
+            per_variant = {}
+            for v in (-1, 0, 1, 2, 3):
+                M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, v)
+                per_variant[str(v)] = round(by / (timed(x, y, nrhs) * 1e-3) / 1e9, 1)
+            M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, M.VARIANT_AUTOTUNE)
+            ms = timed(x, y, nrhs)
             gbs = by / (ms * 1e-3) / 1e9
-            out['nrhs%d' % nrhs] = dict(ms=ms, algorithmic_bytes=by, achieved_gbs=gbs,
-                                        frac_of_measured_hbm=gbs / peaks['hbm_gbs'] if 'hbm_gbs' in peaks else None)
+            out['nrhs%d' % nrhs] = dict(
+                ms=ms, algorithmic_bytes=by, achieved_gbs=gbs,
+                frac_of_measured_hbm=gbs / hbm if hbm else None,
+                variant=M.mgmlmc_get_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, nrhs),
+                gbs_per_variant=per_variant)
         out['lattice'] = list(dims)
     finally:
         M.mgmlmc_destroy(ctx)

@@ -357,6 +357,24 @@ mgmlmc_status mgmlmc_profile(mgmlmc_ctx *ctx, int enable);
 mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *launches,
                                    double *ms, double *bytes, double *flops);
 
+/* ---- kernel variants ------------------------------------------------------ */
+
+/* Kernels with selectable variants. */
+#define MGMLMC_VARIANT_DSLASH_FP32 0
+/* Choose the variant of a kernel for later calls: for the FP32 fine Wilson
+ * operator -2 = autotune (default: the first call per right-hand-side count
+ * outside graph capture times every variant on that call's operands and
+ * keeps the fastest), -1 = one thread per site, 0 .. 3 = the shared-memory
+ * staged kernel: 0 and 1 stage links with the spinors in a ring of 2 or 3
+ * operand sets, 2 and 3 load links into registers beside a ring of 2 or 3
+ * spinor sets.  Every variant computes the same sums in the same order.
+ * Returns MGMLMC_ERR_ARG for an unknown kernel or variant. */
+mgmlmc_status mgmlmc_set_kernel_variant(mgmlmc_ctx *ctx, int kernel, int variant);
+/* The variant that calls with nrhs right-hand sides use (-2 while an
+ * autotuned choice is not yet made). */
+mgmlmc_status mgmlmc_get_kernel_variant(const mgmlmc_ctx *ctx, int kernel, int nrhs,
+                                        int *variant);
+
 #ifdef __cplusplus
 }
 #endif

@@ -337,4 +337,21 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
   });
 }
 
+mgmlmc_status mgmlmc_set_kernel_variant(mgmlmc_ctx *ctx, int kernel, int variant) {
+  return guard(ctx, [&] {
+    if (kernel != MGMLMC_VARIANT_DSLASH_FP32) throw mg::Error(MGMLMC_ERR_ARG, "unknown kernel");
+    E(ctx).set_dslash_variant(variant);
+  });
+}
+
+mgmlmc_status mgmlmc_get_kernel_variant(const mgmlmc_ctx *cctx, int kernel, int nrhs,
+                                        int *variant) {
+  mgmlmc_ctx *ctx = const_cast<mgmlmc_ctx *>(cctx);
+  return guard(ctx, [&] {
+    if (kernel != MGMLMC_VARIANT_DSLASH_FP32) throw mg::Error(MGMLMC_ERR_ARG, "unknown kernel");
+    if (!variant) throw mg::Error(MGMLMC_ERR_ARG, "variant is null");
+    *variant = E(ctx).dslash_variant(nrhs);
+  });
+}
+
 }  // extern "C"

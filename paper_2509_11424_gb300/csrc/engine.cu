@@ -73,6 +73,7 @@ Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
   levels_[0].fine = true;
   levels_[0].U64 = dalloc<double2>((size_t)V * 36);
   levels_[0].U32 = dalloc<float2>((size_t)V * 36);
+  levels_[0].UD32 = dalloc<float2>((size_t)V * 36);
   scal_ = dalloc<double2>(4096);
   flag_dev_ = dalloc<int>(16);
   MG_CUDA(cudaMemset(flag_dev_, 0, 16 * sizeof(int)));
@@ -85,6 +86,7 @@ Engine::~Engine() {
   if (pool_) cudaFree(pool_);
   dfree(levels_[0].U64);
   dfree(levels_[0].U32);
+  dfree(levels_[0].UD32);
   for (auto &kv : ws_) cudaFree(kv.second.first);
   for (auto &p : pending_) {
     cudaEventDestroy(p.a);
@@ -236,6 +238,7 @@ void Engine::set_gauge(const double *U, bool on_device) {
     throw Error(MGMLMC_ERR_NUMERIC, "gauge field contains NaN or Inf");
   }
   convert<float, double>(levels_[0].U64, levels_[0].U32, (int64_t)cnt, stream);
+  link_soa(levels_[0].U32, levels_[0].UD32, fine_.V, stream);
   have_gauge_ = true;
   free_hierarchy();
 }
@@ -290,6 +293,50 @@ void Engine::free_hierarchy() {
 }
 
 // ------------------------------------------------------------------ operators
+void Engine::set_dslash_variant(int v) {
+  const int nv = wilson_staged_variants();
+  if (v < -2 || v >= nv) throw Error(MGMLMC_ERR_ARG, "dslash variant out of range");
+  dslash_force_ = v;
+  dslash_tuned_.clear();
+  drop_graphs();
+}
+
+int Engine::dslash_variant(int nrhs) const {
+  if (dslash_force_ != -2) return dslash_force_;
+  auto it = dslash_tuned_.find(nrhs);
+  return it == dslash_tuned_.end() ? -2 : it->second;
+}
+
+int Engine::dslash_pick(int nrhs, const float2 *in, float2 *out) {
+  if (dslash_force_ != -2) return dslash_force_;
+  auto it = dslash_tuned_.find(nrhs);
+  if (it != dslash_tuned_.end()) return it->second;
+  if (capturing_) return 1;
+  // every variant computes the same sums in the same order, so timing them on
+  // the caller's operands leaves `out` correct whichever runs last
+  const Level &L = levels_[0];
+  cudaEvent_t a, b;
+  MG_CUDA(cudaEventCreate(&a));
+  MG_CUDA(cudaEventCreate(&b));
+  int pick = 1;
+  float best = 1e30f;
+  for (int v = -1; v < wilson_staged_variants(); ++v) {
+    wilson_apply<float>(in, out, L.U32, L.UD32, L.g, m0_, nrhs, v, stream);
+    MG_CUDA(cudaEventRecord(a, stream));
+    for (int rep = 0; rep < 3; ++rep)
+      wilson_apply<float>(in, out, L.U32, L.UD32, L.g, m0_, nrhs, v, stream);
+    MG_CUDA(cudaEventRecord(b, stream));
+    MG_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    MG_CUDA(cudaEventElapsedTime(&ms, a, b));
+    if (ms < best) { best = ms; pick = v; }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  dslash_tuned_[nrhs] = pick;
+  return pick;
+}
+
 template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int nrhs) {
   const Level &L = levels_.at(l);
   cudaEvent_t a = nullptr;
@@ -302,9 +349,12 @@ template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int
   double bytes, flops;
   int cls;
   if (L.fine) {
-    const C<T> *U;
-    if constexpr (sizeof(T) == 8) U = L.U64; else U = L.U32;
-    wilson_apply<T>(in, out, U, L.g, m0_, nrhs, stream);
+    if constexpr (sizeof(T) == 8) {
+      wilson_apply<double>(in, out, L.U64, nullptr, L.g, m0_, nrhs, -1, stream);
+    } else {
+      const int v = dslash_pick(nrhs, in, out);
+      wilson_apply<float>(in, out, L.U32, L.UD32, L.g, m0_, nrhs, v, stream);
+    }
     // unique data: nrhs spinors in and out, 4 links per site; 1368 flop per site
     bytes = (double)L.g.V * (24.0 * nrhs + 36.0) * cs;
     flops = 1368.0 * L.g.V * nrhs;

@@ -19,6 +19,7 @@ struct Level {
   bool fine = false;
   double2 *U64 = nullptr;  // fine links [V][4][3][3]
   float2 *U32 = nullptr;
+  float2 *UD32 = nullptr;  // FP32 links structure-of-arrays [4][3][3][V] (staged Dslash)
   double2 *A64 = nullptr;   // coarse stencil, canonical [V][9][dof][dof]
   double2 *AT64 = nullptr;  // the same blocks transposed [V][9][j][i] (apply)
   float2 *AT32 = nullptr;
@@ -140,6 +141,12 @@ class Engine {
   void profile(bool on);
   KStat kstat(int cls);
 
+  // FP32 Dslash kernel variant per rhs count: -2 = autotune on the first call
+  // outside graph capture (every variant timed on that call's operands, the
+  // fastest kept), -1 = one thread per site, 0.. = staged pipeline depth
+  void set_dslash_variant(int v);
+  int dslash_variant(int nrhs) const;
+
  private:
   template <typename T> C<T> *ws(const std::string &name, int l, size_t count);
   void contraction_vectors(int kind, int nb, double2 *x, double2 *B, double2 *Bt);
@@ -207,6 +214,9 @@ class Engine {
   std::map<std::tuple<int, int, int>, GraphEntry> graphs_;
   void drop_graphs();
   cudaEvent_t ev_enter_ = nullptr, ev_leave_ = nullptr;
+  int dslash_force_ = -2;
+  std::map<int, int> dslash_tuned_;
+  int dslash_pick(int nrhs, const float2 *in, float2 *out);
 };
 
 }  // namespace mg

@@ -79,9 +79,17 @@ void gmres_arnoldi(GmresState st, int i, cudaStream_t s);
 void gmres_solve(GmresState st, cudaStream_t s);
 
 // ------------------------------------------------------------------ operators
+// D psi for nrhs right-hand sides.  FP32 with the structure-of-arrays links
+// UDs, 16-byte aligned in/out and variant >= 0 runs the shared-memory staged
+// kernel (variant 0 .. wilson_staged_variants() - 1 picks the pipeline depth
+// and whether links are staged or loaded into registers); otherwise the
+// one-thread-per-site kernel on the canonical links U.
 template <typename T>
-void wilson_apply(const C<T> *in, C<T> *out, const C<T> *U, Geom g, double m0, int nrhs,
-                  cudaStream_t s);
+void wilson_apply(const C<T> *in, C<T> *out, const C<T> *U, const C<T> *UDs, Geom g, double m0,
+                  int nrhs, int variant, cudaStream_t s);
+int wilson_staged_variants();
+// UDs[mu][a][b][s] = U[s][mu][a][b]
+void link_soa(const float2 *U, float2 *UDs, int V, cudaStream_t s);
 // the 9 hop-class parts of D (Galerkin): out9[h] for h = 0..8, single rhs.
 template <typename T>
 void wilson_split(const C<T> *in, C<T> *out9, const C<T> *U, Geom g, double m0, const int b[4],

@@ -125,6 +125,8 @@ _SIGNATURES = {
     'mgmlmc_learned_stats': [_P, ctypes.POINTER(_I64)],
     'mgmlmc_profile_stats': [_P, _I, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_D),
                              ctypes.POINTER(_D)],
+    'mgmlmc_set_kernel_variant': [_P, _I, _I],
+    'mgmlmc_get_kernel_variant': [_P, _I, _I, ctypes.POINTER(_I)],
 }
 
 
@@ -334,6 +336,20 @@ def mgmlmc_profile_stats(ctx, kernel_class):
 
 def mgmlmc_kernel_launches():
     return int(lib().mgmlmc_kernel_launches())
+
+
+VARIANT_DSLASH_FP32 = 0
+VARIANT_AUTOTUNE, VARIANT_PER_SITE = -2, -1
+
+
+def mgmlmc_set_kernel_variant(ctx, kernel, variant):
+    _check(ctx, lib().mgmlmc_set_kernel_variant(ctx, kernel, variant))
+
+
+def mgmlmc_get_kernel_variant(ctx, kernel, nrhs):
+    v = _I()
+    _check(ctx, lib().mgmlmc_get_kernel_variant(ctx, kernel, nrhs, ctypes.byref(v)))
+    return v.value
 
 
 def mgmlmc_project_noalloc(ctx, level, precision, inp, out, nrhs=1):

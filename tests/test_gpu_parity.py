@@ -66,22 +66,55 @@ def test_dslash_fp64(dims):
         M.mgmlmc_destroy(ctx)
 
 
-@pytest.mark.parametrize('dims', [(4, 4, 4, 4), ODD, (6, 2, 2, 3), (3, 2, 2, 2)])  # last two: V % 32 != 0
-def test_dslash_fp32(dims):
+# V % 32 != 0 for (6, 2, 2, 3) and (3, 2, 2, 2); 32-site tiles straddle x rows
+# for L_x = 12 and 48; (16, 4, 4, 4) puts two x rows in one tile
+FP32_DIMS = [(4, 4, 4, 4), ODD, (6, 2, 2, 3), (3, 2, 2, 2), (12, 4, 2, 2), (48, 2, 2, 2),
+             (16, 4, 4, 4)]
+
+
+@pytest.mark.parametrize('dims', FP32_DIMS)
+@pytest.mark.parametrize('nrhs', [2, 5])
+def test_dslash_fp32(dims, nrhs):
+    """Every FP32 kernel variant (per-site and the four staged ones) against
+    the oracle to 1e-5, and all variants bit-identical to each other (they add
+    the same terms in the same order)."""
     U = synth.gauge_field(dims, 0.5, 7)
     ctx = M.mgmlmc_create(dims, torch.cuda.current_stream())
     try:
         M.mgmlmc_set_gauge(ctx, U)
         M.mgmlmc_set_mass(ctx, 0.1)
         n = dirac.volume(dims) * 12
-        x = synth.complex_normal((2, n), 8).astype(np.complex64)
+        x = synth.complex_normal((nrhs, n), 8).astype(np.complex64)
         xd = dev(x, torch.complex64)
-        yd = torch.empty_like(xd)
-        M.mgmlmc_apply(ctx, M.OP_D, 0, M.FP32, xd, yd, 2)
-        y = host(yd)
-        for r in range(2):
+        outs = []
+        for v in (-1, 0, 1, 2, 3):
+            M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, v)
+            assert M.mgmlmc_get_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, nrhs) == v
+            yd = torch.full_like(xd, float('nan'))
+            M.mgmlmc_apply(ctx, M.OP_D, 0, M.FP32, xd, yd, nrhs)
+            outs.append(host(yd))
+        for r in range(nrhs):
             want = dirac.apply_wilson(U, x[r].astype(np.complex128), 0.1, dims)
-            assert rel(y[r], want) < 1e-5
+            assert rel(outs[0][r], want) < 1e-5
+        for o in outs[1:]:
+            assert np.array_equal(o, outs[0])
+        # autotuned choice: made on the first call, then reported
+        M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, M.VARIANT_AUTOTUNE)
+        assert M.mgmlmc_get_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, nrhs) == -2
+        yd = torch.empty_like(xd)
+        M.mgmlmc_apply(ctx, M.OP_D, 0, M.FP32, xd, yd, nrhs)
+        assert np.array_equal(host(yd), outs[0])
+        assert M.mgmlmc_get_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, nrhs) in (-1, 0, 1, 2, 3)
+    finally:
+        M.mgmlmc_destroy(ctx)
+
+
+def test_dslash_variant_bad_args():
+    ctx = M.mgmlmc_create((4, 4, 4, 4), torch.cuda.current_stream())
+    try:
+        for kern, v in ((0, 4), (0, -3), (1, 0)):
+            with pytest.raises(M.MgmlmcError):
+                M.mgmlmc_set_kernel_variant(ctx, kern, v)
     finally:
         M.mgmlmc_destroy(ctx)
 
