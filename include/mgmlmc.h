@@ -234,12 +234,27 @@ typedef enum {
   MGMLMC_OP_NET = 7       /* out = N(in), the learned network (level 0)       */
 } mgmlmc_op;
 
+/* OR-ed into op of mgmlmc_apply: level-0 MGMLMC_FP32 vectors are already in
+ * the library's internal order (see mgmlmc_reorder), so no reordering pass
+ * runs around the operator.  Other levels and precisions are unaffected. */
+#define MGMLMC_LAYOUT_INTERNAL 0x100
+
 /* Apply an operator to nrhs device vectors.  precision selects the storage
  * type of in/out (complex double for MGMLMC_FP64, complex float for
  * MGMLMC_FP32; MGMLMC_OP_SOLVE accepts MGMLMC_FP64 only, its internal
- * precision is the solver's).  in and out must not overlap. */
+ * precision is the solver's).  in and out must not overlap.  Level-0 FP32
+ * vectors are reordered to and from the internal order around the operator
+ * unless op carries MGMLMC_LAYOUT_INTERNAL. */
 mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op, int level, int precision,
                            const void *in, void *out, int nrhs);
+/* Reorder nrhs level-0 complex-float device vectors between the canonical
+ * layout and the internal one, where the library keeps FP32 fine-level
+ * vectors structure-of-arrays: complex component i (spin-major, 0..11) of
+ * site s at ((i / 2) V + s) * 2 + i % 2, so that consecutive sites are
+ * contiguous for each pair of components.  to_internal = 1: in canonical,
+ * out internal; 0: the reverse.  in and out must not overlap. */
+mgmlmc_status mgmlmc_reorder(mgmlmc_ctx *ctx, const void *in, void *out, int nrhs,
+                             int to_internal);
 /* The projection of MGMLMC_OP_PROJECT, out = (I - P_l P_l^H) in, without any
  * device allocation during the call.  The paper has no counterpart: this is
  * for callers that cannot allocate device memory while they run -- code
@@ -364,12 +379,16 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
 /* Choose the variant of a kernel for later calls: for the FP32 fine Wilson
  * operator -2 = autotune (default: the first call per right-hand-side count
  * outside graph capture times every variant on that call's operands and
- * keeps the fastest), -1 = one thread per site, 0 .. 3 = the shared-memory
- * staged kernel: 0 and 1 stage links with the spinors in a ring of 2 or 3
- * operand sets, 2 and 3 load links into registers beside a ring of 2 or 3
- * spinor sets.  Every variant computes the same sums in the same order.
- * Returns MGMLMC_ERR_ARG for an unknown kernel or variant. */
+ * keeps the fastest), 0 .. 4 = fixed: one thread per site, 128-thread
+ * blocks; 0 and 1 one right-hand side per thread with registers for 6 or 8
+ * resident blocks per SM; 2 and 3 two right-hand sides per thread with
+ * registers for 4 or 5 blocks; 4 one right-hand side with the next operand
+ * set loaded while the current one is used (4 blocks).
+ * Every variant computes the same sums in the same order.  Returns
+ * MGMLMC_ERR_ARG for an unknown kernel or variant. */
 mgmlmc_status mgmlmc_set_kernel_variant(mgmlmc_ctx *ctx, int kernel, int variant);
+/* Number of fixed variants of a kernel (-1 for an unknown kernel). */
+int mgmlmc_kernel_variants(int kernel);
 /* The variant that calls with nrhs right-hand sides use (-2 while an
  * autotuned choice is not yet made). */
 mgmlmc_status mgmlmc_get_kernel_variant(const mgmlmc_ctx *ctx, int kernel, int nrhs,

@@ -178,10 +178,22 @@ mgmlmc_status mgmlmc_disconnected_loop(mgmlmc_ctx *ctx, int kind, int t, int n_s
   });
 }
 
-mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op, int level, int precision, const void *in,
+mgmlmc_status mgmlmc_reorder(mgmlmc_ctx *ctx, const void *in, void *out, int nrhs,
+                             int to_internal) {
+  return guard(ctx, [&] {
+    mg::Engine &e = E(ctx);
+    if (!in || !out || nrhs < 1) throw mg::Error(MGMLMC_ERR_ARG, "bad buffers or nrhs");
+    mg::relayout<float, float>((const float2 *)in, (float2 *)out, nullptr, e.level(0).g.V, nrhs,
+                               to_internal != 0, e.stream);
+  });
+}
+
+mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op_flags, int level, int precision, const void *in,
                            void *out, int nrhs) {
   return guard(ctx, [&] {
     mg::Engine &e = E(ctx);
+    const bool internal = (op_flags & MGMLMC_LAYOUT_INTERNAL) != 0;
+    const int op = op_flags & ~MGMLMC_LAYOUT_INTERNAL;
     if (!in || !out || nrhs < 1) throw mg::Error(MGMLMC_ERR_ARG, "bad buffers or nrhs");
     if (precision != MGMLMC_FP64 && precision != MGMLMC_FP32) throw mg::Error(MGMLMC_ERR_ARG, "bad precision");
     if (level < 0 || level >= e.n_levels()) throw mg::Error(MGMLMC_ERR_ARG, "level out of range");
@@ -190,6 +202,34 @@ mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op, int level, int precision, co
     if (needs_next && (!e.ready() || level + 1 >= e.n_levels()))
       throw mg::Error(MGMLMC_ERR_STATE, "no transfer operator at that level");
     if (level > 0 && !e.ready()) throw mg::Error(MGMLMC_ERR_STATE, "hierarchy not built");
+    const bool fine_op = op == MGMLMC_OP_D || op == MGMLMC_OP_RESTRICT || op == MGMLMC_OP_PROLONG ||
+                         op == MGMLMC_OP_PROJECT || op == MGMLMC_OP_SMOOTH || op == MGMLMC_OP_NET;
+    if (!dp && level == 0 && fine_op && !internal) {
+      // FP32 level-0 vectors live structure-of-arrays inside the library:
+      // the caller's canonical buffers are reordered in and out
+      const mg::Geom &g = e.level(0).g;
+      const size_t cnt = (size_t)g.n() * nrhs;
+      const bool fin = op != MGMLMC_OP_PROLONG, fout = op != MGMLMC_OP_RESTRICT;
+      const float2 *src = (const float2 *)in;
+      float2 *dst = (float2 *)out;
+      if (fin) {
+        float2 *t = e.scratch32("api_in32", cnt);
+        mg::relayout<float, float>(src, t, nullptr, g.V, nrhs, true, e.stream);
+        src = t;
+      }
+      if (fout) dst = e.scratch32("api_out32", cnt);
+      switch (op) {
+        case MGMLMC_OP_D: e.apply_D<float>(0, src, dst, nrhs); break;
+        case MGMLMC_OP_RESTRICT: e.restrict_to<float>(0, src, dst, nrhs); break;
+        case MGMLMC_OP_PROLONG: e.prolong_from<float>(0, src, dst, nrhs, 0.0); break;
+        case MGMLMC_OP_PROJECT: e.project_out<float>(0, src, dst, nrhs); break;
+        case MGMLMC_OP_SMOOTH: e.smooth_apply<float>(0, src, dst, nrhs); break;
+        default: e.net_forward<float>(src, dst, nrhs); break;
+      }
+      if (fout) mg::relayout<float, float>(dst, (float2 *)out, nullptr, g.V, nrhs, false, e.stream);
+      MG_CUDA(cudaGetLastError());
+      return;
+    }
     switch (op) {
       case MGMLMC_OP_D:
         if (dp) e.apply_D<double>(level, (const double2 *)in, (double2 *)out, nrhs);
@@ -335,6 +375,10 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
     if (bytes) *bytes = k.bytes;
     if (flops) *flops = k.flops;
   });
+}
+
+int mgmlmc_kernel_variants(int kernel) {
+  return kernel == MGMLMC_VARIANT_DSLASH_FP32 ? mg::wilson_fp32_variants() : -1;
 }
 
 mgmlmc_status mgmlmc_set_kernel_variant(mgmlmc_ctx *ctx, int kernel, int variant) {

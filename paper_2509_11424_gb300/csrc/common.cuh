@@ -84,6 +84,19 @@ struct Geom {
   }
 };
 
+// FP32 vectors of the fine level are stored structure-of-arrays: complex
+// component i (0..11, spin-major) of site s sits at ((i >> 1) V + s) * 2 +
+// (i & 1), so the 16-byte chunk i >> 1 of consecutive sites is contiguous and
+// a thread-per-site access is coalesced.  FP64 fine vectors and every coarse
+// vector keep the canonical order s * dof + i.
+__host__ __device__ __forceinline__ int64_t soa_index(int64_t s, int i, int64_t V) {
+  return ((int64_t)(i >> 1) * V + s) * 2 + (i & 1);
+}
+template <bool SOA>
+__host__ __device__ __forceinline__ int64_t fidx(int64_t s, int i, int64_t V) {
+  return SOA ? soa_index(s, i, V) : s * 12 + i;
+}
+
 // Block aggregation of a level (Sec. 2.2): aggregates are blocks of extent
 // b[4]; rows of an (aggregate, chirality) pair are site_in_block * half + d.
 struct AggMap {
@@ -94,6 +107,7 @@ struct AggMap {
   int half;       // fine.dof / 2
   int sites;      // sites per aggregate
   int rows;       // sites * half
+  int soa = 0;    // fine vectors in the FP32 fine-level (structure-of-arrays) order
   // fine dof index of (aggregate X, chirality c, row)
   __host__ __device__ __forceinline__ int64_t fine_index(int X, int c, int row) const {
     int cc[4];
@@ -106,6 +120,7 @@ struct AggMap {
     r[3] = sia / b[2];
     int f[4];
     for (int i = 0; i < 4; ++i) f[i] = cc[i] * b[i] + r[i];
+    if (soa) return soa_index(fine.index(f), c * half + d, fine.V);
     return (int64_t)fine.index(f) * fine.dof + c * half + d;
   }
   // aggregate, chirality and row of fine dof i

@@ -19,7 +19,7 @@ struct Level {
   bool fine = false;
   double2 *U64 = nullptr;  // fine links [V][4][3][3]
   float2 *U32 = nullptr;
-  float2 *UD32 = nullptr;  // FP32 links structure-of-arrays [4][3][3][V] (staged Dslash)
+  float2 *UD32 = nullptr;  // FP32 links structure-of-arrays [4][3][3][V] (FP32 kernels)
   double2 *A64 = nullptr;   // coarse stencil, canonical [V][9][dof][dof]
   double2 *AT64 = nullptr;  // the same blocks transposed [V][9][j][i] (apply)
   float2 *AT32 = nullptr;
@@ -140,10 +140,12 @@ class Engine {
 
   void profile(bool on);
   KStat kstat(int cls);
+  // engine-owned FP32 scratch on level 0 (reordering caller vectors)
+  float2 *scratch32(const std::string &name, size_t count) { return ws<float>(name, 0, count); }
 
   // FP32 Dslash kernel variant per rhs count: -2 = autotune on the first call
   // outside graph capture (every variant timed on that call's operands, the
-  // fastest kept), -1 = one thread per site, 0.. = staged pipeline depth
+  // fastest kept), 0 .. wilson_fp32_variants() - 1 = fixed
   void set_dslash_variant(int v);
   int dslash_variant(int nrhs) const;
 
@@ -151,6 +153,9 @@ class Engine {
   template <typename T> C<T> *ws(const std::string &name, int l, size_t count);
   void contraction_vectors(int kind, int nb, double2 *x, double2 *B, double2 *Bt);
   template <typename T> const C<T> *Pmat(int l) const;
+  // the aggregation map of level l for vectors of type T (FP32 level-0
+  // vectors are structure-of-arrays)
+  template <typename T> AggMap agg_of(int l) const;
   template <typename T> const C<T> *Dinv(int l) const;
 
   template <typename T> void smooth(int l, C<T> *z, C<T> *res, int nrhs);

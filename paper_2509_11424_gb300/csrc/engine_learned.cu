@@ -109,7 +109,7 @@ template <typename T> void Engine::net_forward(const C<T> *in, C<T> *out, int B)
     U = L.U64;
     for (int i = 0; i < 3; ++i) W[i] = net_.W64[i];
   } else {
-    U = L.U32;
+    U = L.UD32;  // structure-of-arrays links for the FP32 (SoA) activations
     for (int i = 0; i < 3; ++i) W[i] = net_.W32[i];
   }
   glayer_forward<T>(in, a1, W[0], U, L.g, 1, net_.C, B, stream);
@@ -141,9 +141,10 @@ template <typename T> double Engine::net_loss_grad(const C<T> *r, int B, double2
   std::vector<double2> h(2 * B);
   MG_CUDA(cudaMemcpyAsync(h.data(), nr, sizeof(double2) * 2 * B, cudaMemcpyDeviceToHost, stream));
   // G3 = -D^H v / ||r||^2 = -Gamma5 D Gamma5 v / ||r||^2  (in out)
-  gamma5_apply<T>(t2, t1, L.g.V, 12, B, stream);
+  constexpr bool soa = sizeof(T) == 4;
+  gamma5_apply<T>(t2, t1, L.g.V, 12, B, stream, soa);
   apply_D<T>(0, t1, out, B);
-  gamma5_apply<T>(out, t1, L.g.V, 12, B, stream);
+  gamma5_apply<T>(out, t1, L.g.V, 12, B, stream, soa);
   neg_inv_kernel<<<(B + 63) / 64, 64, 0, stream>>>(sc, nr, B);
   MG_LAUNCH_CHECK();
   scale_rhs<T>(t1, out, sc, n, B, stream);
@@ -153,7 +154,7 @@ template <typename T> double Engine::net_loss_grad(const C<T> *r, int B, double2
     U = L.U64;
     for (int i = 0; i < 3; ++i) W[i] = net_.W64[i];
   } else {
-    U = L.U32;
+    U = L.UD32;  // structure-of-arrays links for the FP32 (SoA) activations
     for (int i = 0; i < 3; ++i) W[i] = net_.W32[i];
   }
   double2 *gW[3] = {grad, grad + net_.cnt[0], grad + net_.cnt[0] + net_.cnt[1]};
@@ -172,7 +173,9 @@ template <typename T> void Engine::record(const C<T> *res, int nrhs) {
   if (!recording_ || pool_n_ >= pool_cap_) return;
   const int64_t n = levels_[0].g.n();
   const int k = std::min(nrhs, pool_cap_ - pool_n_);
-  if constexpr (sizeof(T) == 8) convert<float, double>(res, pool_ + (size_t)pool_n_ * n, n * k, stream);
+  // the pool holds FP32 fine-level vectors, i.e. structure-of-arrays
+  if constexpr (sizeof(T) == 8)
+    relayout<float, double>(res, pool_ + (size_t)pool_n_ * n, nullptr, levels_[0].g.V, k, true, stream);
   else MG_CUDA(cudaMemcpyAsync(pool_ + (size_t)pool_n_ * n, res, sizeof(float2) * n * k, cudaMemcpyDeviceToDevice, stream));
   pool_n_ += k;
 }

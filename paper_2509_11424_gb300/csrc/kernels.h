@@ -46,6 +46,12 @@ void convert(const C<From> *in, C<To> *out, int64_t n, cudaStream_t s);
 // y += x (x in lower precision, y in higher)
 template <typename T, typename Tlo>
 void add_lo(const C<Tlo> *x, C<T> *y, int64_t n, cudaStream_t s);
+// y_r = x_r * scal[r] (null scal: 1) between the canonical order and the
+// fine level's structure-of-arrays order (to_soa: x canonical -> y SoA, else
+// y canonical), converting precision; V sites of 12 complex per vector
+template <typename To, typename From>
+void relayout(const C<From> *x, C<To> *y, const double *scal, int64_t V, int nrhs, bool to_soa,
+              cudaStream_t s);
 // y_r = x_r * scal[r] converting precision (scal real, device)
 template <typename To, typename From>
 void convert_scale(const C<From> *x, C<To> *y, const double *scal, int64_t n, int nrhs,
@@ -79,15 +85,14 @@ void gmres_arnoldi(GmresState st, int i, cudaStream_t s);
 void gmres_solve(GmresState st, cudaStream_t s);
 
 // ------------------------------------------------------------------ operators
-// D psi for nrhs right-hand sides.  FP32 with the structure-of-arrays links
-// UDs, 16-byte aligned in/out and variant >= 0 runs the shared-memory staged
-// kernel (variant 0 .. wilson_staged_variants() - 1 picks the pipeline depth
-// and whether links are staged or loaded into registers); otherwise the
-// one-thread-per-site kernel on the canonical links U.
+// D psi for nrhs right-hand sides.  FP64: canonical vectors and links U.
+// FP32: structure-of-arrays vectors (soa_index) and links UDs, 16-byte
+// aligned; variant 0 .. wilson_fp32_variants() - 1 picks right-hand sides per
+// thread (1 or 2) and the register budget (resident blocks per SM).
 template <typename T>
 void wilson_apply(const C<T> *in, C<T> *out, const C<T> *U, const C<T> *UDs, Geom g, double m0,
                   int nrhs, int variant, cudaStream_t s);
-int wilson_staged_variants();
+int wilson_fp32_variants();
 // UDs[mu][a][b][s] = U[s][mu][a][b]
 void link_soa(const float2 *U, float2 *UDs, int V, cudaStream_t s);
 // the 9 hop-class parts of D (Galerkin): out9[h] for h = 0..8, single rhs.
@@ -110,21 +115,25 @@ void dot_qr(const C<T> *q, const C<T> *r, int64_t n, int nrhs, double2 *out_qr, 
 template <typename T>
 void stencil_split(const C<T> *in, C<T> *out9, const C<T> *A, Geom g, const int b[4],
                    cudaStream_t s);
+// soa: fine-level vectors in the structure-of-arrays order
 template <typename T>
-void gamma5_apply(const C<T> *in, C<T> *out, int64_t nsites, int dof, int nrhs, cudaStream_t s);
+void gamma5_apply(const C<T> *in, C<T> *out, int64_t nsites, int dof, int nrhs, cudaStream_t s,
+                  bool soa = false);
 
 // ------------------------------------------------------------------ SAP
 // blocks b tile the lattice with an even block count in every direction
 bool sap_feasible(const Geom &g, const int b[4]);
 template <typename T> size_t sap_smem_bytes(const int b[4]);
-// one red/black sweep: r (residual, exact on exit), z += correction, e scratch
+// one red/black sweep: r (residual, exact on exit), z += correction, e scratch;
+// FP32: structure-of-arrays vectors and links (UDs), FP64: canonical
 template <typename T>
 void sap_sweep(C<T> *r, C<T> *z, C<T> *e, const C<T> *U, Geom g, const int b[4], double m0,
                int block_iters, int nrhs, cudaStream_t s);
 
 // ------------------------------------------------------------------ learned smoother
 // gauge-covariant layer phi[o] = sum_c sum_h W[h][o][c] T_h psi[c]; activations
-// [b][c][site][12], weights [h][o][c][4][4]
+// [b][c] vectors of the fine level (FP32 structure-of-arrays with the links
+// UDs, FP64 canonical [site][12] with U), weights [h][o][c][4][4]
 template <typename T>
 void glayer_forward(const C<T> *in, C<T> *out, const C<T> *W, const C<T> *U, Geom g, int Cin,
                     int Cout, int B, cudaStream_t s);

@@ -205,6 +205,31 @@ __global__ void convert_scale_kernel(const C<From> *__restrict__ in, C<To> *__re
   }
 }
 
+// y_r = x_r * scal[r] (scal may be null: 1) between the canonical order
+// [site][12] and the fine level's structure-of-arrays order (to_soa: x
+// canonical, y SoA; else the reverse), converting precision.  One thread per
+// (site, chunk of two components), chunks of a site on consecutive threads.
+template <typename To, typename From>
+__global__ void relayout_kernel(const C<From> *__restrict__ x, C<To> *__restrict__ y,
+                                const double *__restrict__ scal, int64_t V, bool to_soa) {
+  const int r = blockIdx.y;
+  const double f = scal ? scal[r] : 1.0;
+  const int64_t n = V * 12;
+  const C<From> *xr = x + r * n;
+  C<To> *yr = y + r * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < V * 6;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = e / 6;
+    const int k = (int)(e - s * 6);
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int64_t ic = s * 12 + 2 * k + j, is = soa_index(s, 2 * k + j, V);
+      const C<From> v = xr[to_soa ? ic : is];
+      yr[to_soa ? is : ic] = mk<To>((To)(v.x * f), (To)(v.y * f));
+    }
+  }
+}
+
 template <typename T, typename Tlo>
 __global__ void add_lo_kernel(const C<Tlo> *__restrict__ x, C<T> *__restrict__ y, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -432,6 +457,14 @@ void convert_scale(const C<From> *x, C<To> *y, const double *scal, int64_t n, in
   MG_LAUNCH_CHECK();
 }
 
+template <typename To, typename From>
+void relayout(const C<From> *x, C<To> *y, const double *scal, int64_t V, int nrhs, bool to_soa,
+              cudaStream_t s) {
+  const int gx = (grid_for(V * 6) + nrhs - 1) / nrhs + 1;
+  relayout_kernel<To, From><<<dim3(gx, nrhs), 256, 0, s>>>(x, y, scal, V, to_soa);
+  MG_LAUNCH_CHECK();
+}
+
 template <typename T, typename Tlo>
 void add_lo(const C<Tlo> *x, C<T> *y, int64_t n, cudaStream_t s) {
   add_lo_kernel<T, Tlo><<<grid_for(n), 256, 0, s>>>(x, y, n);
@@ -483,6 +516,12 @@ template void convert_scale<double, double>(const C<double> *, C<double> *, cons
                                             int64_t, int, cudaStream_t);
 template void convert_scale<double, float>(const C<float> *, C<double> *, const double *, int64_t,
                                            int, cudaStream_t);
+template void relayout<float, double>(const C<double> *, C<float> *, const double *, int64_t, int,
+                                      bool, cudaStream_t);
+template void relayout<double, float>(const C<float> *, C<double> *, const double *, int64_t, int,
+                                      bool, cudaStream_t);
+template void relayout<float, float>(const C<float> *, C<float> *, const double *, int64_t, int,
+                                     bool, cudaStream_t);
 template void add_lo<double, float>(const C<float> *, C<double> *, int64_t, cudaStream_t);
 template void add_lo<double, double>(const C<double> *, C<double> *, int64_t, cudaStream_t);
 

@@ -195,59 +195,31 @@ __global__ void __launch_bounds__(128) wilson_kernel(const C<T> *__restrict__ in
   store_spinor<T>(outr + (int64_t)s * 12, acc);
 }
 
-// ------------------------------------------------------------------ staged FP32
-// The FP32 hop term with the spinor operands staged through shared memory.
-// One warp owns 32 consecutive sites of one right-hand side.  For each of the
-// nine spinor sets it needs (the centre, then the eight neighbours) the warp
-// gathers the 32 records with lane-contiguous cp.async copies: round r of
-// lane l moves 16-byte chunk (32 r + l) of the 32 records, so one warp
-// instruction covers 512 contiguous bytes whenever the neighbours are
-// contiguous (every direction except at a wrap), where a thread-per-site load
-// would touch 32 records spread over 3 KB.  A record lands in a 128-byte row
-// of shared memory with chunk k in slot k ^ (row & 7): the reads of eight
-// consecutive lanes hit eight distinct bank groups and the copies at most
-// five.  A ring of S stages keeps S-1 sets in flight while one is consumed.
-// Links are stored structure-of-arrays, UDs[mu][a][b][s], so a lane's own
-// link components are coalesced across the warp either way: DIRECT loads
-// them into registers two hops ahead, otherwise they ride in the same stage
-// as the spinors (slot [component][lane]).
-namespace staged {
-constexpr int kRow = 128;                 // bytes per staged spinor record
-constexpr int kSpinBytes = 32 * kRow;     // one staged spinor set
-constexpr int kLinkBytes = 9 * 32 * 8;    // one staged link set
-template <bool DIRECT> constexpr int stage_bytes() { return DIRECT ? kSpinBytes : kSpinBytes + kLinkBytes; }
-constexpr int kWarps = 4;
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ void cp16(void *smem, const void *g) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(g) : "memory");
-}
-__device__ __forceinline__ void cp8(void *smem, const void *g) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(a), "l"(g) : "memory");
-}
-__device__ __forceinline__ void commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N> __device__ __forceinline__ void wait_groups() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
-}
-// byte offset of chunk k of record q in a staged spinor set
-__device__ __forceinline__ int slot(int q, int k) { return q * kRow + ((k ^ (q & 7)) << 4); }
-
-struct Tile {
-  const float2 *in;   // this right-hand side
-  const float2 *UDs;  // structure-of-arrays links
+// ------------------------------------------------------------------ FP32 SoA
+// The FP32 operator on the fine level, where spinors are stored
+// structure-of-arrays (chunk k = components 2k, 2k+1 of all sites
+// contiguous) and links likewise, UDs[mu][a][b][s].  One thread per site and
+// R right-hand sides: every load of a warp is 32 consecutive 16-byte chunks
+// (8-byte for links), the neighbour loads of the x direction hit the lines
+// the centre load brought into L1, and each link is read once for R spinors
+// from registers and once per right-hand-side group from L2 (the groups of a
+// site range are neighbouring blocks).
+// The nine operand sets (centre, then the hops x+, x-, y+, ..., t-) are
+// consumed in order; with PIPE they form a register pipeline (set I + 1 is
+// loaded while set I is consumed, two sets of loads in flight per thread).
+namespace soa {
+template <int R> struct Ctx {
+  const float4 *P[R];
+  const float2 *UDs;
   Geom g;
-  float diag;
-  unsigned char *smem;  // this warp's S stages
-  int lane, s0, s;      // s: own site, clamped into the lattice
+  int64_t V;
+  int s, nr;
   int c[4];
-  float2 acc[12];
+  float diag;
+  float2 acc[R][12];
 };
 
-// source site of operand set I for this lane: 0 the site itself, 1 + 2 mu the
-// forward neighbour, 2 + 2 mu the backward neighbour
-template <int I> __device__ __forceinline__ int item_site(const Tile &t) {
+template <int I, int R> __device__ __forceinline__ int item_site(const Ctx<R> &t) {
   if (I == 0) return t.s;
   constexpr int mu = (I - 1) / 2;
   int cn[4] = {t.c[0], t.c[1], t.c[2], t.c[3]};
@@ -255,133 +227,108 @@ template <int I> __device__ __forceinline__ int item_site(const Tile &t) {
   else cn[mu] = (t.c[mu] == 0) ? t.g.L[mu] - 1 : t.c[mu] - 1;
   return t.g.index(cn);
 }
-// the link of hop I (U_mu(x) forward, U_mu(x - mu) backward), component k
-template <int I> __device__ __forceinline__ const float2 *link_ptr(const Tile &t, int ns, int k) {
-  constexpr int mu = (I - 1) / 2;
-  const int ls = (I & 1) ? t.s : ns;
-  return t.UDs + ((int64_t)(mu * 9 + k)) * t.g.V + ls;
-}
 
-template <int I, int S, bool DIRECT> __device__ __forceinline__ void issue(Tile &t) {
-  unsigned char *st = t.smem + (I % S) * stage_bytes<DIRECT>();
-  const int ns = item_site<I>(t);
+template <int I, int R>
+__device__ __forceinline__ void load_item(const Ctx<R> &t, float4 (&p)[R][6], float2 (&u)[9]) {
+  const int sn = item_site<I, R>(t);
 #pragma unroll
-  for (int r = 0; r < 6; ++r) {
-    const int f = r * 32 + t.lane, q = f / 6, k = f - 6 * q;
-    const int src = __shfl_sync(kFull, ns, q);
-    cp16(st + slot(q, k), t.in + (int64_t)src * 12 + 2 * k);
-  }
-  if constexpr (I > 0 && !DIRECT) {
-    float2 *lk = reinterpret_cast<float2 *>(st + kSpinBytes);
+  for (int q = 0; q < R; ++q)
+    if (q < t.nr) {
 #pragma unroll
-    for (int k = 0; k < 9; ++k) cp8(lk + k * 32 + t.lane, link_ptr<I>(t, ns, k));
-  }
-}
-
-template <int I> __device__ __forceinline__ void load_link_direct(const Tile &t, float2 (&u)[9]) {
-  if constexpr (I >= 1 && I <= 8) {
-    const int ns = item_site<I>(t);
-#pragma unroll
-    for (int k = 0; k < 9; ++k) u[k] = __ldg(link_ptr<I>(t, ns, k));
-  }
-}
-
-template <int I, int S, bool DIRECT>
-__device__ __forceinline__ void consume(Tile &t, const float2 (&ud)[9]) {
-  const unsigned char *st = t.smem + (I % S) * stage_bytes<DIRECT>();
-  float2 p[12];
-#pragma unroll
-  for (int k = 0; k < 6; ++k) {
-    const float4 v = *reinterpret_cast<const float4 *>(st + slot(t.lane, k));
-    p[2 * k] = make_float2(v.x, v.y);
-    p[2 * k + 1] = make_float2(v.z, v.w);
-  }
-  if constexpr (I == 0) {
-#pragma unroll
-    for (int i = 0; i < 12; ++i) t.acc[i] = cscale(p[i], t.diag);
-  } else {
-    constexpr int mu = (I - 1) / 2;
-    constexpr bool fwd = (I & 1) != 0;
-    float2 u[9];
-    if constexpr (DIRECT) {
-#pragma unroll
-      for (int k = 0; k < 9; ++k) u[k] = ud[k];
-    } else {
-      const float2 *lk = reinterpret_cast<const float2 *>(st + kSpinBytes);
-#pragma unroll
-      for (int k = 0; k < 9; ++k) u[k] = lk[k * 32 + t.lane];
+      for (int k = 0; k < 6; ++k) p[q][k] = __ldg(t.P[q] + k * t.V + sn);
     }
-    // antiperiodic time: hops across the t boundary change sign
-    const bool wrap = mu == 3 && (fwd ? t.c[3] + 1 == t.g.L[3] : t.c[3] == 0);
-    hop<mu, fwd, float>(p, u, wrap ? 0.5f : -0.5f, t.acc);
+  if constexpr (I > 0) {
+    constexpr int mu = (I - 1) / 2;
+    const float2 *u0 = t.UDs + (int64_t)mu * 9 * t.V + ((I & 1) ? t.s : sn);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = __ldg(u0 + k * t.V);
   }
 }
 
-template <int I, int S, bool DIRECT> __device__ __forceinline__ void prologue(Tile &t) {
-  if constexpr (I < S - 1) {
-    issue<I, S, DIRECT>(t);
-    commit();
-    prologue<I + 1, S, DIRECT>(t);
+template <int I, int R>
+__device__ __forceinline__ void use_item(Ctx<R> &t, const float4 (&p)[R][6], const float2 (&u)[9]) {
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    if (q < t.nr) {
+      float2 v[12];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        v[2 * k] = make_float2(p[q][k].x, p[q][k].y);
+        v[2 * k + 1] = make_float2(p[q][k].z, p[q][k].w);
+      }
+      if constexpr (I == 0) {
+#pragma unroll
+        for (int i = 0; i < 12; ++i) t.acc[q][i] = cscale(v[i], t.diag);
+      } else {
+        constexpr int mu = (I - 1) / 2;
+        constexpr bool fwd = (I & 1) != 0;
+        // antiperiodic time: hops across the t boundary change sign
+        const bool wrap = mu == 3 && (fwd ? t.c[3] + 1 == t.g.L[3] : t.c[3] == 0);
+        hop<mu, fwd, float>(v, u, wrap ? 0.5f : -0.5f, t.acc[q]);
+      }
+    }
   }
 }
 
-// step I: issue set I + S - 1, (DIRECT) load the links of hop I + 2, wait for
-// set I and consume it.  u0, u1: the directly loaded links of hops I, I + 1.
-template <int I, int S, bool DIRECT>
-__device__ __forceinline__ void steps(Tile &t, float2 (&u0)[9], float2 (&u1)[9]) {
-  if constexpr (I + S - 1 <= 8) issue<I + S - 1, S, DIRECT>(t);
-  commit();  // possibly empty: keeps the group count uniform
-  float2 u2[9];
-  if constexpr (DIRECT) load_link_direct<I + 2>(t, u2);
-  wait_groups<S - 1>();
-  __syncwarp();
-  consume<I, S, DIRECT>(t, u0);
-  __syncwarp();
-  if constexpr (I < 8) steps<I + 1, S, DIRECT>(t, u1, u2);
+template <int I, int R>
+__device__ __forceinline__ void step(Ctx<R> &t, float4 (&pc)[R][6], float2 (&uc)[9],
+                                     float4 (&pn)[R][6], float2 (&un)[9]) {
+  if constexpr (I < 8) load_item<I + 1, R>(t, pn, un);
+  use_item<I, R>(t, pc, uc);
+  if constexpr (I < 8) step<I + 1, R>(t, pn, un, pc, uc);
 }
-}  // namespace staged
+// the same sets one after the other: load, consume (scheduling left to the
+// compiler, fewer registers)
+template <int I, int R> __device__ __forceinline__ void serial(Ctx<R> &t) {
+  float4 p[R][6];
+  float2 u[9];
+  load_item<I, R>(t, p, u);
+  use_item<I, R>(t, p, u);
+  if constexpr (I < 8) serial<I + 1, R>(t);
+}
+}  // namespace soa
 
-template <int S, bool DIRECT>
-__global__ void __launch_bounds__(staged::kWarps * 32, 3)
-    wilson_staged_kernel(const float2 *__restrict__ in, float2 *__restrict__ out,
-                         const float2 *__restrict__ UDs, Geom g, float diag, int nrhs) {
-  using namespace staged;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int w = threadIdx.x >> 5;
-  const int64_t gw = (int64_t)blockIdx.x * kWarps + w;
-  const int ntiles = (g.V + 31) >> 5;
-  if (gw >= (int64_t)ntiles * nrhs) return;  // whole warps only: no block barrier below
-  const int tile = (int)(gw / nrhs);
-  const int r = (int)(gw - (int64_t)tile * nrhs);
+template <int R, int BS, int MINB, bool PIPE>
+__global__ void __launch_bounds__(BS, MINB) wilson_soa_kernel(const float2 *__restrict__ in,
+                                                        float2 *__restrict__ out,
+                                                        const float2 *__restrict__ UDs, Geom g,
+                                                        float diag, int nrhs) {
+  // the right-hand-side group varies fastest over consecutive blocks, so the
+  // blocks sharing a site range (and its links) run close together in time
+  const int ng = (nrhs + R - 1) / R;
+  const int sb = (int)(blockIdx.x / ng), rg = (int)(blockIdx.x - (unsigned)sb * ng);
+  const int s = sb * BS + threadIdx.x;
+  if (s >= g.V) return;
+  const int r0 = rg * R;
   const int64_t n = (int64_t)g.V * 12;
-  Tile t;
-  t.in = in + r * n;
+  soa::Ctx<R> t;
+  t.nr = nrhs - r0 < R ? nrhs - r0 : R;
+#pragma unroll
+  for (int q = 0; q < R; ++q)
+    t.P[q] = reinterpret_cast<const float4 *>(in + (r0 + (q < t.nr ? q : 0)) * n);
   t.UDs = UDs;
   t.g = g;
+  t.V = g.V;
+  t.s = s;
   t.diag = diag;
-  t.smem = smem_raw + w * S * stage_bytes<DIRECT>();
-  t.lane = threadIdx.x & 31;
-  t.s0 = tile * 32;
-  t.s = min(t.s0 + t.lane, g.V - 1);
-  g.coords(t.s, t.c);
-  float2 u0[9], u1[9];
-  if constexpr (DIRECT) load_link_direct<1>(t, u1);
-  prologue<0, S, DIRECT>(t);
-  steps<0, S, DIRECT>(t, u0, u1);
-  wait_groups<0>();
-  // transpose the result through stage 0 and store 512 contiguous bytes per
-  // warp instruction
-  unsigned char *st = t.smem;
+  g.coords(s, t.c);
+  if constexpr (PIPE) {
+    float4 pa[R][6], pb[R][6];
+    float2 ua[9], ub[9];
+    soa::load_item<0, R>(t, pa, ua);
+    soa::step<0, R>(t, pa, ua, pb, ub);
+  } else {
+    soa::serial<0, R>(t);
+  }
 #pragma unroll
-  for (int k = 0; k < 6; ++k)
-    *reinterpret_cast<float4 *>(st + slot(t.lane, k)) =
-        make_float4(t.acc[2 * k].x, t.acc[2 * k].y, t.acc[2 * k + 1].x, t.acc[2 * k + 1].y);
-  __syncwarp();
-  float4 *o = reinterpret_cast<float4 *>(out + r * n + (int64_t)t.s0 * 12);
+  for (int q = 0; q < R; ++q) {
+    if (q < t.nr) {
+      float4 *o = reinterpret_cast<float4 *>(out + (r0 + q) * n);
 #pragma unroll
-  for (int rr = 0; rr < 6; ++rr) {
-    const int f = rr * 32 + t.lane, q = f / 6, k = f - 6 * q;
-    if (t.s0 + q < g.V) o[f] = *reinterpret_cast<const float4 *>(st + slot(q, k));
+      for (int k = 0; k < 6; ++k)
+        o[k * t.V + s] = make_float4(t.acc[q][2 * k].x, t.acc[q][2 * k].y, t.acc[q][2 * k + 1].x,
+                                     t.acc[q][2 * k + 1].y);
+    }
   }
 }
 
@@ -396,14 +343,17 @@ __global__ void link_soa_kernel(const float2 *__restrict__ U, float2 *__restrict
   }
 }
 
+// per site the upper half of the dofs keeps its sign, the lower half flips;
+// in the structure-of-arrays order (vec > 0: complex entries per vector) the
+// lower half is the second half of each vector
 template <typename T>
 __global__ void gamma5_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ out, int64_t total,
-                              int dof) {
+                              int dof, int64_t vec) {
   const int half = dof / 2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const int d = (int)(i % dof);
-    out[i] = d < half ? in[i] : cneg(in[i]);
+    const bool upper = vec > 0 ? (i % vec) < vec / 2 : (int)(i % dof) < half;
+    out[i] = upper ? in[i] : cneg(in[i]);
   }
 }
 
@@ -472,43 +422,42 @@ inline int grid_for(int64_t n) {
 }  // namespace
 
 namespace {
-template <int S, bool DIRECT>
-void launch_staged(const float2 *in, float2 *out, const float2 *UDs, Geom g, float diag, int nrhs,
-                   cudaStream_t s) {
-  constexpr int smem = staged::kWarps * S * staged::stage_bytes<DIRECT>();
-  static bool attr = false;
-  if (!attr) {
-    MG_CUDA(cudaFuncSetAttribute(wilson_staged_kernel<S, DIRECT>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    attr = true;
-  }
-  const int64_t warps = (int64_t)((g.V + 31) / 32) * nrhs;
-  wilson_staged_kernel<S, DIRECT><<<div_up(warps, staged::kWarps), staged::kWarps * 32, smem, s>>>(
-      in, out, UDs, g, diag, nrhs);
+template <int R, int MINB, bool PIPE>
+void launch_soa(const float2 *in, float2 *out, const float2 *UDs, Geom g, float diag, int nrhs,
+                cudaStream_t s) {
+  constexpr int BS = 128;
+  const int64_t blocks = (int64_t)div_up(g.V, BS) * div_up(nrhs, R);
+  if (blocks > 0x7fffffff) throw Error(1, "lattice too large for one launch");
+  wilson_soa_kernel<R, BS, MINB, PIPE><<<(unsigned)blocks, BS, 0, s>>>(in, out, UDs, g, diag, nrhs);
   MG_LAUNCH_CHECK();
 }
 }  // namespace
 
-int wilson_staged_variants() { return 4; }
+int wilson_fp32_variants() { return 5; }
 
 template <typename T>
 void wilson_apply(const C<T> *in, C<T> *out, const C<T> *U, const C<T> *UDs, Geom g, double m0,
                   int nrhs, int variant, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    const bool aligned = (((uintptr_t)in | (uintptr_t)out) & 15) == 0;
-    if (UDs && aligned && variant >= 0) {
-      const float diag = (float)(4.0 + m0);
-      switch (variant) {
-        case 0: launch_staged<2, false>(in, out, UDs, g, diag, nrhs, s); return;
-        case 1: launch_staged<3, false>(in, out, UDs, g, diag, nrhs, s); return;
-        case 2: launch_staged<2, true>(in, out, UDs, g, diag, nrhs, s); return;
-        default: launch_staged<3, true>(in, out, UDs, g, diag, nrhs, s); return;
-      }
+    if ((((uintptr_t)in | (uintptr_t)out) & 15) != 0 || !UDs)
+      throw Error(1, "FP32 fine vectors and links must be 16-byte aligned structure-of-arrays");
+    const float diag = (float)(4.0 + m0);
+    // (right-hand sides per thread, resident 128-thread blocks per SM the
+    // register budget is cut for, register pipeline)
+    switch (variant) {
+      case 1: launch_soa<1, 8, false>(in, out, UDs, g, diag, nrhs, s); return;
+      case 2: launch_soa<2, 4, false>(in, out, UDs, g, diag, nrhs, s); return;
+      case 3: launch_soa<2, 5, false>(in, out, UDs, g, diag, nrhs, s); return;
+      case 4: launch_soa<1, 4, true>(in, out, UDs, g, diag, nrhs, s); return;
+      default: launch_soa<1, 6, false>(in, out, UDs, g, diag, nrhs, s); return;
     }
+  } else {
+    (void)UDs;
+    (void)variant;
+    dim3 grid(div_up(g.V, 128), nrhs);
+    wilson_kernel<T, false><<<grid, 128, 0, s>>>(in, out, U, g, (T)(4.0 + m0), 1, 1, 1, 1);
+    MG_LAUNCH_CHECK();
   }
-  dim3 grid(div_up(g.V, 128), nrhs);
-  wilson_kernel<T, false><<<grid, 128, 0, s>>>(in, out, U, g, (T)(4.0 + m0), 1, 1, 1, 1);
-  MG_LAUNCH_CHECK();
 }
 
 void link_soa(const float2 *U, float2 *UDs, int V, cudaStream_t s) {
@@ -525,9 +474,10 @@ void wilson_split(const C<T> *in, C<T> *out9, const C<T> *U, Geom g, double m0, 
 }
 
 template <typename T>
-void gamma5_apply(const C<T> *in, C<T> *out, int64_t nsites, int dof, int nrhs, cudaStream_t s) {
+void gamma5_apply(const C<T> *in, C<T> *out, int64_t nsites, int dof, int nrhs, cudaStream_t s,
+                  bool soa) {
   const int64_t total = nsites * dof * nrhs;
-  gamma5_kernel<T><<<grid_for(total), 256, 0, s>>>(in, out, total, dof);
+  gamma5_kernel<T><<<grid_for(total), 256, 0, s>>>(in, out, total, dof, soa ? nsites * dof : 0);
   MG_LAUNCH_CHECK();
 }
 
@@ -551,7 +501,7 @@ void z4_noise(C<T> *out, Geom g, uint64_t seed, uint64_t sample0, uint64_t term,
                                 int, int, cudaStream_t);                                      \
   template void wilson_split<T>(const C<T> *, C<T> *, const C<T> *, Geom, double, const int *, \
                                 cudaStream_t);                                                \
-  template void gamma5_apply<T>(const C<T> *, C<T> *, int64_t, int, int, cudaStream_t);       \
+  template void gamma5_apply<T>(const C<T> *, C<T> *, int64_t, int, int, cudaStream_t, bool); \
   template void z4_noise<T>(C<T> *, Geom, uint64_t, uint64_t, uint64_t, uint64_t, int, int,   \
                             cudaStream_t);
 INST(double)

@@ -6,7 +6,9 @@
 // h = 0 identity, 1 + 2 mu: U_mu(x) psi(x + mu), 2 + 2 mu: U_mu(x - mu)^H
 // psi(x - mu), with the fermion sign on hops across the time boundary;
 // W[h][o][c] is a complex 4x4 matrix on the spin index.  Activations are
-// stored [b][c][site][12]; weights [h][o][c][4][4].  The adjoint uses that
+// [b][c] fine-level vectors (FP32 in the structure-of-arrays order with
+// structure-of-arrays links, FP64 canonical [site][12]); weights
+// [h][o][c][4][4].  The adjoint uses that
 // the adjoint of hop h is the reversed hop and the adjoint of W is W^H.
 #include "kernels.h"
 
@@ -19,14 +21,17 @@ inline int grid_for(int64_t n) {
   return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
 }
 
+template <typename T> constexpr bool kSoa = sizeof(T) == 4;
+
 // transported spinor t = T_h psi at site s (12 complex), sign folded in
 template <typename T>
 __device__ __forceinline__ void transported(const C<T> *__restrict__ psi, const C<T> *__restrict__ U,
                                             const Geom &g, int s, const int (&c)[4], int h,
                                             C<T> (&t)[12]) {
+  const int64_t V = g.V;
   if (h == 0) {
 #pragma unroll
-    for (int i = 0; i < 12; ++i) t[i] = psi[(int64_t)s * 12 + i];
+    for (int i = 0; i < 12; ++i) t[i] = psi[fidx<kSoa<T>>(s, i, V)];
     return;
   }
   const int mu = (h - 1) >> 1;
@@ -41,16 +46,16 @@ __device__ __forceinline__ void transported(const C<T> *__restrict__ psi, const 
     if (mu == 3 && c[3] == 0) sign = (T)-1;
   }
   const int sn = g.index(cn);
-  const C<T> *p = psi + (int64_t)sn * 12;
-  const C<T> *u = U + ((int64_t)(fwd ? s : sn) * 4 + mu) * 9;
+  const int ls = fwd ? s : sn;
   C<T> uu[9];
 #pragma unroll
-  for (int i = 0; i < 9; ++i) uu[i] = __ldg(u + i);
+  for (int i = 0; i < 9; ++i)
+    uu[i] = kSoa<T> ? __ldg(U + (int64_t)(mu * 9 + i) * V + ls) : __ldg(U + ((int64_t)ls * 4 + mu) * 9 + i);
 #pragma unroll
   for (int sp = 0; sp < 4; ++sp) {
     C<T> v[3];
 #pragma unroll
-    for (int b = 0; b < 3; ++b) v[b] = p[sp * 3 + b];
+    for (int b = 0; b < 3; ++b) v[b] = psi[fidx<kSoa<T>>(sn, sp * 3 + b, V)];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       C<T> z = mk<T>((T)0, (T)0);
@@ -112,9 +117,9 @@ __global__ void __launch_bounds__(128) glayer_forward_kernel(const C<T> *__restr
 #pragma unroll
   for (int k = 0; k < OG; ++k) {
     if (k < og) {
-      C<T> *o_ = out + ((int64_t)b * Cout + o0 + k) * n + (int64_t)s * 12;
+      C<T> *o_ = out + ((int64_t)b * Cout + o0 + k) * n;
 #pragma unroll
-      for (int i = 0; i < 12; ++i) o_[i] = acc[k][i];
+      for (int i = 0; i < 12; ++i) o_[fidx<kSoa<T>>(s, i, g.V)] = acc[k][i];
     }
   }
 }
@@ -159,9 +164,9 @@ __global__ void __launch_bounds__(128) glayer_adjoint_kernel(const C<T> *__restr
         }
     }
   }
-  C<T> *o_ = out + ((int64_t)b * Cin + c) * n + (int64_t)s * 12;
+  C<T> *o_ = out + ((int64_t)b * Cin + c) * n;
 #pragma unroll
-  for (int i = 0; i < 12; ++i) o_[i] = acc[i];
+  for (int i = 0; i < 12; ++i) o_[fidx<kSoa<T>>(s, i, g.V)] = acc[i];
 }
 
 __device__ __forceinline__ double2 warp_sum2(double2 v) {
@@ -194,10 +199,10 @@ __global__ void __launch_bounds__(256) glayer_wgrad_kernel(const C<T> *__restric
     for (int b = 0; b < B; ++b) {
       C<T> t[12];
       transported<T>(in + ((int64_t)b * Cin + ch) * n, U, g, s, cc, h, t);
-      const C<T> *gp = gin + ((int64_t)b * Cout + o) * n + (int64_t)s * 12;
+      const C<T> *gp = gin + ((int64_t)b * Cout + o) * n;
       C<T> gv[12];
 #pragma unroll
-      for (int i = 0; i < 12; ++i) gv[i] = gp[i];
+      for (int i = 0; i < 12; ++i) gv[i] = gp[fidx<kSoa<T>>(s, i, g.V)];
 #pragma unroll
       for (int sp = 0; sp < 4; ++sp)
 #pragma unroll

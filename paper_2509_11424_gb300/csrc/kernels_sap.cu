@@ -15,12 +15,25 @@
 // One CTA per (active block, rhs), one thread per site of the block.  The
 // block's links and its residual live in shared memory for all block
 // iterations (FP32: 256 sites x (36 + 12) complex = 98 KB), so the MR
-// iterations touch HBM once per sweep.
+// iterations touch HBM once per sweep.  FP32 vectors and links are in the
+// fine level's structure-of-arrays order, FP64 ones canonical.
 #include "kernels.h"
 
 namespace mg {
 
 namespace {
+
+template <typename T> constexpr bool kSoa = sizeof(T) == 4;
+
+// the 9 colour entries of U_mu(site): FP32 structure-of-arrays links
+// U[mu][a][b][V], FP64 canonical [V][mu][a][b]
+template <typename T>
+__device__ __forceinline__ void link_at(const C<T> *__restrict__ U, int64_t V, int64_t site, int mu,
+                                        C<T> (&u)[9]) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k)
+    u[k] = kSoa<T> ? U[(int64_t)(mu * 9 + k) * V + site] : U[(site * 4 + mu) * 9 + k];
+}
 
 struct SapGeom {
   Geom g;
@@ -177,8 +190,9 @@ __global__ void __launch_bounds__(256) sap_block_kernel(C<T> *__restrict__ r, C<
   for (int i = 0; i < 4; ++i) gc[i] = bc[i] * sg.b[i] + lc[i];
   const int s = sg.g.index(gc);
   // stage links and the residual of the block
-  for (int i = 0; i < 36; ++i) Us[ls * 36 + i] = U[(int64_t)s * 36 + i];
-  for (int i = 0; i < 12; ++i) rho[ls * 12 + i] = rv[(int64_t)s * 12 + i];
+  const int64_t V = sg.g.V;
+  for (int i = 0; i < 36; ++i) Us[ls * 36 + i] = kSoa<T> ? U[(int64_t)i * V + s] : U[(int64_t)s * 36 + i];
+  for (int i = 0; i < 12; ++i) rho[ls * 12 + i] = rv[fidx<kSoa<T>>(s, i, V)];
   C<T> e[12];
 #pragma unroll
   for (int i = 0; i < 12; ++i) e[i] = mk<T>((T)0, (T)0);
@@ -213,7 +227,7 @@ __global__ void __launch_bounds__(256) sap_block_kernel(C<T> *__restrict__ r, C<
   }
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
-    const int64_t o = (int64_t)s * 12 + i;
+    const int64_t o = fidx<kSoa<T>>(s, i, V);
     zv[o] = cadd(zv[o], e[i]);
     ev[o] = e[i];
     rv[o] = rho[ls * 12 + i];
@@ -233,10 +247,11 @@ __device__ __forceinline__ void cross_pair(const C<T> *__restrict__ ev, const C<
     if (c[MU] / sg.b[MU] != cn[MU] / sg.b[MU]) {
       const int sn = g.index(cn);
       const T k = (MU == 3 && cn[3] == 0) ? (T)0.5 : (T)-0.5;
-      C<T> p[12];
+      C<T> p[12], u[9];
 #pragma unroll
-      for (int i = 0; i < 12; ++i) p[i] = ev[(int64_t)sn * 12 + i];
-      shop<MU, true, T>(p, U + ((int64_t)s * 4 + MU) * 9, k, acc);
+      for (int i = 0; i < 12; ++i) p[i] = ev[fidx<kSoa<T>>(sn, i, g.V)];
+      link_at<T>(U, g.V, s, MU, u);
+      shop<MU, true, T>(p, u, k, acc);
     }
   }
   {
@@ -245,10 +260,11 @@ __device__ __forceinline__ void cross_pair(const C<T> *__restrict__ ev, const C<
     if (c[MU] / sg.b[MU] != cn[MU] / sg.b[MU]) {
       const int sn = g.index(cn);
       const T k = (MU == 3 && c[3] == 0) ? (T)0.5 : (T)-0.5;
-      C<T> p[12];
+      C<T> p[12], u[9];
 #pragma unroll
-      for (int i = 0; i < 12; ++i) p[i] = ev[(int64_t)sn * 12 + i];
-      shop<MU, false, T>(p, U + ((int64_t)sn * 4 + MU) * 9, k, acc);
+      for (int i = 0; i < 12; ++i) p[i] = ev[fidx<kSoa<T>>(sn, i, g.V)];
+      link_at<T>(U, g.V, sn, MU, u);
+      shop<MU, false, T>(p, u, k, acc);
     }
   }
 }
@@ -273,7 +289,10 @@ __global__ void sap_boundary_kernel(C<T> *__restrict__ r, const C<T> *__restrict
   cross_pair<2, T>(ev, U, sg, s, c, acc);
   cross_pair<3, T>(ev, U, sg, s, c, acc);
 #pragma unroll
-  for (int i = 0; i < 12; ++i) rv[(int64_t)s * 12 + i] = csub(rv[(int64_t)s * 12 + i], acc[i]);
+  for (int i = 0; i < 12; ++i) {
+    const int64_t o = fidx<kSoa<T>>(s, i, sg.g.V);
+    rv[o] = csub(rv[o], acc[i]);
+  }
 }
 
 }  // namespace

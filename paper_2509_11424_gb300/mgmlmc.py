@@ -126,6 +126,8 @@ _SIGNATURES = {
     'mgmlmc_profile_stats': [_P, _I, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_D),
                              ctypes.POINTER(_D)],
     'mgmlmc_set_kernel_variant': [_P, _I, _I],
+    'mgmlmc_reorder': [_P, _P, _P, _I, _I],
+    'mgmlmc_kernel_variants': [_I],
     'mgmlmc_get_kernel_variant': [_P, _I, _I, ctypes.POINTER(_I)],
 }
 
@@ -339,7 +341,18 @@ def mgmlmc_kernel_launches():
 
 
 VARIANT_DSLASH_FP32 = 0
-VARIANT_AUTOTUNE, VARIANT_PER_SITE = -2, -1
+LAYOUT_INTERNAL = 0x100
+
+
+def mgmlmc_reorder(ctx, inp, out, nrhs, to_internal):
+    """Level-0 complex-float vectors: canonical <-> the library's internal
+    structure-of-arrays order."""
+    _check(ctx, lib().mgmlmc_reorder(ctx, ptr(inp), ptr(out), nrhs, int(bool(to_internal))))
+VARIANT_AUTOTUNE = -2
+
+
+def mgmlmc_kernel_variants(kernel):
+    return int(lib().mgmlmc_kernel_variants(kernel))
 
 
 def mgmlmc_set_kernel_variant(ctx, kernel, variant):

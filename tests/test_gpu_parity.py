@@ -75,7 +75,8 @@ FP32_DIMS = [(4, 4, 4, 4), ODD, (6, 2, 2, 3), (3, 2, 2, 2), (12, 4, 2, 2), (48, 
 @pytest.mark.parametrize('dims', FP32_DIMS)
 @pytest.mark.parametrize('nrhs', [2, 5])
 def test_dslash_fp32(dims, nrhs):
-    """Every FP32 kernel variant (per-site and the four staged ones) against
+    """Every FP32 kernel variant (1 or 2 right-hand sides per thread, several
+    register budgets) against
     the oracle to 1e-5, and all variants bit-identical to each other (they add
     the same terms in the same order)."""
     U = synth.gauge_field(dims, 0.5, 7)
@@ -87,7 +88,9 @@ def test_dslash_fp32(dims, nrhs):
         x = synth.complex_normal((nrhs, n), 8).astype(np.complex64)
         xd = dev(x, torch.complex64)
         outs = []
-        for v in (-1, 0, 1, 2, 3):
+        nv = M.mgmlmc_kernel_variants(M.VARIANT_DSLASH_FP32)
+        assert nv >= 1
+        for v in range(nv):
             M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, v)
             assert M.mgmlmc_get_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, nrhs) == v
             yd = torch.full_like(xd, float('nan'))
@@ -98,21 +101,34 @@ def test_dslash_fp32(dims, nrhs):
             assert rel(outs[0][r], want) < 1e-5
         for o in outs[1:]:
             assert np.array_equal(o, outs[0])
+        # the internal order: component i of site s at ((i // 2) V + s) * 2 + i % 2
+        V = dirac.volume(dims)
+        xi = torch.empty_like(xd)
+        M.mgmlmc_reorder(ctx, xd, xi, nrhs, 1)
+        want_order = x.reshape(nrhs, V, 6, 2).transpose(0, 2, 1, 3).reshape(nrhs, -1)
+        assert np.array_equal(host(xi), want_order)
+        yi = torch.empty_like(xd)
+        M.mgmlmc_apply(ctx, M.OP_D | M.LAYOUT_INTERNAL, 0, M.FP32, xi, yi, nrhs)
+        yc = torch.empty_like(xd)
+        M.mgmlmc_reorder(ctx, yi, yc, nrhs, 0)
+        assert np.array_equal(host(yc), outs[0])
         # autotuned choice: made on the first call, then reported
         M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, M.VARIANT_AUTOTUNE)
         assert M.mgmlmc_get_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, nrhs) == -2
         yd = torch.empty_like(xd)
         M.mgmlmc_apply(ctx, M.OP_D, 0, M.FP32, xd, yd, nrhs)
         assert np.array_equal(host(yd), outs[0])
-        assert M.mgmlmc_get_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, nrhs) in (-1, 0, 1, 2, 3)
+        assert M.mgmlmc_get_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, nrhs) in range(nv)
     finally:
         M.mgmlmc_destroy(ctx)
 
 
 def test_dslash_variant_bad_args():
+    nv = M.mgmlmc_kernel_variants(M.VARIANT_DSLASH_FP32)
+    assert M.mgmlmc_kernel_variants(1) == -1
     ctx = M.mgmlmc_create((4, 4, 4, 4), torch.cuda.current_stream())
     try:
-        for kern, v in ((0, 4), (0, -3), (1, 0)):
+        for kern, v in ((0, nv), (0, -1), (0, -3), (1, 0)):
             with pytest.raises(M.MgmlmcError):
                 M.mgmlmc_set_kernel_variant(ctx, kern, v)
     finally:
