@@ -133,40 +133,47 @@ __device__ __forceinline__ void block_reduce3(T v0, T v1, T v2, T *s, T *out3) {
   __syncthreads();
 }
 
+// rho [12][sites] and Us [4 * 9][sites] are component-major in shared memory:
+// the threads of a warp (consecutive sites of the block) read consecutive
+// words, free of bank conflicts
 template <typename T, int DIR>
 __device__ __forceinline__ void local_hops(const C<T> *rho, const C<T> *Us, const int (&lc)[4],
-                                           const int *b, int lsite, int sites_stride, T ksign_t,
-                                           C<T> (&acc)[12]) {
-  (void)sites_stride;
-  // forward
+                                           const int *b, int lsite, int sites, C<T> (&acc)[12]) {
+  int stride = 1;
+  for (int i = 0; i < DIR; ++i) stride *= b[i];
+  // the time-boundary sign never applies inside a block: blocks tile the
+  // lattice without wrapping
   if (lc[DIR] + 1 < b[DIR]) {
-    int stride = 1;
-    for (int i = 0; i < DIR; ++i) stride *= b[i];
     const int ln = lsite + stride;
-    // the time-boundary sign never applies inside a block unless the block
-    // wraps, which it cannot (blocks tile the lattice without wrapping)
-    shop<DIR, true, T>(rho + ln * 12, Us + (lsite * 4 + DIR) * 9, (T)-0.5, acc);
+    C<T> p[12], u[9];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) p[i] = rho[i * sites + ln];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = Us[(DIR * 9 + k) * sites + lsite];
+    shop<DIR, true, T>(p, u, (T)-0.5, acc);
   }
   if (lc[DIR] > 0) {
-    int stride = 1;
-    for (int i = 0; i < DIR; ++i) stride *= b[i];
     const int ln = lsite - stride;
-    shop<DIR, false, T>(rho + ln * 12, Us + (ln * 4 + DIR) * 9, (T)-0.5, acc);
+    C<T> p[12], u[9];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) p[i] = rho[i * sites + ln];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = Us[(DIR * 9 + k) * sites + ln];
+    shop<DIR, false, T>(p, u, (T)-0.5, acc);
   }
-  (void)ksign_t;
 }
 
 // One colour of one SAP sweep.  r: residual (in/out), z: solution (+= e),
 // e: correction of this colour (written for the boundary update).
 template <typename T>
-__global__ void __launch_bounds__(256) sap_block_kernel(C<T> *__restrict__ r, C<T> *__restrict__ z,
+__global__ void __launch_bounds__(256, 2) sap_block_kernel(C<T> *__restrict__ r, C<T> *__restrict__ z,
                                                         C<T> *__restrict__ e_out,
                                                         const C<T> *__restrict__ U, SapGeom sg,
                                                         T diag, int color, int iters) {
   extern __shared__ unsigned char smem_raw[];
   const int sites = sg.sites;
-  C<T> *Us = reinterpret_cast<C<T> *>(smem_raw);  // [sites][4][9]
-  C<T> *rho = Us + sites * 36;                      // [sites][12]
+  C<T> *Us = reinterpret_cast<C<T> *>(smem_raw);  // [4][9][sites]
+  C<T> *rho = Us + sites * 36;                      // [12][sites]
   T *red = reinterpret_cast<T *>(rho + sites * 12);  // reduction scratch [3 * warps]
   T *out3 = red + 96;
   const int64_t n = sg.g.n();
@@ -191,8 +198,8 @@ __global__ void __launch_bounds__(256) sap_block_kernel(C<T> *__restrict__ r, C<
   const int s = sg.g.index(gc);
   // stage links and the residual of the block
   const int64_t V = sg.g.V;
-  for (int i = 0; i < 36; ++i) Us[ls * 36 + i] = kSoa<T> ? U[(int64_t)i * V + s] : U[(int64_t)s * 36 + i];
-  for (int i = 0; i < 12; ++i) rho[ls * 12 + i] = rv[fidx<kSoa<T>>(s, i, V)];
+  for (int i = 0; i < 36; ++i) Us[i * sites + ls] = kSoa<T> ? U[(int64_t)i * V + s] : U[(int64_t)s * 36 + i];
+  for (int i = 0; i < 12; ++i) rho[i * sites + ls] = rv[fidx<kSoa<T>>(s, i, V)];
   C<T> e[12];
 #pragma unroll
   for (int i = 0; i < 12; ++i) e[i] = mk<T>((T)0, (T)0);
@@ -200,15 +207,15 @@ __global__ void __launch_bounds__(256) sap_block_kernel(C<T> *__restrict__ r, C<
   for (int it = 0; it < iters; ++it) {
     C<T> q[12];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) q[i] = cscale(rho[ls * 12 + i], diag);
-    local_hops<T, 0>(rho, Us, lc, sg.b, ls, sites, (T)1, q);
-    local_hops<T, 1>(rho, Us, lc, sg.b, ls, sites, (T)1, q);
-    local_hops<T, 2>(rho, Us, lc, sg.b, ls, sites, (T)1, q);
-    local_hops<T, 3>(rho, Us, lc, sg.b, ls, sites, (T)1, q);
+    for (int i = 0; i < 12; ++i) q[i] = cscale(rho[i * sites + ls], diag);
+    local_hops<T, 0>(rho, Us, lc, sg.b, ls, sites, q);
+    local_hops<T, 1>(rho, Us, lc, sg.b, ls, sites, q);
+    local_hops<T, 2>(rho, Us, lc, sg.b, ls, sites, q);
+    local_hops<T, 3>(rho, Us, lc, sg.b, ls, sites, q);
     T qr_re = 0, qr_im = 0, qq = 0;
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
-      const C<T> p = rho[ls * 12 + i];
+      const C<T> p = rho[i * sites + ls];
       qr_re = fma(q[i].x, p.x, fma(q[i].y, p.y, qr_re));
       qr_im = fma(q[i].x, p.y, fma(-q[i].y, p.x, qr_im));
       qq = fma(q[i].x, q[i].x, fma(q[i].y, q[i].y, qq));
@@ -219,9 +226,9 @@ __global__ void __launch_bounds__(256) sap_block_kernel(C<T> *__restrict__ r, C<
     const C<T> al = den > tiny ? mk<T>(out3[0] / den, out3[1] / den) : mk<T>((T)0, (T)0);
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
-      const C<T> p = rho[ls * 12 + i];
+      const C<T> p = rho[i * sites + ls];
       e[i] = cfma(al, p, e[i]);
-      rho[ls * 12 + i] = cfma(cneg(al), q[i], p);
+      rho[i * sites + ls] = cfma(cneg(al), q[i], p);
     }
     __syncthreads();
   }
@@ -230,7 +237,7 @@ __global__ void __launch_bounds__(256) sap_block_kernel(C<T> *__restrict__ r, C<
     const int64_t o = fidx<kSoa<T>>(s, i, V);
     zv[o] = cadd(zv[o], e[i]);
     ev[o] = e[i];
-    rv[o] = rho[ls * 12 + i];
+    rv[o] = rho[i * sites + ls];
   }
 }
 
