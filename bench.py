@@ -66,10 +66,16 @@ def workload():
         return json.load(f)
 
 
-def kernel_source_hash():
+KERNEL_SOURCES = {'wilson': 'kernels_dirac.cu', 'coarse': 'kernels_coarse.cu', 'sap': 'kernels_sap.cu'}
+
+
+def kernel_source_hash(kernel):
+    """sha1 of the source file that holds a kernel class, plus the shared
+    helpers: a recorded ncu traffic figure only applies to this exact code."""
     p = os.path.join(ROOT, 'paper_2509_11424_gb300', 'csrc')
+    src = KERNEL_SOURCES[kernel.split('_')[0]]
     h = hashlib.sha1()
-    for f in ('kernels_dirac.cu', 'kernels_coarse.cu', 'kernels_sap.cu', 'common.cuh'):
+    for f in (src, 'common.cuh'):
         h.update(open(os.path.join(p, f), 'rb').read())
     return h.hexdigest()[:12]
 
@@ -440,7 +446,7 @@ def main():
             peak = hbm if hbm else 6800.0
             roof = dict(bound='hbm', achieved=achieved, peak=peak, unit='GB/s', frac=achieved / peak,
                         peak_source='of measured (MEASURED_PEAKS.json hbm_gbs)' if hbm else 'of fallback 6.8 TB/s')
-        roof['traffic'] = TRAFFIC.get((KERNELS[dom], kernel_source_hash()))
+        roof['traffic'] = TRAFFIC.get((KERNELS[dom], kernel_source_hash(KERNELS[dom])))
         roof.update(kernel=KERNELS[dom], launches=ks['launches'], avg_launch_us=ks['ms'] * 1e3 / ks['launches'],
                     share_of_profiled_step=ks['ms'] / prof_ms, profiled_step_ms=prof_ms,
                     algorithmic_bytes_per_launch=ks['bytes'] / ks['launches'],
