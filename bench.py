@@ -58,7 +58,10 @@ KERNELS = {0: 'wilson_dslash_fp64', 1: 'wilson_dslash_fp32', 2: 'coarse_stencil_
 GROUPS = {6: 'transfer_in_cycle', 7: 'gram_schmidt', 8: 'learned_step', 9: 'coarsest_dense'}
 # dram bytes per launch of a kernel from an ncu capture, keyed by (kernel,
 # sha1 of the kernel sources it was measured on); a stale key gives null
-TRAFFIC = {}
+TRAFFIC = {
+    # one sweep (block + boundary kernel, both colours), 16^4 x 8 rhs
+    ('sap_sweep_fp32', '9a67c5f9b503'): 578.0e6,
+}
 
 
 def workload():
