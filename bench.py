@@ -58,6 +58,7 @@ KERNELS = {0: 'wilson_dslash_fp64', 1: 'wilson_dslash_fp32', 2: 'coarse_stencil_
 GROUPS = {6: 'transfer_in_cycle', 7: 'gram_schmidt', 8: 'learned_step', 9: 'coarsest_dense'}
 # dram bytes per launch of a kernel from an ncu capture, keyed by (kernel,
 # sha1 of the kernel sources it was measured on); a stale key gives null
+SHARD_STRIDE = 1000000  # Z4 sample counters per rank
 TRAFFIC = {
     # one sweep (block + boundary kernel, both colours), 16^4 x 8 rhs
     ('sap_sweep_fp32', '9a67c5f9b503'): 578.0e6,
@@ -149,6 +150,42 @@ def merge_terms(results):
             a['k'] += 1
             a['res'] = max(a['res'], r['max_residual'])
     return acc
+
+
+def allreduce_terms(dist, acc, world, device):
+    """Merge the per-term accumulators of all ranks in place: sums of N, X,
+    |X|^2, iteration counts and seconds (the seconds then averaged over the
+    ranks, which run at the same time), maximum of the true residuals.  Every
+    rank holds the same terms; the only exchange of the sharded path."""
+    import torch
+    keys = sorted(acc)
+    fields = ('n', 'sre', 'sim', 'sab', 'sec', 'it', 'k')
+    vec = torch.tensor([[float(acc[k][f]) for f in fields] for k in keys], dtype=torch.float64,
+                       device=device)
+    dist.all_reduce(vec)
+    res = torch.tensor([float(acc[k]['res']) for k in keys], dtype=torch.float64, device=device)
+    dist.all_reduce(res, op=dist.ReduceOp.MAX)
+    for i, k in enumerate(keys):
+        for j, f in enumerate(fields):
+            acc[k][f] = vec[i, j].item()
+        acc[k]['sec'] /= world
+        acc[k]['n'] = int(round(acc[k]['n']))
+        acc[k]['k'] = int(round(acc[k]['k']))
+        acc[k]['res'] = res[i].item()
+    return acc
+
+
+def max_over_ranks(dist, x, device):
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def first_sample(rank, k, batch):
+    """Counter of the first Z4 sample of step k on a rank: ranks draw from
+    disjoint ranges of SHARD_STRIDE samples."""
+    return rank * SHARD_STRIDE + k * batch
 
 
 def stats_of(a):
@@ -369,13 +406,12 @@ def main():
 
     B = args.batch
     nterm = 2 * len(BLOCKS) + 1
-    base = rank * 1000000
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def step(k, kind=M.EST_ORTHOGONAL):
         n = [B] * nterm if kind == M.EST_ORTHOGONAL else [B]
         return M.mgmlmc_estimate_trace(ctx, M.est_params(kind, n, batch=B, seed=NOISE_SEED,
-                                                         first_sample=base + k * B))
+                                                         first_sample=first_sample(rank, k, B)))
 
     def timed(k0, K, kind=M.EST_ORTHOGONAL):
         res, ms = [], 0.0
@@ -404,21 +440,11 @@ def main():
     launches = M.mgmlmc_kernel_launches() - n_launch0
     clk = clocks.stop()
     if dist:
-        t = torch.tensor([total_ms], device='cuda')
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        total_ms = max_over_ranks(dist, total_ms, 'cuda')
     ms_per_step = total_ms / args.steps
     acc = merge_terms(results)
     if dist:
-        keys = sorted(acc)
-        fields = ('n', 'sre', 'sim', 'sab', 'sec')
-        vec = torch.tensor([[acc[k][f] for f in fields] for k in keys], dtype=torch.float64, device='cuda')
-        dist.all_reduce(vec)
-        for i, k in enumerate(keys):
-            for j, f in enumerate(fields):
-                acc[k][f] = vec[i, j].item()
-            acc[k]['sec'] /= world
-            acc[k]['n'] = int(round(acc[k]['n']))
+        allreduce_terms(dist, acc, world, 'cuda')
     value, det = time_to_variance(acc, world, ms_per_step, args.steps)
 
     # profiled repeat of the first timed step: per-launch events
