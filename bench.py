@@ -61,6 +61,8 @@ GROUPS = {6: 'transfer_in_cycle', 7: 'gram_schmidt', 8: 'learned_step', 9: 'coar
 SHARD_STRIDE = 1000000  # Z4 sample counters per rank
 TRAFFIC = {
     # one sweep (block + boundary kernel, both colours), 16^4 x 8 rhs
+    # one level-1 launch (4^4 x 32 dof, 8 rhs), cold-cache capture
+    ('coarse_stencil_fp32', 'ecf398700957'): 19.43e6,
     ('sap_sweep_fp32', '9a67c5f9b503'): 578.0e6,
 }
 
