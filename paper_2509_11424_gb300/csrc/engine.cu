@@ -77,6 +77,8 @@ Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
   scal_ = dalloc<double2>(4096);
   flag_dev_ = dalloc<int>(16);
   MG_CUDA(cudaMemset(flag_dev_, 0, 16 * sizeof(int)));
+  tickets_ = dalloc<unsigned>(kTickets);
+  MG_CUDA(cudaMemset(tickets_, 0, kTickets * sizeof(unsigned)));
 }
 
 Engine::~Engine() {
@@ -95,6 +97,7 @@ Engine::~Engine() {
   for (auto e : events_) cudaEventDestroy(e);
   dfree(scal_);
   dfree(partial_);
+  dfree(tickets_);
   dfree(flag_dev_);
   if (pinned_) cudaFreeHost(pinned_);
   if (ev_enter_) cudaEventDestroy(ev_enter_);
@@ -188,7 +191,7 @@ void *Engine::pinned(size_t bytes) {
   return pinned_;
 }
 
-double2 *Engine::partials(size_t count) {
+RedScratch Engine::partials(size_t count) {
   if (count > partial_cap_) {
     if (capturing_) throw Error(MGMLMC_ERR_STATE, "reduction scratch growth during graph capture");
     drop_graphs();
@@ -197,7 +200,7 @@ double2 *Engine::partials(size_t count) {
     partial_ = dalloc<double2>(count);
     partial_cap_ = count;
   }
-  return partial_;
+  return RedScratch{partial_, tickets_};
 }
 
 template <typename T> C<T> *Engine::ws(const std::string &name, int l, size_t count) {

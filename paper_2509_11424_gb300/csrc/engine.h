@@ -184,6 +184,7 @@ class Engine {
   std::map<std::string, std::pair<void *, size_t>> ws_;
   double2 *scal_ = nullptr;     // small scalar scratch
   double2 *partial_ = nullptr;  // reduction partials
+  unsigned *tickets_ = nullptr;  // reduction tickets (kTickets, zero between calls)
   size_t partial_cap_ = 0;
   int *flag_dev_ = nullptr;
   static constexpr size_t kPinnedBytes = 1 << 20;
@@ -200,7 +201,7 @@ class Engine {
   // event pair around a launch sequence of one kernel class (no-op unless profiling)
   cudaEvent_t prof_begin();
   void prof_end(cudaEvent_t a, int cls, double bytes, double flops);
-  double2 *partials(size_t count);
+  RedScratch partials(size_t count);
   Net net_;
   void net_free();
   bool recording_ = false;    // copy level-0 post-smoother inputs into the training pool

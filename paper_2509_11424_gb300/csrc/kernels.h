@@ -8,18 +8,27 @@
 
 namespace mg {
 
-// Fixed two-stage reduction width (deterministic: depends on n only).
+// Blocks per reduction output (deterministic: depends on n only).
 int reduce_blocks(int64_t n);
+// Scratch of the single-pass reductions: reduce_blocks(n) partial sums per
+// output, and one ticket per output that is zero between calls (the block
+// that finishes an output last resets it).  Tickets belong to one stream at
+// a time: concurrent reductions need separate ticket arrays.
+constexpr int kTickets = 1 << 16;
+struct RedScratch {
+  double2 *partial;
+  unsigned *ticket;  // kTickets entries
+};
 
 // ------------------------------------------------------------------ BLAS-1
 // out[r] = sum_i conj(x_r[i]) y_r[i]   (double2 results on the device)
 template <typename T>
-void dot(const C<T> *x, const C<T> *y, int64_t n, int nrhs, double2 *out, double2 *partial,
+void dot(const C<T> *x, const C<T> *y, int64_t n, int nrhs, double2 *out, RedScratch scr,
          cudaStream_t s);
 // h[r * ldh + j] = <V_j,r , w_r> for j < k (basis stride vstride)
 template <typename T>
 void multi_dot(const C<T> *V, int64_t vstride, int k, const C<T> *w, int64_t n, int nrhs,
-               double2 *h, int ldh, double2 *partial, cudaStream_t s);
+               double2 *h, int ldh, RedScratch scr, cudaStream_t s);
 // w_r += sign * sum_{j<k} h[r * ldh + j] V_j,r
 template <typename T>
 void multi_axpy(const C<T> *V, int64_t vstride, int k, C<T> *w, int64_t n, int nrhs,
@@ -111,7 +120,7 @@ void stencil_transpose(const double2 *A, C<To> *AT, int64_t nblocks, int m, cuda
 // (<q, r>, <q, q>) for every rhs in one pass: out_qr[r], out_qq[r]
 template <typename T>
 void dot_qr(const C<T> *q, const C<T> *r, int64_t n, int nrhs, double2 *out_qr, double2 *out_qq,
-            double2 *partial, cudaStream_t s);
+            RedScratch scr, cudaStream_t s);
 template <typename T>
 void stencil_split(const C<T> *in, C<T> *out9, const C<T> *A, Geom g, const int b[4],
                    cudaStream_t s);

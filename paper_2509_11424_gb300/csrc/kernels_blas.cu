@@ -2,9 +2,9 @@
 // small-matrix kernels of batched FGMRES.
 //
 // Reductions are deterministic: a fixed number of blocks (a function of n
-// only) writes partial sums that a second kernel adds in a fixed order, so a
-// result never depends on scheduling.  Sums are accumulated in FP64 for both
-// storage precisions.
+// only) writes partial sums that the last block to finish adds in block
+// order, so a result never depends on scheduling.  Sums are accumulated in
+// FP64 for both storage precisions.
 #include "kernels.h"
 
 namespace mg {
@@ -36,11 +36,39 @@ __device__ __forceinline__ double2 block_sum(double2 v) {
   return v;
 }
 
-// partial[(j * nrhs + r) * NB + b] = sum over block b's chunk of conj(x) y
+// Single-pass reductions.  Block b of output g sums its chunk, writes the
+// partial, and takes a ticket; the block that draws the last ticket adds the
+// NB partials of g in block order (so the result never depends on
+// scheduling) and puts the ticket back to zero.  Nothing waits on anything.
+__device__ __forceinline__ bool last_block(unsigned *ticket) {
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's partial is visible before its ticket
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  return last;
+}
+
+__device__ __forceinline__ double2 sum_partials(const double2 *p, int NB) {
+  __threadfence();
+  double2 acc = make_double2(0.0, 0.0);
+  for (int b = threadIdx.x; b < NB; b += blockDim.x) {
+    const double2 v = __ldcg(p + b);
+    acc.x += v.x;
+    acc.y += v.y;
+  }
+  return block_sum(acc);
+}
+
+// out[r * ldh + j] = sum conj(x_j,r) y_r; output g = j * nrhs + r, its NB
+// partials at partial[g * NB ..]
 template <typename T>
-__global__ void dot_stage1(const C<T> *__restrict__ x, int64_t xstride, const C<T> *__restrict__ y,
-                           int64_t n, int64_t chunk, double2 *__restrict__ partial) {
+__global__ void dot_kernel(const C<T> *__restrict__ x, int64_t xstride, const C<T> *__restrict__ y,
+                           int64_t n, int64_t chunk, double2 *__restrict__ partial,
+                           unsigned *__restrict__ ticket, double2 *__restrict__ out, int ldh) {
   const int b = blockIdx.x, r = blockIdx.y, j = blockIdx.z;
+  const int64_t g = (int64_t)j * gridDim.y + r;
   const C<T> *xr = x + j * xstride + r * n;
   const C<T> *yr = y + r * n;
   const int64_t beg = (int64_t)b * chunk;
@@ -53,29 +81,23 @@ __global__ void dot_stage1(const C<T> *__restrict__ x, int64_t xstride, const C<
     const C<T> a = xr[i], c = yr[i];
     acc = cfmac(a, c, acc);
   }
-  double2 tot = block_sum(make_double2((double)acc.x, (double)acc.y));
-  if (threadIdx.x == 0) partial[((int64_t)j * gridDim.y + r) * gridDim.x + b] = tot;
-}
-
-// out[r * ldh + j] = sum_b partial[(j * nrhs + r) * NB + b]
-__global__ void dot_stage2(const double2 *__restrict__ partial, int NB, int nrhs,
-                           double2 *__restrict__ out, int ldh) {
-  const int idx = blockIdx.x;  // j * nrhs + r
-  const int j = idx / nrhs, r = idx - j * nrhs;
-  double2 acc = make_double2(0.0, 0.0);
-  for (int b = threadIdx.x; b < NB; b += blockDim.x) {
-    double2 p = partial[(int64_t)idx * NB + b];
-    acc.x += p.x;
-    acc.y += p.y;
+  const double2 tot = block_sum(make_double2((double)acc.x, (double)acc.y));
+  if (threadIdx.x == 0) partial[g * gridDim.x + b] = tot;
+  if (!last_block(ticket + g)) return;
+  const double2 s = sum_partials(partial + g * gridDim.x, gridDim.x);
+  if (threadIdx.x == 0) {
+    out[r * ldh + j] = s;
+    ticket[g] = 0u;
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) out[r * ldh + j] = acc;
 }
 
-// partial[(r * 2 + o) * NB + b]: o = 0 <q, r>, o = 1 <q, q> over block b's chunk
+// oqr[r] = <q_r, r_r>, oqq[r] = <q_r, q_r>; output r, partials at
+// partial[(2 r + o) * NB ..]
 template <typename T>
-__global__ void dot_qr_stage1(const C<T> *__restrict__ q, const C<T> *__restrict__ rr, int64_t n,
-                              int64_t chunk, double2 *__restrict__ partial) {
+__global__ void dot_qr_kernel(const C<T> *__restrict__ q, const C<T> *__restrict__ rr, int64_t n,
+                              int64_t chunk, double2 *__restrict__ partial,
+                              unsigned *__restrict__ ticket, double2 *__restrict__ oqr,
+                              double2 *__restrict__ oqq) {
   const int b = blockIdx.x, r = blockIdx.y;
   const C<T> *qr = q + r * n;
   const C<T> *xr = rr + r * n;
@@ -94,19 +116,14 @@ __global__ void dot_qr_stage1(const C<T> *__restrict__ q, const C<T> *__restrict
     partial[((int64_t)r * 2 + 0) * gridDim.x + b] = a;
     partial[((int64_t)r * 2 + 1) * gridDim.x + b] = c;
   }
-}
-
-__global__ void dot_qr_stage2(const double2 *__restrict__ partial, int NB, double2 *__restrict__ oqr,
-                              double2 *__restrict__ oqq) {
-  const int idx = blockIdx.x;  // r * 2 + o
-  double2 acc = make_double2(0.0, 0.0);
-  for (int b = threadIdx.x; b < NB; b += blockDim.x) {
-    const double2 p = partial[(int64_t)idx * NB + b];
-    acc.x += p.x;
-    acc.y += p.y;
+  if (!last_block(ticket + r)) return;
+  const double2 sa = sum_partials(partial + ((int64_t)r * 2 + 0) * gridDim.x, gridDim.x);
+  const double2 sc = sum_partials(partial + ((int64_t)r * 2 + 1) * gridDim.x, gridDim.x);
+  if (threadIdx.x == 0) {
+    oqr[r] = sa;
+    oqq[r] = sc;
+    ticket[r] = 0u;
   }
-  acc = block_sum(acc);
-  if (threadIdx.x == 0) (idx & 1 ? oqq : oqr)[idx >> 1] = acc;
 }
 
 template <typename T>
@@ -372,35 +389,32 @@ int reduce_blocks(int64_t n) {
 }
 
 template <typename T>
-void dot(const C<T> *x, const C<T> *y, int64_t n, int nrhs, double2 *out, double2 *partial,
+void dot(const C<T> *x, const C<T> *y, int64_t n, int nrhs, double2 *out, RedScratch scr,
          cudaStream_t s) {
   const int NB = reduce_blocks(n);
   const int64_t chunk = (n + NB - 1) / NB;
-  dot_stage1<T><<<dim3(NB, nrhs, 1), RB, 0, s>>>(x, 0, y, n, chunk, partial);
-  dot_stage2<<<nrhs, RB, 0, s>>>(partial, NB, nrhs, out, 1);
-  MG_COUNT(1);
+  if (nrhs > kTickets) throw Error(1, "reduction: too many outputs for the ticket array");
+  dot_kernel<T><<<dim3(NB, nrhs, 1), RB, 0, s>>>(x, 0, y, n, chunk, scr.partial, scr.ticket, out, 1);
   MG_LAUNCH_CHECK();
 }
 
 template <typename T>
 void dot_qr(const C<T> *q, const C<T> *r, int64_t n, int nrhs, double2 *out_qr, double2 *out_qq,
-            double2 *partial, cudaStream_t s) {
+            RedScratch scr, cudaStream_t s) {
   const int NB = reduce_blocks(n);
   const int64_t chunk = (n + NB - 1) / NB;
-  dot_qr_stage1<T><<<dim3(NB, nrhs), RB, 0, s>>>(q, r, n, chunk, partial);
-  dot_qr_stage2<<<2 * nrhs, RB, 0, s>>>(partial, NB, out_qr, out_qq);
-  MG_COUNT(1);
+  if (nrhs > kTickets) throw Error(1, "reduction: too many outputs for the ticket array");
+  dot_qr_kernel<T><<<dim3(NB, nrhs), RB, 0, s>>>(q, r, n, chunk, scr.partial, scr.ticket, out_qr, out_qq);
   MG_LAUNCH_CHECK();
 }
 
 template <typename T>
 void multi_dot(const C<T> *V, int64_t vstride, int k, const C<T> *w, int64_t n, int nrhs,
-               double2 *h, int ldh, double2 *partial, cudaStream_t s) {
+               double2 *h, int ldh, RedScratch scr, cudaStream_t s) {
   const int NB = reduce_blocks(n);
   const int64_t chunk = (n + NB - 1) / NB;
-  dot_stage1<T><<<dim3(NB, nrhs, k), RB, 0, s>>>(V, vstride, w, n, chunk, partial);
-  dot_stage2<<<k * nrhs, RB, 0, s>>>(partial, NB, nrhs, h, ldh);
-  MG_COUNT(1);
+  if ((int64_t)k * nrhs > kTickets) throw Error(1, "reduction: too many outputs for the ticket array");
+  dot_kernel<T><<<dim3(NB, nrhs, k), RB, 0, s>>>(V, vstride, w, n, chunk, scr.partial, scr.ticket, h, ldh);
   MG_LAUNCH_CHECK();
 }
 
@@ -491,10 +505,10 @@ void gmres_solve(GmresState st, cudaStream_t s) {
 }
 
 #define INST(T)                                                                                  \
-  template void dot<T>(const C<T> *, const C<T> *, int64_t, int, double2 *, double2 *,           \
+  template void dot<T>(const C<T> *, const C<T> *, int64_t, int, double2 *, RedScratch,         \
                        cudaStream_t);                                                            \
   template void multi_dot<T>(const C<T> *, int64_t, int, const C<T> *, int64_t, int, double2 *,  \
-                             int, double2 *, cudaStream_t);                                      \
+                             int, RedScratch, cudaStream_t);                                     \
   template void multi_axpy<T>(const C<T> *, int64_t, int, C<T> *, int64_t, int, const double2 *, \
                               int, double, cudaStream_t);                                        \
   template void axpby<T>(double, const C<T> *, double, C<T> *, int64_t, int, cudaStream_t);      \
@@ -503,7 +517,7 @@ void gmres_solve(GmresState st, cudaStream_t s) {
                              int64_t, int, cudaStream_t);                                        \
   template void check_finite<T>(const C<T> *, int64_t, int *, cudaStream_t);               \
   template void dot_qr<T>(const C<T> *, const C<T> *, int64_t, int, double2 *, double2 *,        \
-                          double2 *, cudaStream_t);                                            \
+                          RedScratch, cudaStream_t);                                           \
   template void mr_dir_update<T>(C<T> *, C<T> *, const C<T> *, const C<T> *, const double2 *,    \
                                  const double2 *, int64_t, int, cudaStream_t);
 INST(double)
