@@ -197,22 +197,29 @@ def stats_of(a):
     return mu, var
 
 
-def time_to_variance(acc, world, step_ms, steps, rel_eps=REL_EPS):
+def time_to_variance(acc, world, step_ms, steps, rel_eps=REL_EPS, var_of=None, eps=None):
     """(predicted seconds, details): per-sample costs from the library's
     per-term device time, rescaled so the terms add up to the measured step
-    time (host gaps included), divided by the number of ranks."""
+    time (host gaps included), divided by the number of ranks.  var_of
+    (term -> variance) and eps replace this run's own estimates: arms that
+    compute the same per-sample values (same estimator, same noise, solves to
+    1e-12) share the variances of the run with the most samples, so they
+    differ only in cost."""
     terms = sorted(acc)
     dev_sec = sum(acc[t]['sec'] for t in terms)
     scale = (step_ms * 1e-3 * steps) / dev_sec if dev_sec > 0 else 1.0
     tr, S, det = 0j, 0.0, {}
     for t in terms:
         mu, var = stats_of(acc[t])
+        if var_of is not None:
+            var = var_of[str(t)]
         C = acc[t]['sec'] * scale / acc[t]['n'] / world
         tr += mu
         S += np.sqrt(var * C)
         det[str(t)] = dict(mean=[mu.real, mu.imag], var=var, cost_s=C, n=acc[t]['n'],
                            iters=acc[t]['it'] / max(1, acc[t]['k']), max_residual=acc[t]['res'])
-    eps = rel_eps * abs(tr)
+    if eps is None:
+        eps = rel_eps * abs(tr)
     return S ** 2 / eps ** 2, dict(trace=[tr.real, tr.imag], eps=eps, terms=det)
 
 
@@ -362,7 +369,7 @@ def main():
     ap.add_argument('--no-cpu', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
     ap.add_argument('--m0', type=float, default=None, help='override the tuned mass (exploration)')
-    ap.add_argument('--learned', type=int, default=2, help='channels of the learned smoother (0: off)')
+    ap.add_argument('--learned', type=int, default=1, help='channels of the learned smoother (0: off)')
     ap.add_argument('--train-steps', type=int, default=200)
     ap.add_argument('--dslash-only', action='store_true', help='only the 32^4 FP32 Dslash measurement')
     args = ap.parse_args()
@@ -498,26 +505,29 @@ def main():
     compare = {}
     if rank == 0 and args.compare_steps > 0:
         k0 = args.warmup  # the timed run's first sample batch: identical noise
-        pres, pms = timed(k0, args.compare_steps, M.EST_PLAIN)
-        pval, pdet = time_to_variance(merge_terms(pres), 1, pms / args.compare_steps, args.compare_steps)
-        compare['plain_hutchinson_same_solver'] = dict(value=pval * (pdet['eps'] / det['eps']) ** 2,
-                                                       ms_per_step=pms / args.compare_steps, detail=pdet)
+        cs = args.compare_steps
+        # one eps for every arm; arms with the same estimator share variances
+        eps0 = det['eps']
+        mvar = {t: v['var'] for t, v in det['terms'].items()}
+        pres, pms = timed(k0, cs, M.EST_PLAIN)
+        pval, pdet = time_to_variance(merge_terms(pres), 1, pms / cs, cs, eps=eps0)
+        compare['plain_hutchinson_same_solver'] = dict(value=pval, ms_per_step=pms / cs, detail=pdet)
+        pvar = {t: v['var'] for t, v in pdet['terms'].items()}
         if args.learned > 0:
             M.mgmlmc_set_solver(ctx, precision=prec, **SOLVER)
             step(k0)
-            sres, sms = timed(k0, args.compare_steps)
-            sval, sdet = time_to_variance(merge_terms(sres), 1, sms / args.compare_steps, args.compare_steps)
-            compare['mlmc_same_precision_sap_only'] = dict(value=sval, ms_per_step=sms / args.compare_steps,
-                                                           detail=sdet)
+            sres, sms = timed(k0, cs)
+            sval, sdet = time_to_variance(merge_terms(sres), 1, sms / cs, cs, var_of=mvar, eps=eps0)
+            compare['mlmc_same_precision_sap_only'] = dict(value=sval, ms_per_step=sms / cs, detail=sdet)
         if prec == M.FP32:
             M.mgmlmc_set_solver(ctx, precision=M.FP64, **SOLVER)
             step(k0)
-            fres, fms = timed(k0, args.compare_steps)
-            fval, fdet = time_to_variance(merge_terms(fres), 1, fms / args.compare_steps, args.compare_steps)
-            compare['mlmc_fp64'] = dict(value=fval, ms_per_step=fms / args.compare_steps, detail=fdet)
+            fres, fms = timed(k0, cs)
+            fval, fdet = time_to_variance(merge_terms(fres), 1, fms / cs, cs, var_of=mvar, eps=eps0)
+            compare['mlmc_fp64'] = dict(value=fval, ms_per_step=fms / cs, detail=fdet)
             pres, pms = timed(k0, 1, M.EST_PLAIN)
-            p64, p64d = time_to_variance(merge_terms(pres), 1, pms, 1)
-            compare['plain_hutchinson_fp64'] = dict(value=p64 * (p64d['eps'] / det['eps']) ** 2, ms_per_step=pms)
+            p64, p64d = time_to_variance(merge_terms(pres), 1, pms, 1, var_of=pvar, eps=eps0)
+            compare['plain_hutchinson_fp64'] = dict(value=p64, ms_per_step=pms)
         M.mgmlmc_set_solver(ctx, precision=prec, **main_solver)
 
     e2e = None
