@@ -524,7 +524,15 @@ def main():
             step(k0)
             fres, fms = timed(k0, cs)
             fval, fdet = time_to_variance(merge_terms(fres), 1, fms / cs, cs, var_of=mvar, eps=eps0)
-            compare['mlmc_fp64'] = dict(value=fval, ms_per_step=fms / cs, detail=fdet)
+            # error of the mixed-precision estimate against FP64, per term, on
+            # the same samples (the first cs timed steps)
+            am, af = merge_terms(results[:cs]), merge_terms(fres)
+            rel = {}
+            for t in sorted(af):
+                mu_m, mu_f = stats_of(am[t])[0], stats_of(af[t])[0]
+                rel[str(t)] = abs(mu_m - mu_f) / abs(mu_f) if mu_f != 0 else abs(mu_m)
+            compare['mlmc_fp64'] = dict(value=fval, ms_per_step=fms / cs, detail=fdet,
+                                        mixed_vs_fp64_rel_diff=rel)
             pres, pms = timed(k0, 1, M.EST_PLAIN)
             p64, p64d = time_to_variance(merge_terms(pres), 1, pms, 1, var_of=pvar, eps=eps0)
             compare['plain_hutchinson_fp64'] = dict(value=p64, ms_per_step=pms)
