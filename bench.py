@@ -418,7 +418,7 @@ def main():
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     def step(k, kind=M.EST_ORTHOGONAL):
-        n = [B] * nterm if kind == M.EST_ORTHOGONAL else [B]
+        n = {M.EST_ORTHOGONAL: [B] * nterm, M.EST_OBLIQUE: [B] * (len(BLOCKS) + 1)}.get(kind, [B])
         return M.mgmlmc_estimate_trace(ctx, M.est_params(kind, n, batch=B, seed=NOISE_SEED,
                                                          first_sample=first_sample(rank, k, B)))
 
@@ -513,6 +513,11 @@ def main():
         pval, pdet = time_to_variance(merge_terms(pres), 1, pms / cs, cs, eps=eps0)
         compare['plain_hutchinson_same_solver'] = dict(value=pval, ms_per_step=pms / cs, detail=pdet)
         pvar = {t: v['var'] for t, v in pdet['terms'].items()}
+        # the paper's earlier decomposition (Eq. oblique_multigrid-multilevel-monte-carlo)
+        # with the same solver: its own terms, variances from its own samples
+        ores, oms = timed(k0, cs, M.EST_OBLIQUE)
+        oval, odet = time_to_variance(merge_terms(ores), 1, oms / cs, cs, eps=eps0)
+        compare['mlmc_oblique_same_solver'] = dict(value=oval, ms_per_step=oms / cs, detail=odet)
         if args.learned > 0:
             M.mgmlmc_set_solver(ctx, precision=prec, **SOLVER)
             step(k0)

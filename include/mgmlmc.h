@@ -122,18 +122,30 @@ typedef struct {
                                      is redone with SAP alone (counted in
                                      mgmlmc_learned_stats) */
 
-typedef enum { MGMLMC_EST_PLAIN = 0, MGMLMC_EST_ORTHOGONAL = 1 } mgmlmc_estimator;
+/* PLAIN: Hutchinson (Sec. 1, Eq. Hutchinson).  ORTHOGONAL: Sec. 3, Eq.
+ * smultigrid-multilevel-monte-carlo (terms O_l, F_l, coarsest).  OBLIQUE:
+ * Sec. 2.2, Eq. oblique_multigrid-multilevel-monte-carlo, the earlier
+ * decomposition the paper compares against: terms M_l = D_l^-1 -
+ * P_l D_{l+1}^-1 P_l^H (Eq. oblique-deflation), sampled as
+ * x^H D_l^-1 x - (P_l^H x)^H D_{l+1}^-1 (P_l^H x), then the coarsest. */
+typedef enum {
+  MGMLMC_EST_PLAIN = 0,
+  MGMLMC_EST_ORTHOGONAL = 1,
+  MGMLMC_EST_OBLIQUE = 2
+} mgmlmc_estimator;
 
 /* Term codes of the results (same numbers as the noise term ids). */
 #define MGMLMC_TERM_PLAIN 0
 #define MGMLMC_TERM_O 16        /* + level */
 #define MGMLMC_TERM_F 32        /* + level */
 #define MGMLMC_TERM_COARSEST 48
+#define MGMLMC_TERM_M 144       /* + level: oblique M_l */
 
 typedef struct {
   int kind;          /* mgmlmc_estimator */
   int n_samples[2 * MGMLMC_MAX_LEVELS]; /* per term in the order
-                       O_0..O_{L-2}, F_0..F_{L-2}, coarsest; plain: [0] */
+                       O_0..O_{L-2}, F_0..F_{L-2}, coarsest; oblique:
+                       M_0..M_{L-2}, coarsest; plain: [0] */
   int batch;         /* right-hand sides solved together, >= 1 */
   uint64_t seed;     /* noise seed */
   uint64_t first_sample; /* sample counter of the first sample */
@@ -165,6 +177,17 @@ const char *mgmlmc_last_error(const mgmlmc_ctx *ctx);
  * double in the canonical link layout; host pointer (on_device = 0) or
  * device pointer (on_device = 1).  Invalidates the hierarchy. */
 mgmlmc_status mgmlmc_set_gauge(mgmlmc_ctx *ctx, const double *U, int on_device);
+/* Generate the gauge field on the device instead: synthetic SU(3) links
+ * U_mu(x) = exp(i eps H) standing in for the paper's ensembles (Sec. 4 uses
+ * real ones), H a random traceless Hermitian matrix per link.  Link
+ * L = 4 s + mu draws the 20 Philox4x64-10 words of counters (L, j, 128, 0),
+ * j = 0..4, key (seed, 0); entry e (row-major) of A uses words 2e, 2e + 1
+ * as uniforms u = ((w >> 12) + 1/2) 2^-52 (inside (0, 1)) and Box-Muller,
+ * A_e = sqrt(-2 ln u1) (cos 2 pi u2 + i sin 2 pi u2) / sqrt 2; then
+ * H = (A + A^H)/2 - tr(.)/3 and U = exp(i eps H) in FP64.  eps = 0 gives the
+ * free field.  Invalidates the hierarchy; MGMLMC_ERR_ARG for a non-finite
+ * eps. */
+mgmlmc_status mgmlmc_gen_gauge(mgmlmc_ctx *ctx, double eps, uint64_t seed);
 /* Bare mass m0 of the Wilson operator.  Invalidates the hierarchy. */
 mgmlmc_status mgmlmc_set_mass(mgmlmc_ctx *ctx, double m0);
 /* Solver parameters (defaults: tol 1e-12, max_iter 2000, restart 16,

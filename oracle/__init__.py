@@ -19,6 +19,9 @@ no blocking, fusion or reordering beyond what the definition states:
 * ``dirac``      the Wilson-Dirac operator D (Sec. 1: 12 dof per site) and
                  Gamma_5 (Sec. 2, 'Deflation for the Dirac operator').
 * ``noise``      Philox4x64-10 and the Z4 distribution (Sec. 1, Eq. z4).
+* ``gauge``      the counter-based synthetic gauge field exp(i eps H) that
+                 the library can draw on the device (stand-in for the
+                 ensembles of Sec. 4), with the same published Philox.
 * ``multigrid``  aggregation, per-aggregate orthonormalised P, R = P^H,
                  Galerkin D_{l+1} = P^H D_l P (Sec. 2.2, Eq. Al_def and the
                  Galerkin paragraph; Sec. 3).

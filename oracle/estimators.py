@@ -12,6 +12,12 @@
      F_l = P_l^H D_l^-1 P_l - D_{l+1}^-1.
   O_l sample (Sec. 3): y = (I - P P^H) x, solve D_l z = y, X = y^H z.
   F_l sample: x on level l+1, X = (P x)^H D_l^-1 (P x) - x^H D_{l+1}^-1 x.
+* Oblique multigrid MLMC (Sec. 2.2, Eq. oblique-deflation and
+  Eq. oblique_multigrid-multilevel-monte-carlo):
+     tr(D^-1) = sum_{l<L} tr(M_l) + tr(D_L^-1),
+     M_l = D_l^-1 - P_l D_{l+1}^-1 R_l = (I - Pi_l) D_l^-1, R_l = P_l^H,
+     Pi_l = P_l D_{l+1}^-1 R_l D_l (an oblique projection by Galerkin).
+  M_l sample: x on level l, X = x^H D_l^-1 x - (R_l x)^H D_{l+1}^-1 (R_l x).
 * Connected correlator (Sec. 1.1, Eq. connected-G; Sec. 4.1, Eq.
   full_ops_orth and Eq. G-split), orthogonal split with
      J_l = (I - P_l P_l^H) D_l^-1,
@@ -81,6 +87,13 @@ class Estimators:
         z2 = self.sol[l + 1](x)
         return np.vdot(y, z1) - np.vdot(x, z2)
 
+    def M(self, l, k):
+        x = nz.z4_vector(self.h.size(l), self.seed, k, nz.TERM_M + l)
+        z1 = self.sol[l](x)
+        xc = self.h.P[l].restrict(x)
+        z2 = self.sol[l + 1](xc)
+        return np.vdot(x, z1) - np.vdot(xc, z2)
+
     def coarsest(self, k):
         L = self.h.n_levels - 1
         x = nz.z4_vector(self.h.size(L), self.seed, k, nz.TERM_COARSEST)
@@ -91,6 +104,13 @@ class Estimators:
         L = self.h.n_levels
         out = [('O%d' % l, lambda k, l=l: self.O(l, k)) for l in range(L - 1)]
         out += [('F%d' % l, lambda k, l=l: self.F(l, k)) for l in range(L - 1)]
+        out.append(('coarsest', self.coarsest))
+        return out
+
+    def oblique_terms(self):
+        """[(name, sampler)] in the order M_0..M_{L-2}, coarsest."""
+        L = self.h.n_levels
+        out = [('M%d' % l, lambda k, l=l: self.M(l, k)) for l in range(L - 1)]
         out.append(('coarsest', self.coarsest))
         return out
 

@@ -101,6 +101,7 @@ TERM_F = 32          # + level (0-based)
 TERM_COARSEST = 48
 TERM_CONNECTED = 64  # aux = source time slice
 TERM_DISCONNECTED = 80  # aux = time slice
+TERM_M = 144         # + level (0-based): oblique M_l
 
 
 def term_id(kind, level=0):

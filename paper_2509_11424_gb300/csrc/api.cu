@@ -78,6 +78,10 @@ mgmlmc_status mgmlmc_set_gauge(mgmlmc_ctx *ctx, const double *U, int on_device) 
   });
 }
 
+mgmlmc_status mgmlmc_gen_gauge(mgmlmc_ctx *ctx, double eps, uint64_t seed) {
+  return guard(ctx, [&] { E(ctx).gen_gauge(eps, seed); });
+}
+
 mgmlmc_status mgmlmc_set_mass(mgmlmc_ctx *ctx, double m0) {
   return guard(ctx, [&] { E(ctx).set_mass(m0); });
 }

@@ -240,6 +240,17 @@ void Engine::set_gauge(const double *U, bool on_device) {
     have_gauge_ = false;
     throw Error(MGMLMC_ERR_NUMERIC, "gauge field contains NaN or Inf");
   }
+  gauge_derived();
+}
+
+void Engine::gen_gauge(double eps, uint64_t seed) {
+  if (!std::isfinite(eps)) throw Error(MGMLMC_ERR_ARG, "eps must be finite");
+  gauge_generate(levels_[0].U64, (int64_t)fine_.V * 4, eps, seed, stream);
+  gauge_derived();
+}
+
+void Engine::gauge_derived() {
+  const size_t cnt = (size_t)fine_.V * 36;
   convert<float, double>(levels_[0].U64, levels_[0].U32, (int64_t)cnt, stream);
   link_soa(levels_[0].U32, levels_[0].UD32, fine_.V, stream);
   have_gauge_ = true;
@@ -940,6 +951,10 @@ void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &ou
     for (int l = 0; l + 1 < L; ++l) terms.push_back({MGMLMC_TERM_O + l, l, 1, p.n_samples[idx++]});
     for (int l = 0; l + 1 < L; ++l) terms.push_back({MGMLMC_TERM_F + l, l, 2, p.n_samples[idx++]});
     terms.push_back({MGMLMC_TERM_COARSEST, L - 1, 3, p.n_samples[idx++]});
+  } else if (p.kind == MGMLMC_EST_OBLIQUE) {
+    int idx = 0;
+    for (int l = 0; l + 1 < L; ++l) terms.push_back({MGMLMC_TERM_M + l, l, 4, p.n_samples[idx++]});
+    terms.push_back({MGMLMC_TERM_COARSEST, L - 1, 3, p.n_samples[idx++]});
   } else {
     throw Error(MGMLMC_ERR_ARG, "unknown estimator kind");
   }
@@ -991,6 +1006,20 @@ void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &ou
         acc.max_res = std::max(acc.max_res, std::max(s1.residual, s2.residual));
         dot<double>(y, z1, n, nb, res, partials((size_t)reduce_blocks(n) * nb), stream);
         dot<double>(x, z2, nc, nb, res + nb, partials((size_t)reduce_blocks(nc) * nb), stream);
+      } else if (td.kind == 4) {
+        // oblique M_l (Eq. oblique-deflation): x^H D_l^-1 x - (P^H x)^H D_{l+1}^-1 (P^H x)
+        const int64_t nc = levels_[l + 1].g.n();
+        double2 *x = ws<double>("estx", l, (size_t)nb * n), *z1 = ws<double>("estz", l, (size_t)nb * n);
+        double2 *xc = ws<double>("estxc", l + 1, (size_t)nb * nc), *z2 = ws<double>("estzc", l + 1, (size_t)nb * nc);
+        noise(l, p.seed, s0, MGMLMC_TERM_M + l, 0, -1, x, nb);
+        SolveInfo s1 = solve(l, x, z1, nb);
+        restrict_to<double>(l, x, xc, nb);
+        SolveInfo s2 = solve(l + 1, xc, z2, nb);
+        acc.iters_sum += s1.iters + s2.iters;
+        acc.solves += 2;
+        acc.max_res = std::max(acc.max_res, std::max(s1.residual, s2.residual));
+        dot<double>(x, z1, n, nb, res, partials((size_t)reduce_blocks(n) * nb), stream);
+        dot<double>(xc, z2, nc, nb, res + nb, partials((size_t)reduce_blocks(nc) * nb), stream);
       } else {
         double2 *x = ws<double>("estx", l, (size_t)nb * n), *z = ws<double>("estz", l, (size_t)nb * n);
         noise(l, p.seed, s0, MGMLMC_TERM_COARSEST, 0, -1, x, nb);
@@ -1006,7 +1035,7 @@ void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &ou
       acc.seconds += ms * 1e-3;
       for (int q = 0; q < nb; ++q) {
         std::complex<double> v(h[q].x, h[q].y);
-        if (td.kind == 2) v -= std::complex<double>(h[nb + q].x, h[nb + q].y);
+        if (td.kind == 2 || td.kind == 4) v -= std::complex<double>(h[nb + q].x, h[nb + q].y);
         X.push_back(v);
       }
     }

@@ -89,6 +89,8 @@ class Engine {
   ~Engine();
 
   void set_gauge(const double *U, bool on_device);
+  // U = exp(i eps H) generated on the device (kernels.h gauge_generate)
+  void gen_gauge(double eps, uint64_t seed);
   void set_mass(double m0);
   void set_solver(const mgmlmc_solver_params &p);
   void set_test_vectors(int level, const double *V, int ntv, int64_t n, bool on_device);
@@ -170,6 +172,7 @@ class Engine {
   SolveInfo solve_mixed(int l, const double2 *b, double2 *x, int nrhs);
   void galerkin(int l);
   void free_hierarchy();
+  void gauge_derived();  // FP32 and structure-of-arrays copies of the new links
   void sync();
 
   int dims_[4];

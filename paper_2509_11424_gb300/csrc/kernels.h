@@ -102,6 +102,10 @@ template <typename T>
 void wilson_apply(const C<T> *in, C<T> *out, const C<T> *U, const C<T> *UDs, Geom g, double m0,
                   int nrhs, int variant, cudaStream_t s);
 int wilson_fp32_variants();
+// nlinks synthetic SU(3) links U = exp(i eps H) from a counter-based draw
+// (seed): Philox4x64-10 words -> Box-Muller normals A -> H = (A + A^H)/2 -
+// tr/3 -> matrix exponential; U row-major per link, canonical link order
+void gauge_generate(double2 *U, int64_t nlinks, double eps, uint64_t seed, cudaStream_t s);
 // UDs[mu][a][b][s] = U[s][mu][a][b]
 void link_soa(const float2 *U, float2 *UDs, int V, cudaStream_t s);
 // the 9 hop-class parts of D (Galerkin): out9[h] for h = 0..8, single rhs.

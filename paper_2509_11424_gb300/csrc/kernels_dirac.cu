@@ -414,6 +414,101 @@ __global__ void z4_kernel(C<T> *__restrict__ out, int64_t n, uint64_t seed, uint
   }
 }
 
+// ------------------------------------------------------------------ gauge
+// Synthetic links U = exp(i eps H), H traceless Hermitian.  Link L = 4 s + mu
+// draws the 20 Philox4x64-10 words of counters (L, j, 128, 0), j = 0..4, key
+// (seed, 0); entry e (row-major) of A uses words 2e, 2e + 1 as uniforms
+// u = ((w >> 12) + 1/2) 2^-52 in (0, 1) (exact: the sum stays below 2^52)
+// and Box-Muller:
+// A_e = sqrt(-2 ln u1) (cos 2 pi u2 + i sin 2 pi u2) / sqrt 2, E|A_e|^2 = 1.
+// H = (A + A^H) / 2 - tr / 3; the exponential by scaling (Frobenius norm
+// <= 1/4), a degree-16 Taylor polynomial and repeated squaring, all FP64.
+constexpr uint64_t kTermGauge = 128;
+
+__device__ __forceinline__ void mat3_mul(const double2 (&a)[9], const double2 (&b)[9],
+                                         double2 (&c)[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double2 z = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) z = cfma(a[3 * i + k], b[3 * k + j], z);
+      c[3 * i + j] = z;
+    }
+}
+
+__global__ void gauge_kernel(double2 *__restrict__ U, int64_t nlinks, double eps, uint64_t seed) {
+  for (int64_t L = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; L < nlinks;
+       L += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t w[20];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+      U64x4 c;
+      c.v[0] = (uint64_t)L;
+      c.v[1] = (uint64_t)j;
+      c.v[2] = kTermGauge;
+      c.v[3] = 0ull;
+      const U64x4 r = philox4x64_10(c, seed, 0ull);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) w[4 * j + k] = r.v[k];
+    }
+    double2 A[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const double u1 = ((double)(w[2 * e] >> 12) + 0.5) * 0x1p-52;
+      const double u2 = ((double)(w[2 * e + 1] >> 12) + 0.5) * 0x1p-52;
+      const double rho = sqrt(-2.0 * log(u1)) * 0.70710678118654752440;
+      double sn, cs;
+      sincospi(2.0 * u2, &sn, &cs);
+      A[e] = make_double2(rho * cs, rho * sn);
+    }
+    double2 X[9];
+    double nrm2 = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        // H_ab = (A_ab + conj(A_ba)) / 2, X = i eps H
+        const double hr = 0.5 * (A[3 * a + b].x + A[3 * b + a].x);
+        const double hi = 0.5 * (A[3 * a + b].y - A[3 * b + a].y);
+        X[3 * a + b] = make_double2(-eps * hi, eps * hr);
+      }
+    const double tr = (X[0].y + X[4].y + X[8].y) / 3.0;  // X diagonal is i eps H_aa
+    X[0].y -= tr;
+    X[4].y -= tr;
+    X[8].y -= tr;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) nrm2 += X[e].x * X[e].x + X[e].y * X[e].y;
+    int k = 0;
+    double scale = 1.0;
+    while (nrm2 * scale * scale > 0.0625 && k < 60) {
+      scale *= 0.5;
+      ++k;
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) X[e] = cscale(X[e], scale);
+    double2 E[9], T[9], Tn[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) E[e] = T[e] = make_double2((e % 4 == 0) ? 1.0 : 0.0, 0.0);
+    for (int m = 1; m <= 16; ++m) {
+      mat3_mul(T, X, Tn);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) {
+        T[e] = cscale(Tn[e], 1.0 / m);
+        E[e] = cadd(E[e], T[e]);
+      }
+    }
+    for (int q = 0; q < k; ++q) {
+      mat3_mul(E, E, Tn);
+#pragma unroll
+      for (int e = 0; e < 9; ++e) E[e] = Tn[e];
+    }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) U[L * 9 + e] = E[e];
+  }
+}
+
 inline int grid_for(int64_t n) {
   int64_t b = (n + 255) / 256;
   return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
@@ -493,6 +588,11 @@ void z4_noise(C<T> *out, Geom g, uint64_t seed, uint64_t sample0, uint64_t term,
   }
   const int gx = grid_for((n + 3) / 4);
   z4_kernel<T><<<dim3(gx, nrhs), 256, 0, s>>>(out, n, seed, sample0, term, aux, lo, hi);
+  MG_LAUNCH_CHECK();
+}
+
+void gauge_generate(double2 *U, int64_t nlinks, double eps, uint64_t seed, cudaStream_t s) {
+  gauge_kernel<<<grid_for(nlinks), 256, 0, s>>>(U, nlinks, eps, seed);
   MG_LAUNCH_CHECK();
 }
 

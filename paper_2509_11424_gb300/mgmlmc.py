@@ -17,9 +17,9 @@ LIB_PATH = os.path.join(HERE, 'libmgmlmc.so')
 
 MAX_LEVELS = 4
 FP64, FP32 = 0, 1
-EST_PLAIN, EST_ORTHOGONAL = 0, 1
+EST_PLAIN, EST_ORTHOGONAL, EST_OBLIQUE = 0, 1, 2
 OP_D, OP_RESTRICT, OP_PROLONG, OP_PROJECT, OP_SOLVE, OP_GAMMA5, OP_SMOOTH, OP_NET = range(8)
-TERM_PLAIN, TERM_O, TERM_F, TERM_COARSEST = 0, 16, 32, 48
+TERM_PLAIN, TERM_O, TERM_F, TERM_COARSEST, TERM_M = 0, 16, 32, 48, 144
 STATUS = {0: 'OK', 1: 'ERR_ARG', 2: 'ERR_STATE', 3: 'ERR_OOM', 4: 'ERR_CUDA',
           5: 'ERR_NOT_CONVERGED', 6: 'ERR_NUMERIC'}
 
@@ -126,6 +126,7 @@ _SIGNATURES = {
     'mgmlmc_profile_stats': [_P, _I, ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.POINTER(_D),
                              ctypes.POINTER(_D)],
     'mgmlmc_set_kernel_variant': [_P, _I, _I],
+    'mgmlmc_gen_gauge': [_P, _D, _U64],
     'mgmlmc_reorder': [_P, _P, _P, _I, _I],
     'mgmlmc_kernel_variants': [_I],
     'mgmlmc_get_kernel_variant': [_P, _I, _I, ctypes.POINTER(_I)],
@@ -349,6 +350,12 @@ def mgmlmc_reorder(ctx, inp, out, nrhs, to_internal):
     structure-of-arrays order."""
     _check(ctx, lib().mgmlmc_reorder(ctx, ptr(inp), ptr(out), nrhs, int(bool(to_internal))))
 VARIANT_AUTOTUNE = -2
+
+
+def mgmlmc_gen_gauge(ctx, eps, seed):
+    """Synthetic SU(3) gauge field U = exp(i eps H) generated on the device
+    (counter-based draw, see include/mgmlmc.h)."""
+    _check(ctx, lib().mgmlmc_gen_gauge(ctx, float(eps), int(seed)))
 
 
 def mgmlmc_kernel_variants(kernel):

@@ -286,6 +286,36 @@ def test_trace_estimator_samples_match_oracle(three):
     assert abs(complex(plain['mean_re'], plain['mean_im']) - X.mean()) < 1e-8 * abs(X.mean())
 
 
+def test_oblique_estimator_samples_match_oracle(three):
+    """the oblique decomposition (Eq. oblique_multigrid-multilevel-monte-carlo):
+    identical noise and P, per-term sample means and variances of M_0, M_1 and
+    the coarsest term equal the oracle's to solve accuracy; the term codes are
+    MGMLMC_TERM_M + level."""
+    h = three.hier
+    sol = [osolve.LevelSolver(h.matrix(l)) for l in range(3)]
+    E = oest.Estimators(h, sol, seed=2233)
+    N = 10
+    res = M.mgmlmc_estimate_trace(three.ctx, M.est_params(M.EST_OBLIQUE, [N] * 3, batch=4, seed=2233))
+    assert [r['term'] for r in res] == [M.TERM_M, M.TERM_M + 1, M.TERM_COARSEST]
+    for r, (name, sampler) in zip(res, E.oblique_terms()):
+        X = np.array([sampler(k) for k in range(N)])
+        mu, var = oest.sample_stats(X)
+        assert r['n'] == N
+        assert abs(complex(r['mean_re'], r['mean_im']) - mu) < 1e-8 * max(1.0, abs(mu)), name
+        assert abs(r['var'] - var) < 1e-7 * max(1.0, var), name
+        assert r['max_residual'] <= 1.5e-12
+
+
+def test_oblique_trace_unbiased_config1(cfg1):
+    """config-1: oblique MG-MLMC (N = 200 per term) within 3 SE of the dense
+    exact tr(D^-1)."""
+    exact_tr = np.trace(np.linalg.inv(cfg1.hier.matrix(0).toarray()))
+    res = M.mgmlmc_estimate_trace(cfg1.ctx, M.est_params(M.EST_OBLIQUE, [200, 200], batch=25, seed=2311))
+    est = sum(complex(r['mean_re'], r['mean_im']) for r in res)
+    se = np.sqrt(sum(r['var'] / r['n'] for r in res))
+    assert abs(est - exact_tr) < 3 * se
+
+
 def test_trace_unbiased_config1(cfg1):
     """config-1: orthogonal MG-MLMC (N = 200 per term, seed 2301) and plain
     Hutchinson (N = 200) each within 3 SE of the dense exact tr(D^-1)."""

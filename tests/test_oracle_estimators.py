@@ -172,3 +172,56 @@ def test_disconnected_exact_and_free_field():
     mu = X.mean(axis=0)
     se = np.sqrt(np.sum(np.abs(X - mu) ** 2, axis=0) / (200 - 1) / 200)
     assert np.all(np.abs(mu - exact.loop_exact(B, dims, 1)) < 5 * se)
+
+
+def _dense_M(h, dt, l):
+    """M_l = D_l^-1 - P_l D_{l+1}^-1 P_l^H from dense inverses (Eq.
+    oblique-deflation), written from the definition."""
+    P = dt.P[l]
+    return dt.Dinv[l] - P @ dt.Dinv[l + 1] @ P.conj().T
+
+
+@pytest.mark.parametrize('fx', ['two_level', 'three_level'])
+def test_oblique_split_telescopes_and_projects(fx, request):
+    """sum_l tr(M_l) + tr(D_L^-1) = tr(D^-1) (Eq.
+    oblique_multigrid-multilevel-monte-carlo) exactly; Pi_l = P D_{l+1}^-1
+    P^H D_l is a projection (Galerkin) but not an orthogonal one, and
+    M_l = (I - Pi_l) D_l^-1."""
+    h, dt, _ = request.getfixturevalue(fx)
+    L = h.n_levels
+    total = sum(np.trace(_dense_M(h, dt, l)) for l in range(L - 1)) + np.trace(dt.Dinv[L - 1])
+    assert abs(total - np.trace(dt.Dinv[0])) < 1e-10 * abs(np.trace(dt.Dinv[0]))
+    for l in range(L - 1):
+        D = h.matrix(l).toarray()
+        P = dt.P[l]
+        Pi = P @ dt.Dinv[l + 1] @ P.conj().T @ D
+        assert np.max(np.abs(Pi @ Pi - Pi)) < 1e-10 * np.max(np.abs(Pi))
+        assert np.max(np.abs(Pi - Pi.conj().T)) > 1e-3  # oblique
+        I = np.eye(D.shape[0])
+        assert np.max(np.abs((I - Pi) @ dt.Dinv[l] - _dense_M(h, dt, l))) < 1e-10 * np.max(np.abs(dt.Dinv[l]))
+
+
+def test_oblique_samples_equal_quadratic_forms(three_level):
+    h, dt, sol = three_level
+    E = est.Estimators(h, sol, seed=2011)
+    from oracle import noise as nz
+    for k in range(3):
+        for l in range(h.n_levels - 1):
+            x = nz.z4_vector(h.size(l), 2011, k, nz.TERM_M + l)
+            assert abs(E.M(l, k) - np.vdot(x, _dense_M(h, dt, l) @ x)) < 1e-9
+    names = [n for n, _ in E.oblique_terms()]
+    assert names == ['M0', 'M1', 'coarsest']
+
+
+def test_oblique_terms_unbiased_and_variance_law(two_level):
+    """fixed seed 2012, N = 300: the M_0 sample mean within 4 SE of tr(M_0),
+    its sample variance near the Z4 law ||offdiag(M_0)||_F^2."""
+    h, dt, sol = two_level
+    E = est.Estimators(h, sol, seed=2012)
+    T = _dense_M(h, dt, 0)
+    N = 300
+    X = np.array([E.M(0, k) for k in range(N)])
+    mu, var = est.sample_stats(X)
+    law = exact.offdiag_fro2(T)
+    assert abs(mu - np.trace(T)) < 4 * np.sqrt(law / N) + 1e-12
+    assert 0.6 * law < var < 1.5 * law, (var, law)
