@@ -350,6 +350,33 @@ def dslash_hbm(M, torch, U16, m0, reps=5):
                 frac_of_measured_hbm=gbs / hbm if hbm else None,
                 variant=M.mgmlmc_get_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, nrhs),
                 gbs_per_variant=per_variant)
+        # BF16 storage, FP32 arithmetic: (24 nrhs + 36) x 4 B per site
+        for nrhs in (1, 8):
+            xc = torch.randn((nrhs, V * 24), dtype=torch.float32, device='cuda').to(torch.bfloat16)
+            x = torch.empty_like(xc)
+            M.mgmlmc_reorder_bf16(ctx, xc, x, nrhs, 1)
+            del xc
+            y = torch.empty_like(x)
+
+            def run_bf16():
+                M.mgmlmc_apply(ctx, op, 0, M.BF16, x, y, nrhs)
+
+            for _ in range(3):
+                run_bf16()
+            ts = []
+            for _ in range(reps):
+                e0.record()
+                for _ in range(10):
+                    run_bf16()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) / 10)
+            ms = float(np.median(ts))
+            by = V * (24.0 * nrhs + 36.0) * 4
+            gbs = by / (ms * 1e-3) / 1e9
+            out['bf16_nrhs%d' % nrhs] = dict(ms=ms, algorithmic_bytes=by, achieved_gbs=gbs,
+                                             frac_of_measured_hbm=gbs / hbm if hbm else None,
+                                             site_updates_per_s=V * nrhs / (ms * 1e-3))
         out['lattice'] = list(dims)
     finally:
         M.mgmlmc_destroy(ctx)

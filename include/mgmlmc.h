@@ -78,7 +78,10 @@ typedef enum {
   MGMLMC_ERR_NUMERIC = 6         /* NaN / Inf / breakdown */
 } mgmlmc_status;
 
-typedef enum { MGMLMC_FP64 = 0, MGMLMC_FP32 = 1 } mgmlmc_precision;
+/* MGMLMC_BF16 (bfloat16 storage, FP32 arithmetic) is accepted by
+ * mgmlmc_apply for MGMLMC_OP_D on level 0 only; the solver runs FP64 or
+ * FP32. */
+typedef enum { MGMLMC_FP64 = 0, MGMLMC_FP32 = 1, MGMLMC_BF16 = 2 } mgmlmc_precision;
 
 /* Multigrid hierarchy (Sec. 2.2: aggregation-based P_l with P_l^H P_l = I,
  * Galerkin D_{l+1} = P_l^H D_l P_l; Sec. 4: test vectors are rough
@@ -265,9 +268,11 @@ typedef enum {
 /* Apply an operator to nrhs device vectors.  precision selects the storage
  * type of in/out (complex double for MGMLMC_FP64, complex float for
  * MGMLMC_FP32; MGMLMC_OP_SOLVE accepts MGMLMC_FP64 only, its internal
- * precision is the solver's).  in and out must not overlap.  Level-0 FP32
- * vectors are reordered to and from the internal order around the operator
- * unless op carries MGMLMC_LAYOUT_INTERNAL. */
+ * precision is the solver's; MGMLMC_BF16, complex bfloat16 storage with
+ * FP32 arithmetic, is accepted for MGMLMC_OP_D on level 0).  in and out
+ * must not overlap.  Level-0 FP32 and BF16 vectors are reordered to and from
+ * the internal order around the operator unless op carries
+ * MGMLMC_LAYOUT_INTERNAL. */
 mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op, int level, int precision,
                            const void *in, void *out, int nrhs);
 /* Reorder nrhs level-0 complex-float device vectors between the canonical
@@ -278,6 +283,11 @@ mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op, int level, int precision,
  * out internal; 0: the reverse.  in and out must not overlap. */
 mgmlmc_status mgmlmc_reorder(mgmlmc_ctx *ctx, const void *in, void *out, int nrhs,
                              int to_internal);
+/* The same for level-0 complex-bfloat16 vectors (pairs re, im of bf16, the
+ * MGMLMC_BF16 storage of mgmlmc_apply): internally component i of site s is
+ * the pair ((i / 4) V + s) * 4 + i % 4, 16-byte chunks of four components. */
+mgmlmc_status mgmlmc_reorder_bf16(mgmlmc_ctx *ctx, const void *in, void *out, int nrhs,
+                                  int to_internal);
 /* The projection of MGMLMC_OP_PROJECT, out = (I - P_l P_l^H) in, without any
  * device allocation during the call.  The paper has no counterpart: this is
  * for callers that cannot allocate device memory while they run -- code

@@ -192,6 +192,15 @@ mgmlmc_status mgmlmc_reorder(mgmlmc_ctx *ctx, const void *in, void *out, int nrh
   });
 }
 
+mgmlmc_status mgmlmc_reorder_bf16(mgmlmc_ctx *ctx, const void *in, void *out, int nrhs,
+                                  int to_internal) {
+  return guard(ctx, [&] {
+    mg::Engine &e = E(ctx);
+    if (!in || !out || nrhs < 1) throw mg::Error(MGMLMC_ERR_ARG, "bad buffers or nrhs");
+    mg::relayout_bf16(in, out, e.level(0).g.V, nrhs, to_internal != 0, e.stream);
+  });
+}
+
 mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op_flags, int level, int precision, const void *in,
                            void *out, int nrhs) {
   return guard(ctx, [&] {
@@ -199,6 +208,24 @@ mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op_flags, int level, int precisi
     const bool internal = (op_flags & MGMLMC_LAYOUT_INTERNAL) != 0;
     const int op = op_flags & ~MGMLMC_LAYOUT_INTERNAL;
     if (!in || !out || nrhs < 1) throw mg::Error(MGMLMC_ERR_ARG, "bad buffers or nrhs");
+    if (precision == MGMLMC_BF16) {
+      if (op != MGMLMC_OP_D || level != 0)
+        throw mg::Error(MGMLMC_ERR_ARG, "BF16 storage is available for the level-0 Wilson operator only");
+      const mg::Geom &g = e.level(0).g;
+      const size_t bytes = (size_t)g.n() * nrhs * 4;
+      const void *src = in;
+      void *dst = out;
+      if (!internal) {
+        void *t = e.scratch32("api_in_bf16", (bytes + 7) / 8);
+        mg::relayout_bf16(in, t, g.V, nrhs, true, e.stream);
+        src = t;
+        dst = e.scratch32("api_out_bf16", (bytes + 7) / 8);
+      }
+      e.apply_D_bf16(src, dst, nrhs);
+      if (!internal) mg::relayout_bf16(dst, out, g.V, nrhs, false, e.stream);
+      MG_CUDA(cudaGetLastError());
+      return;
+    }
     if (precision != MGMLMC_FP64 && precision != MGMLMC_FP32) throw mg::Error(MGMLMC_ERR_ARG, "bad precision");
     if (level < 0 || level >= e.n_levels()) throw mg::Error(MGMLMC_ERR_ARG, "level out of range");
     const bool dp = precision == MGMLMC_FP64;

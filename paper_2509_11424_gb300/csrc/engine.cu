@@ -74,6 +74,7 @@ Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
   levels_[0].U64 = dalloc<double2>((size_t)V * 36);
   levels_[0].U32 = dalloc<float2>((size_t)V * 36);
   levels_[0].UD32 = dalloc<float2>((size_t)V * 36);
+  levels_[0].Ub16 = dalloc<float>((size_t)V * 36);  // 36 bf16 pairs of 4 bytes per site
   scal_ = dalloc<double2>(4096);
   flag_dev_ = dalloc<int>(16);
   MG_CUDA(cudaMemset(flag_dev_, 0, 16 * sizeof(int)));
@@ -89,6 +90,7 @@ Engine::~Engine() {
   dfree(levels_[0].U64);
   dfree(levels_[0].U32);
   dfree(levels_[0].UD32);
+  dfree(levels_[0].Ub16);
   for (auto &kv : ws_) cudaFree(kv.second.first);
   for (auto &p : pending_) {
     cudaEventDestroy(p.a);
@@ -253,6 +255,7 @@ void Engine::gauge_derived() {
   const size_t cnt = (size_t)fine_.V * 36;
   convert<float, double>(levels_[0].U64, levels_[0].U32, (int64_t)cnt, stream);
   link_soa(levels_[0].U32, levels_[0].UD32, fine_.V, stream);
+  link_bf16(levels_[0].U32, levels_[0].Ub16, fine_.V, stream);
   have_gauge_ = true;
   free_hierarchy();
 }
@@ -387,6 +390,12 @@ template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int
     MG_CUDA(cudaEventRecord(b, stream));
     pending_.push_back({cls, a, b, bytes, flops});
   }
+}
+
+void Engine::apply_D_bf16(const void *in, void *out, int nrhs) {
+  if (!have_gauge_) throw Error(MGMLMC_ERR_STATE, "no gauge field");
+  const Level &L = levels_[0];
+  wilson_apply_bf16(in, out, L.Ub16, L.g, m0_, nrhs, stream);
 }
 
 template <typename T> AggMap Engine::agg_of(int l) const {

@@ -20,6 +20,7 @@ struct Level {
   double2 *U64 = nullptr;  // fine links [V][4][3][3]
   float2 *U32 = nullptr;
   float2 *UD32 = nullptr;  // FP32 links structure-of-arrays [4][3][3][V] (FP32 kernels)
+  float *Ub16 = nullptr;   // bf16 links structure-of-arrays (one bf16 pair per float slot)
   double2 *A64 = nullptr;   // coarse stencil, canonical [V][9][dof][dof]
   double2 *AT64 = nullptr;  // the same blocks transposed [V][9][j][i] (apply)
   float2 *AT32 = nullptr;
@@ -102,6 +103,8 @@ class Engine {
 
   // operator hooks (device buffers)
   template <typename T> void apply_D(int l, const C<T> *in, C<T> *out, int nrhs);
+  // level-0 D on complex-bf16 vectors in the chunked internal order
+  void apply_D_bf16(const void *in, void *out, int nrhs);
   template <typename T> void restrict_to(int l, const C<T> *in, C<T> *out, int nrhs);
   template <typename T> void prolong_from(int l, const C<T> *in, C<T> *out, int nrhs, double beta);
   template <typename T> void project_out(int l, const C<T> *in, C<T> *out, int nrhs);

@@ -106,6 +106,15 @@ int wilson_fp32_variants();
 // (seed): Philox4x64-10 words -> Box-Muller normals A -> H = (A + A^H)/2 -
 // tr/3 -> matrix exponential; U row-major per link, canonical link order
 void gauge_generate(double2 *U, int64_t nlinks, double eps, uint64_t seed, cudaStream_t s);
+// BF16 storage, FP32 arithmetic: D psi for nrhs vectors of complex bf16 in
+// the chunked structure-of-arrays order (pair ((i/4) V + s) * 4 + i % 4),
+// links Ub from link_bf16; 16-byte aligned
+void wilson_apply_bf16(const void *in, void *out, const void *Ub, Geom g, double m0, int nrhs,
+                       cudaStream_t s);
+// Ub[mu][a][b][s] = bf16(U[s][mu][a][b]) (round to nearest)
+void link_bf16(const float2 *U, void *Ub, int V, cudaStream_t s);
+// canonical complex-bf16 [rhs][site][12] <-> the chunked order above
+void relayout_bf16(const void *x, void *y, int64_t V, int nrhs, bool to_soa, cudaStream_t s);
 // UDs[mu][a][b][s] = U[s][mu][a][b]
 void link_soa(const float2 *U, float2 *UDs, int V, cudaStream_t s);
 // the 9 hop-class parts of D (Galerkin): out9[h] for h = 0..8, single rhs.

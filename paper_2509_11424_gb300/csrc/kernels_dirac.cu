@@ -13,6 +13,8 @@
 // four.  Time is antiperiodic for the fermion field.
 #include "kernels.h"
 
+#include <cuda_bf16.h>
+
 namespace mg {
 
 namespace {
@@ -332,6 +334,106 @@ __global__ void __launch_bounds__(BS, MINB) wilson_soa_kernel(const float2 *__re
   }
 }
 
+// ------------------------------------------------------------------ BF16
+// BF16 storage, FP32 arithmetic.  Spinors structure-of-arrays in 16-byte
+// chunks of 4 complex entries: component i of site s is bf16 pair
+// ((i / 4) V + s) * 4 + i % 4 (3 chunks per site, 48 B); links
+// structure-of-arrays as bf16 pairs, [mu][a][b][s].  One thread per site:
+// each load of a warp is 32 consecutive 16-byte (spinor) or 4-byte (link)
+// words; results are rounded to nearest on the store.
+__device__ __forceinline__ void bf_load(const uint4 *__restrict__ P, int64_t V, int s, float2 (&p)[12]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint4 v = __ldg(P + k * V + s);
+    const unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      __nv_bfloat162 b;
+      memcpy(&b, &w[j], 4);
+      p[4 * k + j] = __bfloat1622float2(b);
+    }
+  }
+}
+
+template <int MU, bool FWD>
+__device__ __forceinline__ void bf_dir(const uint4 *__restrict__ P, const __nv_bfloat162 *__restrict__ Ub,
+                                       const Geom &g, int s, const int (&c)[4], float2 (&acc)[12]) {
+  int cn[4] = {c[0], c[1], c[2], c[3]};
+  if (FWD) cn[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
+  else cn[MU] = (c[MU] == 0) ? g.L[MU] - 1 : c[MU] - 1;
+  const int sn = g.index(cn);
+  const int64_t V = g.V;
+  float2 u[9], p[12];
+  const __nv_bfloat162 *u0 = Ub + (int64_t)MU * 9 * V + (FWD ? s : sn);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = __bfloat1622float2(u0[k * V]);
+  bf_load(P, V, sn, p);
+  const bool wrap = MU == 3 && (FWD ? c[3] + 1 == g.L[3] : c[3] == 0);
+  hop<MU, FWD, float>(p, u, wrap ? 0.5f : -0.5f, acc);
+}
+
+__global__ void __launch_bounds__(128, 6) wilson_bf16_kernel(const uint4 *__restrict__ in, uint4 *__restrict__ out,
+                                                             const __nv_bfloat162 *__restrict__ Ub, Geom g,
+                                                             float diag) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const int64_t V = g.V;
+  const uint4 *P = in + blockIdx.y * 3 * V;
+  int c[4];
+  g.coords(s, c);
+  float2 acc[12];
+  bf_load(P, V, s, acc);
+#pragma unroll
+  for (int i = 0; i < 12; ++i) acc[i] = cscale(acc[i], diag);
+  bf_dir<0, true>(P, Ub, g, s, c, acc);
+  bf_dir<0, false>(P, Ub, g, s, c, acc);
+  bf_dir<1, true>(P, Ub, g, s, c, acc);
+  bf_dir<1, false>(P, Ub, g, s, c, acc);
+  bf_dir<2, true>(P, Ub, g, s, c, acc);
+  bf_dir<2, false>(P, Ub, g, s, c, acc);
+  bf_dir<3, true>(P, Ub, g, s, c, acc);
+  bf_dir<3, false>(P, Ub, g, s, c, acc);
+  uint4 *o = out + blockIdx.y * 3 * V;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    unsigned w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 b = __float22bfloat162_rn(acc[4 * k + j]);
+      memcpy(&w[j], &b, 4);
+    }
+    o[k * V + s] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// bf16 structure-of-arrays links from the FP32 canonical ones
+__global__ void link_bf16_kernel(const float2 *__restrict__ U, __nv_bfloat162 *__restrict__ Ub, int V) {
+  const int64_t total = (int64_t)V * 36;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = i / 36;
+    const int comp = (int)(i - s * 36);
+    Ub[(int64_t)comp * V + s] = __float22bfloat162_rn(U[i]);
+  }
+}
+
+// canonical complex-bf16 vectors (re, im pairs, [site][12]) <-> the chunked
+// structure-of-arrays order above
+__global__ void relayout_bf16_kernel(const __nv_bfloat162 *__restrict__ x, __nv_bfloat162 *__restrict__ y,
+                                     int64_t V, bool to_soa) {
+  const int64_t n = V * 12;
+  const __nv_bfloat162 *xr = x + blockIdx.y * n;
+  __nv_bfloat162 *yr = y + blockIdx.y * n;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = e / 12;
+    const int i = (int)(e - s * 12);
+    const int64_t is = ((int64_t)(i >> 2) * V + s) * 4 + (i & 3);
+    if (to_soa) yr[is] = xr[e];
+    else yr[e] = xr[is];
+  }
+}
+
 // UDs[mu][a][b][s] = U[s][mu][a][b]
 __global__ void link_soa_kernel(const float2 *__restrict__ U, float2 *__restrict__ UDs, int V) {
   const int64_t total = (int64_t)V * 36;
@@ -553,6 +655,28 @@ void wilson_apply(const C<T> *in, C<T> *out, const C<T> *U, const C<T> *UDs, Geo
     wilson_kernel<T, false><<<grid, 128, 0, s>>>(in, out, U, g, (T)(4.0 + m0), 1, 1, 1, 1);
     MG_LAUNCH_CHECK();
   }
+}
+
+void wilson_apply_bf16(const void *in, void *out, const void *Ub, Geom g, double m0, int nrhs,
+                       cudaStream_t s) {
+  if ((((uintptr_t)in | (uintptr_t)out) & 15) != 0 || !Ub)
+    throw Error(1, "BF16 fine vectors must be 16-byte aligned");
+  dim3 grid(div_up(g.V, 128), nrhs);
+  wilson_bf16_kernel<<<grid, 128, 0, s>>>(static_cast<const uint4 *>(in), static_cast<uint4 *>(out),
+                                          static_cast<const __nv_bfloat162 *>(Ub), g, (float)(4.0 + m0));
+  MG_LAUNCH_CHECK();
+}
+
+void link_bf16(const float2 *U, void *Ub, int V, cudaStream_t s) {
+  link_bf16_kernel<<<grid_for((int64_t)V * 36), 256, 0, s>>>(U, static_cast<__nv_bfloat162 *>(Ub), V);
+  MG_LAUNCH_CHECK();
+}
+
+void relayout_bf16(const void *x, void *y, int64_t V, int nrhs, bool to_soa, cudaStream_t s) {
+  const int gx = (grid_for(V * 12) + nrhs - 1) / nrhs + 1;
+  relayout_bf16_kernel<<<dim3(gx, nrhs), 256, 0, s>>>(static_cast<const __nv_bfloat162 *>(x),
+                                                      static_cast<__nv_bfloat162 *>(y), V, to_soa);
+  MG_LAUNCH_CHECK();
 }
 
 void link_soa(const float2 *U, float2 *UDs, int V, cudaStream_t s) {

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, 'libmgmlmc.so')
 
 MAX_LEVELS = 4
-FP64, FP32 = 0, 1
+FP64, FP32, BF16 = 0, 1, 2
 EST_PLAIN, EST_ORTHOGONAL, EST_OBLIQUE = 0, 1, 2
 OP_D, OP_RESTRICT, OP_PROLONG, OP_PROJECT, OP_SOLVE, OP_GAMMA5, OP_SMOOTH, OP_NET = range(8)
 TERM_PLAIN, TERM_O, TERM_F, TERM_COARSEST, TERM_M = 0, 16, 32, 48, 144
@@ -128,6 +128,7 @@ _SIGNATURES = {
     'mgmlmc_set_kernel_variant': [_P, _I, _I],
     'mgmlmc_gen_gauge': [_P, _D, _U64],
     'mgmlmc_reorder': [_P, _P, _P, _I, _I],
+    'mgmlmc_reorder_bf16': [_P, _P, _P, _I, _I],
     'mgmlmc_kernel_variants': [_I],
     'mgmlmc_get_kernel_variant': [_P, _I, _I, ctypes.POINTER(_I)],
 }
@@ -350,6 +351,11 @@ def mgmlmc_reorder(ctx, inp, out, nrhs, to_internal):
     structure-of-arrays order."""
     _check(ctx, lib().mgmlmc_reorder(ctx, ptr(inp), ptr(out), nrhs, int(bool(to_internal))))
 VARIANT_AUTOTUNE = -2
+
+
+def mgmlmc_reorder_bf16(ctx, inp, out, nrhs, to_internal):
+    """Level-0 complex-bfloat16 vectors: canonical <-> internal chunked order."""
+    _check(ctx, lib().mgmlmc_reorder_bf16(ctx, ptr(inp), ptr(out), nrhs, int(bool(to_internal))))
 
 
 def mgmlmc_gen_gauge(ctx, eps, seed):

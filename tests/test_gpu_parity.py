@@ -123,6 +123,42 @@ def test_dslash_fp32(dims, nrhs):
         M.mgmlmc_destroy(ctx)
 
 
+@pytest.mark.parametrize('dims', [(4, 4, 4, 4), (6, 2, 2, 3), (16, 4, 4, 4)])
+def test_dslash_bf16(dims):
+    """BF16 storage, FP32 arithmetic: against the oracle applied to the same
+    bf16-rounded inputs (links FP64 -> FP32 -> bf16 as the library does,
+    spinors bf16).  What remains is the round-to-nearest of each output
+    component, at most 2^-9 relative, so 3e-3 norm-wise.  The internal-order
+    call (reorder, LAYOUT_INTERNAL, reorder back) is bit-identical."""
+    U = synth.gauge_field(dims, 0.5, 7)
+    nrhs = 3
+    ctx = M.mgmlmc_create(dims, torch.cuda.current_stream())
+    try:
+        M.mgmlmc_set_gauge(ctx, U)
+        M.mgmlmc_set_mass(ctx, 0.1)
+        n = dirac.volume(dims) * 12
+        x = synth.complex_normal((nrhs, n), 8).astype(np.complex64)
+        xb = torch.from_numpy(x.view(np.float32)).to(torch.bfloat16).cuda()     # (nrhs, 2n) re, im
+        yb = torch.empty_like(xb)
+        M.mgmlmc_apply(ctx, M.OP_D, 0, M.BF16, xb, yb, nrhs)
+        got = yb.float().cpu().numpy().view(np.complex64).astype(np.complex128)
+        xr = xb.float().cpu().numpy().view(np.complex64).astype(np.complex128)
+        Ur = torch.from_numpy(U.astype(np.complex64).view(np.float32)).to(torch.bfloat16).float()
+        Ur = Ur.numpy().view(np.complex64).astype(np.complex128)
+        for r in range(nrhs):
+            want = dirac.apply_wilson(Ur, xr[r], 0.1, dims)
+            assert rel(got[r], want) < 3e-3
+        xi, yi, yc = torch.empty_like(xb), torch.empty_like(xb), torch.empty_like(xb)
+        M.mgmlmc_reorder_bf16(ctx, xb, xi, nrhs, 1)
+        M.mgmlmc_apply(ctx, M.OP_D | M.LAYOUT_INTERNAL, 0, M.BF16, xi, yi, nrhs)
+        M.mgmlmc_reorder_bf16(ctx, yi, yc, nrhs, 0)
+        assert torch.equal(yc, yb)
+        with pytest.raises(M.MgmlmcError):
+            M.mgmlmc_apply(ctx, M.OP_PROJECT, 0, M.BF16, xb, yb, nrhs)
+    finally:
+        M.mgmlmc_destroy(ctx)
+
+
 def test_dslash_variant_bad_args():
     nv = M.mgmlmc_kernel_variants(M.VARIANT_DSLASH_FP32)
     assert M.mgmlmc_kernel_variants(1) == -1
