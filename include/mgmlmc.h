@@ -219,9 +219,10 @@ mgmlmc_status mgmlmc_level_info(const mgmlmc_ctx *ctx, int level, int dims[4],
 /* ---- estimators ----------------------------------------------------------- */
 
 /* tr(D^-1) by plain Hutchinson (kind 0) or by the orthogonal multilevel
- * split (kind 1).  Writes one mgmlmc_term_result per term (plain: 1;
- * orthogonal: 2(L-1)+1 in the order O_0.., F_0.., coarsest) into out[max_terms]
- * and their count into *n_terms. */
+ * split (kind 1) or the oblique one (kind 2).  Writes one
+ * mgmlmc_term_result per term (plain: 1; orthogonal: 2(L-1)+1 in the order
+ * O_0.., F_0.., coarsest; oblique: L in the order M_0.., coarsest) into
+ * out[max_terms] and their count into *n_terms. */
 mgmlmc_status mgmlmc_estimate_trace(mgmlmc_ctx *ctx, const mgmlmc_est_params *p,
                                     mgmlmc_term_result *out, int max_terms, int *n_terms);
 /* Exact trace of the coarsest-level inverse, tr(D_L^-1), from its dense
@@ -233,14 +234,18 @@ mgmlmc_status mgmlmc_coarsest_trace(mgmlmc_ctx *ctx, double *re, double *im);
  * every source slice t' in [0, T) (all slices), with Z4 noise x on slice t':
  *   X_rs(t) = (1/T) sum_t' (Btil_s x)|_{t+t'}^H (B_r x)|_{t+t'},
  *   Btil = Gamma5 B^H Gamma5.
- * kind 0 (plain) uses the single operator D^-1 (R = 1).  Output (host):
+ * kind 0 (plain) uses the single operator D^-1 (R = 1); kind 2 (oblique)
+ * the R = L operators B_l of Eq. G-traditional,
+ *   B_l = Phat_{l-1} (D_l^-1 - P_l D_{l+1}^-1 P_l^H) Phat_{l-1}^H, then
+ *   Phat_{L-1} D_L^-1 Phat_{L-1}^H  (here Btil = B).  Output (host):
  * mean[R][R][T] and var[R][R][T] complex mean / real variance over samples. */
 mgmlmc_status mgmlmc_connected_correlator(mgmlmc_ctx *ctx, int kind, int n_samples,
                                           uint64_t seed, uint64_t first_sample,
                                           double *mean, double *var, int *R);
-/* Disconnected loop tr(Gamma5 D^-1(t,t)) = sum_r tr(Gamma5 B_r(t,t)): samples
- * X_r = x^H Gamma5 B_r x with Z4 noise x on slice t.  Output mean[R] complex,
- * var[R] real. */
+/* Disconnected loop tr(Gamma5 D^-1(t,t)) = sum_r tr(Gamma5 B_r(t,t)) (Eq.
+ * trace_equality_disconnected) with the operators of the correlator's kind
+ * (plain R = 1, orthogonal 2L-1, oblique L): samples X_r = x^H Gamma5 B_r x
+ * with Z4 noise x on slice t.  Output mean[R] complex, var[R] real. */
 mgmlmc_status mgmlmc_disconnected_loop(mgmlmc_ctx *ctx, int kind, int t, int n_samples,
                                        uint64_t seed, uint64_t first_sample,
                                        double *mean, double *var, int *R);

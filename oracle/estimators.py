@@ -32,6 +32,9 @@
   Gamma5 B_s(t',t+t') Gamma5 = [Btil_s(t+t',t')]^H, Btil = Gamma5 B^H Gamma5:
      X_rs(t) = (1/T) sum_t' (Btil_s x)|_{t+t'}^H (B_r x)|_{t+t'}.
   The oracle applies Btil literally (solves with D_l^H).
+  Oblique split (Eq. G-traditional, same reading of Phat):
+     B_l = Phat_{l-1} (D_l^-1 - P_l D_{l+1}^-1 P_l^H) Phat_{l-1}^H, l < L,
+     B_L = Phat_{L-1} D_L^-1 Phat_{L-1}^H.
 * Disconnected loop (Sec. 4.3, Eq. trace_equality_disconnected):
   tr(Gamma5 D^-1(t,t)) = sum_r tr(Gamma5 B_r(t,t)); sample X_r = x^H Gamma5 B_r x
   with x on slice t.
@@ -155,24 +158,58 @@ class Estimators:
         last = apply_gamma5(h.prolong_to_fine(sol[L - 1].solve_adjoint(uL), L - 1))
         return J + K + [last]
 
+    def B_apply_oblique(self, x):
+        """[B_l x] of the oblique split: M_l = D_l^-1 - P_l D_{l+1}^-1 P_l^H
+        between Phat_{l-1}^H and Phat_{l-1}, then the coarsest."""
+        h, sol = self.h, self.sol
+        L = h.n_levels
+        out = []
+        for l in range(L - 1):
+            u = h.restrict_from_fine(x, l)
+            P = h.P[l]
+            Ml = sol[l](u) - P.prolong(sol[l + 1](P.restrict(u)))
+            out.append(h.prolong_to_fine(Ml, l))
+        uL = h.restrict_from_fine(x, L - 1)
+        return out + [h.prolong_to_fine(sol[L - 1](uL), L - 1)]
+
+    def Btilde_apply_oblique(self, x):
+        """[Gamma5 B_l^H Gamma5 x] of the oblique split, literally (D^{-H})."""
+        h, sol = self.h, self.sol
+        L = h.n_levels
+        g5x = apply_gamma5(x)
+        out = []
+        for l in range(L - 1):
+            P = h.P[l]
+            u = h.restrict_from_fine(g5x, l)
+            Mh = sol[l].solve_adjoint(u) - P.prolong(sol[l + 1].solve_adjoint(P.restrict(u)))
+            out.append(apply_gamma5(h.prolong_to_fine(Mh, l)))
+        uL = h.restrict_from_fine(g5x, L - 1)
+        return out + [apply_gamma5(h.prolong_to_fine(sol[L - 1].solve_adjoint(uL), L - 1))]
+
+    def _ops(self, kind):
+        if kind == 'oblique':
+            return self.B_apply_oblique, self.Btilde_apply_oblique, self.h.n_levels
+        return self.B_apply, self.Btilde_apply, 2 * (self.h.n_levels - 1) + 1
+
     def _slice_dots(self, a, b):
         """per time slice sum of conj(a) b over a fine vector."""
         dims = self.h.dims[0]
         T = dims[3]
         return np.einsum('ti,ti->t', np.conj(a.reshape(T, -1)), b.reshape(T, -1))
 
-    def connected(self, k, sources=None):
+    def connected(self, k, sources=None, kind='orthogonal'):
         """X_rs(t) for sample k (array (R, R, T)), averaging over the source
-        slices t' (all T when sources is None)."""
+        slices t' (all T when sources is None); kind 'orthogonal' (R = 2L-1)
+        or 'oblique' (R = L)."""
         dims = self.h.dims[0]
         T = dims[3]
         src = range(T) if sources is None else sources
-        R = 2 * (self.h.n_levels - 1) + 1
+        Bop, Btop, R = self._ops(kind)
         X = np.zeros((R, R, T), dtype=np.complex128)
         for tp in src:
             x = nz.z4_slice_vector(dims, 12, tp, self.seed, k, nz.TERM_CONNECTED, aux=tp)
-            b = self.B_apply(x)
-            bt = self.Btilde_apply(x)
+            b = Bop(x)
+            bt = Btop(x)
             for r in range(R):
                 for s in range(R):
                     d = self._slice_dots(bt[s], b[r])  # index: absolute slice
@@ -191,11 +228,11 @@ class Estimators:
             X += np.roll(self._slice_dots(zt, z), -tp)
         return X / len(src)
 
-    def disconnected(self, k, t):
+    def disconnected(self, k, t, kind='orthogonal'):
         """X_r = x^H Gamma5 B_r x, x on slice t, for every r (array (R,))."""
         dims = self.h.dims[0]
         x = nz.z4_slice_vector(dims, 12, t, self.seed, k, nz.TERM_DISCONNECTED, aux=t)
-        b = self.B_apply(x)
+        b = self._ops(kind)[0](x)
         return np.array([np.vdot(x, apply_gamma5(br)) for br in b])
 
     def disconnected_plain(self, k, t):

@@ -137,6 +137,20 @@ class DenseTerms:
         return J + K + [Ph @ self.Dinv[L - 1] @ Ph.conj().T]
 
 
+    def B_matrices_oblique(self):
+        """dense B_l of the oblique split (Sec. 4.1, Eq. G-traditional):
+        Phat_{l-1} (D_l^-1 - P_l D_{l+1}^-1 P_l^H) Phat_{l-1}^H, then
+        Phat_{L-1} D_L^-1 Phat_{L-1}^H."""
+        L = self.h.n_levels
+        out = []
+        for l in range(L - 1):
+            Ph = self.Phat(l)
+            P = self.P[l]
+            out.append(Ph @ (self.Dinv[l] - P @ self.Dinv[l + 1] @ P.conj().T) @ Ph.conj().T)
+        Ph = self.Phat(L - 1)
+        return out + [Ph @ self.Dinv[L - 1] @ Ph.conj().T]
+
+
 def gamma5_matrix(n_sites, dof=12):
     d = np.ones(dof)
     d[dof // 2:] = -1

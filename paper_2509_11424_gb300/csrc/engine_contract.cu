@@ -16,6 +16,14 @@
 // so two level-l solves per level give every B and Btil:
 //   s1 = D_l^-1 (I - P P^H) u,  s2 = D_l^-1 P P^H u,  D_l^-1 u = s1 + s2.
 //
+// Oblique split (Sec. 4.1, the B_l of Eq. G-traditional, same reading of
+// the accumulated prolongation):
+//   B_l = Phat_{l-1} (D_l^-1 - P_l D_{l+1}^-1 P_l^H) Phat_{l-1}^H, l < L,
+//   B_L = Phat_{L-1} D_L^-1 Phat_{L-1}^H;
+// here Btil = Gamma5 B^H Gamma5 = B (Gamma5-hermiticity on every level), so
+// one solve per level gives every B_l: with u_l = Phat_{l-1}^H x and
+// d_l = D_l^-1 u_l, B_l x = Phat_{l-1} (d_l - P_l d_{l+1}).
+//
 // Disconnected loop (Eq. trace_equality_disconnected): X_r = x^H Gamma5 B_r x
 // with Z4 noise x on slice t.
 #include <algorithm>
@@ -26,7 +34,8 @@
 namespace mg {
 
 // B (and, for the correlator, Btil) for nb right-hand sides x on level 0.
-// Layout of B, Bt: [R][nb][n0].  kind 0: R = 1, B = D^-1 x.
+// Layout of B, Bt: [R][nb][n0].  Plain: R = 1, B = D^-1 x; orthogonal:
+// R = 2L - 1; oblique: R = L.
 void Engine::contraction_vectors(int kind, int nb, double2 *x, double2 *B, double2 *Bt) {
   const int L = n_levels();
   const int64_t n0 = levels_[0].g.n();
@@ -34,6 +43,40 @@ void Engine::contraction_vectors(int kind, int nb, double2 *x, double2 *B, doubl
   if (kind == MGMLMC_EST_PLAIN) {
     solve(0, x, B, nb);
     if (Bt) MG_CUDA(cudaMemcpyAsync(Bt, B, sizeof(double2) * s0, cudaMemcpyDeviceToDevice, stream));
+    return;
+  }
+  if (kind == MGMLMC_EST_OBLIQUE) {
+    std::vector<double2 *> u(L), d(L);
+    u[0] = x;
+    for (int l = 0; l < L; ++l) {
+      const int64_t n = levels_[l].g.n();
+      if (l + 1 < L) {
+        u[l + 1] = ws<double>("cvu", l + 1, (size_t)nb * levels_[l + 1].g.n());
+        restrict_to<double>(l, u[l], u[l + 1], nb);
+      }
+      d[l] = ws<double>("cvd", l, (size_t)nb * n);
+      solve(l, u[l], d[l], nb);  // the coarsest level: its dense inverse
+    }
+    for (int l = 0; l < L; ++l) {
+      const int64_t n = levels_[l].g.n();
+      double2 *v = d[l];
+      if (l + 1 < L) {
+        v = ws<double>("cvtmp", l, (size_t)nb * n);
+        prolong_from<double>(l, d[l + 1], v, nb, 0.0);      // P d_{l+1}
+        axpby<double>(1.0, d[l], -1.0, v, n, nb, stream);  // d_l - P d_{l+1}
+      }
+      // Phat_{l-1} v into B_l
+      double2 *cur = v;
+      for (int k = l - 1; k >= 0; --k) {
+        double2 *nxt = (k == 0) ? B + (size_t)l * s0 : ws<double>("cvf", k, (size_t)nb * levels_[k].g.n());
+        prolong_from<double>(k, cur, nxt, nb, 0.0);
+        cur = nxt;
+      }
+      if (l == 0)
+        MG_CUDA(cudaMemcpyAsync(B, v, sizeof(double2) * s0, cudaMemcpyDeviceToDevice, stream));
+    }
+    if (Bt)
+      MG_CUDA(cudaMemcpyAsync(Bt, B, sizeof(double2) * s0 * L, cudaMemcpyDeviceToDevice, stream));
     return;
   }
   const int R = 2 * (L - 1) + 1;
@@ -112,13 +155,14 @@ void Engine::contraction_vectors(int kind, int nb, double2 *x, double2 *B, doubl
 void Engine::connected(int kind, int n_samples, uint64_t seed, uint64_t first,
                        std::vector<double> &mean, std::vector<double> &var, int &R) {
   if (!ready_) throw Error(MGMLMC_ERR_STATE, "hierarchy not built");
-  if (kind != MGMLMC_EST_PLAIN && kind != MGMLMC_EST_ORTHOGONAL) throw Error(MGMLMC_ERR_ARG, "unknown kind");
+  if (kind != MGMLMC_EST_PLAIN && kind != MGMLMC_EST_ORTHOGONAL && kind != MGMLMC_EST_OBLIQUE)
+    throw Error(MGMLMC_ERR_ARG, "unknown kind");
   if (n_samples < 1) throw Error(MGMLMC_ERR_ARG, "n_samples must be >= 1");
   const int L = n_levels();
   const Geom &g0 = levels_[0].g;
   const int T = g0.L[3];
   const int64_t n0 = g0.n(), ns = n0 / T;
-  R = kind == MGMLMC_EST_PLAIN ? 1 : 2 * (L - 1) + 1;
+  R = kind == MGMLMC_EST_PLAIN ? 1 : kind == MGMLMC_EST_OBLIQUE ? L : 2 * (L - 1) + 1;
   const int G = std::min(T, 8);  // source slices solved together
   std::vector<std::complex<double>> sum((size_t)R * R * T), cur((size_t)R * R * T);
   std::vector<double> sabs((size_t)R * R * T, 0.0);
@@ -170,13 +214,14 @@ void Engine::connected(int kind, int n_samples, uint64_t seed, uint64_t first,
 void Engine::disconnected(int kind, int t, int n_samples, uint64_t seed, uint64_t first,
                           std::vector<double> &mean, std::vector<double> &var, int &R) {
   if (!ready_) throw Error(MGMLMC_ERR_STATE, "hierarchy not built");
-  if (kind != MGMLMC_EST_PLAIN && kind != MGMLMC_EST_ORTHOGONAL) throw Error(MGMLMC_ERR_ARG, "unknown kind");
+  if (kind != MGMLMC_EST_PLAIN && kind != MGMLMC_EST_ORTHOGONAL && kind != MGMLMC_EST_OBLIQUE)
+    throw Error(MGMLMC_ERR_ARG, "unknown kind");
   const Geom &g0 = levels_[0].g;
   if (t < 0 || t >= g0.L[3]) throw Error(MGMLMC_ERR_ARG, "time slice out of range");
   if (n_samples < 1) throw Error(MGMLMC_ERR_ARG, "n_samples must be >= 1");
   const int L = n_levels();
   const int64_t n0 = g0.n();
-  R = kind == MGMLMC_EST_PLAIN ? 1 : 2 * (L - 1) + 1;
+  R = kind == MGMLMC_EST_PLAIN ? 1 : kind == MGMLMC_EST_OBLIQUE ? L : 2 * (L - 1) + 1;
   const int G = 8;
   double2 *x = ws<double>("dlx", 0, (size_t)G * n0);
   double2 *g5x = ws<double>("dlg", 0, (size_t)G * n0);

@@ -406,6 +406,32 @@ def test_disconnected_loop_matches_oracle():
         s.close()
 
 
+def test_oblique_correlator_and_loop_match_oracle():
+    """the oblique split (R = L operators B_l of Eq. G-traditional) of the
+    connected correlator and of the disconnected loop: GPU means equal the
+    oracle's on identical noise and P (the oracle applies Gamma5 B^H Gamma5
+    literally with adjoint solves, the library uses that it equals B)."""
+    dims = (2, 2, 2, 8)
+    s = Setup(dims, [(2, 2, 2, 2), (1, 1, 1, 2)], [4, 3], eps=0.4, m0=0.1, gseed=31)
+    try:
+        h = s.hier
+        sol = [osolve.LevelSolver(h.matrix(l)) for l in range(3)]
+        E = oest.Estimators(h, sol, seed=4141)
+        N = 3
+        mean, var = M.mgmlmc_connected_correlator(s.ctx, M.EST_OBLIQUE, N, 4141, 0, 8, 5)
+        X = np.array([E.connected(k, kind='oblique') for k in range(N)])
+        assert mean.shape == X.shape[1:]
+        assert np.max(np.abs(mean - X.mean(axis=0))) < 1e-9 * np.max(np.abs(X.mean(axis=0)))
+        E2 = oest.Estimators(h, sol, seed=5151)
+        N = 12
+        mean, var = M.mgmlmc_disconnected_loop(s.ctx, M.EST_OBLIQUE, 3, N, 5151, 0, 5)
+        Xd = np.array([E2.disconnected(k, 3, kind='oblique') for k in range(N)])
+        assert mean.shape == Xd.shape[1:]
+        assert np.max(np.abs(mean - Xd.mean(axis=0))) < 1e-9 * np.max(np.abs(Xd.mean(axis=0)))
+    finally:
+        s.close()
+
+
 # --------------------------------------------------------------- failures
 def test_failures_return_status_and_context_survives(three):
     from paper_2509_11424_gb300.mgmlmc import MgmlmcError

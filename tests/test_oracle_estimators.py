@@ -225,3 +225,42 @@ def test_oblique_terms_unbiased_and_variance_law(two_level):
     law = exact.offdiag_fro2(T)
     assert abs(mu - np.trace(T)) < 4 * np.sqrt(law / N) + 1e-12
     assert 0.6 * law < var < 1.5 * law, (var, law)
+
+
+def test_oblique_correlator_and_loop_operators():
+    """oblique split of the correlator and loops (Eq. G-traditional, Eq.
+    trace_equality_disconnected): sum_l B_l = D^-1 exactly; each B_l is its
+    own Gamma5-adjoint (Gamma5 B_l^H Gamma5 = B_l, from Gamma5-hermiticity on
+    every level); the oracle's B_l x and its literal Gamma5 B_l^H Gamma5 x
+    equal the dense operators; the correlator and loop samples (seeds 2005,
+    2006) lie within 5 SE of the exact G_ij(t) and tr(Gamma5 B_l(t, t))."""
+    dims = (2, 2, 2, 8)
+    h = make_hier(dims, [(2, 2, 2, 2), (1, 1, 1, 2)], [4, 3], eps=0.4, m0=0.1, seed=31)
+    dt = exact.DenseTerms(h)
+    B = dt.B_matrices_oblique()
+    assert len(B) == h.n_levels
+    assert np.max(np.abs(sum(B) - dt.Dinv[0])) < 1e-11
+    g5 = exact.gamma5_matrix(h.size(0) // 12)
+    for Bm in B:
+        assert np.max(np.abs(g5 @ Bm.conj().T @ g5 - Bm)) < 1e-11
+    E = est.Estimators(h, solvers_for(h), seed=2005)
+    x = synth.complex_normal(h.size(0), 9)
+    for br, bt, Bm in zip(E.B_apply_oblique(x), E.Btilde_apply_oblique(x), B):
+        assert np.max(np.abs(br - Bm @ x)) < 1e-11
+        assert np.max(np.abs(bt - Bm @ x)) < 1e-11
+    Gex = exact.correlator_exact(B, dims)
+    Gplain = exact.correlator_exact([dt.Dinv[0]], dims)[0, 0]
+    assert np.max(np.abs(Gex.sum(axis=(0, 1)) - Gplain)) < 1e-10
+    N = 40
+    S = np.array([E.connected(k, kind='oblique') for k in range(N)])
+    mu = S.mean(axis=0)
+    se = S.std(axis=0, ddof=1) / np.sqrt(N)
+    z = np.abs(mu - Gex) / np.maximum(se, 1e-14)
+    assert np.all(z[se > 1e-12] < 5.0)
+    E2 = est.Estimators(h, solvers_for(h), seed=2006)
+    X = np.array([E2.disconnected(k, 3, kind='oblique') for k in range(200)])
+    mu = X.mean(axis=0)
+    se = np.sqrt(np.sum(np.abs(X - mu) ** 2, axis=0) / (200 - 1) / 200)
+    loops = exact.loop_exact(B, dims, 3)
+    assert abs(loops.sum() - exact.loop_exact([dt.Dinv[0]], dims, 3)[0]) < 1e-11
+    assert np.all(np.abs(mu - loops) < 5 * se)
