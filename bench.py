@@ -545,6 +545,16 @@ def main():
         ores, oms = timed(k0, cs, M.EST_OBLIQUE)
         oval, odet = time_to_variance(merge_terms(ores), 1, oms / cs, cs, eps=eps0)
         compare['mlmc_oblique_same_solver'] = dict(value=oval, ms_per_step=oms / cs, detail=odet)
+        # inexact deflation of plain Hutchinson (Sec. 2.1, the paper's setting of
+        # Sec. 4.2: k = 128, five inverse block power steps, inner solves to
+        # 1e-6); the exact part has no variance, its cost is the basis build
+        dex, dsec = M.mgmlmc_deflation_build(ctx, 128, 5, 1e-6, TV_SEED + 4000)
+        dres, dms = timed(k0, cs, M.EST_DEFLATED)
+        dacc = {t: a for t, a in merge_terms(dres).items() if t == M.TERM_DEFL}
+        dval, ddet = time_to_variance(dacc, 1, dms / cs, cs, eps=eps0)
+        compare['deflated_hutchinson_same_solver'] = dict(
+            value=dval, ms_per_step=dms / cs, setup_s=dsec, exact_part=[dex.real, dex.imag],
+            value_with_setup=dval + dsec, detail=ddet)
         if args.learned > 0:
             M.mgmlmc_set_solver(ctx, precision=prec, **SOLVER)
             step(k0)

@@ -134,7 +134,10 @@ typedef struct {
 typedef enum {
   MGMLMC_EST_PLAIN = 0,
   MGMLMC_EST_ORTHOGONAL = 1,
-  MGMLMC_EST_OBLIQUE = 2
+  MGMLMC_EST_OBLIQUE = 2,
+  MGMLMC_EST_DEFLATED = 3  /* Sec. 2.1, Eq. deflated-estimator: needs
+                              mgmlmc_deflation_build; terms DEFL (n_samples[0]
+                              samples) and DEFL_EXACT (the exact part) */
 } mgmlmc_estimator;
 
 /* Term codes of the results (same numbers as the noise term ids). */
@@ -143,6 +146,9 @@ typedef enum {
 #define MGMLMC_TERM_F 32        /* + level */
 #define MGMLMC_TERM_COARSEST 48
 #define MGMLMC_TERM_M 144       /* + level: oblique M_l */
+#define MGMLMC_TERM_DEFL 160    /* x^H (I - V V^H) D^-1 x */
+#define MGMLMC_TERM_DEFL_EXACT 161 /* tr(V^H D^-1 V), n = 1, variance 0 */
+#define MGMLMC_TERM_DEFL_START 176 /* noise stream of the start vectors */
 
 typedef struct {
   int kind;          /* mgmlmc_estimator */
@@ -225,6 +231,19 @@ mgmlmc_status mgmlmc_level_info(const mgmlmc_ctx *ctx, int level, int dims[4],
  * out[max_terms] and their count into *n_terms. */
 mgmlmc_status mgmlmc_estimate_trace(mgmlmc_ctx *ctx, const mgmlmc_est_params *p,
                                     mgmlmc_term_result *out, int max_terms, int *n_terms);
+/* Inexact deflation basis (Sec. 2.1, 'Deflation for the Dirac operator';
+ * the paper's setting in Sec. 4.2 is k = 128, iters = 5, tol = 1e-6): the k
+ * start columns are the Z4 vectors of samples 0..k-1 of noise stream
+ * MGMLMC_TERM_DEFL_START, orthonormalised (Gram-Schmidt, two passes, column
+ * order); each of `iters` inverse block power steps forms D^-1 Gamma5 V with
+ * the hierarchy's solver at relative tolerance tol and re-orthonormalises.
+ * Then the exact part tr(V^H D^-1 V) is computed with k solves at the
+ * solver's own tolerance and returned in exact[2] (re, im) with the device
+ * seconds of the whole build.  The build's solves run in FP64 whatever the
+ * solver's precision.  1 <= k <= min(128, n); requires a hierarchy;
+ * a new gauge field, mass or hierarchy discards the basis. */
+mgmlmc_status mgmlmc_deflation_build(mgmlmc_ctx *ctx, int k, int iters, double tol, uint64_t seed,
+                                     double *exact, double *seconds);
 /* Exact trace of the coarsest-level inverse, tr(D_L^-1), from its dense
  * inverse (Sec. 3 allows a direct computation of this term). */
 mgmlmc_status mgmlmc_coarsest_trace(mgmlmc_ctx *ctx, double *re, double *im);

@@ -1,6 +1,7 @@
 // extern "C" boundary of libmgmlmc.so (declared in include/mgmlmc.h).  Every
 // entry point catches the engine's exceptions and turns them into a status
 // code plus a message retrievable with mgmlmc_last_error().
+#include <complex>
 #include <cstring>
 #include <new>
 #include <string>
@@ -75,6 +76,20 @@ mgmlmc_status mgmlmc_set_gauge(mgmlmc_ctx *ctx, const double *U, int on_device) 
   return guard(ctx, [&] {
     if (!U) throw mg::Error(MGMLMC_ERR_ARG, "U is NULL");
     E(ctx).set_gauge(U, on_device != 0);
+  });
+}
+
+mgmlmc_status mgmlmc_deflation_build(mgmlmc_ctx *ctx, int k, int iters, double tol, uint64_t seed,
+                                     double *exact, double *seconds) {
+  return guard(ctx, [&] {
+    std::complex<double> ex;
+    double sec = 0.0;
+    E(ctx).deflation_build(k, iters, tol, seed, ex, sec);
+    if (exact) {
+      exact[0] = ex.real();
+      exact[1] = ex.imag();
+    }
+    if (seconds) *seconds = sec;
   });
 }
 

@@ -307,6 +307,9 @@ void Engine::free_hierarchy() {
   }
   levels_.resize(1);
   ready_ = false;
+  dfree(defl_V_);
+  defl_V_ = nullptr;
+  defl_k_ = 0;
 }
 
 // ------------------------------------------------------------------ operators
@@ -960,6 +963,9 @@ void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &ou
     for (int l = 0; l + 1 < L; ++l) terms.push_back({MGMLMC_TERM_O + l, l, 1, p.n_samples[idx++]});
     for (int l = 0; l + 1 < L; ++l) terms.push_back({MGMLMC_TERM_F + l, l, 2, p.n_samples[idx++]});
     terms.push_back({MGMLMC_TERM_COARSEST, L - 1, 3, p.n_samples[idx++]});
+  } else if (p.kind == MGMLMC_EST_DEFLATED) {
+    if (!defl_V_) throw Error(MGMLMC_ERR_STATE, "no deflation basis (mgmlmc_deflation_build)");
+    terms.push_back({MGMLMC_TERM_DEFL, 0, 5, p.n_samples[0]});
   } else if (p.kind == MGMLMC_EST_OBLIQUE) {
     int idx = 0;
     for (int l = 0; l + 1 < L; ++l) terms.push_back({MGMLMC_TERM_M + l, l, 4, p.n_samples[idx++]});
@@ -1015,6 +1021,38 @@ void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &ou
         acc.max_res = std::max(acc.max_res, std::max(s1.residual, s2.residual));
         dot<double>(y, z1, n, nb, res, partials((size_t)reduce_blocks(n) * nb), stream);
         dot<double>(x, z2, nc, nb, res + nb, partials((size_t)reduce_blocks(nc) * nb), stream);
+      } else if (td.kind == 5) {
+        // deflated sample: x^H z - (V^H x)^H (V^H z), z = D^-1 x
+        const int k = defl_k_;
+        double2 *x = ws<double>("estx", 0, (size_t)nb * n), *z = ws<double>("estz", 0, (size_t)nb * n);
+        double2 *cx = ws<double>("dfcx", 0, (size_t)nb * k), *cz = ws<double>("dfcz", 0, (size_t)nb * k);
+        noise(0, p.seed, s0, MGMLMC_TERM_DEFL, 0, -1, x, nb);
+        SolveInfo si = solve(0, x, z, nb);
+        acc.iters_sum += si.iters;
+        acc.solves += 1;
+        acc.max_res = std::max(acc.max_res, si.residual);
+        dot<double>(x, z, n, nb, res, partials((size_t)reduce_blocks(n) * nb), stream);
+        for (int q = 0; q < nb; ++q) {
+          multi_dot<double>(defl_V_, n, k, x + (size_t)q * n, n, 1, cx + (size_t)q * k, k,
+                            partials((size_t)reduce_blocks(n) * k), stream);
+          multi_dot<double>(defl_V_, n, k, z + (size_t)q * n, n, 1, cz + (size_t)q * k, k,
+                            partials((size_t)reduce_blocks(n) * k), stream);
+        }
+        std::vector<double2> hx((size_t)nb * k), hz((size_t)nb * k);
+        MG_CUDA(cudaMemcpyAsync(hx.data(), cx, sizeof(double2) * nb * k, cudaMemcpyDeviceToHost, stream));
+        MG_CUDA(cudaMemcpyAsync(hz.data(), cz, sizeof(double2) * nb * k, cudaMemcpyDeviceToHost, stream));
+        sync();
+        // fold the projected part into res[nb + q] so the common code subtracts it
+        std::vector<double2> sub((size_t)nb);
+        for (int q = 0; q < nb; ++q) {
+          std::complex<double> s(0.0, 0.0);
+          for (int j = 0; j < k; ++j)
+            s += std::conj(std::complex<double>(hx[(size_t)q * k + j].x, hx[(size_t)q * k + j].y)) *
+                 std::complex<double>(hz[(size_t)q * k + j].x, hz[(size_t)q * k + j].y);
+          sub[q] = make_double2(s.real(), s.imag());
+        }
+        MG_CUDA(cudaMemcpyAsync(res + nb, sub.data(), sizeof(double2) * nb, cudaMemcpyHostToDevice, stream));
+        sync();
       } else if (td.kind == 4) {
         // oblique M_l (Eq. oblique-deflation): x^H D_l^-1 x - (P^H x)^H D_{l+1}^-1 (P^H x)
         const int64_t nc = levels_[l + 1].g.n();
@@ -1044,7 +1082,7 @@ void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &ou
       acc.seconds += ms * 1e-3;
       for (int q = 0; q < nb; ++q) {
         std::complex<double> v(h[q].x, h[q].y);
-        if (td.kind == 2 || td.kind == 4) v -= std::complex<double>(h[nb + q].x, h[nb + q].y);
+        if (td.kind == 2 || td.kind == 4 || td.kind == 5) v -= std::complex<double>(h[nb + q].x, h[nb + q].y);
         X.push_back(v);
       }
     }
@@ -1057,8 +1095,112 @@ void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &ou
     acc.samples = X;
     out.push_back(acc);
   }
+  if (p.kind == MGMLMC_EST_DEFLATED) {
+    // the non-stochastic part tr(V^H D^-1 V), computed when the basis was built
+    TermAcc acc;
+    acc.term = MGMLMC_TERM_DEFL_EXACT;
+    acc.n = 1;
+    acc.sre = defl_exact_.real();
+    acc.sim = defl_exact_.imag();
+    acc.sabs2 = std::norm(defl_exact_);
+    acc.seconds = defl_seconds_;
+    acc.samples = {defl_exact_};
+    out.push_back(acc);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+}
+
+// columns of V ([k][n]) orthonormalised by classical Gram-Schmidt run twice,
+// in column order
+void Engine::orthonormalise_cols(double2 *V, int k, int64_t n) {
+  double2 *h = ws<double>("gsh", 0, (size_t)k + 1);
+  for (int j = 0; j < k; ++j) {
+    double2 *v = V + (size_t)j * n;
+    for (int pass = 0; pass < 2 && j > 0; ++pass) {
+      multi_dot<double>(V, n, j, v, n, 1, h, j, partials((size_t)reduce_blocks(n) * j), stream);
+      multi_axpy<double>(V, n, j, v, n, 1, h, j, -1.0, stream);
+    }
+    dot<double>(v, v, n, 1, h + k, partials((size_t)reduce_blocks(n)), stream);
+    double2 nn;
+    MG_CUDA(cudaMemcpyAsync(&nn, h + k, sizeof(double2), cudaMemcpyDeviceToHost, stream));
+    sync();
+    if (!(nn.x > 0.0) || !std::isfinite(nn.x))
+      throw Error(MGMLMC_ERR_NUMERIC, "deflation basis: dependent or non-finite column");
+    axpby<double>(1.0 / std::sqrt(nn.x), v, 0.0, v, n, 1, stream);
+  }
+}
+
+void Engine::deflation_build(int k, int iters, double tol, uint64_t seed,
+                             std::complex<double> &exact, double &seconds) {
+  if (!ready_) throw Error(MGMLMC_ERR_STATE, "hierarchy not built");
+  const int64_t n = levels_[0].g.n();
+  if (k < 1 || k > 128 || k > n) throw Error(MGMLMC_ERR_ARG, "deflation: k must be in [1, min(128, n)]");
+  if (iters < 0 || !(tol > 0.0 && tol < 1.0)) throw Error(MGMLMC_ERR_ARG, "deflation: bad iters or tol");
+  cudaEvent_t a, b;
+  MG_CUDA(cudaEventCreate(&a));
+  MG_CUDA(cudaEventCreate(&b));
+  MG_CUDA(cudaEventRecord(a, stream));
+  dfree(defl_V_);
+  defl_V_ = nullptr;
+  defl_k_ = 0;
+  double2 *V = dalloc<double2>((size_t)k * n);
+  double2 *g = ws<double>("dfg", 0, (size_t)8 * n);
+  double2 *W = ws<double>("dfw", 0, (size_t)k * n);
+  try {
+    noise(0, seed, 0, MGMLMC_TERM_DEFL_START, 0, -1, V, k);
+    orthonormalise_cols(V, k, n);
+    // the build solves in FP64: the basis columns approach the low modes of
+    // Gamma5 D, on which the FP32 inner solves of the mixed scheme stalled
+    // near a 1e-6 relative residual (16^4 benchmark field)
+    const mgmlmc_solver_params keep = sp_;
+    sp_.precision = MGMLMC_FP64;
+    sp_.tol = tol;
+    try {
+      for (int it = 0; it < iters; ++it) {
+        for (int j0 = 0; j0 < k; j0 += 8) {  // W = D^-1 Gamma5 V, 8 columns at a time
+          const int nb = std::min(8, k - j0);
+          gamma5_apply<double>(V + (size_t)j0 * n, g, levels_[0].g.V, 12, nb, stream);
+          solve(0, g, W + (size_t)j0 * n, nb);
+        }
+        orthonormalise_cols(W, k, n);
+        MG_CUDA(cudaMemcpyAsync(V, W, sizeof(double2) * k * n, cudaMemcpyDeviceToDevice, stream));
+      }
+      // exact part, sum_j v_j^H D^-1 v_j, at the solver's tolerance
+      sp_.tol = keep.tol;
+      for (int j0 = 0; j0 < k; j0 += 8) {
+        const int nb = std::min(8, k - j0);
+        solve(0, V + (size_t)j0 * n, W + (size_t)j0 * n, nb);
+      }
+    } catch (...) {
+      sp_ = keep;
+      throw;
+    }
+    sp_ = keep;
+    double2 *d = ws<double>("dfd", 0, (size_t)k);
+    dot<double>(V, W, n, k, d, partials((size_t)reduce_blocks(n) * k), stream);
+    std::vector<double2> hd((size_t)k);
+    MG_CUDA(cudaMemcpyAsync(hd.data(), d, sizeof(double2) * k, cudaMemcpyDeviceToHost, stream));
+    MG_CUDA(cudaEventRecord(b, stream));
+    sync();
+    std::complex<double> s(0.0, 0.0);
+    for (int j = 0; j < k; ++j) s += std::complex<double>(hd[j].x, hd[j].y);
+    float ms = 0.f;
+    MG_CUDA(cudaEventElapsedTime(&ms, a, b));
+    defl_V_ = V;
+    defl_k_ = k;
+    defl_exact_ = s;
+    defl_seconds_ = ms * 1e-3;
+  } catch (...) {
+    cudaFree(V);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    throw;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  exact = defl_exact_;
+  seconds = defl_seconds_;
 }
 
 void Engine::coarsest_trace(double *re, double *im) {

@@ -131,6 +131,13 @@ class Engine {
   void net_train(const mgmlmc_train_params &p, mgmlmc_train_result &out);
   int64_t net_fallbacks() const { return net_.fallbacks; }
 
+  // inexact deflation (Eq. deflated-estimator): V_k by `iters` inverse block
+  // power steps on Gamma5 D with inner solves to tol, then the exact part
+  // tr(V^H D^-1 V) at the solver's tolerance
+  void deflation_build(int k, int iters, double tol, uint64_t seed, std::complex<double> &exact,
+                       double &seconds);
+  int deflation_k() const { return defl_k_; }
+
   void get_prolongator(int l, double *host);
   void get_coarse_op(int l, double *host);
 
@@ -227,6 +234,11 @@ class Engine {
   void drop_graphs();
   cudaEvent_t ev_enter_ = nullptr, ev_leave_ = nullptr;
   int dslash_force_ = -2;
+  double2 *defl_V_ = nullptr;  // [k][n0] orthonormal columns
+  int defl_k_ = 0;
+  std::complex<double> defl_exact_{0.0, 0.0};
+  double defl_seconds_ = 0.0;
+  void orthonormalise_cols(double2 *V, int k, int64_t n);
   std::map<int, int> dslash_tuned_;
   int dslash_pick(int nrhs, const float2 *in, float2 *out);
 };

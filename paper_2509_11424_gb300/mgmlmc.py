@@ -17,9 +17,10 @@ LIB_PATH = os.path.join(HERE, 'libmgmlmc.so')
 
 MAX_LEVELS = 4
 FP64, FP32, BF16 = 0, 1, 2
-EST_PLAIN, EST_ORTHOGONAL, EST_OBLIQUE = 0, 1, 2
+EST_PLAIN, EST_ORTHOGONAL, EST_OBLIQUE, EST_DEFLATED = 0, 1, 2, 3
 OP_D, OP_RESTRICT, OP_PROLONG, OP_PROJECT, OP_SOLVE, OP_GAMMA5, OP_SMOOTH, OP_NET = range(8)
 TERM_PLAIN, TERM_O, TERM_F, TERM_COARSEST, TERM_M = 0, 16, 32, 48, 144
+TERM_DEFL, TERM_DEFL_EXACT, TERM_DEFL_START = 160, 161, 176
 STATUS = {0: 'OK', 1: 'ERR_ARG', 2: 'ERR_STATE', 3: 'ERR_OOM', 4: 'ERR_CUDA',
           5: 'ERR_NOT_CONVERGED', 6: 'ERR_NUMERIC'}
 
@@ -127,6 +128,7 @@ _SIGNATURES = {
                              ctypes.POINTER(_D)],
     'mgmlmc_set_kernel_variant': [_P, _I, _I],
     'mgmlmc_gen_gauge': [_P, _D, _U64],
+    'mgmlmc_deflation_build': [_P, _I, _I, _D, _U64, _P, ctypes.POINTER(_D)],
     'mgmlmc_reorder': [_P, _P, _P, _I, _I],
     'mgmlmc_reorder_bf16': [_P, _P, _P, _I, _I],
     'mgmlmc_kernel_variants': [_I],
@@ -356,6 +358,16 @@ VARIANT_AUTOTUNE = -2
 def mgmlmc_reorder_bf16(ctx, inp, out, nrhs, to_internal):
     """Level-0 complex-bfloat16 vectors: canonical <-> internal chunked order."""
     _check(ctx, lib().mgmlmc_reorder_bf16(ctx, ptr(inp), ptr(out), nrhs, int(bool(to_internal))))
+
+
+def mgmlmc_deflation_build(ctx, k, iters, tol, seed):
+    """Inexact deflation basis (see include/mgmlmc.h); returns (exact part
+    tr(V^H D^-1 V) as a complex, device seconds of the build)."""
+    ex = np.zeros(2)
+    sec = _D()
+    _check(ctx, lib().mgmlmc_deflation_build(ctx, int(k), int(iters), float(tol), int(seed), ptr(ex),
+                                             ctypes.byref(sec)))
+    return complex(ex[0], ex[1]), sec.value
 
 
 def mgmlmc_gen_gauge(ctx, eps, seed):
