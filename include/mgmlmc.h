@@ -89,7 +89,9 @@ typedef enum { MGMLMC_FP64 = 0, MGMLMC_FP32 = 1, MGMLMC_BF16 = 2 } mgmlmc_precis
 typedef struct {
   int n_levels;                        /* L, 1 .. MGMLMC_MAX_LEVELS */
   int block[MGMLMC_MAX_LEVELS - 1][4]; /* aggregate extents for level l -> l+1 */
-  int n_tv[MGMLMC_MAX_LEVELS - 1];     /* test vectors for level l -> l+1 */
+  int n_tv[MGMLMC_MAX_LEVELS - 1];     /* test vectors for level l -> l+1,
+                                          1 .. 128 and at most the rows of a
+                                          (aggregate, chirality) block */
   int setup_rounds;   /* rounds of approximate inverse iteration */
   int setup_iters;    /* Krylov iterations per round (rough solves) */
   uint64_t seed;      /* seed of the initial random test vectors */

@@ -280,7 +280,7 @@ void Engine::set_solver(const mgmlmc_solver_params &p) {
 }
 
 void Engine::set_test_vectors(int level, const double *V, int ntv, int64_t n, bool on_device) {
-  if (level < 0 || level >= MGMLMC_MAX_LEVELS - 1 || ntv < 1 || ntv > 64 || n < 1 || !V)
+  if (level < 0 || level >= MGMLMC_MAX_LEVELS - 1 || ntv < 1 || ntv > 128 || n < 1 || !V)
     throw Error(MGMLMC_ERR_ARG, "set_test_vectors: bad level, count, length or pointer");
   std::vector<double> &h = imported_host_[level];
   h.assign((size_t)ntv * n * 2, 0.0);
@@ -852,7 +852,7 @@ void Engine::build_hierarchy(const mgmlmc_mg_params &p) {
     AggMap &m = maps[l];
     m.fine = geo[l];
     const int ntv = p.n_tv[l];
-    if (ntv < 1 || ntv > 64) throw Error(MGMLMC_ERR_ARG, "n_tv must be in 1..64");
+    if (ntv < 1 || ntv > 128) throw Error(MGMLMC_ERR_ARG, "n_tv must be in 1..128");
     Geom cg{};
     int64_t cv = 1;
     int sites = 1;

@@ -72,6 +72,77 @@ __global__ void stencil_t_kernel(const C<T> *__restrict__ in, C<T> *__restrict__
   }
 }
 
+// Wide coarse operators (m > 112 dofs per site, e.g. 2 N_tv = 128 or 256):
+// one CTA of 8 warps per (site, 32-row tile).  Lane l owns row i0 + l, so
+// the reads of AT[X][d][j][i0..i0+31] are 32 consecutive entries; warp w
+// takes the columns j = w, w + 8, ... of every direction.  The neighbour
+// vectors of the 9 directions for RG right-hand sides are staged in shared
+// memory; the 8 warp partials of a row are added in warp order.
+template <typename T, int RG>
+__global__ void __launch_bounds__(256) stencil_wide_kernel(const C<T> *__restrict__ in,
+                                                           C<T> *__restrict__ out,
+                                                           const C<T> *__restrict__ AT, Geom g,
+                                                           int nrhs) {
+  extern __shared__ unsigned char smem_raw[];
+  const int m = g.dof;
+  C<T> *xs = reinterpret_cast<C<T> *>(smem_raw);  // [9][RG][m]
+  C<T> *part = xs + 9 * RG * m;                   // [8 warps][RG][32]
+  const int X = blockIdx.x, i0 = blockIdx.y * 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int i = i0 + lane;
+  const bool row_ok = i < m;
+  const int64_t n = g.n();
+  for (int r0 = 0; r0 < nrhs; r0 += RG) {
+    const int rg = nrhs - r0 < RG ? nrhs - r0 : RG;
+    __syncthreads();
+    for (int e = threadIdx.x; e < 9 * RG * m; e += blockDim.x) {
+      const int d = e / (RG * m), rem = e - d * RG * m, r = rem / m, j = rem - r * m;
+      xs[e] = r < rg ? in[(int64_t)(r0 + r) * n + (int64_t)g.neighbor(X, d) * m + j] : mk<T>((T)0, (T)0);
+    }
+    __syncthreads();
+    C<T> acc[RG];
+#pragma unroll
+    for (int r = 0; r < RG; ++r) acc[r] = mk<T>((T)0, (T)0);
+    if (row_ok) {
+      for (int d = 0; d < 9; ++d) {
+        const C<T> *Ad = AT + ((int64_t)X * 9 + d) * m * m;
+        const C<T> *xd = xs + d * RG * m;
+        for (int j = w; j < m; j += 8) {
+          const C<T> a = __ldg(Ad + (int64_t)j * m + i);
+#pragma unroll
+          for (int r = 0; r < RG; ++r) acc[r] = cfma(a, xd[r * m + j], acc[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < RG; ++r) part[(w * RG + r) * 32 + lane] = acc[r];
+    __syncthreads();
+    if (w == 0 && row_ok) {
+      for (int r = 0; r < rg; ++r) {
+        C<T> v = part[r * 32 + lane];
+#pragma unroll
+        for (int ww = 1; ww < 8; ++ww) v = cadd(v, part[(ww * RG + r) * 32 + lane]);
+        out[(int64_t)(r0 + r) * n + (int64_t)X * m + i] = v;
+      }
+    }
+  }
+}
+
+template <typename T, int RG>
+void launch_wide(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, cudaStream_t s) {
+  const int m = g.dof;
+  const size_t sm = (size_t)(9 * RG * m + 8 * RG * 32) * sizeof(C<T>);
+  static bool configured = false;
+  if (!configured) {
+    MG_CUDA(cudaFuncSetAttribute(stencil_wide_kernel<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+    configured = true;
+  }
+  if (sm > 200 * 1024) throw Error(1, "coarse stencil: too many dofs per site");
+  stencil_wide_kernel<T, RG><<<dim3(g.V, (m + 31) / 32), 256, sm, s>>>(in, out, AT, g, nrhs);
+  MG_LAUNCH_CHECK();
+}
+
 // ---- TMA bulk staging (cp.async.bulk + mbarrier) --------------------------
 __device__ __forceinline__ unsigned smem_addr(const void *p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -545,7 +616,15 @@ void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, 
                    cudaStream_t s) {
   constexpr int RG = sizeof(T) == 4 ? 8 : 4;
   const int m = g.dof;
-  if (m > 112) throw Error(1, "coarse stencil: more than 112 dofs per site");
+  if (m > 112) {
+    // wide operators: as many right-hand sides per pass as ~96 KB of staged
+    // neighbour vectors allow
+    const size_t per = (size_t)9 * m * sizeof(C<T>);
+    if (per * 4 <= 96 * 1024) launch_wide<T, 4>(in, out, AT, g, nrhs, s);
+    else if (per * 2 <= 96 * 1024) launch_wide<T, 2>(in, out, AT, g, nrhs, s);
+    else launch_wide<T, 1>(in, out, AT, g, nrhs, s);
+    return;
+  }
   const size_t sm_tma = (size_t)(9 * m * m + 2 * 9 * RG * m) * sizeof(C<T>);
   if (sm_tma <= 200 * 1024) {
     static bool configured_tma = false;
