@@ -14,17 +14,22 @@ ill-conditioned point of an oracle scan on this field), three-level
 hierarchy (4^4 then 2^4 aggregates, 16 test vectors per level), noise seed
 2002.  A step is one batch of `--batch` Z4 noise vectors through every term
 of the orthogonal split (O_0, O_1, F_0, F_1, D_2^-1), every solve to a
-relative residual of 1e-12 (FP32 SAP/MG-preconditioned FGMRES inside FP64
-defect correction by default; `--precision fp64` for all-FP64).  Inputs
-(gauge field, hierarchy, vectors) are resident in HBM; a 256 MB write
-flushes the 129 MB L2 between timed steps.
+relative residual of 1e-12 (FP32 MG-preconditioned FGMRES with SAP and a
+one-channel learned post-smoothing step, inside FP64 defect correction, by
+default; `--precision fp64` for all-FP64).  Inputs (gauge field, hierarchy,
+vectors) are resident in HBM; a 256 MB write flushes the 129 MB L2 between
+timed steps.
 
-Also reported: plain Hutchinson and all-FP64 MG-MLMC on the same GPU, the
-roofline of the dominant kernel (CUDA events around its launches in a
-profiled repeat of the first timed step), the clocks sampled during the
-timed region, an end-to-end figure through the C-ABI with the gauge field
-copied from pinned host memory and the hierarchy rebuilt every step, and the
-FP64 CPU oracle timed on the host on a bounded sample.
+Also reported, on the same GPU and noise samples: plain Hutchinson with the
+same solver, the oblique MG-MLMC split, inexact deflation (k = 128), SAP-only
+MG-MLMC, all-FP64 MG-MLMC and plain Hutchinson in FP64, with the per-term
+difference of the mixed-precision estimate against FP64; the FP32 and BF16
+Wilson operator bandwidth at 32^4; the roofline of the dominant kernel class
+(CUDA events around its launches in a profiled repeat of the first timed
+step); the clocks sampled during the timed region; an end-to-end figure
+through the C-ABI (gauge field copied from pinned host memory, hierarchy
+setup, then the sampling to the same eps); and the FP64 CPU oracle timed on
+the host on a bounded sample.
 """
 import argparse
 import hashlib
