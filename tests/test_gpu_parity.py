@@ -383,6 +383,45 @@ def test_oblique_trace_unbiased_config1(cfg1):
     assert abs(est - exact_tr) < 3 * se
 
 
+def test_four_level_hierarchy_matches_oracle():
+    """L = 4 (the ABI's maximum): 8x4x4x8 -> 4x2x2x4 -> 2x2x2x2 -> 1x1x1x1
+    coarse lattices, N_tv = 6, 4, 3.  Every level solve reaches 1.5e-12 with
+    the oracle's operator; the 7 orthogonal and the 4 oblique terms match the
+    oracle per sample on identical noise and P (1e-8)."""
+    s = Setup((8, 4, 4, 8), [(2, 2, 2, 2), (2, 1, 1, 2), (2, 2, 2, 2)], [6, 4, 3],
+              eps=0.4, m0=-0.1, gseed=55)
+    try:
+        h = s.hier
+        assert h.n_levels == 4
+        for l in range(4):
+            A = h.matrix(l)
+            b = synth.complex_normal((2, A.shape[0]), 93 + l)
+            z = torch.empty((2, A.shape[0]), dtype=torch.complex128, device='cuda')
+            M.mgmlmc_apply(s.ctx, M.OP_SOLVE, l, M.FP64, dev(b), z, 2)
+            zs = host(z)
+            for r in range(2):
+                assert np.linalg.norm(b[r] - A @ zs[r]) / np.linalg.norm(b[r]) < 1.5e-12, l
+        sol = [osolve.LevelSolver(h.matrix(l)) for l in range(4)]
+        N = 5
+        E = oest.Estimators(h, sol, seed=2244)
+        res = M.mgmlmc_estimate_trace(s.ctx, M.est_params(M.EST_ORTHOGONAL, [N] * 7, batch=5, seed=2244))
+        terms = dict(E.orthogonal_terms())
+        names = ['O0', 'O1', 'O2', 'F0', 'F1', 'F2', 'coarsest']
+        assert len(res) == 7
+        for r, name in zip(res, names):
+            X = np.array([terms[name](k) for k in range(N)])
+            mu = X.mean()
+            assert abs(complex(r['mean_re'], r['mean_im']) - mu) < 1e-8 * max(1.0, abs(mu)), name
+        res = M.mgmlmc_estimate_trace(s.ctx, M.est_params(M.EST_OBLIQUE, [N] * 4, batch=5, seed=2245))
+        E2 = oest.Estimators(h, sol, seed=2245)
+        assert len(res) == 4
+        for r, (name, sampler) in zip(res, E2.oblique_terms()):
+            mu = np.mean([sampler(k) for k in range(N)])
+            assert abs(complex(r['mean_re'], r['mean_im']) - mu) < 1e-8 * max(1.0, abs(mu)), name
+    finally:
+        s.close()
+
+
 def test_trace_unbiased_config1(cfg1):
     """config-1: orthogonal MG-MLMC (N = 200 per term, seed 2301) and plain
     Hutchinson (N = 200) each within 3 SE of the dense exact tr(D^-1)."""
