@@ -1,0 +1,45 @@
+"""bench.py's time-to-variance (the headline metric) against the oracle's
+MLMC allocation (Sec. 2.2, Eq. MLMC-Nl): for per-term accumulators with
+known sample variances and costs, (sum_l sqrt(V_l C_l))^2 / eps^2 equals the
+total cost of the optimal allocation, and the shared-variance option replaces
+a run's variances and target exactly."""
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+from oracle import estimators as oest  # noqa: E402
+
+
+def _acc(X, sec):
+    X = np.asarray(X)
+    return dict(n=X.size, sre=X.real.sum(), sim=X.imag.sum(), sab=np.sum(np.abs(X) ** 2), sec=sec,
+                it=10.0 * X.size, k=X.size, res=1e-13)
+
+
+def test_time_to_variance_equals_optimal_allocation_cost():
+    rng = np.random.default_rng(5)
+    acc, V, C = {}, [], []
+    for t, (mu, sd, sec) in enumerate([(100.0, 3.0, 0.8), (5.0, 1.0, 0.3), (-2.0, 0.4, 0.05)]):
+        X = mu + sd * (rng.standard_normal(40) + 1j * rng.standard_normal(40))
+        acc[t] = _acc(X, sec)
+        V.append(oest.sample_stats(X)[1])
+        C.append(sec / 40)
+    step_ms = 1e3 * sum(a['sec'] for a in acc.values())  # measured time = device time
+    val, det = bench.time_to_variance(acc, 1, step_ms, 1, rel_eps=1e-3)
+    eps = det['eps']
+    tr = sum(complex(a['sre'], a['sim']) / a['n'] for a in acc.values())
+    assert abs(eps - 1e-3 * abs(tr)) < 1e-12 * eps
+    _, cost = oest.mlmc_allocation(V, C, eps)
+    assert abs(val - cost) < 1e-10 * cost
+    # host gaps: a measured step twice the device time doubles every C_l
+    val2, _ = bench.time_to_variance(acc, 1, 2 * step_ms, 1, rel_eps=1e-3)
+    assert abs(val2 - 2 * val) < 1e-10 * val
+    # shared variances and target
+    var_of = {str(t): 4.0 * V[t] for t in acc}
+    val3, det3 = bench.time_to_variance(acc, 1, step_ms, 1, var_of=var_of, eps=2 * eps)
+    assert abs(val3 - cost) < 1e-10 * cost  # 4x variance, 2x eps
+    assert det3['eps'] == 2 * eps
