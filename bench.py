@@ -66,7 +66,7 @@ GROUPS = {6: 'transfer_in_cycle', 7: 'gram_schmidt', 8: 'learned_step', 9: 'coar
 SHARD_STRIDE = 1000000  # Z4 sample counters per rank
 TRAFFIC = {
     # one level-1 launch (4^4 x 32 dof, 8 rhs), cold-cache capture
-    ('coarse_stencil_fp32', 'ecf398700957'): 19.43e6,
+    ('coarse_stencil_fp32', '26c34d4e25b6'): 19.43e6,
     # one sweep (block + boundary kernel, both colours), 16^4 x 8 rhs
     ('sap_sweep_fp32', '9a67c5f9b503'): 578.0e6,
 }
