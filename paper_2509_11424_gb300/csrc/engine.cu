@@ -223,6 +223,15 @@ template <typename T> C<T> *Engine::ws(const std::string &name, int l, size_t co
   return static_cast<C<T> *>(p);
 }
 
+void Engine::ws_release(const std::string &name, int l, bool dbl) {
+  const std::string key = name + "#" + std::to_string(l) + (dbl ? "d" : "f");
+  auto it = ws_.find(key);
+  if (it == ws_.end()) return;
+  sync();
+  cudaFree(it->second.first);
+  ws_.erase(it);
+}
+
 template <> const C<double> *Engine::Pmat<double>(int l) const { return levels_[l].P64; }
 template <> const C<float> *Engine::Pmat<float>(int l) const { return levels_[l].P32; }
 template <> const C<double> *Engine::Dinv<double>(int l) const { return levels_[l].Dinv64; }
@@ -1195,10 +1204,15 @@ void Engine::deflation_build(int k, int iters, double tol, uint64_t seed,
     cudaFree(V);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
+    ws_release("dfw", 0, true);
+    ws_release("dfg", 0, true);
     throw;
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  // the k x n work columns are needed only while building
+  ws_release("dfw", 0, true);
+  ws_release("dfg", 0, true);
   exact = defl_exact_;
   seconds = defl_seconds_;
 }

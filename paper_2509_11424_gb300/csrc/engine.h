@@ -163,6 +163,8 @@ class Engine {
 
  private:
   template <typename T> C<T> *ws(const std::string &name, int l, size_t count);
+  // free one named workspace (only for buffers no captured graph uses)
+  void ws_release(const std::string &name, int l, bool dbl);
   void contraction_vectors(int kind, int nb, double2 *x, double2 *B, double2 *Bt);
   template <typename T> const C<T> *Pmat(int l) const;
   // the aggregation map of level l for vectors of type T (FP32 level-0
