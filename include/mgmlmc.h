@@ -39,7 +39,10 @@
  *     (i >> 2, sample, term, aux) and key (seed, 0), r = word >> 62 and
  *     x_i = i^r.  term = 0 plain Hutchinson, 16 + l for O_l, 32 + l for F_l,
  *     48 for the coarsest level, 64 for connected-correlator sources
- *     (aux = source slice), 80 for disconnected loops (aux = slice).
+ *     (aux = source slice), 80 for disconnected loops (aux = slice),
+ *     96 + l for the start vectors of the test-vector setup, 144 + l for
+ *     the oblique M_l, 160 for deflated samples, 176 for the deflation
+ *     start columns (sample = column).
  *
  * Ownership and streams
  *   The context owns every device buffer it allocates; caller buffers are
@@ -175,9 +178,10 @@ typedef struct {
 
 /* ---- context -------------------------------------------------------------- */
 
-/* Create a context for a lattice of extents dims[4] (each >= 2 and even
- * extents are not required; aggregation needs divisibility).  stream is a
- * cudaStream_t (NULL = legacy default stream).  Uses the current device. */
+/* Create a context for a lattice of extents dims[4] (each >= 2, even
+ * extents not required, aggregation needs divisibility; 12 V < 2^31 with V
+ * the number of sites).  stream is a cudaStream_t (NULL = legacy default
+ * stream).  Uses the current device.  MGMLMC_ERR_ARG for other extents. */
 mgmlmc_status mgmlmc_create(const int dims[4], void *stream, mgmlmc_ctx **out);
 /* Release every device buffer of the context.  NULL is accepted. */
 void mgmlmc_destroy(mgmlmc_ctx *ctx);

@@ -22,6 +22,23 @@ template <typename T> void dfree(T *&p) {
   if (p) cudaFree(p);
   p = nullptr;
 }
+// a pair of timing events, destroyed on every exit (a failed step throws)
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  EventPair() {
+    MG_CUDA(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      throw Error(MGMLMC_ERR_CUDA, "cudaEventCreate failed");
+    }
+  }
+  ~EventPair() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+  EventPair(const EventPair &) = delete;
+  EventPair &operator=(const EventPair &) = delete;
+};
 
 __global__ void target_kernel(double *target, const double2 *nrm, double tol, int nrhs) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -38,16 +55,19 @@ __global__ void inv_norm_kernel(double *out, double *nrm_out, const double2 *nrm
 }  // namespace
 
 Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
+  // validate before acquiring anything: a throwing constructor runs no destructor
+  for (int i = 0; i < 4; ++i)
+    if (dims[i] < 2) throw Error(MGMLMC_ERR_ARG, "lattice extents must be >= 2");
+  const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
+  // sites are int, and 12 V must index a vector with int arithmetic in places
+  if (V * 12 >= ((int64_t)1 << 31)) throw Error(MGMLMC_ERR_ARG, "lattice too large (12 V >= 2^31)");
   MG_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
   MG_CUDA(cudaEventCreateWithFlags(&ev_enter_, cudaEventDisableTiming));
   MG_CUDA(cudaEventCreateWithFlags(&ev_leave_, cudaEventDisableTiming));
   for (int i = 0; i < 4; ++i) {
-    if (dims[i] < 2) throw Error(MGMLMC_ERR_ARG, "lattice extents must be >= 2");
     dims_[i] = dims[i];
     fine_.L[i] = dims[i];
   }
-  const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
-  if (V * 12 * 9 > ((int64_t)1 << 40)) throw Error(MGMLMC_ERR_ARG, "lattice too large");
   fine_.V = (int)V;
   fine_.dof = 12;
   sp_.tol = 1e-12;
@@ -344,9 +364,8 @@ int Engine::dslash_pick(int nrhs, const float2 *in, float2 *out) {
   // every variant computes the same sums in the same order, so timing them on
   // the caller's operands leaves `out` correct whichever runs last
   const Level &L = levels_[0];
-  cudaEvent_t a, b;
-  MG_CUDA(cudaEventCreate(&a));
-  MG_CUDA(cudaEventCreate(&b));
+  EventPair ev;
+  cudaEvent_t a = ev.a, b = ev.b;
   int pick = 0;
   float best = 1e30f;
   for (int v = 0; v < wilson_fp32_variants(); ++v) {
@@ -360,8 +379,6 @@ int Engine::dslash_pick(int nrhs, const float2 *in, float2 *out) {
     MG_CUDA(cudaEventElapsedTime(&ms, a, b));
     if (ms < best) { best = ms; pick = v; }
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
   dslash_tuned_[nrhs] = pick;
   return pick;
 }
@@ -982,13 +999,13 @@ void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &ou
   } else {
     throw Error(MGMLMC_ERR_ARG, "unknown estimator kind");
   }
+  for (const TermDef &td : terms)
+    if (td.N < 0) throw Error(MGMLMC_ERR_ARG, "negative sample count");
   const int B = std::max(1, p.batch);
-  cudaEvent_t e0, e1;
-  MG_CUDA(cudaEventCreate(&e0));
-  MG_CUDA(cudaEventCreate(&e1));
+  EventPair ev;
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   out.clear();
   for (const TermDef &td : terms) {
-    if (td.N < 0) throw Error(MGMLMC_ERR_ARG, "negative sample count");
     TermAcc acc;
     acc.term = td.code;
     std::vector<std::complex<double>> X;
@@ -1116,8 +1133,6 @@ void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &ou
     acc.samples = {defl_exact_};
     out.push_back(acc);
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
 }
 
 // columns of V ([k][n]) orthonormalised by classical Gram-Schmidt run twice,
@@ -1146,17 +1161,16 @@ void Engine::deflation_build(int k, int iters, double tol, uint64_t seed,
   const int64_t n = levels_[0].g.n();
   if (k < 1 || k > 128 || k > n) throw Error(MGMLMC_ERR_ARG, "deflation: k must be in [1, min(128, n)]");
   if (iters < 0 || !(tol > 0.0 && tol < 1.0)) throw Error(MGMLMC_ERR_ARG, "deflation: bad iters or tol");
-  cudaEvent_t a, b;
-  MG_CUDA(cudaEventCreate(&a));
-  MG_CUDA(cudaEventCreate(&b));
+  EventPair ev;
+  cudaEvent_t a = ev.a, b = ev.b;
   MG_CUDA(cudaEventRecord(a, stream));
   dfree(defl_V_);
   defl_V_ = nullptr;
   defl_k_ = 0;
   double2 *V = dalloc<double2>((size_t)k * n);
-  double2 *g = ws<double>("dfg", 0, (size_t)8 * n);
-  double2 *W = ws<double>("dfw", 0, (size_t)k * n);
   try {
+    double2 *g = ws<double>("dfg", 0, (size_t)8 * n);
+    double2 *W = ws<double>("dfw", 0, (size_t)k * n);
     noise(0, seed, 0, MGMLMC_TERM_DEFL_START, 0, -1, V, k);
     orthonormalise_cols(V, k, n);
     // the build solves in FP64: the basis columns approach the low modes of
@@ -1202,14 +1216,10 @@ void Engine::deflation_build(int k, int iters, double tol, uint64_t seed,
     defl_seconds_ = ms * 1e-3;
   } catch (...) {
     cudaFree(V);
-    cudaEventDestroy(a);
-    cudaEventDestroy(b);
     ws_release("dfw", 0, true);
     ws_release("dfg", 0, true);
     throw;
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
   // the k x n work columns are needed only while building
   ws_release("dfw", 0, true);
   ws_release("dfg", 0, true);
