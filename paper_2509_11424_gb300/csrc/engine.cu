@@ -61,9 +61,6 @@ Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
   const int64_t V = (int64_t)dims[0] * dims[1] * dims[2] * dims[3];
   // sites are int, and 12 V must index a vector with int arithmetic in places
   if (V * 12 >= ((int64_t)1 << 31)) throw Error(MGMLMC_ERR_ARG, "lattice too large (12 V >= 2^31)");
-  MG_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
-  MG_CUDA(cudaEventCreateWithFlags(&ev_enter_, cudaEventDisableTiming));
-  MG_CUDA(cudaEventCreateWithFlags(&ev_leave_, cudaEventDisableTiming));
   for (int i = 0; i < 4; ++i) {
     dims_[i] = dims[i];
     fine_.L[i] = dims[i];
@@ -91,40 +88,58 @@ Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
   levels_.resize(1);
   levels_[0].g = fine_;
   levels_[0].fine = true;
-  levels_[0].U64 = dalloc<double2>((size_t)V * 36);
-  levels_[0].U32 = dalloc<float2>((size_t)V * 36);
-  levels_[0].UD32 = dalloc<float2>((size_t)V * 36);
-  levels_[0].Ub16 = dalloc<float>((size_t)V * 36);  // 36 bf16 pairs of 4 bytes per site
-  scal_ = dalloc<double2>(4096);
-  flag_dev_ = dalloc<int>(16);
-  MG_CUDA(cudaMemset(flag_dev_, 0, 16 * sizeof(int)));
-  tickets_ = dalloc<unsigned>(kTickets);
-  MG_CUDA(cudaMemset(tickets_, 0, kTickets * sizeof(unsigned)));
+  // a throwing constructor runs no destructor: release what was acquired
+  try {
+    MG_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    MG_CUDA(cudaEventCreateWithFlags(&ev_enter_, cudaEventDisableTiming));
+    MG_CUDA(cudaEventCreateWithFlags(&ev_leave_, cudaEventDisableTiming));
+    levels_[0].U64 = dalloc<double2>((size_t)V * 36);
+    levels_[0].U32 = dalloc<float2>((size_t)V * 36);
+    levels_[0].UD32 = dalloc<float2>((size_t)V * 36);
+    levels_[0].Ub16 = dalloc<float>((size_t)V * 36);  // 36 bf16 pairs of 4 bytes per site
+    scal_ = dalloc<double2>(4096);
+    flag_dev_ = dalloc<int>(16);
+    MG_CUDA(cudaMemset(flag_dev_, 0, 16 * sizeof(int)));
+    tickets_ = dalloc<unsigned>(kTickets);
+    MG_CUDA(cudaMemset(tickets_, 0, kTickets * sizeof(unsigned)));
+  } catch (...) {
+    release();
+    throw;
+  }
 }
 
-Engine::~Engine() {
-  cudaStreamSynchronize(stream);
+Engine::~Engine() { release(); }
+
+void Engine::release() {
+  if (stream) cudaStreamSynchronize(stream);
   free_hierarchy();
   net_free();
   if (pool_) cudaFree(pool_);
+  pool_ = nullptr;
   dfree(levels_[0].U64);
   dfree(levels_[0].U32);
   dfree(levels_[0].UD32);
   dfree(levels_[0].Ub16);
   for (auto &kv : ws_) cudaFree(kv.second.first);
+  ws_.clear();
   for (auto &p : pending_) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
   }
+  pending_.clear();
   for (auto e : events_) cudaEventDestroy(e);
+  events_.clear();
   dfree(scal_);
   dfree(partial_);
   dfree(tickets_);
   dfree(flag_dev_);
   if (pinned_) cudaFreeHost(pinned_);
+  pinned_ = nullptr;
   if (ev_enter_) cudaEventDestroy(ev_enter_);
   if (ev_leave_) cudaEventDestroy(ev_leave_);
+  ev_enter_ = ev_leave_ = nullptr;
   if (stream) cudaStreamDestroy(stream);
+  stream = nullptr;
 }
 
 void Engine::enter() {

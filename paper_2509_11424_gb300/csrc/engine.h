@@ -88,6 +88,8 @@ class Engine {
  public:
   Engine(const int dims[4], cudaStream_t s);
   ~Engine();
+  Engine(const Engine &) = delete;
+  Engine &operator=(const Engine &) = delete;
 
   void set_gauge(const double *U, bool on_device);
   // U = exp(i eps H) generated on the device (kernels.h gauge_generate)
@@ -184,6 +186,7 @@ class Engine {
   SolveInfo solve_mixed(int l, const double2 *b, double2 *x, int nrhs);
   void galerkin(int l);
   void free_hierarchy();
+  void release();  // frees everything the context holds; safe on a partly built one
   void gauge_derived();  // FP32 and structure-of-arrays copies of the new links
   void sync();
 
