@@ -35,4 +35,11 @@ no blocking, fusion or reordering beyond what the definition states:
                  (Eq. trace_equality_disconnected).
 * ``exact``      exact targets: dense inverses on tiny lattices and free-field
                  closed forms in momentum space.
+* ``smoother``, ``learned``  the MR/SAP smoothers and the gauge-covariant
+                 learned layers the solver uses.
+* ``deflation``  inexact deflation of Hutchinson's estimator (Sec. 2.1,
+                 Eq. deflated-estimator; inverse block power on Gamma5 D).
+* ``testvectors`` test vectors refined toward the low eigenvectors of
+                 Gamma5 D_l to a chosen eigen-residual (Sec. 2.2 setup phase,
+                 Sec. 5 outlook), by simultaneous inverse iteration.
 """
