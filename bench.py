@@ -48,6 +48,11 @@ METRIC = 'tr(D^-1) MLMC time to fixed variance, learned+mixed vs plain; Dslash G
 DIMS = (16, 16, 16, 16)
 EPS_GAUGE = 0.4
 GAUGE_SEED, NOISE_SEED, TV_SEED = 1002, 2002, 3002
+ARMS = ('plain', 'oblique', 'deflated', 'sap', 'fp64', 'refined')
+# refined arm (Sec. 5): level-0 test vectors refined toward the low modes of
+# Gamma5 D, a block of N_tv + 8 columns, eigen-residual target and the
+# tolerance of the refinement's FP64 solves
+REFINE_BLOCK_EXTRA, REFINE_EIG_TOL, REFINE_SOLVE_TOL = 8, 1e-3, 1e-6
 BLOCKS = [(4, 4, 4, 4), (2, 2, 2, 2)]
 NTV = [16, 16]
 REL_EPS = 1e-5
@@ -404,6 +409,10 @@ def main():
     ap.add_argument('--learned', type=int, default=1, help='channels of the learned smoother (0: off)')
     ap.add_argument('--train-steps', type=int, default=200)
     ap.add_argument('--dslash-only', action='store_true', help='only the 32^4 FP32 Dslash measurement')
+    ap.add_argument('--arms', default=','.join(ARMS),
+                    help='comparison arms to run (comma list of %s)' % ', '.join(ARMS))
+    ap.add_argument('--refine-iters', type=int, default=30,
+                    help='cap on the test-vector refinement steps of the "refined" arm')
     args = ap.parse_args()
 
     dist, rank, world, local = dist_init()
@@ -535,38 +544,46 @@ def main():
     dslash_32 = dslash_hbm(M, torch, U, m0) if rank == 0 else None
 
     compare = {}
+    arms = set(a for a in args.arms.split(',') if a)
+    if arms - set(ARMS):
+        raise SystemExit('unknown arms: %s' % ', '.join(sorted(arms - set(ARMS))))
+    k0 = args.warmup  # the timed run's first sample batch: identical noise
+    cs = args.compare_steps
+    # one eps for every arm; arms with the same estimator share variances
+    eps0 = det['eps']
     if rank == 0 and args.compare_steps > 0:
-        k0 = args.warmup  # the timed run's first sample batch: identical noise
-        cs = args.compare_steps
-        # one eps for every arm; arms with the same estimator share variances
-        eps0 = det['eps']
         mvar = {t: v['var'] for t, v in det['terms'].items()}
-        pres, pms = timed(k0, cs, M.EST_PLAIN)
-        pval, pdet = time_to_variance(merge_terms(pres), 1, pms / cs, cs, eps=eps0)
-        compare['plain_hutchinson_same_solver'] = dict(value=pval, ms_per_step=pms / cs, detail=pdet)
-        pvar = {t: v['var'] for t, v in pdet['terms'].items()}
+        pvar = None
+        if arms & {'plain', 'fp64'}:
+            pres, pms = timed(k0, cs, M.EST_PLAIN)
+            pval, pdet = time_to_variance(merge_terms(pres), 1, pms / cs, cs, eps=eps0)
+            if 'plain' in arms:
+                compare['plain_hutchinson_same_solver'] = dict(value=pval, ms_per_step=pms / cs, detail=pdet)
+            pvar = {t: v['var'] for t, v in pdet['terms'].items()}
         # the paper's earlier decomposition (Eq. oblique_multigrid-multilevel-monte-carlo)
         # with the same solver: its own terms, variances from its own samples
-        ores, oms = timed(k0, cs, M.EST_OBLIQUE)
-        oval, odet = time_to_variance(merge_terms(ores), 1, oms / cs, cs, eps=eps0)
-        compare['mlmc_oblique_same_solver'] = dict(value=oval, ms_per_step=oms / cs, detail=odet)
+        if 'oblique' in arms:
+            ores, oms = timed(k0, cs, M.EST_OBLIQUE)
+            oval, odet = time_to_variance(merge_terms(ores), 1, oms / cs, cs, eps=eps0)
+            compare['mlmc_oblique_same_solver'] = dict(value=oval, ms_per_step=oms / cs, detail=odet)
         # inexact deflation of plain Hutchinson (Sec. 2.1, the paper's setting of
         # Sec. 4.2: k = 128, five inverse block power steps, inner solves to
         # 1e-6); the exact part has no variance, its cost is the basis build
-        dex, dsec = M.mgmlmc_deflation_build(ctx, 128, 5, 1e-6, TV_SEED + 4000)
-        dres, dms = timed(k0, cs, M.EST_DEFLATED)
-        dacc = {t: a for t, a in merge_terms(dres).items() if t == M.TERM_DEFL}
-        dval, ddet = time_to_variance(dacc, 1, dms / cs, cs, eps=eps0)
-        compare['deflated_hutchinson_same_solver'] = dict(
-            value=dval, ms_per_step=dms / cs, setup_s=dsec, exact_part=[dex.real, dex.imag],
-            value_with_setup=dval + dsec, detail=ddet)
-        if args.learned > 0:
+        if 'deflated' in arms:
+            dex, dsec = M.mgmlmc_deflation_build(ctx, 128, 5, 1e-6, TV_SEED + 4000)
+            dres, dms = timed(k0, cs, M.EST_DEFLATED)
+            dacc = {t: a for t, a in merge_terms(dres).items() if t == M.TERM_DEFL}
+            dval, ddet = time_to_variance(dacc, 1, dms / cs, cs, eps=eps0)
+            compare['deflated_hutchinson_same_solver'] = dict(
+                value=dval, ms_per_step=dms / cs, setup_s=dsec, exact_part=[dex.real, dex.imag],
+                value_with_setup=dval + dsec, detail=ddet)
+        if args.learned > 0 and 'sap' in arms:
             M.mgmlmc_set_solver(ctx, precision=prec, **SOLVER)
             step(k0)
             sres, sms = timed(k0, cs)
             sval, sdet = time_to_variance(merge_terms(sres), 1, sms / cs, cs, var_of=mvar, eps=eps0)
             compare['mlmc_same_precision_sap_only'] = dict(value=sval, ms_per_step=sms / cs, detail=sdet)
-        if prec == M.FP32:
+        if prec == M.FP32 and 'fp64' in arms:
             M.mgmlmc_set_solver(ctx, precision=M.FP64, **SOLVER)
             step(k0)
             fres, fms = timed(k0, cs)
@@ -600,6 +617,25 @@ def main():
         e2e = dict(value=t_build + value, unit='s', h2d_bytes_per_step=int(U.nbytes),
                    d2h_bytes_per_step=int(nterm * 88), setup_s=t_build, step_s=t_e2e - t_build,
                    note='gauge field from pinned host memory + hierarchy setup + sampling to the same eps')
+
+    # Sec. 5: test vectors computed to a small eigen-residual.  Last, because
+    # it replaces the level-0 test vectors of the context for good.
+    if rank == 0 and args.compare_steps > 0 and 'refined' in arms and args.refine_iters > 0:
+        torch.cuda.synchronize()
+        t0 = time.time()
+        th, rh, rsteps = M.mgmlmc_refine_test_vectors(ctx, 0, NTV[0] + REFINE_BLOCK_EXTRA, args.refine_iters,
+                                                      REFINE_EIG_TOL, REFINE_SOLVE_TOL, TV_SEED + 5000)
+        torch.cuda.synchronize()
+        rsec = time.time() - t0
+        M.mgmlmc_set_solver(ctx, precision=prec, **main_solver)
+        step(k0)
+        rres, rms = timed(k0, cs)
+        rval, rdet = time_to_variance(merge_terms(rres), 1, rms / cs, cs, eps=eps0)
+        compare['mlmc_refined_test_vectors'] = dict(
+            value=rval, ms_per_step=rms / cs, setup_s=rsec, value_with_setup=rval + rsec, steps=rsteps,
+            block=NTV[0] + REFINE_BLOCK_EXTRA, eig_tol=REFINE_EIG_TOL, solve_tol=REFINE_SOLVE_TOL,
+            eig_res_max=float(rh.max()), eig_res=[float(x) for x in rh], theta=[float(x) for x in th],
+            detail=rdet)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and 'oracle_plain' in wl:

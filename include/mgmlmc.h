@@ -42,7 +42,8 @@
  *     (aux = source slice), 80 for disconnected loops (aux = slice),
  *     96 + l for the start vectors of the test-vector setup, 144 + l for
  *     the oblique M_l, 160 for deflated samples, 176 for the deflation
- *     start columns (sample = column).
+ *     start columns (sample = column), 192 + l for the extra start columns
+ *     of the test-vector refinement (sample = column).
  *
  * Ownership and streams
  *   The context owns every device buffer it allocates; caller buffers are
@@ -154,6 +155,8 @@ typedef enum {
 #define MGMLMC_TERM_DEFL 160    /* x^H (I - V V^H) D^-1 x */
 #define MGMLMC_TERM_DEFL_EXACT 161 /* tr(V^H D^-1 V), n = 1, variance 0 */
 #define MGMLMC_TERM_DEFL_START 176 /* noise stream of the start vectors */
+#define MGMLMC_TERM_TV_EXTRA 192   /* + level: extra start columns of
+                                      mgmlmc_refine_test_vectors */
 
 typedef struct {
   int kind;          /* mgmlmc_estimator */
@@ -250,6 +253,29 @@ mgmlmc_status mgmlmc_estimate_trace(mgmlmc_ctx *ctx, const mgmlmc_est_params *p,
  * a new gauge field, mass or hierarchy discards the basis. */
 mgmlmc_status mgmlmc_deflation_build(mgmlmc_ctx *ctx, int k, int iters, double tol, uint64_t seed,
                                      double *exact, double *seconds);
+/* Test vectors of level `level` refined toward the eigenvectors of
+ * Q_l = Gamma5_l D_l for its smallest |eigenvalues| (Sec. 2.2: the setup
+ * phase builds P_l from test vectors approximating low modes; Sec. 5: more
+ * accurate ones, to eigen-residual 1e-3 .. 1e-4, lower the variance).
+ * Gamma5_l is +1 on the first half of a site's dofs and -1 on the second.
+ * Block of n_vec columns (N_tv <= n_vec <= min(128, n)): the level's
+ * current N_tv test vectors, then Z4 columns of samples N_tv .. n_vec-1 of
+ * noise stream MGMLMC_TERM_TV_EXTRA + level, orthonormalised (Gram-Schmidt,
+ * two passes, column order).  Each step: W = D_l^-1 Gamma5_l V with FP64
+ * solves to relative tolerance solve_tol, W^H W = Y diag(mu) Y^H with mu
+ * descending, V = W Y diag(mu)^-1/2 (simultaneous iteration with the Ritz
+ * step on Q_l^-2).  Steps stop after max_iters, or earlier once every one
+ * of the first N_tv columns has ||Q v - theta v|| <= eig_tol with
+ * theta = v^H Q v (eig_tol = 0: exactly max_iters steps).  Those columns,
+ * each scaled so that its first entry of largest modulus is real and
+ * positive, become the level's test vectors (as if set by
+ * mgmlmc_set_test_vectors; the levels above keep theirs), and the hierarchy
+ * is rebuilt with the parameters of the last mgmlmc_build_hierarchy.
+ * Outputs (each may be NULL): theta[N_tv], eig_res[N_tv] of the returned
+ * columns, *steps taken.  Requires a hierarchy; level < L - 1. */
+mgmlmc_status mgmlmc_refine_test_vectors(mgmlmc_ctx *ctx, int level, int n_vec, int max_iters,
+                                         double eig_tol, double solve_tol, uint64_t seed,
+                                         double *theta, double *eig_res, int *steps);
 /* Exact trace of the coarsest-level inverse, tr(D_L^-1), from its dense
  * inverse (Sec. 3 allows a direct computation of this term). */
 mgmlmc_status mgmlmc_coarsest_trace(mgmlmc_ctx *ctx, double *re, double *im);
@@ -345,6 +371,11 @@ mgmlmc_status mgmlmc_noise(mgmlmc_ctx *ctx, int level, uint64_t seed, uint64_t f
  * site_in_aggregate * dof/2 + (dof within chirality); site_in_aggregate
  * ordered like s inside the block. */
 mgmlmc_status mgmlmc_get_prolongator(mgmlmc_ctx *ctx, int level, double *out);
+/* Copy the N_tv test vectors P_l was built from to host as [k][n] complex
+ * double (n the level's vector length): imported, set up, or refined by
+ * mgmlmc_refine_test_vectors.  Passing them back through
+ * mgmlmc_set_test_vectors reproduces the hierarchy.  level < L - 1. */
+mgmlmc_status mgmlmc_get_test_vectors(mgmlmc_ctx *ctx, int level, double *out);
 /* Copy the stencil blocks of D_l (level >= 1) to host as
  * [X][d][i][j] complex double, d = 0 self, 1 + 2 mu (+mu), 2 + 2 mu (-mu);
  * block d of X collects the fine hops of direction d leaving aggregate X,

@@ -93,6 +93,19 @@ mgmlmc_status mgmlmc_deflation_build(mgmlmc_ctx *ctx, int k, int iters, double t
   });
 }
 
+mgmlmc_status mgmlmc_refine_test_vectors(mgmlmc_ctx *ctx, int level, int n_vec, int max_iters,
+                                         double eig_tol, double solve_tol, uint64_t seed,
+                                         double *theta, double *eig_res, int *steps) {
+  return guard(ctx, [&] {
+    std::vector<double> th, rh;
+    int st = 0;
+    E(ctx).refine_test_vectors(level, n_vec, max_iters, eig_tol, solve_tol, seed, th, rh, st);
+    if (theta) std::memcpy(theta, th.data(), th.size() * sizeof(double));
+    if (eig_res) std::memcpy(eig_res, rh.data(), rh.size() * sizeof(double));
+    if (steps) *steps = st;
+  });
+}
+
 mgmlmc_status mgmlmc_gen_gauge(mgmlmc_ctx *ctx, double eps, uint64_t seed) {
   return guard(ctx, [&] { E(ctx).gen_gauge(eps, seed); });
 }
@@ -333,6 +346,13 @@ mgmlmc_status mgmlmc_get_prolongator(mgmlmc_ctx *ctx, int level, double *out) {
   return guard(ctx, [&] {
     if (!out) throw mg::Error(MGMLMC_ERR_ARG, "NULL argument");
     E(ctx).get_prolongator(level, out);
+  });
+}
+
+mgmlmc_status mgmlmc_get_test_vectors(mgmlmc_ctx *ctx, int level, double *out) {
+  return guard(ctx, [&] {
+    if (!out) throw mg::Error(MGMLMC_ERR_ARG, "NULL argument");
+    E(ctx).get_test_vectors(level, out);
   });
 }
 

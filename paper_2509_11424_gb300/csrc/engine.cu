@@ -4,6 +4,7 @@
 // plays in Sec. 4: every level solved to a relative residual), and the
 // estimators of Sec. 3 / Sec. 4.
 #include "engine.h"
+#include "herm_eig.h"
 
 #include <algorithm>
 #include <cmath>
@@ -38,6 +39,16 @@ struct EventPair {
   }
   EventPair(const EventPair &) = delete;
   EventPair &operator=(const EventPair &) = delete;
+};
+// a device buffer freed on every exit
+template <typename T> struct DevBuf {
+  T *p = nullptr;
+  explicit DevBuf(size_t count) : p(dalloc<T>(count)) {}
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
 };
 
 __global__ void target_kernel(double *target, const double2 *nrm, double tol, int nrhs) {
@@ -983,6 +994,7 @@ void Engine::build_hierarchy(const mgmlmc_mg_params &p) {
   MG_CUDA(cudaMemcpyAsync(&flag, flag_dev_, sizeof(int), cudaMemcpyDeviceToHost, stream));
   sync();
   if (flag) throw Error(MGMLMC_ERR_NUMERIC, "coarsest operator is singular");
+  mgp_ = p;
   ready_ = true;
 }
 
@@ -1165,7 +1177,7 @@ void Engine::orthonormalise_cols(double2 *V, int k, int64_t n) {
     MG_CUDA(cudaMemcpyAsync(&nn, h + k, sizeof(double2), cudaMemcpyDeviceToHost, stream));
     sync();
     if (!(nn.x > 0.0) || !std::isfinite(nn.x))
-      throw Error(MGMLMC_ERR_NUMERIC, "deflation basis: dependent or non-finite column");
+      throw Error(MGMLMC_ERR_NUMERIC, "orthonormalisation: dependent or non-finite column");
     axpby<double>(1.0 / std::sqrt(nn.x), v, 0.0, v, n, 1, stream);
   }
 }
@@ -1242,6 +1254,171 @@ void Engine::deflation_build(int k, int iters, double tol, uint64_t seed,
   seconds = defl_seconds_;
 }
 
+// ------------------------------------------------------- test-vector refinement
+// Simultaneous inverse iteration on Q_l = Gamma5_l D_l (Rutishauser's
+// 'ritzit', with the Ritz step on Q_l^-2, which is positive definite, so the
+// wanted low modes of the indefinite Q_l are its exterior ones):
+//   start: the level's N_tv test vectors, then m - N_tv Z4 columns (noise
+//          term 192 + l, samples N_tv .. m-1), orthonormalised;
+//   step:  W = Q^-1 V = D^-1 Gamma5 V (FP64 solves to solve_tol),
+//          W^H W = Y diag(mu) Y^H (host Jacobi), mu descending,
+//          V = W Y diag(mu)^-1/2;
+//   check: theta_j = v_j^H Q v_j, rho_j = ||Q v_j - theta_j v_j||.
+// The first N_tv columns, each turned so that its largest-modulus entry is
+// real and positive, replace the level's test vectors as if imported; the
+// levels above keep the vectors they were built from, and the hierarchy is
+// rebuilt with the parameters of the last build.
+void Engine::refine_test_vectors(int l, int m, int iters, double tol, double solve_tol, uint64_t seed,
+                                 std::vector<double> &theta, std::vector<double> &rho, int &steps) {
+  if (!ready_) throw Error(MGMLMC_ERR_STATE, "hierarchy not built");
+  if (l < 0 || l + 1 >= n_levels()) throw Error(MGMLMC_ERR_ARG, "refine: the level has no test vectors");
+  const int k = levels_[l].agg.ntv;
+  const Geom G = levels_[l].g;
+  const int64_t n = G.n();
+  if (m < k || m > 128 || m > n) throw Error(MGMLMC_ERR_ARG, "refine: block size must be in [N_tv, min(128, n)]");
+  if (iters < 0 || !(tol >= 0.0) || !(solve_tol > 0.0 && solve_tol < 1.0))
+    throw Error(MGMLMC_ERR_ARG, "refine: bad iteration count or tolerance");
+  auto built_tv = [&](int j, size_t count) -> double2 * {
+    auto it = ws_.find("tv#" + std::to_string(j) + "d");
+    if (it == ws_.end() || it->second.second < count * sizeof(double2))
+      throw Error(MGMLMC_ERR_STATE, "refine: the build's test vectors are gone");
+    return static_cast<double2 *>(it->second.first);
+  };
+  const mgmlmc_mg_params params = mgp_;
+  std::vector<double> hv((size_t)2 * k * n);
+  std::vector<double> th(m), rh(m);
+  {
+    DevBuf<double2> Vb((size_t)m * n), Wb((size_t)m * n);
+    double2 *V = Vb.p, *W = Wb.p;
+    double2 *g = ws<double>("rfg", l, (size_t)8 * n);
+    double2 *d = ws<double>("rfd", 0, (size_t)m);
+    double2 *hc = ws<double>("rfc", 0, (size_t)m * m);
+    MG_CUDA(cudaMemcpyAsync(V, built_tv(l, (size_t)k * n), sizeof(double2) * k * n, cudaMemcpyDeviceToDevice,
+                            stream));
+    if (m > k) z4_noise<double>(V + (size_t)k * n, G, seed, (uint64_t)k, 192 + l, 0, -1, m - k, stream);
+    orthonormalise_cols(V, m, n);
+    std::vector<double2> h((size_t)m * m);
+    auto fetch = [&](const double2 *src, size_t count) {
+      MG_CUDA(cudaMemcpyAsync(h.data(), src, sizeof(double2) * count, cudaMemcpyDeviceToHost, stream));
+      sync();
+    };
+    // theta_r = Re <v_r, Q v_r>, rho_r = ||Q v_r - theta_r v_r|| (W is scratch)
+    auto quotients = [&]() {
+      for (int j0 = 0; j0 < m; j0 += 8)
+        apply_D<double>(l, V + (size_t)j0 * n, W + (size_t)j0 * n, std::min(8, m - j0));
+      gamma5_apply<double>(W, W, G.V, G.dof, m, stream);
+      dot<double>(V, W, n, m, d, partials((size_t)reduce_blocks(n) * m), stream);
+      fetch(d, m);
+      for (int r = 0; r < m; ++r) {
+        th[r] = h[r].x;
+        axpby<double>(-th[r], V + (size_t)r * n, 1.0, W + (size_t)r * n, n, 1, stream);
+      }
+      dot<double>(W, W, n, m, d, partials((size_t)reduce_blocks(n) * m), stream);
+      fetch(d, m);
+      for (int r = 0; r < m; ++r) rh[r] = std::sqrt(std::max(h[r].x, 0.0));
+    };
+    auto step = [&]() {
+      for (int j0 = 0; j0 < m; j0 += 8) {
+        const int nb = std::min(8, m - j0);
+        gamma5_apply<double>(V + (size_t)j0 * n, g, G.V, G.dof, nb, stream);
+        solve(l, g, W + (size_t)j0 * n, nb);
+      }
+      // hc[r m + j] = <W_j, W_r> = (W^H W)_jr
+      for (int r = 0; r < m; ++r)
+        multi_dot<double>(W, n, m, W + (size_t)r * n, n, 1, hc + (size_t)r * m, m,
+                          partials((size_t)reduce_blocks(n) * m), stream);
+      fetch(hc, (size_t)m * m);
+      std::vector<std::complex<double>> Gm((size_t)m * m), Y;
+      for (int j = 0; j < m; ++j)
+        for (int r = 0; r < m; ++r) {
+          const std::complex<double> a(h[(size_t)r * m + j].x, h[(size_t)r * m + j].y);
+          const std::complex<double> b(h[(size_t)j * m + r].x, h[(size_t)j * m + r].y);
+          Gm[(size_t)j * m + r] = 0.5 * (a + std::conj(b));
+        }
+      std::vector<double> mu;
+      if (herm_eig_jacobi(Gm, m, mu, Y) < 0) throw Error(MGMLMC_ERR_NUMERIC, "refine: eigensolver did not converge");
+      std::vector<int> order(m);
+      for (int j = 0; j < m; ++j) order[j] = j;
+      std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return mu[a] > mu[b]; });
+      for (int r = 0; r < m; ++r) {
+        const int o = order[r];
+        if (!(mu[o] > 0.0) || !std::isfinite(mu[o])) throw Error(MGMLMC_ERR_NUMERIC, "refine: rank-deficient block");
+        const double f = 1.0 / std::sqrt(mu[o]);
+        for (int j = 0; j < m; ++j) {
+          const std::complex<double> c = Y[(size_t)j * m + o] * f;
+          h[(size_t)r * m + j] = make_double2(c.real(), c.imag());
+        }
+      }
+      MG_CUDA(cudaMemcpyAsync(hc, h.data(), sizeof(double2) * m * m, cudaMemcpyHostToDevice, stream));
+      MG_CUDA(cudaMemsetAsync(V, 0, sizeof(double2) * m * n, stream));
+      for (int r = 0; r < m; ++r)  // v_r = sum_j W_j C_jr
+        multi_axpy<double>(W, n, m, V + (size_t)r * n, n, 1, hc + (size_t)r * m, m, 1.0, stream);
+      sync();  // h is rewritten by the next fetch
+    };
+    const mgmlmc_solver_params keep = sp_;
+    sp_.precision = MGMLMC_FP64;
+    sp_.tol = solve_tol;
+    try {
+      quotients();
+      steps = 0;
+      auto converged = [&]() {
+        if (!(tol > 0.0)) return false;
+        double mx = 0.0;
+        for (int j = 0; j < k; ++j) mx = std::max(mx, rh[j]);
+        return mx <= tol;
+      };
+      while (!converged() && steps < iters) {
+        step();
+        quotients();
+        ++steps;
+      }
+    } catch (...) {
+      sp_ = keep;
+      ws_release("rfg", l, true);
+      throw;
+    }
+    sp_ = keep;
+    ws_release("rfg", l, true);
+    MG_CUDA(cudaMemcpyAsync(hv.data(), V, sizeof(double2) * k * n, cudaMemcpyDeviceToHost, stream));
+    sync();
+  }
+  // canonical phase: the first entry of largest modulus real and positive
+  for (int j = 0; j < k; ++j) {
+    double *v = hv.data() + (size_t)2 * j * n;
+    int64_t im = 0;
+    double best = -1.0;
+    for (int64_t i = 0; i < n; ++i) {
+      const double a = std::hypot(v[2 * i], v[2 * i + 1]);
+      if (a > best) {
+        best = a;
+        im = i;
+      }
+    }
+    const std::complex<double> ph = std::conj(std::complex<double>(v[2 * im], v[2 * im + 1])) / best;
+    for (int64_t i = 0; i < n; ++i) {
+      const std::complex<double> x = std::complex<double>(v[2 * i], v[2 * i + 1]) * ph;
+      v[2 * i] = x.real();
+      v[2 * i + 1] = x.imag();
+    }
+    v[2 * im] = best;
+    v[2 * im + 1] = 0.0;
+  }
+  // the levels above keep exactly the vectors they were built from
+  for (int j = 0; j < l; ++j) {
+    const int kj = levels_[j].agg.ntv;
+    const int64_t nj = levels_[j].g.n();
+    std::vector<double> hj((size_t)2 * kj * nj);
+    MG_CUDA(cudaMemcpyAsync(hj.data(), built_tv(j, (size_t)kj * nj), sizeof(double2) * kj * nj,
+                            cudaMemcpyDeviceToHost, stream));
+    sync();
+    imported_host_[j] = std::move(hj);
+  }
+  imported_host_[l] = std::move(hv);
+  theta.assign(th.begin(), th.begin() + k);
+  rho.assign(rh.begin(), rh.begin() + k);
+  build_hierarchy(params);
+}
+
 void Engine::coarsest_trace(double *re, double *im) {
   if (!ready_) throw Error(MGMLMC_ERR_STATE, "hierarchy not built");
   const Level &c = levels_.back();
@@ -1261,6 +1438,17 @@ void Engine::get_prolongator(int l, double *host) {
   double2 *tmp = ws<double>("pcan", l, cnt);
   prolongator_to_canonical(f.P64, tmp, f.agg, stream);
   MG_CUDA(cudaMemcpyAsync(host, tmp, cnt * sizeof(double2), cudaMemcpyDeviceToHost, stream));
+  sync();
+}
+
+// the build leaves each level's test vectors in its "tv" workspace
+void Engine::get_test_vectors(int l, double *host) {
+  if (!ready_ || l < 0 || l + 1 >= n_levels()) throw Error(MGMLMC_ERR_ARG, "no test vectors at that level");
+  const size_t cnt = (size_t)levels_[l].agg.ntv * levels_[l].g.n();
+  auto it = ws_.find("tv#" + std::to_string(l) + "d");
+  if (it == ws_.end() || it->second.second < cnt * sizeof(double2))
+    throw Error(MGMLMC_ERR_STATE, "the build's test vectors are gone");
+  MG_CUDA(cudaMemcpyAsync(host, it->second.first, cnt * sizeof(double2), cudaMemcpyDeviceToHost, stream));
   sync();
 }
 

@@ -140,7 +140,18 @@ class Engine {
                        double &seconds);
   int deflation_k() const { return defl_k_; }
 
+  // test vectors of level l refined toward the low eigenvectors of
+  // Q_l = Gamma5_l D_l (Sec. 2.2 setup phase, Sec. 5): block of m >= N_tv
+  // columns, at most `iters` simultaneous inverse-iteration steps with the
+  // Ritz step on Q_l^-2 and FP64 solves to solve_tol, stopping once every
+  // returned column has ||Q v - theta v|| <= tol (tol > 0); the hierarchy is
+  // then rebuilt from them.  theta / rho / steps: Rayleigh quotients and
+  // eigen-residuals of the N_tv returned columns, steps taken.
+  void refine_test_vectors(int l, int m, int iters, double tol, double solve_tol, uint64_t seed,
+                           std::vector<double> &theta, std::vector<double> &rho, int &steps);
+
   void get_prolongator(int l, double *host);
+  void get_test_vectors(int l, double *host);
   void get_coarse_op(int l, double *host);
 
   SolveInfo last_solve;
@@ -199,6 +210,7 @@ class Engine {
   mgmlmc_solver_params sp_{};
   std::vector<Level> levels_;
   std::map<int, std::vector<double>> imported_host_;  // level -> ntv * n complex
+  mgmlmc_mg_params mgp_{};  // parameters of the last successful build
   std::map<std::string, std::pair<void *, size_t>> ws_;
   double2 *scal_ = nullptr;     // small scalar scratch
   double2 *partial_ = nullptr;  // reduction partials

@@ -21,6 +21,7 @@ EST_PLAIN, EST_ORTHOGONAL, EST_OBLIQUE, EST_DEFLATED = 0, 1, 2, 3
 OP_D, OP_RESTRICT, OP_PROLONG, OP_PROJECT, OP_SOLVE, OP_GAMMA5, OP_SMOOTH, OP_NET = range(8)
 TERM_PLAIN, TERM_O, TERM_F, TERM_COARSEST, TERM_M = 0, 16, 32, 48, 144
 TERM_DEFL, TERM_DEFL_EXACT, TERM_DEFL_START = 160, 161, 176
+TERM_TV_EXTRA = 192
 STATUS = {0: 'OK', 1: 'ERR_ARG', 2: 'ERR_STATE', 3: 'ERR_OOM', 4: 'ERR_CUDA',
           5: 'ERR_NOT_CONVERGED', 6: 'ERR_NUMERIC'}
 
@@ -113,6 +114,7 @@ _SIGNATURES = {
     'mgmlmc_apply': [_P, _I, _I, _I, _P, _P, _I],
     'mgmlmc_noise': [_P, _I, _U64, _U64, _U64, _U64, _I, _P, _I],
     'mgmlmc_get_prolongator': [_P, _I, _P],
+    'mgmlmc_get_test_vectors': [_P, _I, _P],
     'mgmlmc_get_coarse_op': [_P, _I, _P],
     'mgmlmc_last_solve_stats': [_P, ctypes.POINTER(_I), ctypes.POINTER(_D)],
     'mgmlmc_profile': [_P, _I],
@@ -129,6 +131,7 @@ _SIGNATURES = {
     'mgmlmc_set_kernel_variant': [_P, _I, _I],
     'mgmlmc_gen_gauge': [_P, _D, _U64],
     'mgmlmc_deflation_build': [_P, _I, _I, _D, _U64, _P, ctypes.POINTER(_D)],
+    'mgmlmc_refine_test_vectors': [_P, _I, _I, _I, _D, _D, _U64, _P, _P, ctypes.POINTER(_I)],
     'mgmlmc_reorder': [_P, _P, _P, _I, _I],
     'mgmlmc_reorder_bf16': [_P, _P, _P, _I, _I],
     'mgmlmc_kernel_variants': [_I],
@@ -314,6 +317,15 @@ def mgmlmc_get_prolongator(ctx, level, out):
     _check(ctx, lib().mgmlmc_get_prolongator(ctx, level, ptr(out)))
 
 
+def mgmlmc_get_test_vectors(ctx, level):
+    """(N_tv, n) complex array: the test vectors P_level was built from."""
+    _, dof, _ = mgmlmc_level_info(ctx, level + 1)
+    n = mgmlmc_level_info(ctx, level)[2]
+    out = np.zeros((dof // 2, n), dtype=np.complex128)
+    _check(ctx, lib().mgmlmc_get_test_vectors(ctx, level, ptr(out)))
+    return out
+
+
 def mgmlmc_get_coarse_op(ctx, level, out):
     _check(ctx, lib().mgmlmc_get_coarse_op(ctx, level, ptr(out)))
 
@@ -368,6 +380,20 @@ def mgmlmc_deflation_build(ctx, k, iters, tol, seed):
     _check(ctx, lib().mgmlmc_deflation_build(ctx, int(k), int(iters), float(tol), int(seed), ptr(ex),
                                              ctypes.byref(sec)))
     return complex(ex[0], ex[1]), sec.value
+
+
+def mgmlmc_refine_test_vectors(ctx, level, n_vec, max_iters, eig_tol, solve_tol, seed):
+    """Refine the test vectors of `level` toward low eigenvectors of
+    Gamma5 D_l and rebuild the hierarchy (see include/mgmlmc.h); returns
+    (theta, eigen-residuals, steps) of the N_tv refined vectors."""
+    ntv = mgmlmc_level_info(ctx, level + 1)[1] // 2
+    th = np.zeros(ntv)
+    rh = np.zeros(ntv)
+    st = _I()
+    _check(ctx, lib().mgmlmc_refine_test_vectors(ctx, int(level), int(n_vec), int(max_iters), float(eig_tol),
+                                                 float(solve_tol), int(seed), ptr(th), ptr(rh),
+                                                 ctypes.byref(st)))
+    return th, rh, st.value
 
 
 def mgmlmc_gen_gauge(ctx, eps, seed):
