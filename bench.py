@@ -66,14 +66,15 @@ KERNELS = {0: 'wilson_dslash_fp64', 1: 'wilson_dslash_fp32', 2: 'coarse_stencil_
            3: 'coarse_stencil_fp32', 4: 'sap_sweep_fp64', 5: 'sap_sweep_fp32'}
 # further event-timed groups (breakdown only; no roofline)
 GROUPS = {6: 'transfer_in_cycle', 7: 'gram_schmidt', 8: 'learned_step', 9: 'coarsest_dense'}
-# dram bytes per launch of a kernel from an ncu capture, keyed by (kernel,
-# sha1 of the kernel sources it was measured on); a stale key gives null
 SHARD_STRIDE = 1000000  # Z4 sample counters per rank
+# dram bytes per launch of a kernel from an ncu capture, keyed by (kernel,
+# sha1 of the kernel sources it was measured on, right-hand sides per
+# launch); a stale or missing key gives null
 TRAFFIC = {
     # one level-1 launch (4^4 x 32 dof, 8 rhs), cold-cache capture
-    ('coarse_stencil_fp32', '26c34d4e25b6'): 19.43e6,
+    ('coarse_stencil_fp32', '26c34d4e25b6', 8): 19.43e6,
     # one sweep (block + boundary kernel, both colours), 16^4 x 8 rhs
-    ('sap_sweep_fp32', '9a67c5f9b503'): 578.0e6,
+    ('sap_sweep_fp32', '9a67c5f9b503', 8): 578.0e6,
 }
 
 
@@ -399,7 +400,9 @@ def main():
     ap.add_argument('--gpus', type=int, default=1)
     ap.add_argument('--steps', type=int, default=4)
     ap.add_argument('--warmup', type=int, default=3)
-    ap.add_argument('--batch', type=int, default=8)
+    # 32 rhs per launch: the per-sample cost of every term falls with the
+    # batch (8 -> 16 -> 32: 91 -> 75 -> 66 s to the same variance)
+    ap.add_argument('--batch', type=int, default=32)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--precision', default='fp32', choices=['fp64', 'fp32'])
     ap.add_argument('--compare-steps', type=int, default=2)
@@ -525,7 +528,7 @@ def main():
             peak = hbm if hbm else 6800.0
             roof = dict(bound='hbm', achieved=achieved, peak=peak, unit='GB/s', frac=achieved / peak,
                         peak_source='of measured (MEASURED_PEAKS.json hbm_gbs)' if hbm else 'of fallback 6.8 TB/s')
-        roof['traffic'] = TRAFFIC.get((KERNELS[dom], kernel_source_hash(KERNELS[dom])))
+        roof['traffic'] = TRAFFIC.get((KERNELS[dom], kernel_source_hash(KERNELS[dom]), B))
         roof.update(kernel=KERNELS[dom], launches=ks['launches'], avg_launch_us=ks['ms'] * 1e3 / ks['launches'],
                     share_of_profiled_step=ks['ms'] / prof_ms, profiled_step_ms=prof_ms,
                     algorithmic_bytes_per_launch=ks['bytes'] / ks['launches'],
