@@ -75,6 +75,10 @@ TRAFFIC = {
     ('coarse_stencil_fp32', '26c34d4e25b6', 8): 19.43e6,
     # one sweep (block + boundary kernel, both colours), 16^4 x 8 rhs
     ('sap_sweep_fp32', '9a67c5f9b503', 8): 578.0e6,
+    # the same sweep at 32 rhs, scaled from the 8-rhs capture by the rhs
+    # count: every right-hand side is its own row of the launch grid and
+    # moves its own residual, correction and block solution
+    ('sap_sweep_fp32', '9a67c5f9b503', 32): 4 * 578.0e6,
 }
 
 
