@@ -37,9 +37,15 @@ import json
 import os
 import subprocess
 import sys
+import threading
 import time
 
-import numpy as np
+# the CPU oracle runs one worker thread per host core, each with a
+# single-threaded BLAS (set before numpy loads its BLAS)
+for _var in ('OPENBLAS_NUM_THREADS', 'OMP_NUM_THREADS', 'MKL_NUM_THREADS'):
+    os.environ.setdefault(_var, '1')
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -239,28 +245,59 @@ def time_to_variance(acc, world, step_ms, steps, rel_eps=REL_EPS, var_of=None, e
 
 
 # ---------------------------------------------------------------- CPU oracle
-def oracle_gmres_cycle(m0):
-    """One bounded sample of the workload with the FP64 oracle on the host:
-    one restart cycle (64 iterations) of the oracle's GMRES(64) on the 16^4
-    plain-Hutchinson system D z = x, x the first Z4 sample.  Returns seconds
-    per GMRES iteration and the setup time."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+_ORACLE_MATRIX = {}
+
+
+def oracle_matrix(m0):
+    """The oracle's sparse 16^4 Wilson matrix (built once per mass) and its
+    build time."""
+    if m0 not in _ORACLE_MATRIX:
+        from oracle import dirac
+        from paper_2509_11424_gb300 import synth
+        t0 = time.time()
+        U = synth.gauge_field(DIMS, EPS_GAUGE, GAUGE_SEED)
+        _ORACLE_MATRIX[m0] = (dirac.wilson_matrix(U, m0, DIMS).tocsr(), time.time() - t0)
+    return _ORACLE_MATRIX[m0]
+
+
+def oracle_gmres_cycle(m0, threads=1, first=0):
+    """Bounded samples of the workload with the FP64 oracle on the host: in
+    each of `threads` concurrent threads one restart cycle (64 iterations) of
+    the oracle's GMRES(64) on the 16^4 plain-Hutchinson system D z = x, x the
+    Z4 sample first + thread.  The threads share one matrix (scipy's sparse
+    products and numpy's vector operations release the GIL).  Returns the
+    host's seconds per GMRES iteration (wall time over the iterations of all
+    threads), the wall and CPU seconds and the setup time."""
     import scipy.sparse.linalg as spla
-    from oracle import dirac, noise
-    from paper_2509_11424_gb300 import synth
-    t0 = time.time()
-    U = synth.gauge_field(DIMS, EPS_GAUGE, GAUGE_SEED)
-    M = dirac.wilson_matrix(U, m0, DIMS).tocsr()
-    x = noise.z4_vector(M.shape[0], NOISE_SEED, 0, noise.TERM_PLAIN)
-    setup = time.time() - t0
-    it = [0]
+    from oracle import noise
+    M, setup = oracle_matrix(m0)
+    its = [0] * threads
 
-    def cb(_):
-        it[0] += 1
+    def run(i):
+        x = noise.z4_vector(M.shape[0], NOISE_SEED, first + i, noise.TERM_PLAIN)
 
-    t1 = time.time()
-    spla.gmres(M, x, rtol=1e-12, atol=0.0, restart=64, maxiter=1, callback=cb, callback_type='pr_norm')
-    el = time.time() - t1
-    return dict(sec_per_iter=el / max(1, it[0]), iters=it[0], seconds=el, setup_s=setup)
+        def cb(_):
+            its[i] += 1
+
+        spla.gmres(M, x, rtol=1e-12, atol=0.0, restart=64, maxiter=1, callback=cb, callback_type='pr_norm')
+
+    workers = [threading.Thread(target=run, args=(i,)) for i in range(threads)]
+    c0, t1 = time.process_time(), time.time()
+    for w in workers:
+        w.start()
+    for w in workers:
+        w.join()
+    el, cpu = time.time() - t1, time.process_time() - c0
+    total = max(1, sum(its))
+    return dict(sec_per_iter=el / total, iters=total, seconds=el, cpu_seconds=cpu, setup_s=setup,
+                threads=threads)
 
 
 def oracle_time_to_variance(sample, wl):
@@ -274,6 +311,24 @@ def oracle_time_to_variance(sample, wl):
     return op['var'] * C / eps ** 2, C
 
 
+def cpu_baseline(m0, wl, threads):
+    """The `cpu_baseline` object of the GPU arm's line: the oracle's plain
+    Hutchinson estimator timed on `threads` host threads (one GMRES cycle
+    each, concurrently), with the single-thread figure beside it."""
+    s1 = oracle_gmres_cycle(m0)
+    sT = oracle_gmres_cycle(m0, threads, 1) if threads > 1 else s1
+    v1, C1 = oracle_time_to_variance(s1, wl)
+    value, C = oracle_time_to_variance(sT, wl)
+    return {'value': value, 'unit': 's', 'cores': threads, 'kind': 'oracle',
+            'sample': 'plain Hutchinson, %d concurrent 64-iteration GMRES(64) cycles of the oracle on the 16^4 '
+                      'system, one per thread (%.1f s wall), scaled by %.0f iterations per 1e-12 solve and the '
+                      'oracle variance' % (threads, sT['seconds'], np.mean(wl['oracle_plain']['gmres_iters'])),
+            'seconds_per_solve': C, 'cpu_utilisation': sT['cpu_seconds'] / sT['seconds'],
+            'single_core': {'value': v1, 'seconds_per_solve': C1, 'cycle_s': s1['seconds'],
+                            'cpu_utilisation': s1['cpu_seconds'] / s1['seconds']},
+            'threads_available': host_cores()}
+
+
 def reference_arm(args, rank, world):
     """The FP64 CPU oracle on this host's cores, same metric and workload:
     each step one bounded sample (a 64-iteration GMRES cycle of the plain
@@ -281,28 +336,31 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     wl = workload()
-    for _ in range(args.warmup):
-        oracle_gmres_cycle(wl['m0'])
+    T = args.oracle_threads or host_cores()
+    for k in range(args.warmup):
+        oracle_gmres_cycle(wl['m0'], T, k * T)
     t = []
     samples = []
-    for _ in range(args.steps):
-        s = oracle_gmres_cycle(wl['m0'])
+    for k in range(args.steps):
+        s = oracle_gmres_cycle(wl['m0'], T, (args.warmup + k) * T)
         samples.append(s)
         t.append(s['seconds'])
     spi = float(np.mean([s['sec_per_iter'] for s in samples]))
     value, C = oracle_time_to_variance(dict(sec_per_iter=spi), wl)
-    sample = ('plain Hutchinson, 16^4 solve by the oracle GMRES(64): one 64-iteration restart cycle '
-              'per step timed, scaled by %.0f iterations per 1e-12 solve and the oracle variance %.4g '
-              '(tests/golden/mass_16x16x16x16.json)' % (np.mean(wl['oracle_plain']['gmres_iters']),
-                                                        wl['oracle_plain']['var']))
+    sample = ('plain Hutchinson, 16^4 solve by the oracle GMRES(64): per step %d concurrent 64-iteration '
+              'restart cycles (one per thread, samples of their own) timed, scaled by %.0f iterations '
+              'per 1e-12 solve and the oracle variance %.4g (tests/golden/mass_16x16x16x16.json)'
+              % (T, np.mean(wl['oracle_plain']['gmres_iters']), wl['oracle_plain']['var']))
+    util = float(np.mean([s['cpu_seconds'] / s['seconds'] for s in samples]))
     line = {'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': 's', 'n_gpus': world,
             'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': 1e3 * float(np.mean(t)),
             'higher_is_better': False, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
             'data': 'synthetic',
             'config': {'workload': '16^4 Wilson-Dirac, SU(3) exp(i 0.4 H) seed 1002, m0 %.4f, '
                                    'plain Hutchinson with the FP64 CPU oracle' % wl['m0']},
-            'cpu_baseline': {'value': value, 'unit': 's', 'cores': 1, 'kind': 'oracle', 'sample': sample,
-                             'seconds_per_solve': C, 'threads_available': os.cpu_count()},
+            'cpu_baseline': {'value': value, 'unit': 's', 'cores': T, 'kind': 'oracle', 'sample': sample,
+                             'seconds_per_solve': C, 'cpu_utilisation': util,
+                             'threads_available': host_cores()},
             'e2e': {'value': value, 'unit': 's', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
     print(json.dumps(line))
 
@@ -418,6 +476,8 @@ def main():
     ap.add_argument('--dslash-only', action='store_true', help='only the 32^4 FP32 Dslash measurement')
     ap.add_argument('--arms', default=','.join(ARMS),
                     help='comparison arms to run (comma list of %s)' % ', '.join(ARMS))
+    ap.add_argument('--oracle-threads', type=int, default=0,
+                    help='host threads of the CPU oracle timing (0: every core of this host)')
     ap.add_argument('--refine-iters', type=int, default=30,
                     help='cap on the test-vector refinement steps of the "refined" arm')
     args = ap.parse_args()
@@ -646,13 +706,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and 'oracle_plain' in wl:
-        s = oracle_gmres_cycle(m0)
-        cval, C = oracle_time_to_variance(s, wl)
-        cpu = {'value': cval, 'unit': 's', 'cores': 1, 'kind': 'oracle',
-               'sample': 'plain Hutchinson, one 64-iteration GMRES(64) cycle of the oracle on the 16^4 system '
-                         '(%.1f s), scaled by %.0f iterations per 1e-12 solve and the oracle variance'
-                         % (s['seconds'], np.mean(wl['oracle_plain']['gmres_iters'])),
-               'seconds_per_solve': C, 'threads_available': os.cpu_count()}
+        cpu = cpu_baseline(m0, wl, args.oracle_threads or host_cores())
 
     if rank == 0:
         line = {
