@@ -252,6 +252,46 @@ def host_cores():
         return os.cpu_count() or 1
 
 
+def host_memory_available():
+    """Bytes this process may still allocate: MemAvailable, capped by the
+    cgroup's limit when one is set (None when neither can be read)."""
+    avail = None
+    try:
+        with open('/proc/meminfo') as f:
+            for line in f:
+                if line.startswith('MemAvailable:'):
+                    avail = int(line.split()[1]) * 1024
+    except OSError:
+        pass
+    try:
+        with open('/sys/fs/cgroup/memory.max') as f:
+            lim = f.read().strip()
+        with open('/sys/fs/cgroup/memory.current') as f:
+            cur = int(f.read().strip())
+        if lim != 'max':
+            left = int(lim) - cur
+            avail = left if avail is None else min(avail, left)
+    except (OSError, ValueError):
+        pass
+    return avail
+
+
+# host bytes of one oracle worker: the GMRES(64) basis of 65 vectors of the
+# 16^4 system (786,432 complex doubles each), with slack for temporaries
+ORACLE_WORKER_BYTES = 1.2e9
+
+
+def oracle_threads(requested):
+    """Worker threads for the oracle timing: the requested count (0: every
+    core), cut to what the host's free memory holds beside the shared
+    matrix and its construction (~8 GB)."""
+    t = requested or host_cores()
+    avail = host_memory_available()
+    if avail is not None:
+        t = min(t, max(1, int((avail - 8e9) / ORACLE_WORKER_BYTES)))
+    return t
+
+
 _ORACLE_MATRIX = {}
 
 
@@ -336,7 +376,7 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     wl = workload()
-    T = args.oracle_threads or host_cores()
+    T = oracle_threads(args.oracle_threads)
     for k in range(args.warmup):
         oracle_gmres_cycle(wl['m0'], T, k * T)
     t = []
@@ -706,7 +746,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and 'oracle_plain' in wl:
-        cpu = cpu_baseline(m0, wl, args.oracle_threads or host_cores())
+        cpu = cpu_baseline(m0, wl, oracle_threads(args.oracle_threads))
 
     if rank == 0:
         line = {
