@@ -1,5 +1,5 @@
 """Parity at the benchmark's full size (16^4, eps 0.4, seed 1002, the
-oracle-chosen m0) in the launch configuration bench.py times (8 right-hand
+oracle-chosen m0) in the launch configuration bench.py times (32 right-hand
 sides, its solver settings): Dslash FP64 / FP32 element by element, Z4 noise
 bit-exact, P orthonormal and the Galerkin relation D_1 = P^H D P checked on
 vectors with the oracle's D, the coarse operators Gamma5-hermitian, and the
@@ -24,7 +24,7 @@ from gpu_util import dev, host, rel, require_lib  # noqa: E402
 M = require_lib()
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 DIMS = (16, 16, 16, 16)
-B = 8
+B = 32  # right-hand sides per launch, as bench.py runs them
 
 
 @pytest.fixture(scope='module')
