@@ -43,3 +43,15 @@ def test_time_to_variance_equals_optimal_allocation_cost():
     val3, det3 = bench.time_to_variance(acc, 1, step_ms, 1, var_of=var_of, eps=2 * eps)
     assert abs(val3 - cost) < 1e-10 * cost  # 4x variance, 2x eps
     assert det3['eps'] == 2 * eps
+
+
+def test_e2e_time_to_variance():
+    """end-to-end time = setup + the first step's one-time extra + the
+    device-timed estimate rescaled to the end-to-end step cost."""
+    import bench
+    # steps at exactly the device cost: setup + first-step extra + value
+    assert bench.e2e_time_to_variance(2.0, 0.5, 0.4, 70.0, 0.4) == 2.0 + 0.1 + 70.0
+    # end-to-end steps 10% dearer than on the device
+    assert abs(bench.e2e_time_to_variance(1.0, 0.44, 0.44, 50.0, 0.4) - (1.0 + 55.0)) < 1e-12
+    # a first step faster than the steady ones adds nothing
+    assert bench.e2e_time_to_variance(0.0, 0.1, 0.4, 10.0, 0.4) == 10.0
