@@ -37,6 +37,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -64,8 +65,8 @@ NTV = [16, 16]
 REL_EPS = 1e-5
 MASS_FILE = os.path.join(ROOT, 'tests', 'golden', 'mass_16x16x16x16.json')
 PEAKS_FILE = os.path.join(ROOT, 'MEASURED_PEAKS.json')
-FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate from the hardware table
-FP32_PEAK_TFLOPS = 80.0  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz (see DESIGN.md)
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP32_PEAK_TFLOPS = 80.0  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 SOLVER = dict(tol=1e-12, restart=24, max_iter=2000, smoother=1, smoother_steps=1, sap_iters=4,
               coarse_iters=4, inner_tol=1e-6, coarse_smoother_steps=4)
 KERNELS = {0: 'wilson_dslash_fp64', 1: 'wilson_dslash_fp32', 2: 'coarse_stencil_fp64',
@@ -116,7 +117,9 @@ class Clocks:
     def __init__(self, device_index):
         self.idx = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, 'gpurun_out', 'clocks_bench_%d.csv' % device_index)
+        # raw samples (the line carries their summary); MGMLMC_CLOCKS_DIR keeps them
+        self.path = os.path.join(os.environ.get('MGMLMC_CLOCKS_DIR', tempfile.gettempdir()),
+                                 'clocks_bench_%d.csv' % device_index)
 
     def start(self):
         try:

@@ -5,7 +5,7 @@ operators are the Galerkin products D_{l+1} = R_l D_l P_l.  Sec. 3 builds the
 orthogonal projector P_l P_l^H from the same P_l.  P_l is built from N_tv test
 vectors (Sec. 2.2, setup phase; Sec. 4: rough approximations to low modes).
 
-Readings this build takes where the paper is silent:
+Readings taken where the paper is silent:
 * aggregates are rectangular blocks of `block` sites; each aggregate is split
   by chirality: the first half of a site's dofs (spins 0, 1 on the fine
   level; the first N_tv coarse dofs on coarser levels) is chirality +, the

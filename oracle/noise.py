@@ -12,7 +12,7 @@ SC'11), written here from that definition in plain uint64 numpy arithmetic:
   10 rounds; after each round but the last the key is bumped by the Weyl
   constants (k0 += W0, k1 += W1).
 
-Z4 map (the reading this build takes; the paper fixes only the
+Z4 map (the reading taken here; the paper fixes only the
 distribution): entry i of a noise vector draws the Philox block with counter
 (i >> 2, sample, term, aux) and key (seed, 0), takes word i & 3 of it and sets
 r = word >> 62 and x_i = i^r  (r = 0, 1, 2, 3 -> 1, i, -1, -i).

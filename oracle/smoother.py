@@ -3,7 +3,7 @@
 The paper solves every level with DD-alpha-AMG (Sec. 4), whose smoother is
 the Schwarz alternating procedure (SAP); the paper states no details and the
 smoother only changes how fast a solve reaches its tolerance, never what it
-returns.  The oracle restates the two smoothers this build uses, so that the
+returns.  The oracle restates the two smoothers the library uses, so that the
 CUDA smoothers can be checked step by step:
 
 * minimal residual (MR), `steps` steps from z = 0 on D z = b:
