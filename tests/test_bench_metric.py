@@ -55,3 +55,17 @@ def test_e2e_time_to_variance():
     assert abs(bench.e2e_time_to_variance(1.0, 0.44, 0.44, 50.0, 0.4) - (1.0 + 55.0)) < 1e-12
     # a first step faster than the steady ones adds nothing
     assert bench.e2e_time_to_variance(0.0, 0.1, 0.4, 10.0, 0.4) == 10.0
+
+
+def test_oracle_threads_bounded_by_memory(monkeypatch):
+    """the CPU oracle's worker count: every core by default, an explicit
+    request as given, and never more than the free memory holds."""
+    import bench
+    monkeypatch.setattr(bench, 'host_cores', lambda: 16)
+    monkeypatch.setattr(bench, 'host_memory_available', lambda: None)
+    assert bench.oracle_threads(0) == 16 and bench.oracle_threads(3) == 3
+    monkeypatch.setattr(bench, 'host_memory_available', lambda: 8e9 + 4.5 * bench.ORACLE_WORKER_BYTES)
+    assert bench.oracle_threads(0) == 4
+    monkeypatch.setattr(bench, 'host_memory_available', lambda: 1e9)
+    assert bench.oracle_threads(0) == 1
+    assert bench.host_cores() == 16
