@@ -72,7 +72,7 @@ __global__ void stencil_t_kernel(const C<T> *__restrict__ in, C<T> *__restrict__
   }
 }
 
-// Wide coarse operators (m > 112 dofs per site, e.g. 2 N_tv = 128 or 256):
+// Wide coarse operators (m > 64 dofs per site, e.g. 2 N_tv = 100, 128, 256):
 // one CTA of 8 warps per (site, 32-row tile).  Lane l owns row i0 + l, so
 // the reads of AT[X][d][j][i0..i0+31] are 32 consecutive entries; warp w
 // takes the columns j = w, w + 8, ... of every direction.  The neighbour
@@ -616,7 +616,9 @@ void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, 
                    cudaStream_t s) {
   constexpr int RG = sizeof(T) == 4 ? 8 : 4;
   const int m = g.dof;
-  if (m > 112) {
+  // the (m, 9)-thread kernels below need 9 m threads of ~80 registers, which
+  // one SM holds only up to m ~ 91; wider operators take the tiled kernel
+  if (m > 64) {
     // wide operators: as many right-hand sides per pass as ~96 KB of staged
     // neighbour vectors allow
     const size_t per = (size_t)9 * m * sizeof(C<T>);

@@ -299,12 +299,12 @@ def test_solve_mixed_precision():
         s.close()
 
 
-@pytest.mark.parametrize('ntv', [32, 64, 96])
+@pytest.mark.parametrize('ntv', [32, 50, 64, 96])
 def test_wide_coarse_operator(ntv):
     """N_tv = 32 (64 dofs per coarse site: too large for the TMA-staged
-    kernel's shared memory, so the plain staged stencil kernel), 64 and 96
-    (128, 192 dofs: the wide coarse-stencil kernel): D_1 in FP64 (1e-12) and
-    FP32 (1e-5) against the
+    kernel's shared memory, so the plain staged stencil kernel), 50, 64 and
+    96 (100, 128, 192 dofs: the wide coarse-stencil kernel, 100 with a
+    partial last row tile): D_1 in FP64 (1e-12) and FP32 (1e-5) against the
     oracle's Galerkin operator, and a level-0 solve through this hierarchy to
     the 1.5e-12 residual measured with the oracle's D."""
     s = Setup((4, 4, 4, 4), [(2, 2, 2, 2)], [ntv], eps=0.3, m0=-0.2)
