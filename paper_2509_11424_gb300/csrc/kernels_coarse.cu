@@ -684,10 +684,18 @@ void restrict_op(const C<T> *in, C<T> *out, const C<T> *P, const AggMap &m, int 
 template <typename T>
 void prolong_op(const C<T> *in, C<T> *out, const C<T> *P, const AggMap &m, int nrhs, double beta,
                 cudaStream_t s) {
-  const size_t sm = (size_t)nrhs * m.ntv * sizeof(C<T>);
-  if (sm > 48 * 1024) throw Error(1, "prolong: too many right-hand sides");
-  prolong_kernel<T, 4><<<m.coarse.V * 2, 256, sm, s>>>(in, out, P, m, nrhs, (T)beta);
-  MG_LAUNCH_CHECK();
+  // the coarse coefficients of every right-hand side of a launch are staged
+  // in 48 KB of shared memory: launch groups of right-hand sides that fit
+  const int per = (int)((48 * 1024) / ((size_t)m.ntv * sizeof(C<T>)));
+  if (per < 1) throw Error(1, "prolong: too many test vectors");
+  const int64_t nf = m.fine.n(), nc = m.coarse.n();
+  for (int r0 = 0; r0 < nrhs; r0 += per) {
+    const int rg = nrhs - r0 < per ? nrhs - r0 : per;
+    const size_t sm = (size_t)rg * m.ntv * sizeof(C<T>);
+    prolong_kernel<T, 4><<<m.coarse.V * 2, 256, sm, s>>>(in + (int64_t)r0 * nc, out + (int64_t)r0 * nf, P, m,
+                                                         rg, (T)beta);
+    MG_LAUNCH_CHECK();
+  }
 }
 
 void probe_column(double2 *out, const double2 *P, const AggMap &m, int col, cudaStream_t s) {

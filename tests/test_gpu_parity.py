@@ -328,6 +328,15 @@ def test_wide_coarse_operator(ntv):
         zs = host(z)
         for r in range(2):
             assert np.linalg.norm(b[r] - A0 @ zs[r]) / np.linalg.norm(b[r]) < 1.5e-12
+        # P for more right-hand sides than 48 KB of staged coefficients hold
+        # in one launch (40 x N_tv complex doubles > 48 KB from N_tv = 77)
+        nr = 40
+        xc = synth.complex_normal((nr, n1), 93)
+        f = torch.empty((nr, A0.shape[0]), dtype=torch.complex128, device='cuda')
+        M.mgmlmc_apply(s.ctx, M.OP_PROLONG, 0, M.FP64, dev(xc), f, nr)
+        fs = host(f)
+        for r in (0, 31, 32, nr - 1):
+            assert rel(fs[r], s.hier.P[0].prolong(xc[r])) < 1e-12
     finally:
         s.close()
 
