@@ -52,6 +52,24 @@ def test_deflation_matches_oracle(cfg):
     assert res[1]['var'] == 0.0
 
 
+def test_deflation_ragged_block_matches_oracle(cfg):
+    """k = 11 columns: the build's solves and the estimator's projections run
+    in batches of 8 and 3; exact part and samples against the oracle."""
+    k, iters = 11, 2
+    exact, _ = M.mgmlmc_deflation_build(cfg.ctx, k, iters, 1e-12, 64)
+    A = cfg.hier.matrix(0)
+    sol = osolve.LevelSolver(A)
+    V = odf.block_power(sol, A.shape[0], k, iters, 64)
+    want = odf.exact_part(sol, V)
+    assert abs(exact - want) < 1e-8 * abs(want)
+    N = 6
+    res = M.mgmlmc_estimate_trace(cfg.ctx, M.est_params(M.EST_DEFLATED, [N], batch=4, seed=65))
+    X = np.array([odf.sample(sol, V, 65, q) for q in range(N)])
+    mu, _ = oest.sample_stats(X)
+    assert res[0]['n'] == N
+    assert abs(complex(res[0]['mean_re'], res[0]['mean_im']) - mu) < 1e-8 * abs(mu)
+
+
 def test_deflated_trace_unbiased_and_bad_args(cfg):
     exact_tr = np.trace(np.linalg.inv(cfg.hier.matrix(0).toarray()))
     ex, _ = M.mgmlmc_deflation_build(cfg.ctx, 16, 5, 1e-6, 63)
