@@ -55,7 +55,7 @@ METRIC = 'tr(D^-1) MLMC time to fixed variance, learned+mixed vs plain; Dslash G
 DIMS = (16, 16, 16, 16)
 EPS_GAUGE = 0.4
 GAUGE_SEED, NOISE_SEED, TV_SEED = 1002, 2002, 3002
-ARMS = ('plain', 'oblique', 'deflated', 'sap', 'fp64', 'refined')
+ARMS = ('plain', 'oblique', 'deflated', 'sap', 'fp64', 'refined', 'augmented')
 # refined arm (Sec. 5): level-0 test vectors refined toward the low modes of
 # Gamma5 D, a block of N_tv + 8 columns, eigen-residual target and the
 # tolerance of the refinement's FP64 solves
@@ -765,6 +765,7 @@ def main():
     # Sec. 5: test vectors computed to a small eigen-residual.  Last, because
     # it replaces the level-0 test vectors of the context for good.
     if rank == 0 and args.compare_steps > 0 and 'refined' in arms and args.refine_iters > 0:
+        rough_tv = M.mgmlmc_get_test_vectors(ctx, 0) if 'augmented' in arms else None
         torch.cuda.synchronize()
         t0 = time.time()
         th, rh, rsteps = M.mgmlmc_refine_test_vectors(ctx, 0, NTV[0] + REFINE_BLOCK_EXTRA, args.refine_iters,
@@ -780,6 +781,27 @@ def main():
             block=NTV[0] + REFINE_BLOCK_EXTRA, eig_tol=REFINE_EIG_TOL, solve_tol=REFINE_SOLVE_TOL,
             eig_res_max=float(rh.max()), eig_res=[float(x) for x in rh], theta=[float(x) for x in th],
             detail=rdet)
+        # more test vectors as well as more accurate ones (Sec. 5 raises N_tv
+        # too): the rough and the refined level-0 vectors together
+        if rough_tv is not None:
+            try:
+                aug = np.ascontiguousarray(np.concatenate([rough_tv, M.mgmlmc_get_test_vectors(ctx, 0)]))
+                torch.cuda.synchronize()
+                t0 = time.time()
+                M.mgmlmc_set_test_vectors(ctx, 0, aug, aug.shape[0], aug.shape[1], on_device=False)
+                M.mgmlmc_build_hierarchy(ctx, M.mg_params(BLOCKS, [aug.shape[0]] + NTV[1:], setup_rounds=6,
+                                                          setup_iters=30, seed=TV_SEED))
+                torch.cuda.synchronize()
+                asec = time.time() - t0
+                M.mgmlmc_set_solver(ctx, precision=prec, **main_solver)
+                step(k0)
+                ares, ams = timed(k0, cs)
+                aval, adet = time_to_variance(merge_terms(ares), 1, ams / cs, cs, eps=eps0)
+                compare['mlmc_rough_plus_refined_test_vectors'] = dict(
+                    value=aval, ms_per_step=ams / cs, setup_s=rsec + asec, value_with_setup=aval + rsec + asec,
+                    n_tv=[aug.shape[0]] + NTV[1:], detail=adet)
+            except Exception as exc:  # a comparison arm never costs the line
+                compare['mlmc_rough_plus_refined_test_vectors'] = dict(error=str(exc)[:300])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu and 'oracle_plain' in wl:
