@@ -64,3 +64,43 @@ def test_struct_layouts_match_c():
         assert int(got[cname]) == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert int(got['%s.%s' % (cname, f)]) == getattr(py, f).offset, (cname, f)
+
+
+def _prototypes():
+    text = open(HEADER).read()
+    text = re.sub(r'/\*.*?\*/', '', text, flags=re.S)
+    protos = {}
+    for name, params in re.findall(r'\b(mgmlmc_[a-z0-9_]+)\s*\(([^)]*)\)\s*;', text):
+        params = params.strip()
+        protos[name] = [] if params in ('', 'void') else [p.strip() for p in params.split(',')]
+    return protos
+
+
+def _c_class(param):
+    if '*' in param or '[' in param:
+        return 'ptr'
+    for key, cls in (('uint64_t', 'u64'), ('int64_t', 'i64'), ('double', 'f64'), ('int', 'i32')):
+        if re.search(r'\b%s\b' % key, param):
+            return cls
+    raise AssertionError('unclassified parameter: ' + param)
+
+
+def test_binding_signatures_match_prototypes():
+    """every ctypes argument list has the prototype's length and, position by
+    position, the same kind of argument (pointer, int, int64, uint64, double)."""
+    import ctypes
+    from paper_2509_11424_gb300 import mgmlmc
+    protos = _prototypes()
+    assert set(protos) == set(declared_functions())
+
+    def py_class(t):
+        if t is ctypes.c_void_p or isinstance(t, type) and issubclass(t, ctypes._Pointer):
+            return 'ptr'
+        return {ctypes.c_int: 'i32', ctypes.c_int64: 'i64', ctypes.c_uint64: 'u64',
+                ctypes.c_double: 'f64', ctypes.c_char_p: 'ptr'}[t]
+
+    for name, params in protos.items():
+        args = mgmlmc._SIGNATURES[name]
+        assert len(args) == len(params), (name, len(args), len(params))
+        for i, (t, p) in enumerate(zip(args, params)):
+            assert py_class(t) == _c_class(p), (name, i, p)
