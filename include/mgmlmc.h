@@ -119,6 +119,11 @@ typedef struct {
                           else 2^4); otherwise MR is used. */
   int sap_iters;       /* MR iterations inside each SAP block */
   int coarse_smoother_steps; /* MR steps of the smoother on levels >= 1 */
+  int fine_batch;      /* memory bound of the fine level: mgmlmc_estimate_trace
+                          solves level-0 systems (the O_0, F_0, M_0 and plain
+                          terms) in blocks of at most fine_batch right-hand
+                          sides; 0 = the estimator's batch.  Samples, noise
+                          counters and results do not depend on it. */
 } mgmlmc_solver_params;
 
 #define MGMLMC_SMOOTHER_MR 0
@@ -240,6 +245,14 @@ mgmlmc_status mgmlmc_level_info(const mgmlmc_ctx *ctx, int level, int dims[4],
  * out[max_terms] and their count into *n_terms. */
 mgmlmc_status mgmlmc_estimate_trace(mgmlmc_ctx *ctx, const mgmlmc_est_params *p,
                                     mgmlmc_term_result *out, int max_terms, int *n_terms);
+/* The per-sample values X_k of Hutchinson's estimator (Sec. 1, Eq.
+ * Hutchinson: X_k = x_k^H A x_k for the term's operator A) of term `index`
+ * (0-based position in the result array) of the last mgmlmc_estimate_trace
+ * call on this context, in sample order: out[2k], out[2k + 1] = re, im of
+ * sample first_sample + k.  *n receives the sample count; MGMLMC_ERR_ARG when
+ * it exceeds max_samples or there is no such term (a failed estimate keeps
+ * none). */
+mgmlmc_status mgmlmc_last_samples(mgmlmc_ctx *ctx, int index, double *out, int max_samples, int *n);
 /* Inexact deflation basis (Sec. 2.1, 'Deflation for the Dirac operator';
  * the paper's setting in Sec. 4.2 is k = 128, iters = 5, tol = 1e-6): the k
  * start columns are the Z4 vectors of samples 0..k-1 of noise stream
@@ -326,7 +339,7 @@ typedef enum {
  * MGMLMC_FP32; MGMLMC_OP_SOLVE accepts MGMLMC_FP64 only, its internal
  * precision is the solver's; MGMLMC_BF16, complex bfloat16 storage with
  * FP32 arithmetic, is accepted for MGMLMC_OP_D on level 0).  in and out
- * must not overlap.  Level-0 FP32 and BF16 vectors are reordered to and from
+ * must not overlap (MGMLMC_ERR_ARG if their byte ranges intersect).  Level-0 FP32 and BF16 vectors are reordered to and from
  * the internal order around the operator unless op carries
  * MGMLMC_LAYOUT_INTERNAL. */
 mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op, int level, int precision,
@@ -351,7 +364,8 @@ mgmlmc_status mgmlmc_reorder_bf16(mgmlmc_ctx *ctx, const void *in, void *out, in
  * whose device memory is reserved up front by a pool they do not control,
  * or loops that forbid allocator calls on their critical path.  in/out are
  * device buffers as for mgmlmc_apply (complex double for MGMLMC_FP64,
- * complex float for MGMLMC_FP32), nrhs vectors of level `level`.
+ * complex float for MGMLMC_FP32), nrhs vectors of level `level`; in and out
+ * must be distinct (MGMLMC_ERR_ARG if their byte ranges intersect).
  * The coarse intermediate P_l^H in lives in a fixed device array of 2 MiB
  * (131072 complex doubles, 262144 complex floats) that every GPU loading the
  * library holds until exit; calls with nrhs * n_{l+1} beyond that return
@@ -381,6 +395,14 @@ mgmlmc_status mgmlmc_get_test_vectors(mgmlmc_ctx *ctx, int level, double *out);
  * block d of X collects the fine hops of direction d leaving aggregate X,
  * block 0 the diagonal and the hops staying inside X. */
 mgmlmc_status mgmlmc_get_coarse_op(mgmlmc_ctx *ctx, int level, double *out);
+/* Free every device work buffer the context has grown (Krylov bases,
+ * smoother and estimator vectors, reduction and transfer scratch) and the
+ * captured graphs that use them; the gauge field, the hierarchy (P_l, D_l,
+ * the coarsest inverse, the kept test vectors), a deflation basis and the
+ * learned network stay.  Later calls allocate what they need again.  For
+ * callers that switch between configurations of very different memory
+ * footprint on a large lattice (e.g. FP32 and FP64 solvers, or batch sizes). */
+mgmlmc_status mgmlmc_release_workspaces(mgmlmc_ctx *ctx);
 /* Statistics of the last solve: outer iterations (max over rhs) and true
  * relative residual (max over rhs). */
 mgmlmc_status mgmlmc_last_solve_stats(const mgmlmc_ctx *ctx, int *iters, double *residual);

@@ -151,9 +151,11 @@ mgmlmc_status mgmlmc_estimate_trace(mgmlmc_ctx *ctx, const mgmlmc_est_params *p,
   return guard(ctx, [&] {
     if (!p || !out || !n_terms) throw mg::Error(MGMLMC_ERR_ARG, "NULL argument");
     std::vector<mg::TermAcc> acc;
+    ctx->last_samples.clear();
     E(ctx).estimate_trace(*p, acc);
     if ((int)acc.size() > max_terms) throw mg::Error(MGMLMC_ERR_ARG, "max_terms too small");
     *n_terms = (int)acc.size();
+    for (const mg::TermAcc &a : acc) ctx->last_samples.push_back(a.samples);
     for (size_t i = 0; i < acc.size(); ++i) {
       const mg::TermAcc &a = acc[i];
       mgmlmc_term_result &r = out[i];
@@ -175,6 +177,26 @@ mgmlmc_status mgmlmc_estimate_trace(mgmlmc_ctx *ctx, const mgmlmc_est_params *p,
       }
     }
   });
+}
+
+mgmlmc_status mgmlmc_last_samples(mgmlmc_ctx *ctx, int index, double *out, int max_samples, int *n) {
+  return guard(ctx, [&] {
+    if (!n) throw mg::Error(MGMLMC_ERR_ARG, "NULL argument");
+    if (index < 0 || index >= (int)ctx->last_samples.size())
+      throw mg::Error(MGMLMC_ERR_ARG, "no such term in the last estimate");
+    const auto &X = ctx->last_samples[index];
+    *n = (int)X.size();
+    if ((int)X.size() > max_samples || (!out && !X.empty()))
+      throw mg::Error(MGMLMC_ERR_ARG, "output holds fewer samples than the term has");
+    for (size_t k = 0; k < X.size(); ++k) {
+      out[2 * k] = X[k].real();
+      out[2 * k + 1] = X[k].imag();
+    }
+  });
+}
+
+mgmlmc_status mgmlmc_release_workspaces(mgmlmc_ctx *ctx) {
+  return guard(ctx, [&] { E(ctx).release_workspaces(); });
 }
 
 mgmlmc_status mgmlmc_coarsest_trace(mgmlmc_ctx *ctx, double *re, double *im) {
@@ -241,6 +263,7 @@ mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op_flags, int level, int precisi
         throw mg::Error(MGMLMC_ERR_ARG, "BF16 storage is available for the level-0 Wilson operator only");
       const mg::Geom &g = e.level(0).g;
       const size_t bytes = (size_t)g.n() * nrhs * 4;
+      require_disjoint(in, bytes, out, bytes);
       const void *src = in;
       void *dst = out;
       if (!internal) {
@@ -261,6 +284,13 @@ mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op_flags, int level, int precisi
     if (needs_next && (!e.ready() || level + 1 >= e.n_levels()))
       throw mg::Error(MGMLMC_ERR_STATE, "no transfer operator at that level");
     if (level > 0 && !e.ready()) throw mg::Error(MGMLMC_ERR_STATE, "hierarchy not built");
+    {
+      const size_t es = dp ? sizeof(double2) : sizeof(float2);
+      const size_t nl = (size_t)e.level(level).g.n();
+      const size_t nn = needs_next ? (size_t)e.level(level + 1).g.n() : nl;
+      const size_t nin = op == MGMLMC_OP_PROLONG ? nn : nl, nout = op == MGMLMC_OP_RESTRICT ? nn : nl;
+      require_disjoint(in, nin * nrhs * es, out, nout * nrhs * es);
+    }
     const bool fine_op = op == MGMLMC_OP_D || op == MGMLMC_OP_RESTRICT || op == MGMLMC_OP_PROLONG ||
                          op == MGMLMC_OP_PROJECT || op == MGMLMC_OP_SMOOTH || op == MGMLMC_OP_NET;
     if (!dp && level == 0 && fine_op && !internal) {

@@ -164,4 +164,10 @@ std::atomic<int64_t> &launch_counter();
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Raise the dynamic shared-memory limit of kernel `func` to `bytes` on the
+// current device.  The attribute is per device, so the call is made once per
+// (kernel, device) and remembered under a lock: launchers may run on several
+// host threads and devices.
+void smem_optin(const void *func, int bytes);
+
 }  // namespace mg

@@ -105,7 +105,6 @@ Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
     MG_CUDA(cudaEventCreateWithFlags(&ev_enter_, cudaEventDisableTiming));
     MG_CUDA(cudaEventCreateWithFlags(&ev_leave_, cudaEventDisableTiming));
     levels_[0].U64 = dalloc<double2>((size_t)V * 36);
-    levels_[0].U32 = dalloc<float2>((size_t)V * 36);
     levels_[0].UD32 = dalloc<float2>((size_t)V * 36);
     levels_[0].Ub16 = dalloc<float>((size_t)V * 36);  // 36 bf16 pairs of 4 bytes per site
     scal_ = dalloc<double2>(4096);
@@ -128,7 +127,6 @@ void Engine::release() {
   if (pool_) cudaFree(pool_);
   pool_ = nullptr;
   dfree(levels_[0].U64);
-  dfree(levels_[0].U32);
   dfree(levels_[0].UD32);
   dfree(levels_[0].Ub16);
   for (auto &kv : ws_) cudaFree(kv.second.first);
@@ -273,6 +271,7 @@ void Engine::ws_release(const std::string &name, int l, bool dbl) {
   const std::string key = name + "#" + std::to_string(l) + (dbl ? "d" : "f");
   auto it = ws_.find(key);
   if (it == ws_.end()) return;
+  drop_graphs();  // a captured graph may hold the buffer's address
   sync();
   cudaFree(it->second.first);
   ws_.erase(it);
@@ -308,9 +307,13 @@ void Engine::gen_gauge(double eps, uint64_t seed) {
 
 void Engine::gauge_derived() {
   const size_t cnt = (size_t)fine_.V * 36;
-  convert<float, double>(levels_[0].U64, levels_[0].U32, (int64_t)cnt, stream);
-  link_soa(levels_[0].U32, levels_[0].UD32, fine_.V, stream);
-  link_bf16(levels_[0].U32, levels_[0].Ub16, fine_.V, stream);
+  // the canonical FP32 links are only the intermediate of the two layouts the
+  // FP32 and BF16 kernels read
+  DevBuf<float2> u32(cnt);
+  convert<float, double>(levels_[0].U64, u32.p, (int64_t)cnt, stream);
+  link_soa(u32.p, levels_[0].UD32, fine_.V, stream);
+  link_bf16(u32.p, levels_[0].Ub16, fine_.V, stream);
+  sync();
   have_gauge_ = true;
   free_hierarchy();
 }
@@ -328,7 +331,7 @@ void Engine::set_solver(const mgmlmc_solver_params &p) {
       (p.precision == MGMLMC_FP32 && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)) ||
       (p.smoother != MGMLMC_SMOOTHER_MR && p.smoother != MGMLMC_SMOOTHER_SAP &&
        p.smoother != MGMLMC_SMOOTHER_LEARNED) || p.sap_iters < 1 || p.coarse_smoother_steps < 0 ||
-      p.sap_iters > 64)
+      p.sap_iters > 64 || p.fine_batch < 0)
     throw Error(MGMLMC_ERR_ARG, "invalid solver parameters");
   drop_graphs();  // captured preconditioners bake in smoother / inner iteration counts
   sp_ = p;
@@ -395,10 +398,10 @@ int Engine::dslash_pick(int nrhs, const float2 *in, float2 *out) {
   int pick = 0;
   float best = 1e30f;
   for (int v = 0; v < wilson_fp32_variants(); ++v) {
-    wilson_apply<float>(in, out, L.U32, L.UD32, L.g, m0_, nrhs, v, stream);
+    wilson_apply<float>(in, out, nullptr, L.UD32, L.g, m0_, nrhs, v, stream);
     MG_CUDA(cudaEventRecord(a, stream));
     for (int rep = 0; rep < 3; ++rep)
-      wilson_apply<float>(in, out, L.U32, L.UD32, L.g, m0_, nrhs, v, stream);
+      wilson_apply<float>(in, out, nullptr, L.UD32, L.g, m0_, nrhs, v, stream);
     MG_CUDA(cudaEventRecord(b, stream));
     MG_CUDA(cudaEventSynchronize(b));
     float ms = 0.f;
@@ -425,7 +428,7 @@ template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int
       wilson_apply<double>(in, out, L.U64, nullptr, L.g, m0_, nrhs, -1, stream);
     } else {
       const int v = dslash_pick(nrhs, in, out);
-      wilson_apply<float>(in, out, L.U32, L.UD32, L.g, m0_, nrhs, v, stream);
+      wilson_apply<float>(in, out, nullptr, L.UD32, L.g, m0_, nrhs, v, stream);
     }
     // unique data: nrhs spinors in and out, 4 links per site; 1368 flop per site
     bytes = (double)L.g.V * (24.0 * nrhs + 36.0) * cs;
@@ -509,7 +512,7 @@ template <typename T> void Engine::smooth(int l, C<T> *z, C<T> *res, int nrhs) {
     if (post_smooth_) record<T>(res, nrhs);
     if (learned && post_smooth_) {
       if (!net_.C) throw Error(MGMLMC_ERR_STATE, "learned smoother selected but the network is not initialised");
-      C<T> *q = ws<T>("netq", l, (size_t)n * nrhs);
+      C<T> *q = ws<T>("smq", l, (size_t)n * nrhs);
       double2 *d = ws<double>("netd", l, 2 * (size_t)nrhs);
       cudaEvent_t pa = prof_begin();
       net_forward<T>(res, e, nrhs);
@@ -552,7 +555,9 @@ template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nr
   }
   const int64_t nc = levels_[l + 1].g.n();
   C<T> *res = ws<T>("mgres", l, (size_t)n * nrhs);
-  C<T> *q = ws<T>("mgq", l, (size_t)n * nrhs);
+  // q = D z of the post-smoothing residual shares the smoothers' work vector
+  // (dead whenever the smoother runs)
+  C<T> *q = ws<T>("smq", l, (size_t)n * nrhs);
   C<T> *rc = ws<T>("mgrc", l + 1, (size_t)nc * nrhs);
   C<T> *ec = ws<T>("mgec", l + 1, (size_t)nc * nrhs);
   MG_CUDA(cudaMemsetAsync(z, 0, sizeof(C<T>) * n * nrhs, stream));
@@ -581,29 +586,28 @@ template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nr
   }
 }
 
+// The graphs are keyed by the operand addresses as well: an outer FGMRES
+// cycle preconditions V_i into Z_i, i < m, whose addresses are fixed while
+// its workspaces live, so m graphs per (level, nrhs, precision) replay the
+// cycle on the caller's vectors directly (no staging copies in and out).
 template <typename T> void Engine::precond_top(int l, const C<T> *r, C<T> *z, int nrhs) {
   if (!graphs_on_ || prof_ || recording_ || l == n_levels() - 1) {
     precond<T>(l, r, z, nrhs);
     return;
   }
-  const int64_t n = levels_[l].g.n();
-  const size_t bytes = sizeof(C<T>) * n * nrhs;
-  const auto key = std::make_tuple(l, nrhs, (int)sizeof(T));
+  const auto key = std::make_tuple(l, nrhs, (int)sizeof(T), (const void *)r, (void *)z);
   auto it = graphs_.find(key);
   if (it == graphs_.end()) {
-    C<T> *in = ws<T>("gin", l, (size_t)n * nrhs);
-    C<T> *out = ws<T>("gout", l, (size_t)n * nrhs);
-    // eager run: sizes every workspace the captured sequence touches
-    MG_CUDA(cudaMemcpyAsync(in, r, bytes, cudaMemcpyDeviceToDevice, stream));
-    precond<T>(l, in, out, nrhs);
-    MG_CUDA(cudaMemcpyAsync(z, out, bytes, cudaMemcpyDeviceToDevice, stream));
+    // eager run: sizes every workspace the captured sequence touches (z gets
+    // the result; the captured replay recomputes the same values)
+    precond<T>(l, r, z, nrhs);
     sync();
     cudaGraph_t graph = nullptr;
     MG_CUDA(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
     capturing_ = true;
     const int64_t launches_before = launch_counter().load();
     try {
-      precond<T>(l, in, out, nrhs);
+      precond<T>(l, r, z, nrhs);
     } catch (...) {
       capturing_ = false;
       cudaStreamEndCapture(stream, &graph);
@@ -616,13 +620,11 @@ template <typename T> void Engine::precond_top(int l, const C<T> *r, C<T> *z, in
     const cudaError_t e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     MG_CUDA(e);
-    graphs_[key] = GraphEntry{exec, in, out, launch_counter().load() - launches_before};
+    graphs_[key] = GraphEntry{exec, launch_counter().load() - launches_before};
     return;  // z already holds the eager result
   }
-  MG_CUDA(cudaMemcpyAsync(it->second.in, r, bytes, cudaMemcpyDeviceToDevice, stream));
   MG_CUDA(cudaGraphLaunch(it->second.exec, stream));
   MG_COUNT(it->second.kernels);  // the kernels replayed by the graph
-  MG_CUDA(cudaMemcpyAsync(z, it->second.out, bytes, cudaMemcpyDeviceToDevice, stream));
 }
 
 // ------------------------------------------------------------------ FGMRES
@@ -633,9 +635,10 @@ SolveInfo Engine::fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, in
   const int64_t n = L.g.n();
   const int64_t vs = n * nrhs;
   const std::string tag = fixed ? "k" : "t";
+  // basis V_0..V_m; the new direction of iteration i is formed in V_{i+1}
+  // itself (orthogonalised and normalised in place), so no extra work vector
   C<T> *V = ws<T>("gmV" + tag, l, (size_t)(m + 1) * vs);
   C<T> *Z = use_precond ? ws<T>("gmZ" + tag, l, (size_t)m * vs) : nullptr;
-  C<T> *w = ws<T>("gmw" + tag, l, (size_t)vs);
   GmresState st;
   st.m = m;
   st.nrhs = nrhs;
@@ -684,6 +687,7 @@ SolveInfo Engine::fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, in
     for (int i = 0; i < m; ++i) {
       C<T> *vi = V + i * vs;
       C<T> *zi = use_precond ? Z + i * vs : vi;
+      C<T> *w = V + (i + 1) * vs;
       if (use_precond) {
         if (fixed) precond<T>(l, vi, zi, nrhs);
         else precond_top<T>(l, vi, zi, nrhs);
@@ -699,7 +703,7 @@ SolveInfo Engine::fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, in
       // twice for the updates, w read/written four times
       prof_end(po, K_ORTHO, (double)vs * sizeof(C<T>) * (4.0 * (i + 1) + 9.0), 0.0);
       gmres_arnoldi(st, i, stream);
-      scale_rhs<T>(w, V + (i + 1) * vs, st.inv, n, nrhs, stream);
+      scale_rhs<T>(w, w, st.inv, n, nrhs, stream);
       ++it;
       ++total;
       if (total >= max_iter) break;
@@ -715,10 +719,10 @@ SolveInfo Engine::fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, in
     gmres_solve(st, stream);
     multi_axpy<T>(use_precond ? Z : V, vs, it, x, n, nrhs, st.y, m, 1.0, stream);
     if (fixed && total >= max_iter) break;
-    // true residual
-    apply_D<T>(l, x, w, nrhs);
+    // true residual (V_1 as the work vector: the cycle's basis is spent)
+    apply_D<T>(l, x, V + vs, nrhs);
     MG_CUDA(cudaMemcpyAsync(V, b, sizeof(C<T>) * vs, cudaMemcpyDeviceToDevice, stream));
-    axpby<T>(-1.0, w, 1.0, V, n, nrhs, stream);
+    axpby<T>(-1.0, V + vs, 1.0, V, n, nrhs, stream);
     if (fixed) continue;
     dot<T>(V, V, n, nrhs, st.nrm, part(1), stream);
     double2 *h = static_cast<double2 *>(pinned(sizeof(double2) * nrhs));
@@ -748,10 +752,12 @@ SolveInfo Engine::fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, in
   return info;
 }
 
+// FP64 defect correction around FP32 inner solves.  One FP64 work vector t:
+// the residual of the current x (b itself before the first correction), then
+// the correction e converted up, then D x and b - D x again.
 SolveInfo Engine::solve_mixed(int l, const double2 *b, double2 *x, int nrhs) {
   const int64_t n = levels_[l].g.n();
   const int64_t vs = n * nrhs;
-  double2 *r = ws<double>("dcr", l, (size_t)vs);
   double2 *t = ws<double>("dct", l, (size_t)vs);
   float2 *r32 = ws<float>("dcr32", l, (size_t)vs);
   float2 *e32 = ws<float>("dce32", l, (size_t)vs);
@@ -765,7 +771,7 @@ SolveInfo Engine::solve_mixed(int l, const double2 *b, double2 *x, int nrhs) {
   std::vector<double> bn(nrhs);
   for (int q = 0; q < nrhs; ++q) bn[q] = std::sqrt(std::max(h[q].x, 0.0));
   MG_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * vs, stream));
-  MG_CUDA(cudaMemcpyAsync(r, b, sizeof(double2) * vs, cudaMemcpyDeviceToDevice, stream));
+  const double2 *r = b;  // residual of x = 0
   SolveInfo info;
   int total = 0;
   for (int outer = 0;; ++outer) {
@@ -794,8 +800,8 @@ SolveInfo Engine::solve_mixed(int l, const double2 *b, double2 *x, int nrhs) {
     else convert_scale<double, float>(e32, t, rn, n, nrhs, stream);
     axpby<double>(1.0, t, 1.0, x, n, nrhs, stream);
     apply_D<double>(l, x, t, nrhs);
-    MG_CUDA(cudaMemcpyAsync(r, b, sizeof(double2) * vs, cudaMemcpyDeviceToDevice, stream));
-    axpby<double>(-1.0, t, 1.0, r, n, nrhs, stream);
+    axpby<double>(1.0, b, -1.0, t, n, nrhs, stream);  // t = b - D x
+    r = t;
   }
   info.iters = total;
   return info;
@@ -950,20 +956,7 @@ void Engine::build_hierarchy(const mgmlmc_mg_params &p) {
       MG_CUDA(cudaMemcpyAsync(V, imp->second.data(), sizeof(double2) * ntv * n, cudaMemcpyHostToDevice, stream));
     } else {
       z4_noise<double>(V, f.g, p.seed, 0, 96 + l, 0, -1, ntv, stream);
-      if (p.setup_rounds > 0) {
-        double2 *X = ws<double>("tvx", l, (size_t)ntv * n);
-        double *inv = reinterpret_cast<double *>(ws<double>("tvinv", l, (size_t)ntv));
-        double *nr = reinterpret_cast<double *>(ws<double>("tvnr", l, (size_t)ntv));
-        double2 *d = ws<double>("tvd", l, (size_t)ntv);
-        for (int round = 0; round < p.setup_rounds; ++round) {
-          const int it = std::max(1, p.setup_iters);
-          fgmres<double>(l, V, X, ntv, 0.0, it, std::min(it, 64), false, true);
-          dot<double>(X, X, n, ntv, d, partials((size_t)reduce_blocks(n) * ntv), stream);
-          inv_norm_kernel<<<(ntv + 63) / 64, 64, 0, stream>>>(inv, nr, d, ntv);
-          MG_LAUNCH_CHECK();
-          scale_rhs<double>(X, V, inv, n, ntv, stream);
-        }
-      }
+      if (p.setup_rounds > 0) setup_test_vectors(l, V, ntv, p);
     }
     f.P64 = dalloc<double2>((size_t)ntv * n);
     f.P32 = dalloc<float2>((size_t)ntv * n);
@@ -994,8 +987,87 @@ void Engine::build_hierarchy(const mgmlmc_mg_params &p) {
   MG_CUDA(cudaMemcpyAsync(&flag, flag_dev_, sizeof(int), cudaMemcpyDeviceToHost, stream));
   sync();
   if (flag) throw Error(MGMLMC_ERR_NUMERIC, "coarsest operator is singular");
+  // the build's scratch is not needed by the solves: give it back (large
+  // lattices need the room for the Krylov bases); a level's test vectors are
+  // kept for mgmlmc_get_test_vectors unless they exceed kKeepTestVectorBytes
+  for (const char *name : {"galp", "gal9", "galc", "tvx", "tv32", "tvx32", "gj"})
+    for (int l = 0; l < p.n_levels; ++l) {
+      ws_release(name, l, true);
+      ws_release(name, l, false);
+    }
+  for (int l = 0; l + 1 < p.n_levels; ++l)
+    if ((double)levels_[l].agg.ntv * levels_[l].g.n() * sizeof(double2) > kKeepTestVectorBytes)
+      ws_release("tv", l, true);
   mgp_ = p;
   ready_ = true;
+}
+
+// Sec. 4 setup: `setup_rounds` rounds of v <- w / ||w||, w the result of
+// `setup_iters` unpreconditioned GMRES iterations on D_l w = v (a rough
+// solve).  All N_tv columns at once would need a GMRES basis of N_tv (m + 1)
+// level vectors, more than a large lattice leaves free, so the columns go in
+// groups sized to the free device memory; every column sees the same
+// iterations whatever the grouping.  When the solver runs FP32 inner solves
+// the setup runs in FP32 too (the vectors only need a rough residual).
+void Engine::setup_test_vectors(int l, double2 *V, int ntv, const mgmlmc_mg_params &p) {
+  const Geom &g = levels_[l].g;
+  const int64_t n = g.n();
+  const int it = std::max(1, p.setup_iters);
+  const int m = std::min(it, 64);
+  const bool fp32 = sp_.precision == MGMLMC_FP32;
+  const double es = fp32 ? sizeof(float2) : sizeof(double2);
+  size_t freeb = 0, totalb = 0;
+  MG_CUDA(cudaMemGetInfo(&freeb, &totalb));
+  // per column: the basis (m + 1), the iterate, the converted input
+  const double per_col = (double)n * es * (m + 3);
+  const int group = std::max(1, std::min(ntv, (int)(0.7 * (double)freeb / per_col)));
+  double *inv = reinterpret_cast<double *>(ws<double>("tvinv", l, (size_t)ntv));
+  double *nr = reinterpret_cast<double *>(ws<double>("tvnr", l, (size_t)ntv));
+  double2 *d = ws<double>("tvd", l, (size_t)ntv);
+  for (int c0 = 0; c0 < ntv; c0 += group) {
+    const int gs = std::min(group, ntv - c0);
+    double2 *Vg = V + (size_t)c0 * n;
+    for (int round = 0; round < p.setup_rounds; ++round) {
+      if (fp32) {
+        float2 *v32 = ws<float>("tv32", l, (size_t)gs * n);
+        float2 *x32 = ws<float>("tvx32", l, (size_t)gs * n);
+        if (l == 0) relayout<float, double>(Vg, v32, nullptr, g.V, gs, true, stream);
+        else convert<float, double>(Vg, v32, (int64_t)gs * n, stream);
+        fgmres<float>(l, v32, x32, gs, 0.0, it, m, false, true);
+        dot<float>(x32, x32, n, gs, d, partials((size_t)reduce_blocks(n) * gs), stream);
+        inv_norm_kernel<<<(gs + 63) / 64, 64, 0, stream>>>(inv, nr, d, gs);
+        MG_LAUNCH_CHECK();
+        if (l == 0) relayout<double, float>(x32, Vg, inv, g.V, gs, false, stream);
+        else convert_scale<double, float>(x32, Vg, inv, n, gs, stream);
+      } else {
+        double2 *X = ws<double>("tvx", l, (size_t)gs * n);
+        fgmres<double>(l, Vg, X, gs, 0.0, it, m, false, true);
+        dot<double>(X, X, n, gs, d, partials((size_t)reduce_blocks(n) * gs), stream);
+        inv_norm_kernel<<<(gs + 63) / 64, 64, 0, stream>>>(inv, nr, d, gs);
+        MG_LAUNCH_CHECK();
+        scale_rhs<double>(X, Vg, inv, n, gs, stream);
+      }
+    }
+  }
+  // the fixed-length GMRES workspaces of the setup (recreated on demand)
+  for (const char *name : {"gmVk", "gmZk", "gsHk", "gsh1k", "gsh2k", "gssnk", "gsgk", "gsyk", "gsnrmk",
+                           "gssck", "gsik"}) {
+    ws_release(name, l, true);
+    ws_release(name, l, false);
+  }
+}
+
+void Engine::release_workspaces() {
+  drop_graphs();
+  sync();
+  for (auto it = ws_.begin(); it != ws_.end();) {
+    if (it->first.rfind("tv#", 0) == 0) {  // a level's test vectors
+      ++it;
+      continue;
+    }
+    cudaFree(it->second.first);
+    it = ws_.erase(it);
+  }
 }
 
 // ------------------------------------------------------------------ estimators
@@ -1036,8 +1108,10 @@ void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &ou
     TermAcc acc;
     acc.term = td.code;
     std::vector<std::complex<double>> X;
-    for (int k0 = 0; k0 < td.N; k0 += B) {
-      const int nb = std::min(B, td.N - k0);
+    // terms that solve on the fine level take its memory bound (fine_batch)
+    const int Bt = (td.level == 0 && td.kind != 3 && sp_.fine_batch > 0) ? std::min(B, sp_.fine_batch) : B;
+    for (int k0 = 0; k0 < td.N; k0 += Bt) {
+      const int nb = std::min(Bt, td.N - k0);
       const uint64_t s0 = p.first_sample + (uint64_t)k0;
       double2 *res = ws<double>("est_res", 0, 2 * (size_t)nb);
       MG_CUDA(cudaEventRecord(e0, stream));
@@ -1052,10 +1126,11 @@ void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &ou
         acc.max_res = std::max(acc.max_res, si.residual);
         dot<double>(x, z, n, nb, res, partials((size_t)reduce_blocks(n) * nb), stream);
       } else if (td.kind == 1) {
-        double2 *x = ws<double>("estx", l, (size_t)nb * n), *y = ws<double>("esty", l, (size_t)nb * n);
-        double2 *z = ws<double>("estz", l, (size_t)nb * n);
-        noise(l, p.seed, s0, MGMLMC_TERM_O + l, 0, -1, x, nb);
-        project_out<double>(l, x, y, nb);
+        // the noise x is drawn into z's buffer and projected into y; the
+        // solve then overwrites z (two level-l vectors instead of three)
+        double2 *y = ws<double>("esty", l, (size_t)nb * n), *z = ws<double>("estz", l, (size_t)nb * n);
+        noise(l, p.seed, s0, MGMLMC_TERM_O + l, 0, -1, z, nb);
+        project_out<double>(l, z, y, nb);
         SolveInfo si = solve(l, y, z, nb);
         acc.iters_sum += si.iters;
         acc.solves += 1;

@@ -18,7 +18,6 @@ struct Level {
   Geom g{};
   bool fine = false;
   double2 *U64 = nullptr;  // fine links [V][4][3][3]
-  float2 *U32 = nullptr;
   float2 *UD32 = nullptr;  // FP32 links structure-of-arrays [4][3][3][V] (FP32 kernels)
   float *Ub16 = nullptr;   // bf16 links structure-of-arrays (one bf16 pair per float slot)
   double2 *A64 = nullptr;   // coarse stencil, canonical [V][9][dof][dof]
@@ -162,6 +161,9 @@ class Engine {
   void enter();
   void leave();
   void set_graphs(bool on) { graphs_on_ = on; if (!on) drop_graphs(); }
+  // free every workspace (and the graphs that use them) except the levels'
+  // test vectors; later calls allocate what they need again
+  void release_workspaces();
 
   void profile(bool on);
   KStat kstat(int cls);
@@ -188,7 +190,8 @@ class Engine {
   template <typename T> void smooth(int l, C<T> *z, C<T> *res, int nrhs);
   template <typename T> void precond(int l, const C<T> *r, C<T> *z, int nrhs);
   // the preconditioner of an outer solve: replayed from a CUDA graph captured
-  // once per (level, nrhs, precision) unless profiling or graphs are off
+  // once per (level, nrhs, precision, operand addresses) unless profiling or
+  // graphs are off
   template <typename T> void precond_top(int l, const C<T> *r, C<T> *z, int nrhs);
   // batched FGMRES; fixed = run exactly max_iter iterations with no host check
   template <typename T>
@@ -196,6 +199,9 @@ class Engine {
                    bool use_precond, bool fixed);
   SolveInfo solve_mixed(int l, const double2 *b, double2 *x, int nrhs);
   void galerkin(int l);
+  void setup_test_vectors(int l, double2 *V, int ntv, const mgmlmc_mg_params &p);
+  // larger test-vector sets are not kept after the build (see build_hierarchy)
+  static constexpr double kKeepTestVectorBytes = 8e9;
   void free_hierarchy();
   void release();  // frees everything the context holds; safe on a partly built one
   void gauge_derived();  // FP32 and structure-of-arrays copies of the new links
@@ -243,11 +249,10 @@ class Engine {
   bool capturing_ = false;
   struct GraphEntry {
     cudaGraphExec_t exec;
-    void *in;
-    void *out;
     int64_t kernels;  // kernel nodes in the graph
   };
-  std::map<std::tuple<int, int, int>, GraphEntry> graphs_;
+  // (level, nrhs, sizeof(T), input, output) -> captured preconditioner
+  std::map<std::tuple<int, int, int, const void *, void *>, GraphEntry> graphs_;
   void drop_graphs();
   cudaEvent_t ev_enter_ = nullptr, ev_leave_ = nullptr;
   int dslash_force_ = -2;

@@ -7,6 +7,10 @@
 // FP64 for both storage precisions.
 #include "kernels.h"
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 namespace mg {
 
 namespace {
@@ -160,7 +164,7 @@ __global__ void axpby_kernel(T a, const C<T> *__restrict__ x, T b, C<T> *__restr
 }
 
 template <typename T>
-__global__ void scale_rhs_kernel(const C<T> *__restrict__ x, C<T> *__restrict__ y,
+__global__ void scale_rhs_kernel(const C<T> *x, C<T> *y,  // may alias (in-place scaling)
                                  const double *__restrict__ scal, int64_t n) {
   const int r = blockIdx.y;
   const T f = (T)scal[r];
@@ -376,6 +380,19 @@ __global__ void gmres_solve_kernel(GmresState st) {
 std::atomic<int64_t> &launch_counter() {
   static std::atomic<int64_t> c{0};
   return c;
+}
+
+void smem_optin(const void *func, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void *, int>, int> done;  // (kernel, device) -> bytes set
+  int dev = 0;
+  MG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_pair(func, dev);
+  auto it = done.find(key);
+  if (it != done.end() && it->second >= bytes) return;
+  MG_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  done[key] = bytes;
 }
 
 // blocks of the first reduction stage: chunks of >= 4096 elements, at most

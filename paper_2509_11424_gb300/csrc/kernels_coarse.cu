@@ -132,12 +132,7 @@ template <typename T, int RG>
 void launch_wide(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, cudaStream_t s) {
   const int m = g.dof;
   const size_t sm = (size_t)(9 * RG * m + 8 * RG * 32) * sizeof(C<T>);
-  static bool configured = false;
-  if (!configured) {
-    MG_CUDA(cudaFuncSetAttribute(stencil_wide_kernel<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024));
-    configured = true;
-  }
+  smem_optin((const void *)stencil_wide_kernel<T, RG>, 200 * 1024);
   if (sm > 200 * 1024) throw Error(1, "coarse stencil: too many dofs per site");
   stencil_wide_kernel<T, RG><<<dim3(g.V, (m + 31) / 32), 256, sm, s>>>(in, out, AT, g, nrhs);
   MG_LAUNCH_CHECK();
@@ -629,23 +624,13 @@ void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, 
   }
   const size_t sm_tma = (size_t)(9 * m * m + 2 * 9 * RG * m) * sizeof(C<T>);
   if (sm_tma <= 200 * 1024) {
-    static bool configured_tma = false;
-    if (!configured_tma) {
-      MG_CUDA(cudaFuncSetAttribute(stencil_tma_kernel<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   200 * 1024));
-      configured_tma = true;
-    }
+    smem_optin((const void *)stencil_tma_kernel<T, RG>, 200 * 1024);
     stencil_tma_kernel<T, RG><<<g.V, dim3(m, 9), sm_tma, s>>>(in, out, AT, g, nrhs, err);
     MG_LAUNCH_CHECK();
     return;
   }
   const size_t sm = (size_t)2 * 9 * RG * m * sizeof(C<T>);
-  static bool configured = false;
-  if (!configured) {
-    MG_CUDA(cudaFuncSetAttribute(stencil_t_kernel<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024));
-    configured = true;
-  }
+  smem_optin((const void *)stencil_t_kernel<T, RG>, 200 * 1024);
   stencil_t_kernel<T, RG><<<g.V, dim3(m, 9), sm, s>>>(in, out, AT, g, nrhs);
   MG_LAUNCH_CHECK();
 }
@@ -671,12 +656,7 @@ void restrict_op(const C<T> *in, C<T> *out, const C<T> *P, const AggMap &m, int 
   constexpr int RG = 4;
   const size_t sm = (size_t)RG * m.rows * sizeof(C<T>);
   if (sm > 200 * 1024) throw Error(1, "restrict: aggregate too large for shared memory");
-  static bool configured = false;
-  if (!configured) {
-    MG_CUDA(cudaFuncSetAttribute(restrict_kernel<T, RG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 200 * 1024));
-    configured = true;
-  }
+  smem_optin((const void *)restrict_kernel<T, RG>, 200 * 1024);
   restrict_kernel<T, RG><<<m.coarse.V * 2, 256, sm, s>>>(in, out, P, m, nrhs);
   MG_LAUNCH_CHECK();
 }

@@ -274,12 +274,7 @@ template <typename T, int OG>
 static void glayer_forward_og(const C<T> *in, C<T> *out, const C<T> *W, const C<T> *U, Geom g, int Cin,
                               int Cout, int B, cudaStream_t s) {
   const size_t sm = (size_t)9 * Cin * OG * 16 * sizeof(C<T>);
-  static bool configured = false;
-  if (!configured) {
-    MG_CUDA(cudaFuncSetAttribute(glayer_forward_kernel<T, OG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 160 * 1024));
-    configured = true;
-  }
+  smem_optin((const void *)glayer_forward_kernel<T, OG>, 160 * 1024);
   glayer_forward_kernel<T, OG><<<dim3(div_up(g.V, 128), div_up(Cout, OG), B), 128, sm, s>>>(in, out, W, U,
                                                                                           g, Cin, Cout);
   MG_LAUNCH_CHECK();
@@ -297,12 +292,7 @@ template <typename T>
 void glayer_adjoint(const C<T> *gin, C<T> *out, const C<T> *W, const C<T> *U, Geom g, int Cin,
                     int Cout, int B, cudaStream_t s) {
   const size_t sm = (size_t)9 * Cout * 16 * sizeof(C<T>);
-  static bool configured = false;
-  if (!configured) {
-    MG_CUDA(cudaFuncSetAttribute(glayer_adjoint_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 100 * 1024));
-    configured = true;
-  }
+  smem_optin((const void *)glayer_adjoint_kernel<T>, 100 * 1024);
   glayer_adjoint_kernel<T><<<dim3(div_up(g.V, 128), Cin, B), 128, sm, s>>>(gin, out, W, U, g, Cin, Cout);
   MG_LAUNCH_CHECK();
 }

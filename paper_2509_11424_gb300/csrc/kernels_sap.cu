@@ -334,12 +334,7 @@ void sap_sweep(C<T> *r, C<T> *z, C<T> *e, const C<T> *U, Geom g, const int b[4],
     nblocks *= sg.nb[i];
   }
   const size_t sm = sap_smem_bytes<T>(b);
-  static bool configured = false;
-  if (!configured) {
-    MG_CUDA(cudaFuncSetAttribute(sap_block_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(220 * 1024)));
-    configured = true;
-  }
+  smem_optin((const void *)sap_block_kernel<T>, (int)(220 * 1024));
   if (sm > 220 * 1024) throw Error(1, "SAP block too large for shared memory");
   for (int color = 0; color < 2; ++color) {
     sap_block_kernel<T><<<dim3(nblocks / 2, nrhs), sg.sites, sm, s>>>(r, z, e, U, sg, (T)(4.0 + m0),

@@ -62,6 +62,8 @@ extern "C" mgmlmc_status mgmlmc_project_noalloc(mgmlmc_ctx *ctx, int level, int 
       throw mg::Error(MGMLMC_ERR_ARG,
                       "project_noalloc: nrhs * coarse length = " + std::to_string(nc * nrhs) +
                           " exceeds the fixed scratch of " + std::to_string(capacity) + " complex entries");
+    const size_t es = precision == MGMLMC_FP64 ? sizeof(double2) : sizeof(float2);
+    require_disjoint(in, (size_t)n * nrhs * es, out, (size_t)n * nrhs * es);
     void *scratch = scratch_address();
     e.enter();
     struct Leave {

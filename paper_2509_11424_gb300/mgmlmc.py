@@ -45,7 +45,8 @@ class SolverParams(ctypes.Structure):
                 ('inner_tol', ctypes.c_double),
                 ('smoother', ctypes.c_int),
                 ('sap_iters', ctypes.c_int),
-                ('coarse_smoother_steps', ctypes.c_int)]
+                ('coarse_smoother_steps', ctypes.c_int),
+                ('fine_batch', ctypes.c_int)]
 
 
 class EstParams(ctypes.Structure):
@@ -109,6 +110,8 @@ _SIGNATURES = {
     'mgmlmc_estimate_trace': [_P, ctypes.POINTER(EstParams), ctypes.POINTER(TermResult), _I,
                               ctypes.POINTER(_I)],
     'mgmlmc_coarsest_trace': [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
+    'mgmlmc_last_samples': [_P, _I, _P, _I, ctypes.POINTER(_I)],
+    'mgmlmc_release_workspaces': [_P],
     'mgmlmc_connected_correlator': [_P, _I, _I, _U64, _U64, _P, _P, ctypes.POINTER(_I)],
     'mgmlmc_disconnected_loop': [_P, _I, _I, _I, _U64, _U64, _P, _P, ctypes.POINTER(_I)],
     'mgmlmc_apply': [_P, _I, _I, _I, _P, _P, _I],
@@ -218,9 +221,9 @@ SMOOTHER_MR, SMOOTHER_SAP, SMOOTHER_LEARNED = 0, 1, 2
 
 def solver_params(tol=1e-12, max_iter=2000, restart=16, smoother_steps=4, coarse_iters=8,
                   precision=FP64, inner_tol=1e-6, smoother=SMOOTHER_MR, sap_iters=4,
-                  coarse_smoother_steps=4):
+                  coarse_smoother_steps=4, fine_batch=0):
     return SolverParams(tol, max_iter, restart, smoother_steps, coarse_iters, precision, inner_tol,
-                        smoother, sap_iters, coarse_smoother_steps)
+                        smoother, sap_iters, coarse_smoother_steps, fine_batch)
 
 
 def mgmlmc_set_solver(ctx, params=None, **kw):
@@ -276,6 +279,17 @@ def mgmlmc_estimate_trace(ctx, params):
     _check(ctx, lib().mgmlmc_estimate_trace(ctx, ctypes.byref(params), out, 2 * MAX_LEVELS,
                                             ctypes.byref(nt)))
     return [out[i].as_dict() for i in range(nt.value)]
+
+
+def mgmlmc_last_samples(ctx, index, max_samples):
+    out = np.zeros(2 * max(1, max_samples))
+    n = _I()
+    _check(ctx, lib().mgmlmc_last_samples(ctx, index, ptr(out), max_samples, ctypes.byref(n)))
+    return out[:2 * n.value].view(np.complex128).copy()
+
+
+def mgmlmc_release_workspaces(ctx):
+    _check(ctx, lib().mgmlmc_release_workspaces(ctx))
 
 
 def mgmlmc_coarsest_trace(ctx):

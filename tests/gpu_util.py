@@ -31,7 +31,15 @@ def host(t):
 
 
 def rel(a, b):
-    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+    """Relative error of a against b, element by element as well as by norm:
+    the larger of ||a - b|| / ||b|| and max_i |a_i - b_i| / max_i |b_i|.  The
+    second keeps one wrong entry (a boundary or tail site) from hiding in the
+    norm of a large vector."""
+    a, b = np.ravel(a), np.ravel(b)
+    d = np.abs(a - b)
+    norm = float(np.linalg.norm(d) / max(np.linalg.norm(b), 1e-300))
+    elem = float(d.max(initial=0.0) / max(np.abs(b).max(initial=0.0), 1e-300))
+    return max(norm, elem)
 
 
 class Setup:

@@ -103,3 +103,57 @@ def test_solve_full_size(full):
     xs = host(x)
     for r in range(B):
         assert np.linalg.norm(b[r] - Mx @ xs[r]) / np.linalg.norm(b[r]) < 1.5e-12
+
+
+def test_estimator_samples_full_size():
+    """Per-sample values of every orthogonal term at the benchmark's size and
+    batch (16^4, 32 right-hand sides per launch, mixed-precision solver with
+    SAP) against the oracle on identical noise and identical P (test vectors
+    imported from the seeded generator on both sides).  The coarse terms O_1,
+    F_1 and the coarsest term are compared on all 32 samples (the oracle
+    factors the coarse operators); the fine terms O_0 and F_0, whose oracle
+    samples each need an unpreconditioned GMRES solve of the 786,432-dof
+    system (~430 iterations), on the batch's last sample (O_0) and sample 7
+    (F_0), the two solves run side by side.  Each
+    sample is exact to the solves' 1e-12 times the condition number (~45), so
+    1e-8 relative to the largest sample of the term."""
+    import concurrent.futures as cf
+
+    import bench
+    from oracle import estimators as oest, multigrid as omg, solve as osolve
+    m0 = json.load(open(os.path.join(ROOT, 'tests', 'golden', 'mass_16x16x16x16.json')))['m0']
+    U = synth.gauge_field(DIMS, bench.EPS_GAUGE, bench.GAUGE_SEED)
+    ctx = M.mgmlmc_create(DIMS, torch.cuda.current_stream())
+    try:
+        M.mgmlmc_set_gauge(ctx, U)
+        M.mgmlmc_set_mass(ctx, m0)
+        M.mgmlmc_set_solver(ctx, precision=M.FP32, **bench.SOLVER)
+        tvs, cur, dof = [], DIMS, 12
+        for l, (b, k) in enumerate(zip(bench.BLOCKS, bench.NTV)):
+            n = int(np.prod(cur)) * dof
+            tv = synth.random_test_vectors(n, k, 3900 + l)
+            tvs.append(tv)
+            M.mgmlmc_set_test_vectors(ctx, l, np.ascontiguousarray(tv.T), k, n, on_device=False)
+            cur = tuple(c // bb for c, bb in zip(cur, b))
+            dof = 2 * k
+        M.mgmlmc_build_hierarchy(ctx, M.mg_params(bench.BLOCKS, bench.NTV, setup_rounds=0))
+        seed = 2929
+        M.mgmlmc_estimate_trace(ctx, M.est_params(M.EST_ORTHOGONAL, [B] * 5, batch=B, seed=seed))
+        got = [M.mgmlmc_last_samples(ctx, i, B) for i in range(5)]
+    finally:
+        M.mgmlmc_destroy(ctx)
+    h = omg.Hierarchy(dirac.wilson_stencil(U, m0, DIMS), DIMS, bench.BLOCKS, tvs)
+    sol = [osolve.LevelSolver(h.matrix(l)) for l in range(3)]
+    terms = dict(oest.Estimators(h, sol, seed=seed).orthogonal_terms())
+    order = ['O0', 'O1', 'F0', 'F1', 'coarsest']
+    picks = {'O0': [B - 1], 'F0': [7], 'O1': range(B), 'F1': range(B), 'coarsest': range(B)}
+    jobs = [(name, k) for name in order for k in picks[name]]
+    fine = [j for j in jobs if j[0] in ('O0', 'F0')]
+    with cf.ThreadPoolExecutor(max_workers=len(fine)) as ex:
+        fut = {j: ex.submit(terms[j[0]], j[1]) for j in fine}
+        want = {j: terms[j[0]](j[1]) for j in jobs if j not in fut}
+        want.update({j: f.result() for j, f in fut.items()})
+    for i, name in enumerate(order):
+        scale = max(abs(want[(name, k)]) for k in picks[name])
+        for k in picks[name]:
+            assert abs(got[i][k] - want[(name, k)]) < 1e-8 * max(1.0, scale), (name, k)

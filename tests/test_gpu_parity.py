@@ -352,16 +352,41 @@ def test_trace_estimator_samples_match_oracle(three):
     res = M.mgmlmc_estimate_trace(three.ctx, M.est_params(M.EST_ORTHOGONAL, [N] * 5, batch=4, seed=2222))
     names = ['O0', 'O1', 'F0', 'F1', 'coarsest']
     terms = dict(E.orthogonal_terms())
-    for r, name in zip(res, names):
+    for i, (r, name) in enumerate(zip(res, names)):
         X = np.array([terms[name](k) for k in range(N)])
         mu, var = oest.sample_stats(X)
         assert r['n'] == N
         assert abs(complex(r['mean_re'], r['mean_im']) - mu) < 1e-8 * max(1.0, abs(mu)), name
         assert abs(r['var'] - var) < 1e-7 * max(1.0, var), name
         assert r['max_residual'] <= 1.5e-12
+        # sample by sample, not only through the mean and the variance
+        got = M.mgmlmc_last_samples(three.ctx, i, N)
+        assert got.shape == (N,)
+        assert np.max(np.abs(got - X)) < 1e-8 * max(1.0, np.max(np.abs(X))), name
     plain = M.mgmlmc_estimate_trace(three.ctx, M.est_params(M.EST_PLAIN, [N], batch=3, seed=2222))[0]
     X = np.array([E.plain(k) for k in range(N)])
     assert abs(complex(plain['mean_re'], plain['mean_im']) - X.mean()) < 1e-8 * abs(X.mean())
+    got = M.mgmlmc_last_samples(three.ctx, 0, N)
+    assert np.max(np.abs(got - X)) < 1e-8 * np.max(np.abs(X))
+
+
+def test_trace_samples_config1_per_sample(cfg1):
+    """config-1 (4^4, two levels): every per-sample value X_k of the
+    orthogonal terms O_0, F_0 and the coarsest term and of plain Hutchinson
+    equals the oracle's x_k^H A x_k on identical noise and P (1e-8: solves to
+    1e-12 times the condition number ~10)."""
+    h = cfg1.hier
+    sol = [osolve.LevelSolver(h.matrix(l)) for l in range(2)]
+    N = 24
+    E = oest.Estimators(h, sol, seed=2424)
+    M.mgmlmc_estimate_trace(cfg1.ctx, M.est_params(M.EST_ORTHOGONAL, [N] * 3, batch=8, seed=2424))
+    for i, (name, f) in enumerate(E.orthogonal_terms()):
+        X = np.array([f(k) for k in range(N)])
+        got = M.mgmlmc_last_samples(cfg1.ctx, i, N)
+        assert np.max(np.abs(got - X)) < 1e-8 * max(1.0, np.max(np.abs(X))), name
+    M.mgmlmc_estimate_trace(cfg1.ctx, M.est_params(M.EST_PLAIN, [N], batch=8, seed=2424))
+    X = np.array([E.plain(k) for k in range(N)])
+    assert np.max(np.abs(M.mgmlmc_last_samples(cfg1.ctx, 0, N) - X)) < 1e-8 * np.max(np.abs(X))
 
 
 def test_oblique_estimator_samples_match_oracle(three):
@@ -419,10 +444,12 @@ def test_four_level_hierarchy_matches_oracle():
         terms = dict(E.orthogonal_terms())
         names = ['O0', 'O1', 'O2', 'F0', 'F1', 'F2', 'coarsest']
         assert len(res) == 7
-        for r, name in zip(res, names):
+        for i, (r, name) in enumerate(zip(res, names)):
             X = np.array([terms[name](k) for k in range(N)])
             mu = X.mean()
             assert abs(complex(r['mean_re'], r['mean_im']) - mu) < 1e-8 * max(1.0, abs(mu)), name
+            got = M.mgmlmc_last_samples(s.ctx, i, N)
+            assert np.max(np.abs(got - X)) < 1e-8 * max(1.0, np.max(np.abs(X))), name
         res = M.mgmlmc_estimate_trace(s.ctx, M.est_params(M.EST_OBLIQUE, [N] * 4, batch=5, seed=2245))
         E2 = oest.Estimators(h, sol, seed=2245)
         assert len(res) == 4
@@ -459,12 +486,19 @@ def test_connected_correlator_matches_oracle():
         mp, vp = M.mgmlmc_connected_correlator(s.ctx, M.EST_PLAIN, N, 4040, 0, 8, 1)
         Xp = np.array([E.connected_plain(k) for k in range(N)])
         assert np.max(np.abs(mp[0, 0] - Xp.mean(axis=0))) < 1e-9 * np.max(np.abs(Xp.mean(axis=0)))
-        # the split sums to the plain estimator's expectation; per sample the
-        # sum over (r, s) differs (different operators), so compare means of
-        # the totals loosely against the exact value
+        # unbiasedness against the exact split (Eq. connected-G, Eq. G-split):
+        # the dense G_rs(t) of the oracle's dense operators, every (r, s, t)
+        # within 5 standard errors of the mean of 256 samples (fixed seed)
         B = exact.DenseTerms(h).B_matrices()
         G = exact.correlator_exact(B, dims)
-        assert np.all(np.isfinite(mean)) and G.shape == mean.shape
+        Ns = 256
+        mean, var = M.mgmlmc_connected_correlator(s.ctx, M.EST_ORTHOGONAL, Ns, 4042, 0, 8, 5)
+        assert G.shape == mean.shape
+        se = np.sqrt(var / Ns)
+        assert np.all(np.abs(mean - G) <= 5 * se + 1e-12 * np.max(np.abs(G)))
+        # and the sum over (r, s) is the full correlator G(t)
+        assert np.allclose(G.sum(axis=(0, 1)), exact.correlator_exact([np.linalg.inv(h.matrix(0).toarray())],
+                                                                     dims)[0, 0], rtol=1e-10, atol=0)
     finally:
         s.close()
 
@@ -547,3 +581,24 @@ def test_nan_gauge_rejected():
         assert e.value.status == 2
     finally:
         M.mgmlmc_destroy(ctx)
+
+
+def test_fine_batch_and_released_workspaces_keep_samples(three):
+    """fine_batch (the level-0 memory bound) only regroups the right-hand
+    sides of the fine-level solves: the per-sample values of every
+    orthogonal term agree with the ungrouped run to the solves' accuracy,
+    also after mgmlmc_release_workspaces freed every work buffer."""
+    N = 10
+    p = M.est_params(M.EST_ORTHOGONAL, [N] * 5, batch=5, seed=2626)
+    M.mgmlmc_estimate_trace(three.ctx, p)
+    ref = [M.mgmlmc_last_samples(three.ctx, i, N) for i in range(5)]
+    try:
+        M.mgmlmc_set_solver(three.ctx, fine_batch=2)
+        M.mgmlmc_release_workspaces(three.ctx)
+        res = M.mgmlmc_estimate_trace(three.ctx, p)
+        assert [r['n'] for r in res] == [N] * 5
+        for i in range(5):
+            got = M.mgmlmc_last_samples(three.ctx, i, N)
+            assert np.max(np.abs(got - ref[i])) < 1e-8 * max(1.0, np.max(np.abs(ref[i]))), i
+    finally:
+        M.mgmlmc_set_solver(three.ctx)
