@@ -7,33 +7,44 @@ Metric: time to reach a fixed standard error eps = 1e-5 |tr| of the
 tr(D^-1) estimate, predicted from the measured per-sample device cost C_l
 and sample variance V_l of every term with the optimal allocation
 (sum_l sqrt(V_l C_l))^2 / eps^2 (Sec. 2.2, Eq. MLMC-Nl); lower is better.
+The allocation is then run at a coarser eps_val (chosen so that it takes
+about --validate-s seconds) and the achieved standard error and time are
+reported beside the prediction.
 
-Workload: 16^4 lattice, synthetic SU(3) links U = exp(i 0.4 H) (seed 1002),
-Wilson mass m0 from tests/golden/mass_16x16x16x16.json (the most
-ill-conditioned point of an oracle scan on this field), three-level
-hierarchy (4^4 then 2^4 aggregates, 16 test vectors per level), noise seed
-2002.  A step is one batch of `--batch` Z4 noise vectors through every term
-of the orthogonal split (O_0, O_1, F_0, F_1, D_2^-1), every solve to a
-relative residual of 1e-12 (FP32 MG-preconditioned FGMRES with SAP and a
-one-channel learned post-smoothing step, inside FP64 defect correction, by
-default; `--precision fp64` for all-FP64).  Inputs (gauge field, hierarchy,
-vectors) are resident in HBM; a 256 MB write flushes the 129 MB L2 between
-timed steps.
+Default workload (`--workload 48x48x48x96`): a 48^3 x 96 lattice, synthetic
+SU(3) links U = exp(i 0.4 H) drawn on the device (seed 1005), m0 = -0.40,
+four-level hierarchy (4^4, 2^4, 2^4 aggregates, 16 test vectors per level,
+coarsest level 3^3 x 6 inverted densely), every solve to a relative
+residual of 1e-12: FP32 MG-preconditioned FGMRES(8) with SAP and a learned
+one-channel post-smoothing step inside FP64 defect correction.  The network
+is trained on the GPU on 2000 residual / error pairs of the solver on a
+16^4 field of the same generator (seed 1006) and its weights carried over
+(the layers are translation and gauge covariant).  A step is one call of
+mgmlmc_estimate_trace with 4 Z4 samples for each fine-level term (O_0,
+F_0; one right-hand-side block, the fine level's memory bound) and 32 for
+each coarse term (O_1, O_2, F_1, F_2, coarsest).  Inputs are resident in HBM
+and every launch of a step touches far more than the 129 MB L2 (one fine
+FP32 vector is 1 GB); the L2 is flushed between steps anyway.
+
+`--workload 16x16x16x16`: the 16^4 lattice (host-drawn field seed 1002,
+m0 from tests/golden/mass_16x16x16x16.json, three levels, 32 samples per
+term per step) with every comparison arm, including inexact deflation and
+refined test vectors.
 
 Also reported, on the same GPU and noise samples: plain Hutchinson with the
-same solver, the oblique MG-MLMC split, inexact deflation (k = 128), SAP-only
-MG-MLMC, all-FP64 MG-MLMC and plain Hutchinson in FP64, with the per-term
-difference of the mixed-precision estimate against FP64; the FP32 and BF16
-Wilson operator bandwidth at 32^4; the roofline of the dominant kernel class
-(CUDA events around its launches in a profiled repeat of the first timed
-step); the clocks sampled during the timed region; an end-to-end figure
-through the C-ABI (gauge field copied from pinned host memory, hierarchy
-setup, then the sampling to the same eps); and the FP64 CPU oracle timed on
-the host on a bounded sample.
+same solver, the oblique MG-MLMC split, SAP-only MG-MLMC and all-FP64
+MG-MLMC with the per-term difference of the mixed-precision estimate against
+FP64; the FP32 and BF16 Wilson operator bandwidth at 32^4; the roofline of
+the dominant kernel class (CUDA events around its launches in a profiled
+repeat of the first timed step); the clocks sampled during the timed region;
+an end-to-end figure through the C-ABI (gauge field copied from pinned host
+memory, hierarchy setup, network training, then the sampling to the same
+eps); and the FP64 CPU oracle timed on the host on a bounded sample.
 """
 import argparse
 import hashlib
 import json
+import math
 import os
 import subprocess
 import sys
@@ -52,6 +63,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = 'tr(D^-1) MLMC time to fixed variance, learned+mixed vs plain; Dslash GB/s'
+# the 16^4 workload (its oracle statistics are stored in the mass file)
 DIMS = (16, 16, 16, 16)
 EPS_GAUGE = 0.4
 GAUGE_SEED, NOISE_SEED, TV_SEED = 1002, 2002, 3002
@@ -69,25 +81,34 @@ FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 rate: 152 SMs x 2 FP64 FMA/clk x 2 flop x 
 FP32_PEAK_TFLOPS = 80.0  # 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
 SOLVER = dict(tol=1e-12, restart=24, max_iter=2000, smoother=1, smoother_steps=1, sap_iters=4,
               coarse_iters=4, inner_tol=1e-6, coarse_smoother_steps=4)
+
+# Workloads.  fine_n / coarse_n: samples per step of the terms that solve on
+# the fine level / only on coarser ones; the fine level's right-hand sides
+# per solve are capped at fine_batch (its vectors are the memory bound).
+WORKLOADS = {
+    '48x48x48x96': dict(
+        dims=(48, 48, 48, 96), eps=0.4, gauge='device', gauge_seed=1005, noise_seed=2005, tv_seed=3005,
+        m0=-0.40, blocks=[(4, 4, 4, 4), (2, 2, 2, 2), (2, 2, 2, 2)], ntv=[16, 16, 16],
+        fine_n=4, coarse_n=32, batch=32, setup_rounds=6, setup_iters=30,
+        solver=dict(SOLVER, restart=8, fine_batch=4),
+        train=dict(dims=(16, 16, 16, 16), gauge_seed=1006, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)], ntv=[16, 16]),
+        arms=('plain', 'oblique', 'sap', 'fp64'), fp64_fine_n=2, fp64_coarse_n=8),
+    '16x16x16x16': dict(
+        dims=DIMS, eps=EPS_GAUGE, gauge='host', gauge_seed=GAUGE_SEED, noise_seed=NOISE_SEED, tv_seed=TV_SEED,
+        m0=None, blocks=BLOCKS, ntv=NTV, fine_n=32, coarse_n=32, batch=32, setup_rounds=6, setup_iters=30,
+        solver=dict(SOLVER), train=None, arms=ARMS, fp64_fine_n=32, fp64_coarse_n=32),
+}
+DEFAULT_WORKLOAD = '48x48x48x96'
 KERNELS = {0: 'wilson_dslash_fp64', 1: 'wilson_dslash_fp32', 2: 'coarse_stencil_fp64',
            3: 'coarse_stencil_fp32', 4: 'sap_sweep_fp64', 5: 'sap_sweep_fp32'}
 # further event-timed groups (breakdown only; no roofline)
 GROUPS = {6: 'transfer_in_cycle', 7: 'gram_schmidt', 8: 'learned_step', 9: 'coarsest_dense'}
 SHARD_STRIDE = 1000000  # Z4 sample counters per rank
+VALIDATE_FIRST = 500000  # sample counters of the allocation check (fresh samples)
 # dram bytes per launch of a kernel from an ncu capture, keyed by (kernel,
 # sha1 of the kernel sources it was measured on, right-hand sides per
-# launch); a stale or missing key gives null
-TRAFFIC = {
-    # one level-1 launch (4^4 x 32 dof, 8 rhs), cold-cache capture (the TMA
-    # kernel's code and the shared helpers are byte-identical to the capture)
-    ('coarse_stencil_fp32', 'f3db7ca784d1', 8): 19.43e6,
-    # one sweep (block + boundary kernel, both colours), 16^4 x 8 rhs
-    ('sap_sweep_fp32', '9a67c5f9b503', 8): 578.0e6,
-    # the same sweep at 32 rhs, scaled from the 8-rhs capture by the rhs
-    # count: every right-hand side is its own row of the launch grid and
-    # moves its own residual, correction and block solution
-    ('sap_sweep_fp32', '9a67c5f9b503', 32): 4 * 578.0e6,
-}
+# launch, lattice); a stale or missing key gives null
+TRAFFIC = {}
 
 
 def workload():
@@ -375,7 +396,22 @@ def e2e_time_to_variance(setup_s, first_step_s, step_s, value, device_step_s):
     return setup_s + max(0.0, first_step_s - step_s) + value * step_s / device_step_s
 
 
-def cpu_baseline(m0, wl, threads):
+def extrapolation_note(wlb):
+    """How the oracle's 16^4 timing stands for a larger lattice: the cost of
+    a solve grows with the volume V and the samples needed for the same
+    relative eps shrink with it (the variance ||offdiag(D^-1)||_F^2 and
+    |tr(D^-1)| are both extensive), so the time to variance carries over
+    unchanged; the oracle's iterations per solve at 16^4 are a lower bound
+    for the larger, more ill-conditioned lattice."""
+    if wlb is None or tuple(wlb['dims']) == DIMS:
+        return ''
+    r = float(np.prod(wlb['dims'])) / float(np.prod(DIMS))
+    return ('; extrapolated to %s: cost per solve x %.0f (volume), samples for the same relative eps / %.0f '
+            '(variance and |tr| extensive), so the same time; the 16^4 iteration count is a lower bound there'
+            % ('x'.join(map(str, wlb['dims'])), r, r))
+
+
+def cpu_baseline(m0, wl, threads, wlb=None):
     """The `cpu_baseline` object of the GPU arm's line: the oracle's plain
     Hutchinson estimator timed on `threads` host threads (one GMRES cycle
     each, concurrently), with the single-thread figure beside it."""
@@ -386,17 +422,20 @@ def cpu_baseline(m0, wl, threads):
     return {'value': value, 'unit': 's', 'cores': threads, 'kind': 'oracle',
             'sample': 'plain Hutchinson, %d concurrent 64-iteration GMRES(64) cycles of the oracle on the 16^4 '
                       'system, one per thread (%.1f s wall), scaled by %.0f iterations per 1e-12 solve and the '
-                      'oracle variance' % (threads, sT['seconds'], np.mean(wl['oracle_plain']['gmres_iters'])),
+                      'oracle variance%s' % (threads, sT['seconds'], np.mean(wl['oracle_plain']['gmres_iters']),
+                                             extrapolation_note(wlb)),
             'seconds_per_solve': C, 'cpu_utilisation': sT['cpu_seconds'] / sT['seconds'],
             'single_core': {'value': v1, 'seconds_per_solve': C1, 'cycle_s': s1['seconds'],
                             'cpu_utilisation': s1['cpu_seconds'] / s1['seconds']},
             'threads_available': host_cores()}
 
 
-def reference_arm(args, rank, world):
+def reference_arm(args, rank, world, wlb=None):
     """The FP64 CPU oracle on this host's cores, same metric and workload:
     each step one bounded sample (a 64-iteration GMRES cycle of the plain
-    Hutchinson solve), the value its time to the same variance."""
+    Hutchinson solve on the 16^4 system), the value its time to the same
+    variance (carried over to a larger workload lattice by volume, see
+    extrapolation_note)."""
     if rank != 0:
         return
     wl = workload()
@@ -413,15 +452,17 @@ def reference_arm(args, rank, world):
     value, C = oracle_time_to_variance(dict(sec_per_iter=spi), wl)
     sample = ('plain Hutchinson, 16^4 solve by the oracle GMRES(64): per step %d concurrent 64-iteration '
               'restart cycles (one per thread, samples of their own) timed, scaled by %.0f iterations '
-              'per 1e-12 solve and the oracle variance %.4g (tests/golden/mass_16x16x16x16.json)'
-              % (T, np.mean(wl['oracle_plain']['gmres_iters']), wl['oracle_plain']['var']))
+              'per 1e-12 solve and the oracle variance %.4g (tests/golden/mass_16x16x16x16.json)%s'
+              % (T, np.mean(wl['oracle_plain']['gmres_iters']), wl['oracle_plain']['var'],
+                 extrapolation_note(wlb)))
+    lat = 'x'.join(map(str, (wlb or {}).get('dims', DIMS)))
     util = float(np.mean([s['cpu_seconds'] / s['seconds'] for s in samples]))
     line = {'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': 's', 'n_gpus': world,
             'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': 1e3 * float(np.mean(t)),
             'higher_is_better': False, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
             'data': 'synthetic',
-            'config': {'workload': '16^4 Wilson-Dirac, SU(3) exp(i 0.4 H) seed 1002, m0 %.4f, '
-                                   'plain Hutchinson with the FP64 CPU oracle' % wl['m0']},
+            'config': {'workload': '%s Wilson-Dirac, SU(3) exp(i 0.4 H), m0 %.4f, plain Hutchinson with the '
+                                   'FP64 CPU oracle (timed on the 16^4 system)' % (lat, wl['m0'])},
             'cpu_baseline': {'value': value, 'unit': 's', 'cores': T, 'kind': 'oracle', 'sample': sample,
                              'seconds_per_solve': C, 'cpu_utilisation': util,
                              'threads_available': host_cores()},
@@ -521,85 +562,208 @@ def dslash_hbm(M, torch, U16, m0, reps=5):
 
 
 # ---------------------------------------------------------------- GPU arm
+def term_counts(M, wl, kind, n_levels, fine_n=None, coarse_n=None):
+    """Samples per term of one step: fine_n for the terms that solve on the
+    fine level, coarse_n for the others (orthogonal order O_0.., F_0..,
+    coarsest; oblique M_0.., coarsest; plain [0])."""
+    f = wl['fine_n'] if fine_n is None else fine_n
+    c = wl['coarse_n'] if coarse_n is None else coarse_n
+    L = n_levels
+    if kind == M.EST_ORTHOGONAL:
+        return [f] + [c] * (L - 2) + [f] + [c] * (L - 2) + [c]
+    if kind == M.EST_OBLIQUE:
+        return [f] + [c] * (L - 2) + [c]
+    return [f]
+
+
+def build_context(M, torch, wl, stream, U=None, dims=None, blocks=None, ntv=None, gauge_seed=None):
+    """A context on the workload's lattice (or the given one) with the gauge
+    field, mass, FP32 solver and hierarchy; returns (ctx, setup seconds)."""
+    dims = dims or wl['dims']
+    ctx = M.mgmlmc_create(dims, stream)
+    if U is not None:
+        M.mgmlmc_set_gauge(ctx, U)
+    else:
+        M.mgmlmc_gen_gauge(ctx, wl['eps'], gauge_seed or wl['gauge_seed'])
+    M.mgmlmc_set_mass(ctx, wl['m0'])
+    M.mgmlmc_set_solver(ctx, precision=M.FP32, **wl['solver'])
+    torch.cuda.synchronize()
+    t0 = time.time()
+    M.mgmlmc_build_hierarchy(ctx, M.mg_params(blocks or wl['blocks'], ntv or wl['ntv'],
+                                               setup_rounds=wl['setup_rounds'], setup_iters=wl['setup_iters'],
+                                               seed=wl['tv_seed']))
+    torch.cuda.synchronize()
+    return ctx, time.time() - t0
+
+
+def train_network(M, torch, wl, ctx, stream, channels, steps):
+    """The gauge-covariant network trained on the solver's own residuals
+    (mgmlmc_learned_train).  Workloads with a `train` entry train on that
+    smaller lattice of the same generator and carry the weights over to ctx
+    (the layers act the same way on any lattice); returns (train result,
+    wall seconds including the side context's setup)."""
+    kw = dict(channels=channels, steps=steps, batch=8, pool=2000, lr=1e-3, seed=5002)
+    t0 = time.time()
+    if not wl['train']:
+        res = M.mgmlmc_learned_train(ctx, **kw)
+        return res, time.time() - t0
+    tw = wl['train']
+    side, _ = build_context(M, torch, wl, stream, dims=tw['dims'], blocks=tw['blocks'], ntv=tw['ntv'],
+                            gauge_seed=tw['gauge_seed'])
+    try:
+        res = M.mgmlmc_learned_train(side, **kw)
+        W = np.zeros(2 * M.mgmlmc_learned_size(side))
+        M.mgmlmc_learned_weights(side, W, 0)
+    finally:
+        M.mgmlmc_destroy(side)
+    M.mgmlmc_learned_init(ctx, channels, 5002)
+    M.mgmlmc_learned_weights(ctx, W, 1)
+    torch.cuda.synchronize()
+    res = dict(res, trained_on=list(tw['dims']))
+    return res, time.time() - t0
+
+
+def roofline_of(kst, prof_ms, B, wl_name, M):
+    """Roofline of the kernel class with the largest time in the profiled step."""
+    dom = max(kst, key=lambda c: kst[c]['ms'])
+    ks = kst[dom]
+    if ks['launches'] == 0:
+        return None
+    sec = ks['ms'] * 1e-3
+    peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
+    hbm = peaks.get('hbm_gbs')
+    if dom in (0, 2, 4):  # FP64 kernels are bound by the FP64 pipe on this part
+        achieved = ks['flops'] / sec / 1e12
+        roof = dict(bound='alu', achieved=achieved, peak=FP64_PEAK_TFLOPS, unit='TFLOP/s',
+                    frac=achieved / FP64_PEAK_TFLOPS, peak_source='GB300 FP64 rate 1.25 TFLOP/s (table)')
+    else:
+        achieved = ks['bytes'] / sec / 1e9
+        peak = hbm if hbm else 6800.0
+        roof = dict(bound='hbm', achieved=achieved, peak=peak, unit='GB/s', frac=achieved / peak,
+                    peak_source='of measured (MEASURED_PEAKS.json hbm_gbs)' if hbm else 'of fallback 6.8 TB/s')
+    roof['traffic'] = TRAFFIC.get((KERNELS[dom], kernel_source_hash(KERNELS[dom]), B, wl_name))
+    roof.update(kernel=KERNELS[dom], launches=ks['launches'], avg_launch_us=ks['ms'] * 1e3 / ks['launches'],
+                share_of_profiled_step=ks['ms'] / prof_ms, profiled_step_ms=prof_ms,
+                algorithmic_bytes_per_launch=ks['bytes'] / ks['launches'],
+                algorithmic_flops_per_launch=ks['flops'] / ks['launches'],
+                fp32_alu_tflops=ks['flops'] / sec / 1e12,
+                fp32_alu_frac=ks['flops'] / sec / 1e12 / FP32_PEAK_TFLOPS)
+    return roof
+
+
+def validate_allocation(M, ctx, det, kinds_n, est, B, val_s, eps_scale):
+    """Sec. 2.2 / Eq. MLMC-Nl run for real: N_l = eps^-2 sqrt(V_l / C_l)
+    sum_i sqrt(V_i C_i) fresh samples per term at eps_val = eps * eps_scale,
+    eps_scale chosen so that the predicted cost is about val_s seconds.
+    Returns the achieved standard error (from this run's own variances) and
+    the measured device seconds beside eps_val and the prediction."""
+    terms = sorted(det['terms'], key=lambda t: kinds_n.index(int(t)))
+    V = np.array([det['terms'][t]['var'] for t in terms])
+    C = np.array([det['terms'][t]['cost_s'] for t in terms])
+    S = float(np.sum(np.sqrt(V * C)))
+    eps = det['eps'] * eps_scale
+    if eps_scale is None or eps_scale <= 0:
+        eps = S / math.sqrt(val_s)  # predicted cost S^2 / eps^2 = val_s
+    N = [max(2, int(math.ceil(math.sqrt(v / c) * S / eps ** 2))) if c > 0 else 2 for v, c in zip(V, C)]
+    predicted = float(np.sum(np.array(N) * C))
+    res = M.mgmlmc_estimate_trace(ctx, M.est_params(M.EST_ORTHOGONAL, N, batch=B, seed=est['seed'],
+                                                    first_sample=VALIDATE_FIRST))
+    secs = sum(r['seconds'] for r in res) * est['scale']
+    se = math.sqrt(sum(r['var'] / r['n'] for r in res))
+    tr = sum(complex(r['mean_re'], r['mean_im']) for r in res)
+    return dict(eps_val=eps, n_l=N, predicted_s=predicted, measured_s=secs, achieved_se=se,
+                se_over_eps=se / eps, trace=[tr.real, tr.imag])
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
     ap.add_argument('--steps', type=int, default=4)
     ap.add_argument('--warmup', type=int, default=3)
-    # 32 rhs per launch: the per-sample cost of every term falls with the
-    # batch (8 -> 16 -> 32: 91 -> 75 -> 66 s to the same variance)
-    ap.add_argument('--batch', type=int, default=32)
+    ap.add_argument('--workload', default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument('--batch', type=int, default=None, help='samples per coarse term per step')
+    ap.add_argument('--fine-n', type=int, default=None, help='samples per fine-level term per step')
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--precision', default='fp32', choices=['fp64', 'fp32'])
     ap.add_argument('--compare-steps', type=int, default=2)
     ap.add_argument('--no-cpu', action='store_true')
     ap.add_argument('--no-e2e', action='store_true')
-    ap.add_argument('--m0', type=float, default=None, help='override the tuned mass (exploration)')
+    ap.add_argument('--no-dslash', action='store_true')
+    ap.add_argument('--validate-s', type=float, default=20.0,
+                    help='device seconds the allocation check may take (0: skip)')
+    ap.add_argument('--m0', type=float, default=None, help='override the mass (exploration)')
     ap.add_argument('--learned', type=int, default=1, help='channels of the learned smoother (0: off)')
     ap.add_argument('--train-steps', type=int, default=200)
     ap.add_argument('--dslash-only', action='store_true', help='only the 32^4 FP32 Dslash measurement')
-    ap.add_argument('--arms', default=','.join(ARMS),
-                    help='comparison arms to run (comma list of %s)' % ', '.join(ARMS))
+    ap.add_argument('--arms', default=None, help='comparison arms to run (comma list of %s)' % ', '.join(ARMS))
     ap.add_argument('--oracle-threads', type=int, default=0,
                     help='host threads of the CPU oracle timing (0: every core of this host)')
     ap.add_argument('--refine-iters', type=int, default=30,
                     help='cap on the test-vector refinement steps of the "refined" arm')
+    ap.add_argument('--detail-out', default=os.environ.get('MGMLMC_BENCH_DETAIL'),
+                    help='file for the full per-term and per-arm detail (the JSON line keeps a summary)')
     args = ap.parse_args()
 
     dist, rank, world, local = dist_init()
+    wl = dict(WORKLOADS[args.workload])
     if args.impl == 'reference':
-        reference_arm(args, rank, world)
+        reference_arm(args, rank, world, wl)
         if dist:
             dist.destroy_process_group()
         return
-    wl = workload() if (args.m0 is None or os.path.exists(MASS_FILE)) else {}
-    m0 = args.m0 if args.m0 is not None else wl['m0']
+    mass = workload()
+    if wl['m0'] is None:
+        wl['m0'] = mass['m0']
+    if args.m0 is not None:
+        wl['m0'] = args.m0
+    if args.fine_n:
+        wl['fine_n'] = args.fine_n
+    if args.batch:
+        wl['coarse_n'] = wl['batch'] = args.batch
+        if wl['fine_n'] > args.batch:
+            wl['fine_n'] = args.batch
+    m0 = wl['m0']
+    B = wl['batch']
 
     import torch
     from paper_2509_11424_gb300 import mgmlmc as M, synth
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
-    U = synth.gauge_field(DIMS, EPS_GAUGE, GAUGE_SEED)
+    U16 = synth.gauge_field(DIMS, EPS_GAUGE, GAUGE_SEED)
     if args.dslash_only:
-        print(json.dumps({'dslash_hbm': dslash_hbm(M, torch, U, m0)}))
+        print(json.dumps({'dslash_hbm': dslash_hbm(M, torch, U16, mass['m0'])}))
         return
-    ctx = M.mgmlmc_create(DIMS, stream)
+    # the metric's Dslash GB/s at 32^4, before the large context takes the memory
+    dslash_32 = dslash_hbm(M, torch, U16, mass['m0']) if rank == 0 and not args.no_dslash else None
+
     prec = M.FP64 if args.precision == 'fp64' else M.FP32
-    M.mgmlmc_set_gauge(ctx, U)
-    M.mgmlmc_set_mass(ctx, m0)
-    M.mgmlmc_set_solver(ctx, precision=prec, **SOLVER)
-    mgp = M.mg_params(BLOCKS, NTV, setup_rounds=6, setup_iters=30, seed=TV_SEED)
-    torch.cuda.synchronize()
-    t_setup = time.time()
-    M.mgmlmc_build_hierarchy(ctx, mgp)
-    torch.cuda.synchronize()
-    t_setup = time.time() - t_setup
-    train = None
-    main_solver = dict(SOLVER)
+    U = synth.gauge_field(wl['dims'], wl['eps'], wl['gauge_seed']) if wl['gauge'] == 'host' else None
+    ctx, t_setup = build_context(M, torch, wl, stream, U=U)
+    if prec == M.FP64:
+        M.mgmlmc_set_solver(ctx, precision=prec, **wl['solver'])
+    L = len(wl['blocks']) + 1
+    train, t_train = None, 0.0
+    main_solver = dict(wl['solver'])
     if args.learned > 0:
-        # gauge-covariant network trained on the solver's own post-SAP residuals
-        train = M.mgmlmc_learned_train(ctx, channels=args.learned, steps=args.train_steps, batch=8,
-                                       pool=2000, lr=1e-3, seed=5002)
+        train, t_train = train_network(M, torch, wl, ctx, stream, args.learned, args.train_steps)
         main_solver['smoother'] = M.SMOOTHER_LEARNED
         M.mgmlmc_set_solver(ctx, precision=prec, **main_solver)
     print('kernel launches after setup: %d' % M.mgmlmc_kernel_launches(), file=sys.stderr)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device='cuda')  # 256 MB > L2
-
-    B = args.batch
-    nterm = 2 * len(BLOCKS) + 1
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nseed = wl['noise_seed']
 
-    def step(k, kind=M.EST_ORTHOGONAL):
-        n = {M.EST_ORTHOGONAL: [B] * nterm, M.EST_OBLIQUE: [B] * (len(BLOCKS) + 1)}.get(kind, [B])
-        return M.mgmlmc_estimate_trace(ctx, M.est_params(kind, n, batch=B, seed=NOISE_SEED,
+    def step(k, kind=M.EST_ORTHOGONAL, fine_n=None, coarse_n=None):
+        n = term_counts(M, wl, kind, L, fine_n, coarse_n)
+        return M.mgmlmc_estimate_trace(ctx, M.est_params(kind, n, batch=B, seed=nseed,
                                                          first_sample=first_sample(rank, k, B)))
 
-    def timed(k0, K, kind=M.EST_ORTHOGONAL):
+    def timed(k0, K, kind=M.EST_ORTHOGONAL, **kw):
         res, ms = [], 0.0
         for k in range(K):
             flush.zero_()
             e0.record(stream)
-            res.append(step(k0 + k, kind))
+            res.append(step(k0 + k, kind, **kw))
             e1.record(stream)
             torch.cuda.synchronize()
             ms += e0.elapsed_time(e1)
@@ -613,13 +777,13 @@ def main():
     clocks = Clocks(local)
     clocks.start()
     n_launch0 = M.mgmlmc_kernel_launches()
-    # profiler range = the timed steps (ncu --profile-from-start off captures
-    # exactly these launches; a no-op without a profiler)
     torch.cuda.profiler.start()
     results, total_ms = timed(args.warmup, args.steps)
     torch.cuda.profiler.stop()
     launches = M.mgmlmc_kernel_launches() - n_launch0
     clk = clocks.stop()
+    if train is not None:
+        train['fallbacks'] = M.mgmlmc_learned_stats(ctx)
     if dist:
         total_ms = max_over_ranks(dist, total_ms, 'cuda')
     ms_per_step = total_ms / args.steps
@@ -627,6 +791,9 @@ def main():
     if dist:
         allreduce_terms(dist, acc, world, 'cuda')
     value, det = time_to_variance(acc, world, ms_per_step, args.steps)
+    # device seconds of the library's per-term timers -> wall step time
+    dev_sec = sum(acc[t]['sec'] for t in acc)
+    scale = (ms_per_step * 1e-3 * args.steps) / dev_sec if dev_sec > 0 else 1.0
 
     # profiled repeat of the first timed step: per-launch events
     flush.zero_()
@@ -640,28 +807,7 @@ def main():
     kst = {c: M.mgmlmc_profile_stats(ctx, c) for c in KERNELS}
     gst = {GROUPS[c]: M.mgmlmc_profile_stats(ctx, c) for c in GROUPS}
     M.mgmlmc_profile(ctx, 0)
-    dom = max(kst, key=lambda c: kst[c]['ms'])
-    ks = kst[dom]
-    roof = None
-    if ks['launches'] > 0:
-        sec = ks['ms'] * 1e-3
-        peaks = json.load(open(PEAKS_FILE)) if os.path.exists(PEAKS_FILE) else {}
-        hbm = peaks.get('hbm_gbs')
-        if dom in (0, 2, 4):  # FP64 kernels are bound by the FP64 pipe on this part
-            achieved = ks['flops'] / sec / 1e12
-            roof = dict(bound='alu', achieved=achieved, peak=FP64_PEAK_TFLOPS, unit='TFLOP/s',
-                        frac=achieved / FP64_PEAK_TFLOPS, peak_source='GB300 FP64 rate 1.25 TFLOP/s (table)')
-        else:
-            achieved = ks['bytes'] / sec / 1e9
-            peak = hbm if hbm else 6800.0
-            roof = dict(bound='hbm', achieved=achieved, peak=peak, unit='GB/s', frac=achieved / peak,
-                        peak_source='of measured (MEASURED_PEAKS.json hbm_gbs)' if hbm else 'of fallback 6.8 TB/s')
-        roof['traffic'] = TRAFFIC.get((KERNELS[dom], kernel_source_hash(KERNELS[dom]), B))
-        roof.update(kernel=KERNELS[dom], launches=ks['launches'], avg_launch_us=ks['ms'] * 1e3 / ks['launches'],
-                    share_of_profiled_step=ks['ms'] / prof_ms, profiled_step_ms=prof_ms,
-                    algorithmic_bytes_per_launch=ks['bytes'] / ks['launches'],
-                    algorithmic_flops_per_launch=ks['flops'] / ks['launches'])
-    # FP32 Dslash on its own terms (the metric's 'Dslash GB/s')
+    roof = roofline_of(kst, prof_ms, wl['fine_n'], args.workload, M)
     dslash = None
     ws = kst[1] if prec == M.FP32 else kst[0]
     if ws['launches'] > 0:
@@ -669,20 +815,23 @@ def main():
         gbs = ws['bytes'] / (ws['ms'] * 1e-3) / 1e9
         dslash = dict(kernel=KERNELS[1 if prec == M.FP32 else 0], achieved_gbs=gbs,
                       frac_of_measured_hbm=gbs / peaks['hbm_gbs'] if 'hbm_gbs' in peaks else None,
-                      avg_launch_us=ws['ms'] * 1e3 / ws['launches'], nrhs=B,
-                      note='16^4 x 8 rhs working set ~0.12 GB is L2-resident within a step')
+                      avg_launch_us=ws['ms'] * 1e3 / ws['launches'], launches=ws['launches'])
 
-    dslash_32 = dslash_hbm(M, torch, U, m0) if rank == 0 else None
+    # the optimal allocation run for real at a coarser eps (bounded time)
+    check = None
+    if rank == 0 and args.validate_s > 0:
+        order = [r['term'] for r in results[0]]
+        check = validate_allocation(M, ctx, det, order, dict(seed=nseed, scale=scale), B, args.validate_s, None)
 
     compare = {}
-    arms = set(a for a in args.arms.split(',') if a)
+    arms = set((args.arms or ','.join(wl['arms'])).split(',')) - {''}
     if arms - set(ARMS):
         raise SystemExit('unknown arms: %s' % ', '.join(sorted(arms - set(ARMS))))
     k0 = args.warmup  # the timed run's first sample batch: identical noise
     cs = args.compare_steps
-    # one eps for every arm; arms with the same estimator share variances
     eps0 = det['eps']
-    if rank == 0 and args.compare_steps > 0:
+    big = args.workload != '16x16x16x16'
+    if rank == 0 and cs > 0:
         mvar = {t: v['var'] for t, v in det['terms'].items()}
         pvar = None
         if arms & {'plain', 'fp64'}:
@@ -692,16 +841,13 @@ def main():
                 compare['plain_hutchinson_same_solver'] = dict(value=pval, ms_per_step=pms / cs, detail=pdet)
             pvar = {t: v['var'] for t, v in pdet['terms'].items()}
         # the paper's earlier decomposition (Eq. oblique_multigrid-multilevel-monte-carlo)
-        # with the same solver: its own terms, variances from its own samples
         if 'oblique' in arms:
             ores, oms = timed(k0, cs, M.EST_OBLIQUE)
             oval, odet = time_to_variance(merge_terms(ores), 1, oms / cs, cs, eps=eps0)
             compare['mlmc_oblique_same_solver'] = dict(value=oval, ms_per_step=oms / cs, detail=odet)
-        # inexact deflation of plain Hutchinson (Sec. 2.1, the paper's setting of
-        # Sec. 4.2: k = 128, five inverse block power steps, inner solves to
-        # 1e-6); the exact part has no variance, its cost is the basis build
-        if 'deflated' in arms:
-            dex, dsec = M.mgmlmc_deflation_build(ctx, 128, 5, 1e-6, TV_SEED + 4000)
+        # inexact deflation (Sec. 2.1; the paper's setting of Sec. 4.2)
+        if 'deflated' in arms and not big:
+            dex, dsec = M.mgmlmc_deflation_build(ctx, 128, 5, 1e-6, wl['tv_seed'] + 4000)
             dres, dms = timed(k0, cs, M.EST_DEFLATED)
             dacc = {t: a for t, a in merge_terms(dres).items() if t == M.TERM_DEFL}
             dval, ddet = time_to_variance(dacc, 1, dms / cs, cs, eps=eps0)
@@ -709,41 +855,63 @@ def main():
                 value=dval, ms_per_step=dms / cs, setup_s=dsec, exact_part=[dex.real, dex.imag],
                 value_with_setup=dval + dsec, detail=ddet)
         if args.learned > 0 and 'sap' in arms:
-            M.mgmlmc_set_solver(ctx, precision=prec, **SOLVER)
+            M.mgmlmc_set_solver(ctx, precision=prec, **wl['solver'])
             step(k0)
             sres, sms = timed(k0, cs)
             sval, sdet = time_to_variance(merge_terms(sres), 1, sms / cs, cs, var_of=mvar, eps=eps0)
             compare['mlmc_same_precision_sap_only'] = dict(value=sval, ms_per_step=sms / cs, detail=sdet)
         if prec == M.FP32 and 'fp64' in arms:
-            M.mgmlmc_set_solver(ctx, precision=M.FP64, **SOLVER)
-            step(k0)
-            fres, fms = timed(k0, cs)
-            fval, fdet = time_to_variance(merge_terms(fres), 1, fms / cs, cs, var_of=mvar, eps=eps0)
-            # error of the mixed-precision estimate against FP64, per term, on
-            # the same samples (the first cs timed steps)
-            am, af = merge_terms(results[:cs]), merge_terms(fres)
+            # all-FP64 MG-MLMC (the plain method on this GPU), SAP smoother:
+            # the same samples, fewer per step on a large lattice (FP64
+            # Krylov bases); the costs per sample enter with the variances of
+            # the main run
+            M.mgmlmc_release_workspaces(ctx)
+            M.mgmlmc_set_solver(ctx, precision=M.FP64, **dict(wl['solver'], fine_batch=wl['fp64_fine_n']))
+            fn, cn = wl['fp64_fine_n'], wl['fp64_coarse_n']
+            fcs = 1 if big else cs
+            if not big:
+                step(k0, fine_n=fn, coarse_n=cn)
+            fres, fms = timed(k0, fcs, fine_n=fn, coarse_n=cn)
+            fval, fdet = time_to_variance(merge_terms(fres), 1, fms / fcs, fcs, var_of=mvar, eps=eps0)
+            fp64_samples = [M.mgmlmc_last_samples(ctx, i, r['n']) for i, r in enumerate(fres[-1])]
+            compare['mlmc_fp64'] = dict(value=fval, ms_per_step=fms / fcs, steps=fcs, fine_n=fn, coarse_n=cn,
+                                        detail=fdet)
+            if not big:
+                pres, pms = timed(k0, 1, M.EST_PLAIN)
+                p64, _ = time_to_variance(merge_terms(pres), 1, pms, 1, var_of=pvar, eps=eps0)
+                compare['plain_hutchinson_fp64'] = dict(value=p64, ms_per_step=pms)
+            M.mgmlmc_release_workspaces(ctx)
+            # the learned + mixed solver on the FP64 arm's last samples: the
+            # largest relative difference of the per-sample values, per term
+            M.mgmlmc_set_solver(ctx, precision=prec, **main_solver)
+            step(k0 + fcs - 1, fine_n=fn, coarse_n=cn)
             rel = {}
-            for t in sorted(af):
-                mu_m, mu_f = stats_of(am[t])[0], stats_of(af[t])[0]
-                rel[str(t)] = abs(mu_m - mu_f) / abs(mu_f) if mu_f != 0 else abs(mu_m)
-            compare['mlmc_fp64'] = dict(value=fval, ms_per_step=fms / cs, detail=fdet,
-                                        mixed_vs_fp64_rel_diff=rel)
-            pres, pms = timed(k0, 1, M.EST_PLAIN)
-            p64, p64d = time_to_variance(merge_terms(pres), 1, pms, 1, var_of=pvar, eps=eps0)
-            compare['plain_hutchinson_fp64'] = dict(value=p64, ms_per_step=pms)
+            for i, xf in enumerate(fp64_samples):
+                xm = M.mgmlmc_last_samples(ctx, i, len(xf))
+                rel[str(fres[-1][i]['term'])] = float(np.max(np.abs(xm - xf)) / max(np.max(np.abs(xf)), 1e-300))
+            compare['mlmc_fp64']['mixed_vs_fp64_max_rel_diff'] = rel
         M.mgmlmc_set_solver(ctx, precision=prec, **main_solver)
 
     e2e = None
     if not args.no_e2e and rank == 0:
         # the whole job through the ABI, wall clock: the gauge field from
-        # pinned host memory, the hierarchy, then estimate_trace calls (each
-        # returns its term results to the host)
-        Uh = torch.from_numpy(U.view(np.float64)).pin_memory()
+        # pinned host memory, the hierarchy, the network weights, then
+        # estimate_trace calls (each returns its term results to the host);
+        # network training enters with its measured wall time
+        Uh = torch.empty(int(np.prod(wl['dims'])) * 72, dtype=torch.float64).pin_memory()
+        M.mgmlmc_get_gauge(ctx, Uh.numpy(), on_device=False)
+        W = None
+        if args.learned > 0:
+            W = np.zeros(2 * M.mgmlmc_learned_size(ctx))
+            M.mgmlmc_learned_weights(ctx, W, 0)
         torch.cuda.synchronize()
         t0 = time.time()
         M.mgmlmc_set_gauge(ctx, Uh.numpy(), on_device=False)
         M.mgmlmc_set_mass(ctx, m0)
-        M.mgmlmc_build_hierarchy(ctx, mgp)
+        M.mgmlmc_build_hierarchy(ctx, M.mg_params(wl['blocks'], wl['ntv'], setup_rounds=wl['setup_rounds'],
+                                                  setup_iters=wl['setup_iters'], seed=wl['tv_seed']))
+        if W is not None:
+            M.mgmlmc_learned_weights(ctx, W, 1)
         torch.cuda.synchronize()
         t_build = time.time() - t0
         t1 = time.time()
@@ -753,18 +921,16 @@ def main():
         for k in range(E2E_STEPS):
             step(40001 + k)
         step_s = (time.time() - t1) / E2E_STEPS
-        e2e = dict(value=e2e_time_to_variance(t_build, t_first, step_s, value, ms_per_step * 1e-3), unit='s',
-                   h2d_bytes_per_step=0, d2h_bytes_per_step=int(nterm * 2 * B * 16),
-                   setup_h2d_bytes=int(U.nbytes), setup_s=t_build, first_step_s=t_first, step_s=step_s,
-                   steps=E2E_STEPS,
-                   note='wall clock through the ABI: gauge field from pinned host memory and hierarchy setup, '
-                        'then estimate_trace steps at their end-to-end cost to the same eps; a step takes '
-                        'no input bytes (its Z4 noise is drawn on the device from counters) and reads '
-                        'its per-sample values back')
+        nterm = len(results[0])
+        e2e = dict(value=t_train + e2e_time_to_variance(t_build, t_first, step_s, value, ms_per_step * 1e-3),
+                   unit='s', h2d_bytes_per_step=0,
+                   d2h_bytes_per_step=int(16 * sum(term_counts(M, wl, M.EST_ORTHOGONAL, L)) + 88 * nterm),
+                   setup_h2d_bytes=int(Uh.numel() * 8), setup_s=t_build, train_s=t_train, first_step_s=t_first,
+                   step_s=step_s, steps=E2E_STEPS)
+        del Uh
 
-    # Sec. 5: test vectors computed to a small eigen-residual.  Last, because
-    # it replaces the level-0 test vectors of the context for good.
-    if rank == 0 and args.compare_steps > 0 and 'refined' in arms and args.refine_iters > 0:
+    # Sec. 5 (16^4 workload): test vectors computed to a small eigen-residual
+    if rank == 0 and cs > 0 and not big and 'refined' in arms and args.refine_iters > 0:
         rough_tv = M.mgmlmc_get_test_vectors(ctx, 0) if 'augmented' in arms else None
         torch.cuda.synchronize()
         t0 = time.time()
@@ -779,10 +945,7 @@ def main():
         compare['mlmc_refined_test_vectors'] = dict(
             value=rval, ms_per_step=rms / cs, setup_s=rsec, value_with_setup=rval + rsec, steps=rsteps,
             block=NTV[0] + REFINE_BLOCK_EXTRA, eig_tol=REFINE_EIG_TOL, solve_tol=REFINE_SOLVE_TOL,
-            eig_res_max=float(rh.max()), eig_res=[float(x) for x in rh], theta=[float(x) for x in th],
-            detail=rdet)
-        # more test vectors as well as more accurate ones (Sec. 5 raises N_tv
-        # too): the rough and the refined level-0 vectors together
+            eig_res_max=float(rh.max()), detail=rdet)
         if rough_tv is not None:
             try:
                 aug = np.ascontiguousarray(np.concatenate([rough_tv, M.mgmlmc_get_test_vectors(ctx, 0)]))
@@ -804,31 +967,87 @@ def main():
                 compare['mlmc_rough_plus_refined_test_vectors'] = dict(error=str(exc)[:300])
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu and 'oracle_plain' in wl:
-        cpu = cpu_baseline(m0, wl, oracle_threads(args.oracle_threads))
+    if rank == 0 and world == 1 and not args.no_cpu and 'oracle_plain' in mass:
+        cpu = cpu_baseline(mass['m0'], mass, oracle_threads(args.oracle_threads), wl)
 
     if rank == 0:
-        line = {
-            'metric': METRIC, 'value': value, 'unit': 's', 'n_gpus': world, 'steps': args.steps,
-            'warmup': args.warmup, 'ms_per_step': ms_per_step, 'higher_is_better': False,
-            'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64' if prec == M.FP64 else 'f32+f64',
-            'data': 'synthetic',
-            'config': {'workload': '16^4 Wilson-Dirac, SU(3) exp(i 0.4 H) seed 1002, m0 %.4f, orthogonal '
-                                   'MG-MLMC 3 levels (4^4, 2^4 aggregates, 16 tv), SAP%s-MG FGMRES, Z4 batch %d '
-                                   'per term per step, solves to 1e-12'
-                                   % (m0, ' + learned(%d ch)' % args.learned if args.learned else '', B),
-                       'global_batch': B * nterm * world, 'lattice': list(DIMS), 'rel_eps': REL_EPS,
-                       'l2': 'flushed between steps (256 MB write)', 'parallelism': 'samples sharded, dp%d' % world},
-            'dslash_hbm': dslash_32, 'setup_s': t_setup, 'learned': train, 'learned_fallbacks': M.mgmlmc_learned_stats(ctx),
-            'detail': det, 'compare': compare, 'roofline': roof, 'dslash': dslash,
-            'clocks': clk, 'e2e': e2e, 'gpu_launches': launches,
-            'kernel_stats': {KERNELS[c]: kst[c] for c in kst}, 'group_stats': gst, 'cpu_baseline': cpu,
-        }
-        print(json.dumps(line))
+        full = dict(detail=det, compare=compare, dslash_hbm=dslash_32, kernel_stats={KERNELS[c]: kst[c] for c in kst},
+                    group_stats=gst, learned=train, validation=check, roofline=roof, e2e=e2e, cpu_baseline=cpu)
+        if args.detail_out:
+            with open(args.detail_out, 'w') as f:
+                json.dump(full, f, indent=1)
+        print(json.dumps(compact_line(args, wl, world, value, ms_per_step, launches, clk, det, compare,
+                                      dslash_32, dslash, roof, check, train, M, prec, e2e, cpu, t_setup, kst,
+                                      gst, prof_ms)))
     M.mgmlmc_destroy(ctx)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _r(x, d=4):
+    """Round for the compact line (significant digits)."""
+    if x is None or not isinstance(x, float) or x == 0 or not math.isfinite(x):
+        return x
+    return float('%.*g' % (d, x))
+
+
+def compact_line(args, wl, world, value, ms_per_step, launches, clk, det, compare, dslash_32, dslash, roof,
+                 check, train, M, prec, e2e, cpu, t_setup, kst, gst, prof_ms):
+    """The one JSON line: the summaries first, the contract's keys last (the
+    driver keeps the line's tail); the full detail goes to --detail-out."""
+    terms = {t: [_r(v['mean'][0], 7), _r(v['var']), _r(v['cost_s']), v['n'], _r(v['iters'], 3)]
+             for t, v in det['terms'].items()}
+    arms = {k: dict(value=_r(v.get('value')), ms_per_step=_r(v.get('ms_per_step')),
+                    **({'error': v['error']} if 'error' in v else {}),
+                    **({'mixed_vs_fp64_max_rel_diff': {t: _r(x, 2) for t, x in v['mixed_vs_fp64_max_rel_diff'].items()}}
+                       if 'mixed_vs_fp64_max_rel_diff' in v else {}),
+                    **({'setup_s': _r(v['setup_s'])} if 'setup_s' in v else {}))
+            for k, v in compare.items()}
+    ds = None
+    if dslash_32:
+        ds = {k: dict(gbs=_r(v['achieved_gbs']), frac=_r(v['frac_of_measured_hbm'], 3))
+              for k, v in dslash_32.items() if isinstance(v, dict)}
+    lat = 'x'.join(str(d) for d in wl['dims'])
+    line = {
+        'terms': terms, 'terms_key': '[mean_re, var, cost_s, n, iters]',
+        'group_ms': {k: _r(v['ms']) for k, v in gst.items()},
+        'kernel_ms': {k: _r(kst[c]['ms']) for c, k in KERNELS.items() if kst[c]['launches']},
+        'profiled_step_ms': _r(prof_ms),
+        'learned': (dict(channels=args.learned, loss_init=_r(train['loss_init']), loss_last=_r(train['loss_last']),
+                         pairs=train['pairs'], trained_on=train.get('trained_on'),
+                         fallbacks=train.get('fallbacks')) if train else None),
+        'setup_s': _r(t_setup),
+        'dslash_hbm_32x32x32x32': ds,
+        'dslash_in_step': dict(gbs=_r(dslash['achieved_gbs']), frac=_r(dslash['frac_of_measured_hbm'], 3),
+                               launches=dslash['launches']) if dslash else None,
+        'compare': arms,
+        'mlmc_check': ({k: (_r(v) if isinstance(v, float) else v) for k, v in check.items() if k != 'trace'}
+                       if check else None),
+        'metric': METRIC, 'value': value, 'unit': 's', 'n_gpus': world, 'steps': args.steps,
+        'warmup': args.warmup, 'ms_per_step': ms_per_step, 'higher_is_better': False, 'scaling': 'weak',
+        'vs_baseline': None, 'dtype': 'f64' if prec == M.FP64 else 'f32+f64', 'data': 'synthetic',
+        'config': {'workload': '%s Wilson-Dirac, SU(3) exp(i %.1f H) seed %d (%s), m0 %.4f, orthogonal MG-MLMC %d '
+                               'levels (%s aggregates, %s tv), SAP%s-MG FGMRES(%d) in FP64 defect correction, Z4 '
+                               '%d samples per fine-level term and %d per coarse term per step, fine solves in '
+                               'blocks of %d rhs, all solves to 1e-12'
+                               % (lat, wl['eps'], wl['gauge_seed'], 'device generator' if wl['gauge'] == 'device'
+                                  else 'host', wl['m0'], len(wl['blocks']) + 1,
+                                  ', '.join('%d^4' % b[0] for b in wl['blocks']), '/'.join(map(str, wl['ntv'])),
+                                  ' + learned(%d ch)' % args.learned if args.learned else '',
+                                  wl['solver']['restart'], wl['fine_n'], wl['coarse_n'],
+                                  wl['solver'].get('fine_batch') or wl['batch']),
+                   'global_batch': sum(v['n'] for v in det['terms'].values()) // max(1, args.steps) * world,
+                   'lattice': list(wl['dims']), 'rel_eps': REL_EPS,
+                   'l2': 'flushed between steps (256 MB write); every fine-level launch moves > 1 GB',
+                   'parallelism': 'samples sharded, dp%d' % world},
+        'roofline': ({k: (_r(v) if isinstance(v, float) else v) for k, v in roof.items()} if roof else None),
+        'clocks': clk, 'gpu_launches': launches,
+        'e2e': ({k: (_r(v) if isinstance(v, float) else v) for k, v in e2e.items()} if e2e else None),
+        'cpu_baseline': ({k: (_r(v) if isinstance(v, float) else v) for k, v in cpu.items()
+                          if k not in ('single_core',)} if cpu else None),
+    }
+    return line
 
 
 if __name__ == '__main__':

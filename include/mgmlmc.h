@@ -211,6 +211,11 @@ mgmlmc_status mgmlmc_set_gauge(mgmlmc_ctx *ctx, const double *U, int on_device);
  * free field.  Invalidates the hierarchy; MGMLMC_ERR_ARG for a non-finite
  * eps. */
 mgmlmc_status mgmlmc_gen_gauge(mgmlmc_ctx *ctx, double eps, uint64_t seed);
+/* Copy the context's gauge field out, in the layout mgmlmc_set_gauge takes
+ * (4 * V * 9 complex double), to a host (on_device = 0) or device
+ * (on_device = 1) buffer: checkpoints of a field drawn by mgmlmc_gen_gauge,
+ * or its transfer to another context. */
+mgmlmc_status mgmlmc_get_gauge(mgmlmc_ctx *ctx, double *U, int on_device);
 /* Bare mass m0 of the Wilson operator.  Invalidates the hierarchy. */
 mgmlmc_status mgmlmc_set_mass(mgmlmc_ctx *ctx, double m0);
 /* Solver parameters (defaults: tol 1e-12, max_iter 2000, restart 16,

@@ -79,6 +79,13 @@ mgmlmc_status mgmlmc_set_gauge(mgmlmc_ctx *ctx, const double *U, int on_device) 
   });
 }
 
+mgmlmc_status mgmlmc_get_gauge(mgmlmc_ctx *ctx, double *U, int on_device) {
+  return guard(ctx, [&] {
+    if (!U) throw mg::Error(MGMLMC_ERR_ARG, "U is NULL");
+    E(ctx).get_gauge(U, on_device != 0);
+  });
+}
+
 mgmlmc_status mgmlmc_deflation_build(mgmlmc_ctx *ctx, int k, int iters, double tol, uint64_t seed,
                                      double *exact, double *seconds) {
   return guard(ctx, [&] {

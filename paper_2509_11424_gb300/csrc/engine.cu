@@ -299,6 +299,13 @@ void Engine::set_gauge(const double *U, bool on_device) {
   gauge_derived();
 }
 
+void Engine::get_gauge(double *U, bool on_device) {
+  if (!have_gauge_) throw Error(MGMLMC_ERR_STATE, "no gauge field");
+  MG_CUDA(cudaMemcpyAsync(U, levels_[0].U64, (size_t)fine_.V * 36 * sizeof(double2),
+                          on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, stream));
+  sync();
+}
+
 void Engine::gen_gauge(double eps, uint64_t seed) {
   if (!std::isfinite(eps)) throw Error(MGMLMC_ERR_ARG, "eps must be finite");
   gauge_generate(levels_[0].U64, (int64_t)fine_.V * 4, eps, seed, stream);

@@ -91,6 +91,7 @@ class Engine {
   Engine &operator=(const Engine &) = delete;
 
   void set_gauge(const double *U, bool on_device);
+  void get_gauge(double *U, bool on_device);
   // U = exp(i eps H) generated on the device (kernels.h gauge_generate)
   void gen_gauge(double eps, uint64_t seed);
   void set_mass(double m0);

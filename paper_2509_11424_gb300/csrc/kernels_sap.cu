@@ -169,7 +169,7 @@ template <typename T>
 __global__ void __launch_bounds__(256, 2) sap_block_kernel(C<T> *__restrict__ r, C<T> *__restrict__ z,
                                                         C<T> *__restrict__ e_out,
                                                         const C<T> *__restrict__ U, SapGeom sg,
-                                                        T diag, int color, int iters) {
+                                                        T diag, int color, int iters, int nrhs) {
   extern __shared__ unsigned char smem_raw[];
   const int sites = sg.sites;
   C<T> *Us = reinterpret_cast<C<T> *>(smem_raw);  // [4][9][sites]
@@ -177,12 +177,14 @@ __global__ void __launch_bounds__(256, 2) sap_block_kernel(C<T> *__restrict__ r,
   T *red = reinterpret_cast<T *>(rho + sites * 12);  // reduction scratch [3 * warps]
   T *out3 = red + 96;
   const int64_t n = sg.g.n();
-  const int rr = blockIdx.y;
+  // the right-hand side varies fastest over the grid: the CTAs of one block
+  // run together and read its links from L2 after the first of them
+  const int rr = (int)(blockIdx.x % (unsigned)nrhs);
   C<T> *rv = r + rr * n;
   C<T> *zv = z + rr * n;
   C<T> *ev = e_out + rr * n;
   int bc[4];
-  active_block(sg, blockIdx.x, color, bc);
+  active_block(sg, (int)(blockIdx.x / (unsigned)nrhs), color, bc);
   const int ls = threadIdx.x;
   int lc[4];
   {
@@ -278,16 +280,19 @@ __device__ __forceinline__ void cross_pair(const C<T> *__restrict__ ev, const C<
 
 template <typename T>
 __global__ void sap_boundary_kernel(C<T> *__restrict__ r, const C<T> *__restrict__ e,
-                                    const C<T> *__restrict__ U, SapGeom sg, int color) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+                                    const C<T> *__restrict__ U, SapGeom sg, int color, int nrhs) {
+  // right-hand side fastest over the grid: the CTAs of one site range share
+  // its links through L2
+  const int rr = (int)(blockIdx.x % (unsigned)nrhs);
+  const int s = (int)(blockIdx.x / (unsigned)nrhs) * blockDim.x + threadIdx.x;
   if (s >= sg.g.V) return;
   int c[4];
   sg.g.coords(s, c);
   const int par = (c[0] / sg.b[0] + c[1] / sg.b[1] + c[2] / sg.b[2] + c[3] / sg.b[3]) & 1;
   if (par == color) return;  // residual of active blocks was written by the block kernel
   const int64_t n = sg.g.n();
-  const C<T> *ev = e + blockIdx.y * n;
-  C<T> *rv = r + blockIdx.y * n;
+  const C<T> *ev = e + rr * n;
+  C<T> *rv = r + rr * n;
   C<T> acc[12];
 #pragma unroll
   for (int i = 0; i < 12; ++i) acc[i] = mk<T>((T)0, (T)0);
@@ -337,10 +342,11 @@ void sap_sweep(C<T> *r, C<T> *z, C<T> *e, const C<T> *U, Geom g, const int b[4],
   smem_optin((const void *)sap_block_kernel<T>, (int)(220 * 1024));
   if (sm > 220 * 1024) throw Error(1, "SAP block too large for shared memory");
   for (int color = 0; color < 2; ++color) {
-    sap_block_kernel<T><<<dim3(nblocks / 2, nrhs), sg.sites, sm, s>>>(r, z, e, U, sg, (T)(4.0 + m0),
-                                                                      color, block_iters);
+    sap_block_kernel<T><<<(unsigned)(nblocks / 2) * (unsigned)nrhs, sg.sites, sm, s>>>(
+        r, z, e, U, sg, (T)(4.0 + m0), color, block_iters, nrhs);
     MG_LAUNCH_CHECK();
-    sap_boundary_kernel<T><<<dim3(div_up(g.V, 128), nrhs), 128, 0, s>>>(r, e, U, sg, color);
+    sap_boundary_kernel<T><<<(unsigned)div_up(g.V, 128) * (unsigned)nrhs, 128, 0, s>>>(r, e, U, sg, color,
+                                                                                    nrhs);
     MG_LAUNCH_CHECK();
   }
 }

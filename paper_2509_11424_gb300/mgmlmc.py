@@ -112,6 +112,7 @@ _SIGNATURES = {
     'mgmlmc_coarsest_trace': [_P, ctypes.POINTER(_D), ctypes.POINTER(_D)],
     'mgmlmc_last_samples': [_P, _I, _P, _I, ctypes.POINTER(_I)],
     'mgmlmc_release_workspaces': [_P],
+    'mgmlmc_get_gauge': [_P, _P, _I],
     'mgmlmc_connected_correlator': [_P, _I, _I, _U64, _U64, _P, _P, ctypes.POINTER(_I)],
     'mgmlmc_disconnected_loop': [_P, _I, _I, _I, _U64, _U64, _P, _P, ctypes.POINTER(_I)],
     'mgmlmc_apply': [_P, _I, _I, _I, _P, _P, _I],
@@ -286,6 +287,12 @@ def mgmlmc_last_samples(ctx, index, max_samples):
     n = _I()
     _check(ctx, lib().mgmlmc_last_samples(ctx, index, ptr(out), max_samples, ctypes.byref(n)))
     return out[:2 * n.value].view(np.complex128).copy()
+
+
+def mgmlmc_get_gauge(ctx, U, on_device=None):
+    if on_device is None:
+        on_device = bool(getattr(U, 'is_cuda', False))
+    _check(ctx, lib().mgmlmc_get_gauge(ctx, ptr(U), int(on_device)))
 
 
 def mgmlmc_release_workspaces(ctx):
