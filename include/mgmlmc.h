@@ -102,7 +102,10 @@ typedef struct {
 } mgmlmc_mg_params;
 
 /* Level solver: FGMRES(restart) preconditioned by a multigrid K-cycle that
- * starts at the level being solved (Sec. 4: all levels to 1e-12). */
+ * starts at the level being solved (Sec. 4: all levels to 1e-12).  With
+ * MGMLMC_FP32 each inner FP32 solve of the FP64 defect correction also ends
+ * when a restart cycle fails to halve its true residual (the precision floor
+ * of FP32 on an ill-conditioned level); the outer loop continues from it. */
 typedef struct {
   double tol;          /* relative residual target ||b - D x|| / ||b|| */
   int max_iter;        /* cap on outer FGMRES iterations per solve */
@@ -119,6 +122,8 @@ typedef struct {
                           else 2^4); otherwise MR is used. */
   int sap_iters;       /* MR iterations inside each SAP block */
   int coarse_smoother_steps; /* MR steps of the smoother on levels >= 1 */
+  int coarse_restart;  /* FGMRES restart length of the solves on levels >= 1
+                          (their vectors are small), 1 .. 64; 0 = restart */
   int fine_batch;      /* memory bound of the fine level: mgmlmc_estimate_trace
                           solves level-0 systems (the O_0, F_0, M_0 and plain
                           terms) in blocks of at most fine_batch right-hand
@@ -408,6 +413,15 @@ mgmlmc_status mgmlmc_get_coarse_op(mgmlmc_ctx *ctx, int level, double *out);
  * callers that switch between configurations of very different memory
  * footprint on a large lattice (e.g. FP32 and FP64 solvers, or batch sizes). */
 mgmlmc_status mgmlmc_release_workspaces(mgmlmc_ctx *ctx);
+/* Failure injection for tests (process-wide, not in the paper): the
+ * coarse-stencil kernels arm the mbarrier of their shared-memory staging
+ * copy with extra_bytes (a multiple of 16, at most 4096) more than the copy
+ * delivers, so the copy lands in full but the barrier never completes: the
+ * kernel's bounded wait (1 s of the GPU's global timer, then a second one
+ * before the block leaves) runs out, the kernel sets its error flag and the
+ * call that launched it returns MGMLMC_ERR_CUDA with the context usable.  0
+ * (the default) restores normal operation. */
+mgmlmc_status mgmlmc_test_staging_extra(mgmlmc_ctx *ctx, int extra_bytes);
 /* Statistics of the last solve: outer iterations (max over rhs) and true
  * relative residual (max over rhs). */
 mgmlmc_status mgmlmc_last_solve_stats(const mgmlmc_ctx *ctx, int *iters, double *residual);
@@ -497,6 +511,18 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
 
 /* Kernels with selectable variants. */
 #define MGMLMC_VARIANT_DSLASH_FP32 0
+/* The FP32 coarse stencil D_l, l >= 1 (Galerkin, Sec. 2.2): 0 = FP32 on the
+ * CUDA cores (default); 1 .. 3 = the 5th-generation tensor cores (tcgen05.mma
+ * kind::tf32, operands staged in shared memory by a bulk copy, FP32
+ * accumulators in tensor memory) for levels with 32 dofs per site (N_tv =
+ * 16; other levels keep variant 0): the products take the operands as TF32
+ * (10-bit mantissa, relative rounding <= 2^-11 per operand) and accumulate
+ * in FP32, so results differ from variant 0 by that rounding; the variants
+ * differ only in how the accumulator is read back; -2 = autotune between 0
+ * and 1 per (level, nrhs) on the first call outside graph capture (opt-in,
+ * since the choice changes the rounding).  Inside the solver the FP64
+ * defect correction decides convergence with the true residual either way. */
+#define MGMLMC_VARIANT_STENCIL_FP32 1
 /* Choose the variant of a kernel for later calls: for the FP32 fine Wilson
  * operator -2 = autotune (default: the first call per right-hand-side count
  * outside graph capture times every variant on that call's operands and
@@ -511,7 +537,7 @@ mgmlmc_status mgmlmc_set_kernel_variant(mgmlmc_ctx *ctx, int kernel, int variant
 /* Number of fixed variants of a kernel (-1 for an unknown kernel). */
 int mgmlmc_kernel_variants(int kernel);
 /* The variant that calls with nrhs right-hand sides use (-2 while an
- * autotuned choice is not yet made). */
+ * autotuned choice is not yet made; for the stencil, that of level 1). */
 mgmlmc_status mgmlmc_get_kernel_variant(const mgmlmc_ctx *ctx, int kernel, int nrhs,
                                         int *variant);
 

@@ -202,6 +202,14 @@ mgmlmc_status mgmlmc_last_samples(mgmlmc_ctx *ctx, int index, double *out, int m
   });
 }
 
+mgmlmc_status mgmlmc_test_staging_extra(mgmlmc_ctx *ctx, int extra_bytes) {
+  return guard(ctx, [&] {
+    if (extra_bytes < 0 || extra_bytes > 4096 || extra_bytes % 16)
+      throw mg::Error(MGMLMC_ERR_ARG, "extra_bytes must be a multiple of 16 in 0 .. 4096");
+    mg::set_staging_extra_bytes((unsigned)extra_bytes);
+  });
+}
+
 mgmlmc_status mgmlmc_release_workspaces(mgmlmc_ctx *ctx) {
   return guard(ctx, [&] { E(ctx).release_workspaces(); });
 }
@@ -330,6 +338,7 @@ mgmlmc_status mgmlmc_apply(mgmlmc_ctx *ctx, int op_flags, int level, int precisi
       case MGMLMC_OP_D:
         if (dp) e.apply_D<double>(level, (const double2 *)in, (double2 *)out, nrhs);
         else e.apply_D<float>(level, (const float2 *)in, (float2 *)out, nrhs);
+        if (level > 0) e.check_staging();  // a bounded wait of the stencil ran out
         break;
       case MGMLMC_OP_RESTRICT:
         if (dp) e.restrict_to<double>(level, (const double2 *)in, (double2 *)out, nrhs);
@@ -481,13 +490,16 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
 }
 
 int mgmlmc_kernel_variants(int kernel) {
-  return kernel == MGMLMC_VARIANT_DSLASH_FP32 ? mg::wilson_fp32_variants() : -1;
+  if (kernel == MGMLMC_VARIANT_DSLASH_FP32) return mg::wilson_fp32_variants();
+  if (kernel == MGMLMC_VARIANT_STENCIL_FP32) return mg::Engine::stencil_variants();
+  return -1;
 }
 
 mgmlmc_status mgmlmc_set_kernel_variant(mgmlmc_ctx *ctx, int kernel, int variant) {
   return guard(ctx, [&] {
-    if (kernel != MGMLMC_VARIANT_DSLASH_FP32) throw mg::Error(MGMLMC_ERR_ARG, "unknown kernel");
-    E(ctx).set_dslash_variant(variant);
+    if (kernel == MGMLMC_VARIANT_DSLASH_FP32) E(ctx).set_dslash_variant(variant);
+    else if (kernel == MGMLMC_VARIANT_STENCIL_FP32) E(ctx).set_stencil_variant(variant);
+    else throw mg::Error(MGMLMC_ERR_ARG, "unknown kernel");
   });
 }
 
@@ -495,9 +507,10 @@ mgmlmc_status mgmlmc_get_kernel_variant(const mgmlmc_ctx *cctx, int kernel, int 
                                         int *variant) {
   mgmlmc_ctx *ctx = const_cast<mgmlmc_ctx *>(cctx);
   return guard(ctx, [&] {
-    if (kernel != MGMLMC_VARIANT_DSLASH_FP32) throw mg::Error(MGMLMC_ERR_ARG, "unknown kernel");
     if (!variant) throw mg::Error(MGMLMC_ERR_ARG, "variant is null");
-    *variant = E(ctx).dslash_variant(nrhs);
+    if (kernel == MGMLMC_VARIANT_DSLASH_FP32) *variant = E(ctx).dslash_variant(nrhs);
+    else if (kernel == MGMLMC_VARIANT_STENCIL_FP32) *variant = E(ctx).stencil_variant(1, nrhs);
+    else throw mg::Error(MGMLMC_ERR_ARG, "unknown kernel");
   });
 }
 

@@ -164,6 +164,21 @@ std::atomic<int64_t> &launch_counter();
 
 inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
+// Device-side waits (mbarrier polls) give up after kWaitNs of the GPU's
+// global timer and report through an error flag instead of hanging.
+constexpr unsigned long long kWaitNs = 1000000000ull;  // 1 s
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Failure injection for tests: extra bytes the staging barriers of the coarse
+// stencil kernels expect beyond what their bulk copy delivers (0 in normal
+// operation; a positive value makes their bounded wait run out).
+void set_staging_extra_bytes(unsigned bytes);
+unsigned staging_extra_bytes();
+
 // Raise the dynamic shared-memory limit of kernel `func` to `bytes` on the
 // current device.  The attribute is per device, so the call is made once per
 // (kernel, device) and remembered under a lock: launchers may run on several

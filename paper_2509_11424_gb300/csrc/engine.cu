@@ -331,8 +331,13 @@ void Engine::set_mass(double m0) {
   free_hierarchy();
 }
 
+int Engine::restart_of(int l) const {
+  return (l > 0 && sp_.coarse_restart > 0) ? sp_.coarse_restart : sp_.restart;
+}
+
 void Engine::set_solver(const mgmlmc_solver_params &p) {
   if (!(p.tol > 0.0) || p.max_iter < 1 || p.restart < 1 || p.restart > 64 || p.smoother_steps < 0 ||
+      p.coarse_restart < 0 || p.coarse_restart > 64 ||
       p.coarse_iters < 1 || p.coarse_iters > 64 ||
       (p.precision != MGMLMC_FP64 && p.precision != MGMLMC_FP32) ||
       (p.precision == MGMLMC_FP32 && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)) ||
@@ -367,6 +372,7 @@ void Engine::free_hierarchy() {
       dfree(L.A64);
       dfree(L.AT64);
       dfree(L.AT32);
+      dfree(L.ATC);
     }
     L.has_next = false;
   }
@@ -390,6 +396,54 @@ int Engine::dslash_variant(int nrhs) const {
   if (dslash_force_ != -2) return dslash_force_;
   auto it = dslash_tuned_.find(nrhs);
   return it == dslash_tuned_.end() ? -2 : it->second;
+}
+
+int Engine::stencil_variants() { return 4; }
+
+void Engine::set_stencil_variant(int v) {
+  if (v < -2 || v == -1 || v >= stencil_variants()) throw Error(MGMLMC_ERR_ARG, "stencil variant out of range");
+  stencil_force_ = v;
+  stencil_tuned_.clear();
+  drop_graphs();
+}
+
+int Engine::stencil_variant(int l, int nrhs) const {
+  if (stencil_force_ != -2) return stencil_force_;
+  auto it = stencil_tuned_.find({l, nrhs});
+  return it == stencil_tuned_.end() ? -2 : it->second;
+}
+
+void Engine::stencil_run(int l, int v, const float2 *in, float2 *out, int nrhs) {
+  const Level &L = levels_[l];
+  if (v > 0 && L.ATC) stencil_apply_tc(in, out, L.ATC, L.g, nrhs, flag_dev_ + 1, v - 1, stream);
+  else stencil_apply<float>(in, out, L.AT32, L.g, nrhs, flag_dev_ + 1, stream);
+}
+
+// the tensor-core variants compute TF32 products, so the variant changes the
+// numbers: autotuning (-2) is an opt-in; every variant is timed on the
+// caller's operands and the fastest kept per (level, nrhs)
+int Engine::stencil_pick(int l, int nrhs, const float2 *in, float2 *out) {
+  if (stencil_force_ != -2) return levels_[l].ATC ? stencil_force_ : 0;
+  if (!levels_[l].ATC) return 0;
+  auto it = stencil_tuned_.find({l, nrhs});
+  if (it != stencil_tuned_.end()) return it->second;
+  if (capturing_) return 0;
+  EventPair ev;
+  int pick = 0;
+  float best = 1e30f;
+  // the read-back layout of the tensor-core kernel is fixed: variant 1
+  for (int v : {0, 1}) {
+    stencil_run(l, v, in, out, nrhs);
+    MG_CUDA(cudaEventRecord(ev.a, stream));
+    for (int rep = 0; rep < 3; ++rep) stencil_run(l, v, in, out, nrhs);
+    MG_CUDA(cudaEventRecord(ev.b, stream));
+    MG_CUDA(cudaEventSynchronize(ev.b));
+    float ms = 0.f;
+    MG_CUDA(cudaEventElapsedTime(&ms, ev.a, ev.b));
+    if (ms < best) { best = ms; pick = v; }
+  }
+  stencil_tuned_[{l, nrhs}] = pick;
+  return pick;
 }
 
 int Engine::dslash_pick(int nrhs, const float2 *in, float2 *out) {
@@ -442,9 +496,11 @@ template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int
     flops = 1368.0 * L.g.V * nrhs;
     cls = sizeof(T) == 8 ? K_WILSON64 : K_WILSON32;
   } else {
-    const C<T> *A;
-    if constexpr (sizeof(T) == 8) A = L.AT64; else A = L.AT32;
-    stencil_apply<T>(in, out, A, L.g, nrhs, flag_dev_ + 1, stream);
+    if constexpr (sizeof(T) == 8) {
+      stencil_apply<T>(in, out, L.AT64, L.g, nrhs, flag_dev_ + 1, stream);
+    } else {
+      stencil_run(l, stencil_pick(l, nrhs, in, out), in, out, nrhs);
+    }
     const double m = L.g.dof;
     bytes = (double)L.g.V * (9.0 * m * m + 2.0 * m * nrhs) * cs;
     flops = 8.0 * 9.0 * m * m * L.g.V * nrhs;
@@ -637,7 +693,8 @@ template <typename T> void Engine::precond_top(int l, const C<T> *r, C<T> *z, in
 // ------------------------------------------------------------------ FGMRES
 template <typename T>
 SolveInfo Engine::fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, int max_iter, int m,
-                         bool use_precond, bool fixed) {
+                         bool use_precond, bool fixed, bool stall_exit) {
+  double prev_worst = 1e300;
   const Level &L = levels_[l];
   const int64_t n = L.g.n();
   const int64_t vs = n * nrhs;
@@ -754,6 +811,14 @@ SolveInfo Engine::fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, in
       info.converged = false;
       break;
     }
+    // an inner solve of the defect correction ends at the precision floor
+    // of its arithmetic: a restart cycle that did not halve the true
+    // residual returns what it has (the FP64 outer loop continues from it)
+    if (stall_exit && worst > 0.5 * prev_worst) {
+      info.converged = false;
+      break;
+    }
+    prev_worst = worst;
   }
   info.iters = total;
   return info;
@@ -800,8 +865,8 @@ SolveInfo Engine::solve_mixed(int l, const double2 *b, double2 *x, int nrhs) {
     MG_LAUNCH_CHECK();
     if (l == 0) relayout<float, double>(r, r32, inv, levels_[0].g.V, nrhs, true, stream);
     else convert_scale<float, double>(r, r32, inv, n, nrhs, stream);
-    SolveInfo in = fgmres<float>(l, r32, e32, nrhs, sp_.inner_tol, sp_.max_iter - total,
-                                 sp_.restart, true, false);
+    SolveInfo in = fgmres<float>(l, r32, e32, nrhs, sp_.inner_tol, sp_.max_iter - total, restart_of(l),
+                                 true, false, true);
     total += in.iters;
     if (l == 0) relayout<double, float>(e32, t, rn, levels_[0].g.V, nrhs, false, stream);
     else convert_scale<double, float>(e32, t, rn, n, nrhs, stream);
@@ -831,7 +896,7 @@ SolveInfo Engine::solve(int l, const double2 *b, double2 *x, int nrhs) {
     try {
       info = sp_.precision == MGMLMC_FP32
                  ? solve_mixed(l, b, x, nrhs)
-                 : fgmres<double>(l, b, x, nrhs, sp_.tol, sp_.max_iter, sp_.restart, true, false);
+                 : fgmres<double>(l, b, x, nrhs, sp_.tol, sp_.max_iter, restart_of(l), true, false);
       ok = info.converged;
     } catch (const Error &e) {
       if (e.code != MGMLMC_ERR_NUMERIC && e.code != MGMLMC_ERR_NOT_CONVERGED) {
@@ -848,7 +913,7 @@ SolveInfo Engine::solve(int l, const double2 *b, double2 *x, int nrhs) {
       try {
         info = sp_.precision == MGMLMC_FP32
                    ? solve_mixed(l, b, x, nrhs)
-                   : fgmres<double>(l, b, x, nrhs, sp_.tol, sp_.max_iter, sp_.restart, true, false);
+                   : fgmres<double>(l, b, x, nrhs, sp_.tol, sp_.max_iter, restart_of(l), true, false);
       } catch (...) {
         sp_.smoother = MGMLMC_SMOOTHER_LEARNED;
         drop_graphs();
@@ -860,19 +925,10 @@ SolveInfo Engine::solve(int l, const double2 *b, double2 *x, int nrhs) {
   } else if (sp_.precision == MGMLMC_FP32) {
     info = solve_mixed(l, b, x, nrhs);
   } else {
-    info = fgmres<double>(l, b, x, nrhs, sp_.tol, sp_.max_iter, sp_.restart, true, false);
+    info = fgmres<double>(l, b, x, nrhs, sp_.tol, sp_.max_iter, restart_of(l), true, false);
   }
   last_solve = info;
-  {
-    // a TMA staging wait that ran out of its bound sets flag_dev_[1]
-    int tma_err = 0;
-    MG_CUDA(cudaMemcpyAsync(&tma_err, flag_dev_ + 1, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    sync();
-    if (tma_err) {
-      MG_CUDA(cudaMemsetAsync(flag_dev_ + 1, 0, sizeof(int), stream));
-      throw Error(MGMLMC_ERR_CUDA, "a shared-memory staging copy did not complete within its bounded wait");
-    }
-  }
+  check_staging();
   if (!info.converged)
     throw Error(MGMLMC_ERR_NOT_CONVERGED,
                 "level " + std::to_string(l) + " solve stopped after " + std::to_string(info.iters) +
@@ -903,6 +959,10 @@ void Engine::galerkin(int l) {
   }
   stencil_transpose<double>(c.A64, c.AT64, (int64_t)c.g.V * 9, dofc, stream);
   stencil_transpose<float>(c.A64, c.AT32, (int64_t)c.g.V * 9, dofc, stream);
+  if (stencil_tc_supported(c.g)) {
+    c.ATC = dalloc<float>(stencil_tc_floats(c.g));
+    stencil_tile_tc(c.A64, c.ATC, c.g, stream);
+  }
 }
 
 void Engine::build_hierarchy(const mgmlmc_mg_params &p) {
@@ -1061,6 +1121,19 @@ void Engine::setup_test_vectors(int l, double2 *V, int ntv, const mgmlmc_mg_para
                            "gssck", "gsik"}) {
     ws_release(name, l, true);
     ws_release(name, l, false);
+  }
+}
+
+void Engine::check_staging() {
+  // a staging wait of a coarse-stencil kernel that ran out of its bound sets
+  // flag_dev_[1] (2: CUDA-core kernel, 3: tensor-core kernel)
+  int tma_err = 0;
+  MG_CUDA(cudaMemcpyAsync(&tma_err, flag_dev_ + 1, sizeof(int), cudaMemcpyDeviceToHost, stream));
+  sync();
+  if (tma_err) {
+    MG_CUDA(cudaMemsetAsync(flag_dev_ + 1, 0, sizeof(int), stream));
+    sync();
+    throw Error(MGMLMC_ERR_CUDA, "a shared-memory staging copy did not complete within its bounded wait");
   }
 }
 

@@ -23,6 +23,7 @@ struct Level {
   double2 *A64 = nullptr;   // coarse stencil, canonical [V][9][dof][dof]
   double2 *AT64 = nullptr;  // the same blocks transposed [V][9][j][i] (apply)
   float2 *AT32 = nullptr;
+  float *ATC = nullptr;     // tensor-core tiles (32 dofs per site only), see stencil_tile_tc
   bool has_next = false;
   AggMap agg{};            // to level + 1
   double2 *P64 = nullptr;  // [X][c][k][row]
@@ -165,6 +166,9 @@ class Engine {
   // free every workspace (and the graphs that use them) except the levels'
   // test vectors; later calls allocate what they need again
   void release_workspaces();
+  // MGMLMC_ERR_CUDA (and the flag cleared) if a coarse-stencil kernel's
+  // bounded staging wait ran out since the last check; synchronises
+  void check_staging();
 
   void profile(bool on);
   KStat kstat(int cls);
@@ -176,6 +180,12 @@ class Engine {
   // fastest kept), 0 .. wilson_fp32_variants() - 1 = fixed
   void set_dslash_variant(int v);
   int dslash_variant(int nrhs) const;
+  // FP32 coarse stencil per rhs count: 0 = FP32 CUDA cores, 1.. = tcgen05
+  // TF32 (stencil_tc_layouts() read-back layouts), -2 = the fastest on the
+  // first call outside capture
+  void set_stencil_variant(int v);
+  int stencil_variant(int l, int nrhs) const;
+  static int stencil_variants();
 
  private:
   template <typename T> C<T> *ws(const std::string &name, int l, size_t count);
@@ -196,8 +206,10 @@ class Engine {
   template <typename T> void precond_top(int l, const C<T> *r, C<T> *z, int nrhs);
   // batched FGMRES; fixed = run exactly max_iter iterations with no host check
   template <typename T>
+  // stall_exit: stop once a restart cycle fails to halve the true residual
   SolveInfo fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, int max_iter, int m,
-                   bool use_precond, bool fixed);
+                   bool use_precond, bool fixed, bool stall_exit = false);
+  int restart_of(int l) const;  // FGMRES restart length of level l's solves
   SolveInfo solve_mixed(int l, const double2 *b, double2 *x, int nrhs);
   void galerkin(int l);
   void setup_test_vectors(int l, double2 *V, int ntv, const mgmlmc_mg_params &p);
@@ -263,6 +275,10 @@ class Engine {
   double defl_seconds_ = 0.0;
   void orthonormalise_cols(double2 *V, int k, int64_t n);
   std::map<int, int> dslash_tuned_;
+  int stencil_force_ = 0;
+  std::map<std::pair<int, int>, int> stencil_tuned_;  // (level, nrhs) -> variant
+  int stencil_pick(int l, int nrhs, const float2 *in, float2 *out);
+  void stencil_run(int l, int v, const float2 *in, float2 *out, int nrhs);
   int dslash_pick(int nrhs, const float2 *in, float2 *out);
 };
 

@@ -127,6 +127,17 @@ void wilson_split(const C<T> *in, C<T> *out9, const C<T> *U, Geom g, double m0, 
 template <typename T>
 void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, int *err,
                    cudaStream_t s);
+// Tensor-core (tcgen05 kind::tf32) coarse stencil for 32 dofs per site:
+// ATC holds each site's nine stacked [Re A_d; Im A_d] tiles in the MMA's
+// shared-memory image (stencil_tile_tc builds it from the canonical A);
+// FP32 vectors, TF32 products, FP32 accumulation.  layout selects how the
+// accumulator rows are read back (see kernels_tc.cu).  err[0] = 3 if a
+// bounded wait runs out.
+bool stencil_tc_supported(const Geom &g);
+size_t stencil_tc_floats(const Geom &g);
+void stencil_tile_tc(const double2 *A, float *ATC, const Geom &g, cudaStream_t s);
+void stencil_apply_tc(const float2 *in, float2 *out, const float *ATC, Geom g, int nrhs, int *err, int layout,
+                      cudaStream_t s);
 // AT = blockwise transpose of the canonical A[X][d][i][j] (nblocks = 9 V)
 template <typename To>
 void stencil_transpose(const double2 *A, C<To> *AT, int64_t nblocks, int m, cudaStream_t s);

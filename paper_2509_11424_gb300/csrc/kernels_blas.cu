@@ -382,6 +382,12 @@ std::atomic<int64_t> &launch_counter() {
   return c;
 }
 
+namespace {
+std::atomic<unsigned> g_staging_extra{0};
+}
+void set_staging_extra_bytes(unsigned bytes) { g_staging_extra.store(bytes); }
+unsigned staging_extra_bytes() { return g_staging_extra.load(); }
+
 void smem_optin(const void *func, int bytes) {
   static std::mutex mu;
   static std::map<std::pair<const void *, int>, int> done;  // (kernel, device) -> bytes set

@@ -170,8 +170,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *mbar, unsigned parity) {
 }
 // bounded wait: false (and *err set) if the copy did not land in time
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, unsigned parity, int *err) {
-  for (int it = 0; it < (1 << 22); ++it)
+  const unsigned long long t0 = global_ns();
+  for (int it = 0; it < (1 << 26); ++it) {
     if (mbar_try_wait(mbar, parity)) return true;
+    if ((it & 63) == 63 && global_ns() - t0 > kWaitNs) break;
+  }
   if (err) atomicExch(err, 2);
   return false;
 }
@@ -182,7 +185,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *mbar, unsigned parit
 // block entry is then read from shared memory for all right-hand sides.
 template <typename T, int RG>
 __global__ void stencil_tma_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ out,
-                                   const C<T> *__restrict__ AT, Geom g, int nrhs, int *err) {
+                                   const C<T> *__restrict__ AT, Geom g, int nrhs, int *err,
+                                   unsigned extra_tx) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t mbar;
   const int m = g.dof;
@@ -197,7 +201,7 @@ __global__ void stencil_tma_kernel(const C<T> *__restrict__ in, C<T> *__restrict
   if (tid == 0) mbar_init(&mbar, 1);
   __syncthreads();
   if (tid == 0) {
-    mbar_expect_tx(&mbar, bytes);
+    mbar_expect_tx(&mbar, bytes + extra_tx);  // extra_tx = 0 but in failure-injection tests
     bulk_g2s(As, AT + (int64_t)X * 9 * m * m, bytes, &mbar);
   }
   const int nb = g.neighbor(X, d);
@@ -625,7 +629,7 @@ void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, 
   const size_t sm_tma = (size_t)(9 * m * m + 2 * 9 * RG * m) * sizeof(C<T>);
   if (sm_tma <= 200 * 1024) {
     smem_optin((const void *)stencil_tma_kernel<T, RG>, 200 * 1024);
-    stencil_tma_kernel<T, RG><<<g.V, dim3(m, 9), sm_tma, s>>>(in, out, AT, g, nrhs, err);
+    stencil_tma_kernel<T, RG><<<g.V, dim3(m, 9), sm_tma, s>>>(in, out, AT, g, nrhs, err, staging_extra_bytes());
     MG_LAUNCH_CHECK();
     return;
   }

@@ -46,6 +46,7 @@ class SolverParams(ctypes.Structure):
                 ('smoother', ctypes.c_int),
                 ('sap_iters', ctypes.c_int),
                 ('coarse_smoother_steps', ctypes.c_int),
+                ('coarse_restart', ctypes.c_int),
                 ('fine_batch', ctypes.c_int)]
 
 
@@ -113,6 +114,7 @@ _SIGNATURES = {
     'mgmlmc_last_samples': [_P, _I, _P, _I, ctypes.POINTER(_I)],
     'mgmlmc_release_workspaces': [_P],
     'mgmlmc_get_gauge': [_P, _P, _I],
+    'mgmlmc_test_staging_extra': [_P, _I],
     'mgmlmc_connected_correlator': [_P, _I, _I, _U64, _U64, _P, _P, ctypes.POINTER(_I)],
     'mgmlmc_disconnected_loop': [_P, _I, _I, _I, _U64, _U64, _P, _P, ctypes.POINTER(_I)],
     'mgmlmc_apply': [_P, _I, _I, _I, _P, _P, _I],
@@ -222,9 +224,9 @@ SMOOTHER_MR, SMOOTHER_SAP, SMOOTHER_LEARNED = 0, 1, 2
 
 def solver_params(tol=1e-12, max_iter=2000, restart=16, smoother_steps=4, coarse_iters=8,
                   precision=FP64, inner_tol=1e-6, smoother=SMOOTHER_MR, sap_iters=4,
-                  coarse_smoother_steps=4, fine_batch=0):
+                  coarse_smoother_steps=4, coarse_restart=0, fine_batch=0):
     return SolverParams(tol, max_iter, restart, smoother_steps, coarse_iters, precision, inner_tol,
-                        smoother, sap_iters, coarse_smoother_steps, fine_batch)
+                        smoother, sap_iters, coarse_smoother_steps, coarse_restart, fine_batch)
 
 
 def mgmlmc_set_solver(ctx, params=None, **kw):
@@ -293,6 +295,10 @@ def mgmlmc_get_gauge(ctx, U, on_device=None):
     if on_device is None:
         on_device = bool(getattr(U, 'is_cuda', False))
     _check(ctx, lib().mgmlmc_get_gauge(ctx, ptr(U), int(on_device)))
+
+
+def mgmlmc_test_staging_extra(ctx, extra_bytes):
+    _check(ctx, lib().mgmlmc_test_staging_extra(ctx, extra_bytes))
 
 
 def mgmlmc_release_workspaces(ctx):
@@ -378,6 +384,7 @@ def mgmlmc_kernel_launches():
 
 
 VARIANT_DSLASH_FP32 = 0
+VARIANT_STENCIL_FP32 = 1
 LAYOUT_INTERNAL = 0x100
 
 

@@ -1,0 +1,48 @@
+"""Failure detection on the GPU without a fault: the coarse-stencil kernels
+stage a site's blocks with one bulk copy onto an mbarrier and wait for it
+with a bound (1 s of the GPU's global timer).  mgmlmc_test_staging_extra
+arms that barrier with 16 bytes more than the copy delivers, so the copy
+lands in full but the wait runs out: the call must return MGMLMC_ERR_CUDA,
+and with the injection off the same context must compute the right result
+again."""
+import numpy as np
+import pytest
+
+from paper_2509_11424_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip('torch')
+if not torch.cuda.is_available():
+    pytest.skip('needs a CUDA GPU', allow_module_level=True)
+
+from gpu_util import Setup, dev, host, rel  # noqa: E402
+
+
+@pytest.mark.parametrize('variant', [0, 1])
+def test_staging_wait_runs_out_and_context_survives(variant):
+    # a 2^4 coarse lattice of 16 sites: one wave of blocks waits its 2 x 1 s
+    s = Setup((4, 4, 4, 4), [(2, 2, 2, 2)], [16], eps=0.3, m0=-0.2, gseed=81)
+    M = s.M
+    from paper_2509_11424_gb300.mgmlmc import MgmlmcError
+    try:
+        A1 = s.hier.matrix(1).tocsr()
+        n1 = A1.shape[0]
+        x = synth.complex_normal((2, n1), 82)
+        y = torch.empty((2, n1), dtype=torch.complex64, device='cuda')
+        M.mgmlmc_set_kernel_variant(s.ctx, M.VARIANT_STENCIL_FP32, variant)
+        M.mgmlmc_test_staging_extra(s.ctx, 16)
+        try:
+            with pytest.raises(MgmlmcError) as e:
+                M.mgmlmc_apply(s.ctx, M.OP_D, 1, M.FP32, dev(x, torch.complex64), y, 2)
+        finally:
+            M.mgmlmc_test_staging_extra(s.ctx, 0)
+        assert e.value.status == 4 and 'bounded wait' in str(e.value)
+        # usable again, right result
+        M.mgmlmc_apply(s.ctx, M.OP_D, 1, M.FP32, dev(x, torch.complex64), y, 2)
+        got = host(y)
+        want = np.array([A1 @ v.astype(np.complex64).astype(np.complex128) for v in x])
+        assert rel(got, want) < (1e-5 if variant == 0 else 3e-3)
+    finally:
+        M.mgmlmc_set_kernel_variant(s.ctx, M.VARIANT_STENCIL_FP32, 0)
+        s.close()
