@@ -90,13 +90,13 @@ WORKLOADS = {
         dims=(48, 48, 48, 96), eps=0.4, gauge='device', gauge_seed=1005, noise_seed=2005, tv_seed=3005,
         m0=-0.40, blocks=[(4, 4, 4, 4), (2, 2, 2, 2), (2, 2, 2, 2)], ntv=[16, 16, 16],
         fine_n=4, coarse_n=32, batch=32, setup_rounds=6, setup_iters=30,
-        solver=dict(SOLVER, restart=8, fine_batch=4),
+        solver=dict(SOLVER, restart=8, fine_batch=4, coarse_restart=16), stencil_variant=-2,
         train=dict(dims=(16, 16, 16, 16), gauge_seed=1006, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)], ntv=[16, 16]),
         arms=('plain', 'oblique', 'sap', 'fp64'), fp64_fine_n=2, fp64_coarse_n=8),
     '16x16x16x16': dict(
         dims=DIMS, eps=EPS_GAUGE, gauge='host', gauge_seed=GAUGE_SEED, noise_seed=NOISE_SEED, tv_seed=TV_SEED,
         m0=None, blocks=BLOCKS, ntv=NTV, fine_n=32, coarse_n=32, batch=32, setup_rounds=6, setup_iters=30,
-        solver=dict(SOLVER), train=None, arms=ARMS, fp64_fine_n=32, fp64_coarse_n=32),
+        solver=dict(SOLVER), stencil_variant=0, train=None, arms=ARMS, fp64_fine_n=32, fp64_coarse_n=32),
 }
 DEFAULT_WORKLOAD = '48x48x48x96'
 KERNELS = {0: 'wilson_dslash_fp64', 1: 'wilson_dslash_fp32', 2: 'coarse_stencil_fp64',
@@ -587,6 +587,8 @@ def build_context(M, torch, wl, stream, U=None, dims=None, blocks=None, ntv=None
         M.mgmlmc_gen_gauge(ctx, wl['eps'], gauge_seed or wl['gauge_seed'])
     M.mgmlmc_set_mass(ctx, wl['m0'])
     M.mgmlmc_set_solver(ctx, precision=M.FP32, **wl['solver'])
+    # the tensor-core (TF32) coarse stencil serves the preconditioner only
+    M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_STENCIL_FP32, wl['stencil_variant'])
     torch.cuda.synchronize()
     t0 = time.time()
     M.mgmlmc_build_hierarchy(ctx, M.mg_params(blocks or wl['blocks'], ntv or wl['ntv'],
@@ -661,8 +663,9 @@ def validate_allocation(M, ctx, det, kinds_n, est, B, val_s, eps_scale):
     V = np.array([det['terms'][t]['var'] for t in terms])
     C = np.array([det['terms'][t]['cost_s'] for t in terms])
     S = float(np.sum(np.sqrt(V * C)))
-    eps = det['eps'] * eps_scale
-    if eps_scale is None or eps_scale <= 0:
+    if eps_scale:
+        eps = det['eps'] * eps_scale
+    else:
         eps = S / math.sqrt(val_s)  # predicted cost S^2 / eps^2 = val_s
     N = [max(2, int(math.ceil(math.sqrt(v / c) * S / eps ** 2))) if c > 0 else 2 for v, c in zip(V, C)]
     predicted = float(np.sum(np.array(N) * C))

@@ -512,16 +512,21 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
 /* Kernels with selectable variants. */
 #define MGMLMC_VARIANT_DSLASH_FP32 0
 /* The FP32 coarse stencil D_l, l >= 1 (Galerkin, Sec. 2.2): 0 = FP32 on the
- * CUDA cores (default); 1 .. 3 = the 5th-generation tensor cores (tcgen05.mma
+ * CUDA cores (default); 1, 2 = the 5th-generation tensor cores (tcgen05.mma
  * kind::tf32, operands staged in shared memory by a bulk copy, FP32
  * accumulators in tensor memory) for levels with 32 dofs per site (N_tv =
  * 16; other levels keep variant 0): the products take the operands as TF32
  * (10-bit mantissa, relative rounding <= 2^-11 per operand) and accumulate
- * in FP32, so results differ from variant 0 by that rounding; the variants
- * differ only in how the accumulator is read back; -2 = autotune between 0
+ * in FP32, so results differ from variant 0 by that rounding; 1 issues
+ * M = 64 MMAs (two accumulators, real and imaginary parts of the blocks
+ * stacked), 2 the same as M = 128 MMAs whose extra rows are discarded (the
+ * same numbers, twice the tensor work); -2 = autotune between 0
  * and 1 per (level, nrhs) on the first call outside graph capture (opt-in,
- * since the choice changes the rounding).  Inside the solver the FP64
- * defect correction decides convergence with the true residual either way. */
+ * since the choice changes the rounding).  Inside a solve the variant applies
+ * to the multigrid preconditioner only (smoothers, coarse-grid corrections);
+ * the Krylov operator of every FGMRES keeps variant 0, so the FP32 inner
+ * solves reach their tolerance as with FP32 throughout, and the FP64 defect
+ * correction decides convergence with the true residual either way. */
 #define MGMLMC_VARIANT_STENCIL_FP32 1
 /* Choose the variant of a kernel for later calls: for the FP32 fine Wilson
  * operator -2 = autotune (default: the first call per right-hand-side count

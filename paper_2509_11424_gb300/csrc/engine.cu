@@ -398,7 +398,7 @@ int Engine::dslash_variant(int nrhs) const {
   return it == dslash_tuned_.end() ? -2 : it->second;
 }
 
-int Engine::stencil_variants() { return 4; }
+int Engine::stencil_variants() { return 3; }
 
 void Engine::set_stencil_variant(int v) {
   if (v < -2 || v == -1 || v >= stencil_variants()) throw Error(MGMLMC_ERR_ARG, "stencil variant out of range");
@@ -423,6 +423,9 @@ void Engine::stencil_run(int l, int v, const float2 *in, float2 *out, int nrhs) 
 // numbers: autotuning (-2) is an opt-in; every variant is timed on the
 // caller's operands and the fastest kept per (level, nrhs)
 int Engine::stencil_pick(int l, int nrhs, const float2 *in, float2 *out) {
+  // inside a solve the variant serves the multigrid preconditioner only;
+  // every FGMRES keeps the FP32 stencil as its Krylov operator
+  if (solving_ > 0 && precond_depth_ == 0) return 0;
   if (stencil_force_ != -2) return levels_[l].ATC ? stencil_force_ : 0;
   if (!levels_[l].ATC) return 0;
   auto it = stencil_tuned_.find({l, nrhs});
@@ -610,6 +613,13 @@ template void Engine::smooth_apply<float>(int, const C<float> *, C<float> *, int
 // FGMRES iterations on the next level, exact dense solve on the coarsest),
 // post-smoothing.
 template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nrhs) {
+  // operator applications below belong to the preconditioner: the FP32
+  // stencil variant applies there (not to the Krylov operator of a solve)
+  struct Depth {
+    int &d;
+    explicit Depth(int &x) : d(x) { ++d; }
+    ~Depth() { --d; }
+  } depth(precond_depth_);
   const Level &L = levels_[l];
   const int64_t n = L.g.n();
   if (l == n_levels() - 1) {
@@ -881,6 +891,11 @@ SolveInfo Engine::solve_mixed(int l, const double2 *b, double2 *x, int nrhs) {
 
 SolveInfo Engine::solve(int l, const double2 *b, double2 *x, int nrhs) {
   if (!ready_) throw Error(MGMLMC_ERR_STATE, "hierarchy not built");
+  struct Solving {
+    int &d;
+    explicit Solving(int &x) : d(x) { ++d; }
+    ~Solving() { --d; }
+  } solving(solving_);
   const int64_t n = levels_.at(l).g.n();
   SolveInfo info;
   if (l == n_levels() - 1) {

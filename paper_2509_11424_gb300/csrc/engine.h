@@ -180,9 +180,9 @@ class Engine {
   // fastest kept), 0 .. wilson_fp32_variants() - 1 = fixed
   void set_dslash_variant(int v);
   int dslash_variant(int nrhs) const;
-  // FP32 coarse stencil per rhs count: 0 = FP32 CUDA cores, 1.. = tcgen05
-  // TF32 (stencil_tc_layouts() read-back layouts), -2 = the fastest on the
-  // first call outside capture
+  // FP32 coarse stencil per rhs count: 0 = FP32 CUDA cores, 1 = tcgen05
+  // TF32 with M = 64 MMAs, 2 = the same with M = 128 MMAs, -2 = the faster of
+  // 0 and 1 on the first call outside capture
   void set_stencil_variant(int v);
   int stencil_variant(int l, int nrhs) const;
   static int stencil_variants();
@@ -276,6 +276,8 @@ class Engine {
   void orthonormalise_cols(double2 *V, int k, int64_t n);
   std::map<int, int> dslash_tuned_;
   int stencil_force_ = 0;
+  int precond_depth_ = 0;  // > 0 while the multigrid preconditioner runs
+  int solving_ = 0;        // > 0 inside solve()
   std::map<std::pair<int, int>, int> stencil_tuned_;  // (level, nrhs) -> variant
   int stencil_pick(int l, int nrhs, const float2 *in, float2 *out);
   void stencil_run(int l, int v, const float2 *in, float2 *out, int nrhs);

@@ -130,9 +130,9 @@ void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, 
 // Tensor-core (tcgen05 kind::tf32) coarse stencil for 32 dofs per site:
 // ATC holds each site's nine stacked [Re A_d; Im A_d] tiles in the MMA's
 // shared-memory image (stencil_tile_tc builds it from the canonical A);
-// FP32 vectors, TF32 products, FP32 accumulation.  layout selects how the
-// accumulator rows are read back (see kernels_tc.cu).  err[0] = 3 if a
-// bounded wait runs out.
+// FP32 vectors, TF32 products, FP32 accumulation.  layout 0: M = 64 MMAs,
+// 1: M = 128 MMAs with half the rows discarded (see kernels_tc.cu).  err[0] =
+// 3 if a bounded wait runs out.
 bool stencil_tc_supported(const Geom &g);
 size_t stencil_tc_floats(const Geom &g);
 void stencil_tile_tc(const double2 *A, float *ATC, const Geom &g, cudaStream_t s);

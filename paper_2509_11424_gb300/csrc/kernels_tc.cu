@@ -117,10 +117,11 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
 }
 
 // Accumulator row held by TMEM lane 32 warp + lane (-1: none of the 64
-// rows).  LAYOUT 0: M = 64 MMAs with rows 16w .. 16w + 15 in the first 16
-// lanes of warp w's lane quarter; LAYOUT 1: M = 64 MMAs with row i in lane i;
-// LAYOUT 2: M = 128 MMAs (row i in lane i) whose rows 64..127 read the next
-// core matrices of the tile and are discarded.
+// rows).  LAYOUT 0: M = 64 MMAs, whose accumulator rows 16w .. 16w + 15 sit
+// in the first 16 lanes of warp w's lane quarter (checked against the
+// oracle; row i in lane i does not hold for M = 64).  LAYOUT 2: M = 128 MMAs
+// (row i in lane i) whose rows 64..127 read the next core matrices of the
+// tile and are discarded: twice the tensor work, the same result.
 template <int LAYOUT> __device__ __forceinline__ int acc_row_of_lane(int warp, int lane) {
   if (LAYOUT == 0) return lane < 16 ? 16 * warp + lane : -1;
   return warp < 2 ? 32 * warp + lane : -1;
@@ -304,13 +305,9 @@ void stencil_apply_tc(const float2 *in, float2 *out, const float *ATC, Geom g, i
   if ((((uintptr_t)in | (uintptr_t)out | (uintptr_t)ATC) & 15) != 0)
     throw Error(1, "tensor-core stencil: operands must be 16-byte aligned");
   const size_t sm = (size_t)(9 * kTcTileFloats + 9 * 2 * kTcMaxN * kTcM + 2 * 64 * kTcMaxN) * sizeof(float);
-  if (layout == 2) {
+  if (layout == 1) {
     smem_optin((const void *)stencil_tc_kernel<2>, (int)sm);
     stencil_tc_kernel<2><<<g.V, kTcThreads, sm, s>>>(in, out, ATC, g, nrhs, err,
-                                                             staging_extra_bytes());
-  } else if (layout == 1) {
-    smem_optin((const void *)stencil_tc_kernel<1>, (int)sm);
-    stencil_tc_kernel<1><<<g.V, kTcThreads, sm, s>>>(in, out, ATC, g, nrhs, err,
                                                              staging_extra_bytes());
   } else {
     smem_optin((const void *)stencil_tc_kernel<0>, (int)sm);

@@ -51,7 +51,7 @@ def bound_check(got, x32, A1):
     return bool(ok_re.all() and ok_im.all()), float(np.max(np.abs(got - want) / bnd))
 
 
-@pytest.mark.parametrize('variant', [1, 2, 3])
+@pytest.mark.parametrize('variant', [1, 2])
 @pytest.mark.parametrize('nrhs', [1, 8, 32, 37])
 def test_tensor_stencil_matches_oracle(tc, variant, nrhs):
     M = tc.M
