@@ -124,6 +124,9 @@ typedef struct {
   int coarse_smoother_steps; /* MR steps of the smoother on levels >= 1 */
   int coarse_restart;  /* FGMRES restart length of the solves on levels >= 1
                           (their vectors are small), 1 .. 64; 0 = restart */
+  int post_smoothing_only; /* 1: the multigrid cycle smooths after the
+                          coarse-grid correction only (no pre-smoothing);
+                          0 (default): before and after */
   int fine_batch;      /* memory bound of the fine level: mgmlmc_estimate_trace
                           solves level-0 systems (the O_0, F_0, M_0 and plain
                           terms) in blocks of at most fine_batch right-hand
@@ -531,11 +534,13 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
 /* Choose the variant of a kernel for later calls: for the FP32 fine Wilson
  * operator -2 = autotune (default: the first call per right-hand-side count
  * outside graph capture times every variant on that call's operands and
- * keeps the fastest), 0 .. 4 = fixed: one thread per site, 128-thread
- * blocks; 0 and 1 one right-hand side per thread with registers for 6 or 8
- * resident blocks per SM; 2 and 3 two right-hand sides per thread with
- * registers for 4 or 5 blocks; 4 one right-hand side with the next operand
- * set loaded while the current one is used (4 blocks).
+ * keeps the fastest), 0 .. 6 = fixed: one thread per site; 0 .. 4 in
+ * 128-thread blocks, 0 and 1 one right-hand side per thread with registers
+ * for 6 or 8 resident blocks per SM; 2 and 3 two right-hand sides per thread
+ * with registers for 4 or 5 blocks; 4 one right-hand side with the next
+ * operand set loaded while the current one is used (4 blocks); 5 and 6 put 4
+ * or 8 right-hand sides of the same 32 sites in the warps of one block, so
+ * those warps read the sites' links from L1 after the first.
  * Every variant computes the same sums in the same order.  Returns
  * MGMLMC_ERR_ARG for an unknown kernel or variant. */
 mgmlmc_status mgmlmc_set_kernel_variant(mgmlmc_ctx *ctx, int kernel, int variant);

@@ -337,7 +337,7 @@ int Engine::restart_of(int l) const {
 
 void Engine::set_solver(const mgmlmc_solver_params &p) {
   if (!(p.tol > 0.0) || p.max_iter < 1 || p.restart < 1 || p.restart > 64 || p.smoother_steps < 0 ||
-      p.coarse_restart < 0 || p.coarse_restart > 64 ||
+      p.coarse_restart < 0 || p.coarse_restart > 64 || (p.post_smoothing_only != 0 && p.post_smoothing_only != 1) ||
       p.coarse_iters < 1 || p.coarse_iters > 64 ||
       (p.precision != MGMLMC_FP64 && p.precision != MGMLMC_FP32) ||
       (p.precision == MGMLMC_FP32 && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)) ||
@@ -635,7 +635,7 @@ template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nr
   C<T> *ec = ws<T>("mgec", l + 1, (size_t)nc * nrhs);
   MG_CUDA(cudaMemsetAsync(z, 0, sizeof(C<T>) * n * nrhs, stream));
   MG_CUDA(cudaMemcpyAsync(res, r, sizeof(C<T>) * n * nrhs, cudaMemcpyDeviceToDevice, stream));
-  smooth<T>(l, z, res, nrhs);
+  if (!sp_.post_smoothing_only) smooth<T>(l, z, res, nrhs);
   cudaEvent_t pr = prof_begin();
   restrict_op<T>(res, rc, Pmat<T>(l), agg_of<T>(l), nrhs, stream);
   prof_end(pr, K_TRANSFER, 0.0, 0.0);

@@ -334,6 +334,39 @@ __global__ void __launch_bounds__(BS, MINB) wilson_soa_kernel(const float2 *__re
   }
 }
 
+// The right-hand sides of a group in the warps of one CTA: warp w of a CTA
+// of 32 RW threads takes right-hand side r0 + w of the same 32 sites, so the
+// links (and the neighbour sites' index arithmetic) of those sites are read
+// by RW warps of one SM: from L1 after the first, instead of once per
+// right-hand side from L2.  Same sums in the same order as the kernel above.
+template <int RW, int MINB>
+__global__ void __launch_bounds__(32 * RW, MINB) wilson_soa_rw_kernel(const float2 *__restrict__ in,
+                                                                  float2 *__restrict__ out,
+                                                                  const float2 *__restrict__ UDs, Geom g,
+                                                                  float diag, int nrhs) {
+  const int ng = (nrhs + RW - 1) / RW;
+  const int sb = (int)(blockIdx.x / ng), rg = (int)(blockIdx.x - (unsigned)sb * ng);
+  const int s = sb * 32 + (int)(threadIdx.x & 31);
+  const int q = rg * RW + (int)(threadIdx.x >> 5);
+  if (s >= g.V || q >= nrhs) return;
+  const int64_t n = (int64_t)g.V * 12;
+  soa::Ctx<1> t;
+  t.nr = 1;
+  t.P[0] = reinterpret_cast<const float4 *>(in + q * n);
+  t.UDs = UDs;
+  t.g = g;
+  t.V = g.V;
+  t.s = s;
+  t.diag = diag;
+  g.coords(s, t.c);
+  soa::serial<0, 1>(t);
+  float4 *o = reinterpret_cast<float4 *>(out + q * n);
+#pragma unroll
+  for (int k = 0; k < 6; ++k)
+    o[k * t.V + s] = make_float4(t.acc[0][2 * k].x, t.acc[0][2 * k].y, t.acc[0][2 * k + 1].x,
+                                 t.acc[0][2 * k + 1].y);
+}
+
 // ------------------------------------------------------------------ BF16
 // BF16 storage, FP32 arithmetic.  Spinors structure-of-arrays in 16-byte
 // chunks of 4 complex entries: component i of site s is bf16 pair
@@ -619,6 +652,15 @@ inline int grid_for(int64_t n) {
 }  // namespace
 
 namespace {
+template <int RW, int MINB>
+void launch_soa_rw(const float2 *in, float2 *out, const float2 *UDs, Geom g, float diag, int nrhs,
+                   cudaStream_t s) {
+  const int64_t blocks = (int64_t)div_up(g.V, 32) * div_up(nrhs, RW);
+  if (blocks > 0x7fffffff) throw Error(1, "lattice too large for one launch");
+  wilson_soa_rw_kernel<RW, MINB><<<(unsigned)blocks, 32 * RW, 0, s>>>(in, out, UDs, g, diag, nrhs);
+  MG_LAUNCH_CHECK();
+}
+
 template <int R, int MINB, bool PIPE>
 void launch_soa(const float2 *in, float2 *out, const float2 *UDs, Geom g, float diag, int nrhs,
                 cudaStream_t s) {
@@ -630,7 +672,7 @@ void launch_soa(const float2 *in, float2 *out, const float2 *UDs, Geom g, float 
 }
 }  // namespace
 
-int wilson_fp32_variants() { return 5; }
+int wilson_fp32_variants() { return 7; }
 
 template <typename T>
 void wilson_apply(const C<T> *in, C<T> *out, const C<T> *U, const C<T> *UDs, Geom g, double m0,
@@ -646,6 +688,8 @@ void wilson_apply(const C<T> *in, C<T> *out, const C<T> *U, const C<T> *UDs, Geo
       case 2: launch_soa<2, 4, false>(in, out, UDs, g, diag, nrhs, s); return;
       case 3: launch_soa<2, 5, false>(in, out, UDs, g, diag, nrhs, s); return;
       case 4: launch_soa<1, 4, true>(in, out, UDs, g, diag, nrhs, s); return;
+      case 5: launch_soa_rw<4, 5>(in, out, UDs, g, diag, nrhs, s); return;
+      case 6: launch_soa_rw<8, 2>(in, out, UDs, g, diag, nrhs, s); return;
       default: launch_soa<1, 6, false>(in, out, UDs, g, diag, nrhs, s); return;
     }
   } else {

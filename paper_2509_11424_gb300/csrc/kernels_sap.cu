@@ -10,13 +10,19 @@
 // D_BB e_B = r_B with the block-local Wilson operator (hops that leave B are
 // dropped); then z_B += e_B, the residual inside B becomes the block MR
 // residual, and the residual of the other colour loses the hops of e that
-// cross block faces.  The residual r = b - D z stays exact throughout.
+// cross block faces.  The residual r = b - D z is exact at the end of the
+// sweep.  That last update is done for the black sites by the black blocks
+// themselves as they stage their residual (the red corrections across their
+// faces enter before their iterations start), and for the red sites by one
+// boundary pass after the black blocks: three launches per sweep.
 //
-// One CTA per (active block, rhs), one thread per site of the block.  The
-// block's links and its residual live in shared memory for all block
-// iterations (FP32: 256 sites x (36 + 12) complex = 98 KB), so the MR
-// iterations touch HBM once per sweep.  FP32 vectors and links are in the
-// fine level's structure-of-arrays order, FP64 ones canonical.
+// One CTA per (active block, rhs), one thread per site of the block; the
+// right-hand side varies fastest over the grid, so the CTAs of a block share
+// its links through L2.  The block's links and its residual live in shared
+// memory for all block iterations (FP32: 256 sites x (36 + 12) complex = 98
+// KB), so the MR iterations touch HBM once per sweep.  FP32 vectors and
+// links are in the fine level's structure-of-arrays order, FP64 ones
+// canonical.
 #include "kernels.h"
 
 namespace mg {
@@ -163,13 +169,53 @@ __device__ __forceinline__ void local_hops(const C<T> *rho, const C<T> *Us, cons
   }
 }
 
+// residual of the inactive colour: r(x) -= hops of e that cross a block face
+// into x from a block of the active colour.
+template <int MU, typename T>
+__device__ __forceinline__ void cross_pair(const C<T> *__restrict__ ev, const C<T> *__restrict__ U,
+                                           const SapGeom &sg, int s, const int (&c)[4],
+                                           C<T> (&acc)[12], T sign = (T)1) {
+  const Geom &g = sg.g;
+  {
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    cn[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
+    if (c[MU] / sg.b[MU] != cn[MU] / sg.b[MU]) {
+      const int sn = g.index(cn);
+      const T k = sign * ((MU == 3 && cn[3] == 0) ? (T)0.5 : (T)-0.5);
+      C<T> p[12], u[9];
+#pragma unroll
+      for (int i = 0; i < 12; ++i) p[i] = ev[fidx<kSoa<T>>(sn, i, g.V)];
+      link_at<T>(U, g.V, s, MU, u);
+      shop<MU, true, T>(p, u, k, acc);
+    }
+  }
+  {
+    int cn[4] = {c[0], c[1], c[2], c[3]};
+    cn[MU] = (c[MU] == 0) ? g.L[MU] - 1 : c[MU] - 1;
+    if (c[MU] / sg.b[MU] != cn[MU] / sg.b[MU]) {
+      const int sn = g.index(cn);
+      const T k = sign * ((MU == 3 && c[3] == 0) ? (T)0.5 : (T)-0.5);
+      C<T> p[12], u[9];
+#pragma unroll
+      for (int i = 0; i < 12; ++i) p[i] = ev[fidx<kSoa<T>>(sn, i, g.V)];
+      link_at<T>(U, g.V, sn, MU, u);
+      shop<MU, false, T>(p, u, k, acc);
+    }
+  }
+}
+
 // One colour of one SAP sweep.  r: residual (in/out), z: solution (+= e),
-// e: correction of this colour (written for the boundary update).
+// e: correction of this colour (written for the boundary update).  With
+// fuse_in the block's residual first takes the hops of the other colour's
+// corrections across its faces (the boundary update of the previous pass,
+// done here on the block's own sites instead of by a separate kernel).
+// FP32: two CTAs per SM (98 KB of shared memory each); FP64 (196 KB) fits
+// one, so it takes the whole register file
 template <typename T>
-__global__ void __launch_bounds__(256, 2) sap_block_kernel(C<T> *__restrict__ r, C<T> *__restrict__ z,
-                                                        C<T> *__restrict__ e_out,
-                                                        const C<T> *__restrict__ U, SapGeom sg,
-                                                        T diag, int color, int iters, int nrhs) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sap_block_kernel(C<T> *__restrict__ r, C<T> *__restrict__ z,
+                                                        C<T> *e_out, const C<T> *__restrict__ U,
+                                                        SapGeom sg, T diag, int color, int iters,
+                                                        int nrhs, int fuse_in) {
   extern __shared__ unsigned char smem_raw[];
   const int sites = sg.sites;
   C<T> *Us = reinterpret_cast<C<T> *>(smem_raw);  // [4][9][sites]
@@ -201,7 +247,21 @@ __global__ void __launch_bounds__(256, 2) sap_block_kernel(C<T> *__restrict__ r,
   // stage links and the residual of the block
   const int64_t V = sg.g.V;
   for (int i = 0; i < 36; ++i) Us[i * sites + ls] = kSoa<T> ? U[(int64_t)i * V + s] : U[(int64_t)s * 36 + i];
-  for (int i = 0; i < 12; ++i) rho[i * sites + ls] = rv[fidx<kSoa<T>>(s, i, V)];
+  {
+    C<T> p[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i) p[i] = rv[fidx<kSoa<T>>(s, i, V)];
+    if (fuse_in) {
+      // the other colour's blocks are the face neighbours: their fresh
+      // corrections e enter this block's residual, r -= hops of e
+      cross_pair<0, T>(ev, U, sg, s, gc, p, (T)-1);
+      cross_pair<1, T>(ev, U, sg, s, gc, p, (T)-1);
+      cross_pair<2, T>(ev, U, sg, s, gc, p, (T)-1);
+      cross_pair<3, T>(ev, U, sg, s, gc, p, (T)-1);
+    }
+#pragma unroll
+    for (int i = 0; i < 12; ++i) rho[i * sites + ls] = p[i];
+  }
   C<T> e[12];
 #pragma unroll
   for (int i = 0; i < 12; ++i) e[i] = mk<T>((T)0, (T)0);
@@ -240,41 +300,6 @@ __global__ void __launch_bounds__(256, 2) sap_block_kernel(C<T> *__restrict__ r,
     zv[o] = cadd(zv[o], e[i]);
     ev[o] = e[i];
     rv[o] = rho[i * sites + ls];
-  }
-}
-
-// residual of the inactive colour: r(x) -= hops of e that cross a block face
-// into x from a block of the active colour.
-template <int MU, typename T>
-__device__ __forceinline__ void cross_pair(const C<T> *__restrict__ ev, const C<T> *__restrict__ U,
-                                           const SapGeom &sg, int s, const int (&c)[4],
-                                           C<T> (&acc)[12]) {
-  const Geom &g = sg.g;
-  {
-    int cn[4] = {c[0], c[1], c[2], c[3]};
-    cn[MU] = (c[MU] + 1 == g.L[MU]) ? 0 : c[MU] + 1;
-    if (c[MU] / sg.b[MU] != cn[MU] / sg.b[MU]) {
-      const int sn = g.index(cn);
-      const T k = (MU == 3 && cn[3] == 0) ? (T)0.5 : (T)-0.5;
-      C<T> p[12], u[9];
-#pragma unroll
-      for (int i = 0; i < 12; ++i) p[i] = ev[fidx<kSoa<T>>(sn, i, g.V)];
-      link_at<T>(U, g.V, s, MU, u);
-      shop<MU, true, T>(p, u, k, acc);
-    }
-  }
-  {
-    int cn[4] = {c[0], c[1], c[2], c[3]};
-    cn[MU] = (c[MU] == 0) ? g.L[MU] - 1 : c[MU] - 1;
-    if (c[MU] / sg.b[MU] != cn[MU] / sg.b[MU]) {
-      const int sn = g.index(cn);
-      const T k = (MU == 3 && c[3] == 0) ? (T)0.5 : (T)-0.5;
-      C<T> p[12], u[9];
-#pragma unroll
-      for (int i = 0; i < 12; ++i) p[i] = ev[fidx<kSoa<T>>(sn, i, g.V)];
-      link_at<T>(U, g.V, sn, MU, u);
-      shop<MU, false, T>(p, u, k, acc);
-    }
   }
 }
 
@@ -341,14 +366,15 @@ void sap_sweep(C<T> *r, C<T> *z, C<T> *e, const C<T> *U, Geom g, const int b[4],
   const size_t sm = sap_smem_bytes<T>(b);
   smem_optin((const void *)sap_block_kernel<T>, (int)(220 * 1024));
   if (sm > 220 * 1024) throw Error(1, "SAP block too large for shared memory");
+  // red blocks; black blocks, which first take the red corrections across
+  // their faces; then the red sites take the black corrections (r exact again)
   for (int color = 0; color < 2; ++color) {
     sap_block_kernel<T><<<(unsigned)(nblocks / 2) * (unsigned)nrhs, sg.sites, sm, s>>>(
-        r, z, e, U, sg, (T)(4.0 + m0), color, block_iters, nrhs);
-    MG_LAUNCH_CHECK();
-    sap_boundary_kernel<T><<<(unsigned)div_up(g.V, 128) * (unsigned)nrhs, 128, 0, s>>>(r, e, U, sg, color,
-                                                                                    nrhs);
+        r, z, e, U, sg, (T)(4.0 + m0), color, block_iters, nrhs, color);
     MG_LAUNCH_CHECK();
   }
+  sap_boundary_kernel<T><<<(unsigned)div_up(g.V, 128) * (unsigned)nrhs, 128, 0, s>>>(r, e, U, sg, 1, nrhs);
+  MG_LAUNCH_CHECK();
 }
 
 template void sap_sweep<double>(C<double> *, C<double> *, C<double> *, const C<double> *, Geom,
