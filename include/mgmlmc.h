@@ -523,8 +523,14 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
  * in FP32, so results differ from variant 0 by that rounding; 1 issues
  * M = 64 MMAs (two accumulators, real and imaginary parts of the blocks
  * stacked), 2 the same as M = 128 MMAs whose extra rows are discarded (the
- * same numbers, twice the tensor work); -2 = autotune between 0
- * and 1 per (level, nrhs) on the first call outside graph capture (opt-in,
+ * same numbers, twice the tensor work); 3 = the blocks stored as BF16 pairs
+ * (half the bytes, relative rounding <= 2^-9 per entry) with FP32
+ * arithmetic, for up to 8 right-hand sides at 32 dofs per site (variant 0
+ * otherwise).  Variant 0 runs up to 8 right-hand sides at 32 dofs per site in
+ * a pipelined kernel (persistent blocks, a two-stage ring of bulk copies
+ * over sites) with results identical to the one-site-per-block kernels.
+ * -2 = autotune among 0, 1 and 3 per (level, nrhs) on the first call
+ * outside graph capture (opt-in,
  * since the choice changes the rounding).  Inside a solve the variant applies
  * to the multigrid preconditioner only (smoothers, coarse-grid corrections);
  * the Krylov operator of every FGMRES keeps variant 0, so the FP32 inner

@@ -373,6 +373,7 @@ void Engine::free_hierarchy() {
       dfree(L.AT64);
       dfree(L.AT32);
       dfree(L.ATC);
+      dfree(L.ATB16);
     }
     L.has_next = false;
   }
@@ -398,7 +399,7 @@ int Engine::dslash_variant(int nrhs) const {
   return it == dslash_tuned_.end() ? -2 : it->second;
 }
 
-int Engine::stencil_variants() { return 3; }
+int Engine::stencil_variants() { return 4; }
 
 void Engine::set_stencil_variant(int v) {
   if (v < -2 || v == -1 || v >= stencil_variants()) throw Error(MGMLMC_ERR_ARG, "stencil variant out of range");
@@ -413,9 +414,15 @@ int Engine::stencil_variant(int l, int nrhs) const {
   return it == stencil_tuned_.end() ? -2 : it->second;
 }
 
+// 0: FP32 (the pipelined kernel where it applies, same sums as the
+// one-site-per-CTA kernels); 1, 2: tensor cores (TF32); 3: BF16-stored
+// blocks, FP32 arithmetic (pipelined kernel, up to 8 right-hand sides)
 void Engine::stencil_run(int l, int v, const float2 *in, float2 *out, int nrhs) {
   const Level &L = levels_[l];
-  if (v > 0 && L.ATC) stencil_apply_tc(in, out, L.ATC, L.g, nrhs, flag_dev_ + 1, v - 1, stream);
+  const bool pipe = stencil_pipe_supported(L.g) && nrhs <= 8;
+  if ((v == 1 || v == 2) && L.ATC) stencil_apply_tc(in, out, L.ATC, L.g, nrhs, flag_dev_ + 1, v - 1, stream);
+  else if (v == 3 && L.ATB16 && pipe) stencil_apply_pipe(in, out, L.ATB16, true, L.g, nrhs, flag_dev_ + 1, stream);
+  else if (pipe) stencil_apply_pipe(in, out, L.AT32, false, L.g, nrhs, flag_dev_ + 1, stream);
   else stencil_apply<float>(in, out, L.AT32, L.g, nrhs, flag_dev_ + 1, stream);
 }
 
@@ -434,8 +441,9 @@ int Engine::stencil_pick(int l, int nrhs, const float2 *in, float2 *out) {
   EventPair ev;
   int pick = 0;
   float best = 1e30f;
-  // the read-back layout of the tensor-core kernel is fixed: variant 1
-  for (int v : {0, 1}) {
+  // variant 2 is variant 1 with twice the tensor work: not a candidate
+  for (int v : {0, 1, 3}) {
+    if (v == 3 && !(levels_[l].ATB16 && nrhs <= 8)) continue;
     stencil_run(l, v, in, out, nrhs);
     MG_CUDA(cudaEventRecord(ev.a, stream));
     for (int rep = 0; rep < 3; ++rep) stencil_run(l, v, in, out, nrhs);
@@ -977,6 +985,10 @@ void Engine::galerkin(int l) {
   if (stencil_tc_supported(c.g)) {
     c.ATC = dalloc<float>(stencil_tc_floats(c.g));
     stencil_tile_tc(c.A64, c.ATC, c.g, stream);
+  }
+  if (stencil_pipe_supported(c.g)) {
+    c.ATB16 = dalloc<float>(acnt);  // one bf16 pair (4 bytes) per complex entry
+    stencil_to_bf16(c.AT32, c.ATB16, (int64_t)acnt, stream);
   }
 }
 

@@ -138,6 +138,15 @@ size_t stencil_tc_floats(const Geom &g);
 void stencil_tile_tc(const double2 *A, float *ATC, const Geom &g, cudaStream_t s);
 void stencil_apply_tc(const float2 *in, float2 *out, const float *ATC, Geom g, int nrhs, int *err, int layout,
                       cudaStream_t s);
+// Pipelined FP32 coarse stencil for 32 dofs per site and 1 .. 8 right-hand
+// sides: persistent CTAs with a two-stage ring of bulk copies over sites.
+// AT: the transposed blocks as FP32 (identical results to stencil_apply) or,
+// bf16 = true, as BF16 pairs from stencil_to_bf16 (FP32 arithmetic).
+// err[0] = 2 if a bounded wait runs out.
+bool stencil_pipe_supported(const Geom &g);
+void stencil_apply_pipe(const float2 *in, float2 *out, const void *AT, bool bf16, Geom g, int nrhs, int *err,
+                        cudaStream_t s);
+void stencil_to_bf16(const float2 *AT32, void *ATB, int64_t count, cudaStream_t s);
 // AT = blockwise transpose of the canonical A[X][d][i][j] (nblocks = 9 V)
 template <typename To>
 void stencil_transpose(const double2 *A, C<To> *AT, int64_t nblocks, int m, cudaStream_t s);

@@ -4,6 +4,10 @@
 // construction, and the dense coarsest-level inverse.
 #include "kernels.h"
 
+#include <cuda_bf16.h>
+
+#include <mutex>
+
 namespace mg {
 
 namespace {
@@ -245,6 +249,138 @@ __global__ void stencil_tma_kernel(const C<T> *__restrict__ in, C<T> *__restrict
     }
     __syncthreads();
   }
+}
+
+// Pipelined form for few right-hand sides (nrhs <= RG): a persistent CTA
+// walks over coarse sites X = blockIdx.x, + gridDim.x, ... with a two-stage
+// ring of bulk copies, so the next site's 9 blocks stream in while the
+// current one is multiplied (one site per CTA leaves the copy latency
+// exposed when there is little arithmetic per block).  Thread (i, d) forms
+// row i of direction d as in stencil_tma_kernel, in the same order, from
+// blocks stored as S: float2 (FP32, identical results) or __nv_bfloat162
+// (BF16 storage for the multigrid preconditioner: half the bytes, the
+// products and sums in FP32).
+__device__ __forceinline__ float2 ld_blk(const float2 *p) { return *p; }
+__device__ __forceinline__ float2 ld_blk(const __nv_bfloat162 *p) { return __bfloat1622float2(*p); }
+
+template <typename S, int RG>
+__global__ void __launch_bounds__(32 * 9, 1) stencil_pipe_kernel(const float2 *__restrict__ in,
+                                                                float2 *__restrict__ out,
+                                                                const S *__restrict__ AT, Geom g, int nrhs,
+                                                                int *err, unsigned extra_tx) {
+  constexpr int m = 32;
+  constexpr int TILE = 9 * m * m;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  S *As = reinterpret_cast<S *>(smem_raw);                         // [2][9][j][i]
+  float2 *xs = reinterpret_cast<float2 *>(smem_raw + 2 * TILE * sizeof(S));  // [9][RG][m]
+  float2 *part = xs + 9 * RG * m;                                  // [9][RG][m]
+  const int i = threadIdx.x, d = threadIdx.y, tid = d * 32 + i;
+  const int64_t n = g.n();
+  const unsigned bytes = (unsigned)(TILE * sizeof(S));
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+  }
+  __syncthreads();
+  // the copies of the CTA's first two sites
+  if (tid == 0) {
+    for (int st = 0; st < 2; ++st) {
+      const int X = blockIdx.x + st * gridDim.x;
+      if (X < g.V) {
+        mbar_expect_tx(&bar[st], bytes + extra_tx);  // extra_tx = 0 but in failure-injection tests
+        bulk_g2s(As + st * TILE, AT + (int64_t)X * TILE, bytes, &bar[st]);
+      }
+    }
+  }
+  unsigned phase[2] = {0u, 0u};
+  bool pending[2] = {blockIdx.x < (unsigned)g.V, blockIdx.x + gridDim.x < (unsigned)g.V};
+  int k = 0;
+  bool failed = false;
+  for (int X = blockIdx.x; X < g.V; X += gridDim.x, ++k) {
+    const int st = k & 1;
+    const int nb = g.neighbor(X, d);
+#pragma unroll
+    for (int r = 0; r < RG; ++r)
+      xs[(d * RG + r) * m + i] = r < nrhs ? in[(int64_t)r * n + (int64_t)nb * m + i] : make_float2(0.f, 0.f);
+    const bool ready = mbar_wait_bounded(&bar[st], phase[st], err);
+    if (__syncthreads_or(ready ? 0 : 1)) {
+      failed = true;
+      break;
+    }
+    phase[st] ^= 1u;
+    pending[st] = false;
+    float2 acc[RG];
+#pragma unroll
+    for (int r = 0; r < RG; ++r) acc[r] = make_float2(0.f, 0.f);
+    const float2 *xd = xs + d * RG * m;
+    const S *Ad = As + st * TILE + d * m * m;
+#pragma unroll 4
+    for (int j = 0; j < m; ++j) {
+      const float2 a = ld_blk(Ad + j * m + i);
+#pragma unroll
+      for (int r = 0; r < RG; ++r) acc[r] = cfma(a, xd[r * m + j], acc[r]);
+    }
+#pragma unroll
+    for (int r = 0; r < RG; ++r) part[(d * RG + r) * m + i] = acc[r];
+    __syncthreads();
+    // every thread is done with this stage: refill it two sites ahead
+    if (tid == 0) {
+      const int Xn = X + 2 * (int)gridDim.x;
+      if (Xn < g.V) {
+        mbar_expect_tx(&bar[st], bytes + extra_tx);
+        bulk_g2s(As + st * TILE, AT + (int64_t)Xn * TILE, bytes, &bar[st]);
+      }
+    }
+    pending[st] = X + 2 * (int)gridDim.x < g.V;
+    if (d == 0) {
+      for (int r = 0; r < nrhs; ++r) {
+        float2 v = part[r * m + i];
+#pragma unroll
+        for (int dd = 1; dd < 9; ++dd) v = cadd(v, part[(dd * RG + r) * m + i]);
+        out[(int64_t)r * n + (int64_t)X * m + i] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (failed && tid == 0) {
+    // copies still in flight must land before the CTA leaves (bounded)
+    for (int st = 0; st < 2; ++st)
+      if (pending[st]) mbar_wait_bounded(&bar[st], phase[st], nullptr);
+  }
+}
+
+// BF16 pairs of the transposed blocks (round to nearest)
+__global__ void stencil_bf16_kernel(const float2 *__restrict__ AT32, __nv_bfloat162 *__restrict__ ATB,
+                                    int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    ATB[e] = __float22bfloat162_rn(AT32[e]);
+}
+
+int sm_count() {
+  static std::mutex mu;
+  static int cached[64] = {0};
+  int dev = 0;
+  MG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+  int n = 0;
+  MG_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  if (dev >= 0 && dev < 64) cached[dev] = n;
+  return n;
+}
+
+template <typename S, int RG>
+void launch_pipe(const float2 *in, float2 *out, const S *AT, Geom g, int nrhs, int *err, cudaStream_t s) {
+  const size_t sm = (size_t)2 * 9 * 32 * 32 * sizeof(S) + (size_t)2 * 9 * RG * 32 * sizeof(float2);
+  smem_optin((const void *)stencil_pipe_kernel<S, RG>, (int)sm);
+  // as many CTAs as fit at once (shared memory bound: 1 per SM for FP32
+  // blocks, 2 for BF16), each walking over its share of the sites
+  const int per_sm = sm * 2 <= 220 * 1024 ? 2 : 1;
+  const int grid = (int)std::min<int64_t>(g.V, (int64_t)sm_count() * per_sm);
+  stencil_pipe_kernel<S, RG><<<grid, dim3(32, 9), sm, s>>>(in, out, AT, g, nrhs, err, staging_extra_bytes());
+  MG_LAUNCH_CHECK();
 }
 
 // AT[X][d][j][i] = A[X][d][i][j], converted to the storage type To.
@@ -636,6 +772,28 @@ void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, 
   const size_t sm = (size_t)2 * 9 * RG * m * sizeof(C<T>);
   smem_optin((const void *)stencil_t_kernel<T, RG>, 200 * 1024);
   stencil_t_kernel<T, RG><<<g.V, dim3(m, 9), sm, s>>>(in, out, AT, g, nrhs);
+  MG_LAUNCH_CHECK();
+}
+
+bool stencil_pipe_supported(const Geom &g) { return g.dof == 32; }
+
+void stencil_apply_pipe(const float2 *in, float2 *out, const void *AT, bool bf16, Geom g, int nrhs, int *err,
+                        cudaStream_t s) {
+  if (!stencil_pipe_supported(g) || nrhs > 8 || nrhs < 1)
+    throw Error(1, "pipelined stencil: 32 dofs per site and 1 .. 8 right-hand sides");
+  if ((((uintptr_t)in | (uintptr_t)out | (uintptr_t)AT) & 15) != 0)
+    throw Error(1, "pipelined stencil: operands must be 16-byte aligned");
+  if (bf16) {
+    if (nrhs <= 4) launch_pipe<__nv_bfloat162, 4>(in, out, (const __nv_bfloat162 *)AT, g, nrhs, err, s);
+    else launch_pipe<__nv_bfloat162, 8>(in, out, (const __nv_bfloat162 *)AT, g, nrhs, err, s);
+  } else {
+    if (nrhs <= 4) launch_pipe<float2, 4>(in, out, (const float2 *)AT, g, nrhs, err, s);
+    else launch_pipe<float2, 8>(in, out, (const float2 *)AT, g, nrhs, err, s);
+  }
+}
+
+void stencil_to_bf16(const float2 *AT32, void *ATB, int64_t count, cudaStream_t s) {
+  stencil_bf16_kernel<<<grid_for(count), 256, 0, s>>>(AT32, (__nv_bfloat162 *)ATB, count);
   MG_LAUNCH_CHECK();
 }
 

@@ -69,3 +69,77 @@ def test_tensor_stencil_matches_oracle(tc, variant, nrhs):
     for r in range(nrhs):
         ok, worst = bound_check(got[r], x32[r], A1)
         assert ok, (variant, nrhs, r, worst)
+
+
+@pytest.mark.parametrize('nrhs', [1, 4, 5, 8])
+def test_fp32_stencil_pipelined_matches_oracle_and_staged_kernel(tc, nrhs):
+    """Variant 0 at 32 dofs per site: up to 8 right-hand sides run in the
+    pipelined kernel (persistent blocks, two-stage bulk-copy ring), more in
+    the one-site-per-block kernel.  Both against the oracle to the FP32
+    tolerance 1e-5 element-wise, and bit-identical to each other (the same
+    products summed in the same order)."""
+    from gpu_util import rel
+    M = tc.M
+    A1 = tc.hier.matrix(1).tocsr()
+    n1 = A1.shape[0]
+    x = synth.complex_normal((9, n1), 600 + nrhs)
+    xd = dev(x, torch.complex64)
+    y = torch.empty((nrhs, n1), dtype=torch.complex64, device='cuda')
+    y9 = torch.empty((9, n1), dtype=torch.complex64, device='cuda')
+    M.mgmlmc_apply(tc.ctx, M.OP_D, 1, M.FP32, xd[:nrhs].contiguous(), y, nrhs)  # pipelined
+    M.mgmlmc_apply(tc.ctx, M.OP_D, 1, M.FP32, xd, y9, 9)                          # staged
+    got, got9 = host(y), host(y9)
+    assert np.array_equal(got, got9[:nrhs])
+    x32 = x.astype(np.complex64).astype(np.complex128)
+    for r in range(nrhs):
+        assert rel(got[r], A1 @ x32[r]) < 1e-5
+
+
+@pytest.mark.parametrize('nrhs', [1, 4, 7])
+def test_bf16_stencil_matches_oracle(tc, nrhs):
+    """Variant 3: the blocks stored as BF16 pairs (round to nearest, relative
+    error <= 2^-9 per real entry), FP32 products and sums.  Bound per output
+    entry, real and imaginary parts: 2^-9 sum_k |a_k| |b_k| from the storage
+    rounding, plus FP32 accumulation (300 x 2^-24 of the same sum)."""
+    M = tc.M
+    A1 = tc.hier.matrix(1).tocsr()
+    n1 = A1.shape[0]
+    x = synth.complex_normal((nrhs, n1), 700 + nrhs)
+    x32 = x.astype(np.complex64).astype(np.complex128)
+    y = torch.empty((nrhs, n1), dtype=torch.complex64, device='cuda')
+    M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, 3)
+    try:
+        M.mgmlmc_apply(tc.ctx, M.OP_D, 1, M.FP32, dev(x, torch.complex64), y, nrhs)
+        got = host(y).astype(np.complex128)
+    finally:
+        M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, 0)
+    want = np.array([A1 @ v for v in x32])
+    Aabs = abs(A1.real) + abs(A1.imag)
+    for r in range(nrhs):
+        bnd = (2.0 ** -9 + K_FP32) * (Aabs @ (np.abs(x32[r].real) + np.abs(x32[r].imag))) + 1e-30
+        assert np.all(np.abs(got[r].real - want[r].real) <= bnd), r
+        assert np.all(np.abs(got[r].imag - want[r].imag) <= bnd), r
+        assert np.max(np.abs(got[r] - want[r])) > 0  # it is not the FP32 result
+
+
+def test_solve_with_preconditioner_variants(tc):
+    """The tensor-core and BF16 stencils inside the multigrid preconditioner
+    of FP32 inner solves: every level-0 solve still reaches the 1e-12 true
+    residual measured with the oracle's D (the FP64 defect correction)."""
+    M = tc.M
+    A0 = tc.hier.matrix(0).tocsr()
+    n = A0.shape[0]
+    b = synth.complex_normal((3, n), 801)
+    M.mgmlmc_set_solver(tc.ctx, precision=M.FP32, restart=8, coarse_restart=16, smoother=1, smoother_steps=1,
+                        coarse_iters=4, inner_tol=1e-6)
+    try:
+        for v in (1, 3, -2):
+            M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, v)
+            x = torch.empty((3, n), dtype=torch.complex128, device='cuda')
+            M.mgmlmc_apply(tc.ctx, M.OP_SOLVE, 0, M.FP64, dev(b), x, 3)
+            xs = host(x)
+            for r in range(3):
+                assert np.linalg.norm(b[r] - A0 @ xs[r]) / np.linalg.norm(b[r]) < 1.5e-12, v
+    finally:
+        M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, 0)
+        M.mgmlmc_set_solver(tc.ctx)
