@@ -90,7 +90,8 @@ WORKLOADS = {
         dims=(48, 48, 48, 96), eps=0.4, gauge='device', gauge_seed=1005, noise_seed=2005, tv_seed=3005,
         m0=-0.40, blocks=[(4, 4, 4, 4), (2, 2, 2, 2), (2, 2, 2, 2)], ntv=[16, 16, 16],
         fine_n=4, coarse_n=32, batch=32, setup_rounds=6, setup_iters=30,
-        solver=dict(SOLVER, restart=8, fine_batch=4, coarse_restart=16), stencil_variant=-2,
+        solver=dict(SOLVER, restart=8, fine_batch=4, coarse_restart=16, post_smoothing_only=1, smoother_steps=2),
+        stencil_variant=-2,
         train=dict(dims=(16, 16, 16, 16), gauge_seed=1006, blocks=[(4, 4, 4, 4), (2, 2, 2, 2)], ntv=[16, 16]),
         arms=('plain', 'oblique', 'sap', 'fp64'), fp64_fine_n=2, fp64_coarse_n=8),
     '16x16x16x16': dict(
@@ -696,6 +697,8 @@ def main():
                     help='device seconds the allocation check may take (0: skip)')
     ap.add_argument('--m0', type=float, default=None, help='override the mass (exploration)')
     ap.add_argument('--learned', type=int, default=1, help='channels of the learned smoother (0: off)')
+    ap.add_argument('--net-mode', default='after-sap', choices=['after-sap', 'replace-sap'],
+                    help='the network as one step after the SAP sweeps, or in place of SAP')
     ap.add_argument('--train-steps', type=int, default=200)
     ap.add_argument('--dslash-only', action='store_true', help='only the 32^4 FP32 Dslash measurement')
     ap.add_argument('--arms', default=None, help='comparison arms to run (comma list of %s)' % ', '.join(ARMS))
@@ -749,7 +752,7 @@ def main():
     main_solver = dict(wl['solver'])
     if args.learned > 0:
         train, t_train = train_network(M, torch, wl, ctx, stream, args.learned, args.train_steps)
-        main_solver['smoother'] = M.SMOOTHER_LEARNED
+        main_solver['smoother'] = M.SMOOTHER_LEARNED if args.net_mode == 'after-sap' else M.SMOOTHER_NET
         M.mgmlmc_set_solver(ctx, precision=prec, **main_solver)
     print('kernel launches after setup: %d' % M.mgmlmc_kernel_launches(), file=sys.stderr)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device='cuda')  # 256 MB > L2
@@ -1017,7 +1020,8 @@ def compact_line(args, wl, world, value, ms_per_step, launches, clk, det, compar
         'group_ms': {k: _r(v['ms']) for k, v in gst.items()},
         'kernel_ms': {k: _r(kst[c]['ms']) for c, k in KERNELS.items() if kst[c]['launches']},
         'profiled_step_ms': _r(prof_ms),
-        'learned': (dict(channels=args.learned, loss_init=_r(train['loss_init']), loss_last=_r(train['loss_last']),
+        'learned': (dict(channels=args.learned, mode=args.net_mode, loss_init=_r(train['loss_init']),
+                         loss_last=_r(train['loss_last']),
                          pairs=train['pairs'], trained_on=train.get('trained_on'),
                          fallbacks=train.get('fallbacks')) if train else None),
         'setup_s': _r(t_setup),
@@ -1037,7 +1041,9 @@ def compact_line(args, wl, world, value, ms_per_step, launches, clk, det, compar
                                % (lat, wl['eps'], wl['gauge_seed'], 'device generator' if wl['gauge'] == 'device'
                                   else 'host', wl['m0'], len(wl['blocks']) + 1,
                                   ', '.join('%d^4' % b[0] for b in wl['blocks']), '/'.join(map(str, wl['ntv'])),
-                                  ' + learned(%d ch)' % args.learned if args.learned else '',
+                                  ('' if not args.learned else ' + learned(%d ch)' % args.learned
+                                   if args.net_mode == 'after-sap' else ' -> learned(%d ch) in place of SAP'
+                                   % args.learned),
                                   wl['solver']['restart'], wl['fine_n'], wl['coarse_n'],
                                   wl['solver'].get('fine_batch') or wl['batch']),
                    'global_batch': sum(v['n'] for v in det['terms'].values()) // max(1, args.steps) * world,

@@ -143,6 +143,10 @@ typedef struct {
                                      that does not converge within max_iter / 4
                                      is redone with SAP alone (counted in
                                      mgmlmc_learned_stats) */
+#define MGMLMC_SMOOTHER_NET 3     /* fine level: the trained network in place of
+                                     SAP, smoother_steps residual-minimising
+                                     steps z += alpha N(r) per smoothing, with
+                                     the same SAP fallback */
 
 /* PLAIN: Hutchinson (Sec. 1, Eq. Hutchinson).  ORTHOGONAL: Sec. 3, Eq.
  * smultigrid-multilevel-monte-carlo (terms O_l, F_l, coarsest).  OBLIQUE:

@@ -342,7 +342,8 @@ void Engine::set_solver(const mgmlmc_solver_params &p) {
       (p.precision != MGMLMC_FP64 && p.precision != MGMLMC_FP32) ||
       (p.precision == MGMLMC_FP32 && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)) ||
       (p.smoother != MGMLMC_SMOOTHER_MR && p.smoother != MGMLMC_SMOOTHER_SAP &&
-       p.smoother != MGMLMC_SMOOTHER_LEARNED) || p.sap_iters < 1 || p.coarse_smoother_steps < 0 ||
+       p.smoother != MGMLMC_SMOOTHER_LEARNED && p.smoother != MGMLMC_SMOOTHER_NET) || p.sap_iters < 1 ||
+      p.coarse_smoother_steps < 0 ||
       p.sap_iters > 64 || p.fine_batch < 0)
     throw Error(MGMLMC_ERR_ARG, "invalid solver parameters");
   drop_graphs();  // captured preconditioners bake in smoother / inner iteration counts
@@ -565,6 +566,23 @@ void Engine::noise(int l, uint64_t seed, uint64_t sample0, uint64_t term, uint64
 template <typename T> void Engine::smooth(int l, C<T> *z, C<T> *res, int nrhs) {
   const int64_t n = levels_[l].g.n();
   const bool learned = l == 0 && sp_.smoother == MGMLMC_SMOOTHER_LEARNED;
+  if (l == 0 && sp_.smoother == MGMLMC_SMOOTHER_NET) {
+    // the network in place of SAP: smoother_steps residual-minimising steps
+    // z += alpha N(res), res -= alpha D N(res)
+    if (!net_.C) throw Error(MGMLMC_ERR_STATE, "network smoother selected but the network is not initialised");
+    C<T> *e = ws<T>("sape", l, (size_t)n * nrhs);
+    C<T> *q = ws<T>("smq", l, (size_t)n * nrhs);
+    double2 *d = ws<double>("netd", l, 2 * (size_t)nrhs);
+    for (int s = 0; s < sp_.smoother_steps; ++s) {
+      cudaEvent_t pa = prof_begin();
+      net_forward<T>(res, e, nrhs);
+      prof_end(pa, K_NET, 0.0, 0.0);
+      apply_D<T>(0, e, q, nrhs);
+      dot_qr<T>(q, res, n, nrhs, d, d + nrhs, partials((size_t)reduce_blocks(n) * nrhs * 2), stream);
+      mr_dir_update<T>(z, res, e, q, d, d + nrhs, n, nrhs, stream);
+    }
+    return;
+  }
   if (l == 0 && (sp_.smoother == MGMLMC_SMOOTHER_SAP || learned) && sap_b_[0] > 0) {
     C<T> *e = ws<T>("sape", l, (size_t)n * nrhs);
     const C<T> *U;
@@ -910,9 +928,10 @@ SolveInfo Engine::solve(int l, const double2 *b, double2 *x, int nrhs) {
     dense_apply<double>(levels_[l].Dinv64, b, x, (int)n, nrhs, stream);
     info.iters = 0;
     info.residual = 0.0;
-  } else if (l == 0 && sp_.smoother == MGMLMC_SMOOTHER_LEARNED) {
+  } else if (l == 0 && (sp_.smoother == MGMLMC_SMOOTHER_LEARNED || sp_.smoother == MGMLMC_SMOOTHER_NET)) {
     // learned smoother first; the true residual judges it, SAP takes over
     // when it does not converge within a quarter of the iteration budget
+    const int mode = sp_.smoother;
     const int full = sp_.max_iter;
     sp_.max_iter = std::max(1, full / 4);
     bool ok = true;
@@ -938,11 +957,11 @@ SolveInfo Engine::solve(int l, const double2 *b, double2 *x, int nrhs) {
                    ? solve_mixed(l, b, x, nrhs)
                    : fgmres<double>(l, b, x, nrhs, sp_.tol, sp_.max_iter, restart_of(l), true, false);
       } catch (...) {
-        sp_.smoother = MGMLMC_SMOOTHER_LEARNED;
+        sp_.smoother = mode;
         drop_graphs();
         throw;
       }
-      sp_.smoother = MGMLMC_SMOOTHER_LEARNED;
+      sp_.smoother = mode;
       drop_graphs();
     }
   } else if (sp_.precision == MGMLMC_FP32) {

@@ -191,7 +191,8 @@ void Engine::net_train(const mgmlmc_train_params &p, mgmlmc_train_result &out) {
   //    smoother during solves of Z4 right-hand sides (SAP when the learned
   //    smoother is selected, so the pairs never depend on the network)
   const int saved = sp_.smoother;
-  if (sp_.smoother == MGMLMC_SMOOTHER_LEARNED) sp_.smoother = MGMLMC_SMOOTHER_SAP;
+  if (sp_.smoother == MGMLMC_SMOOTHER_LEARNED || sp_.smoother == MGMLMC_SMOOTHER_NET)
+    sp_.smoother = MGMLMC_SMOOTHER_SAP;
   drop_graphs();
   if (pool_) cudaFree(pool_);
   pool_ = nullptr;

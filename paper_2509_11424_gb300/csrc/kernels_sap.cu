@@ -139,6 +139,38 @@ __device__ __forceinline__ void block_reduce3(T v0, T v1, T v2, T *s, T *out3) {
   __syncthreads();
 }
 
+// block_reduce3 over the threads of one right-hand-side slot of a CTA that
+// holds RS slots of `sites` threads each (sites a multiple of 32): lt is the
+// thread's index within its slot, s / out3 the slot's scratch
+template <typename T>
+__device__ __forceinline__ void slot_reduce3(T v0, T v1, T v2, T *s, T *out3, int lt, int nw) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v0 += __shfl_down_sync(0xffffffffu, v0, o);
+    v1 += __shfl_down_sync(0xffffffffu, v1, o);
+    v2 += __shfl_down_sync(0xffffffffu, v2, o);
+  }
+  const int w = lt >> 5, l = lt & 31;
+  if (l == 0) {
+    s[3 * w] = v0;
+    s[3 * w + 1] = v1;
+    s[3 * w + 2] = v2;
+  }
+  __syncthreads();
+  if (lt == 0) {
+    T a = 0, b = 0, c = 0;
+    for (int i = 0; i < nw; ++i) {
+      a += s[3 * i];
+      b += s[3 * i + 1];
+      c += s[3 * i + 2];
+    }
+    out3[0] = a;
+    out3[1] = b;
+    out3[2] = c;
+  }
+  __syncthreads();
+}
+
 // rho [12][sites] and Us [4 * 9][sites] are component-major in shared memory:
 // the threads of a warp (consecutive sites of the block) read consecutive
 // words, free of bank conflicts
@@ -209,29 +241,35 @@ __device__ __forceinline__ void cross_pair(const C<T> *__restrict__ ev, const C<
 // fuse_in the block's residual first takes the hops of the other colour's
 // corrections across its faces (the boundary update of the previous pass,
 // done here on the block's own sites instead of by a separate kernel).
-// FP32: two CTAs per SM (98 KB of shared memory each); FP64 (196 KB) fits
-// one, so it takes the whole register file
-template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sap_block_kernel(C<T> *__restrict__ r, C<T> *__restrict__ z,
-                                                        C<T> *e_out, const C<T> *__restrict__ U,
-                                                        SapGeom sg, T diag, int color, int iters,
-                                                        int nrhs, int fuse_in) {
+// RS right-hand sides per CTA (RS = 2 needs blocks of a multiple of 32
+// sites): the block's links are staged once for all of them, each slot of
+// `sites` threads iterates on its own right-hand side.  FP32 with RS = 1:
+// two CTAs per SM (98 KB of shared memory each); RS = 2: one of 512 threads
+// (123 KB); FP64 (196 KB) fits one, so it takes the whole register file.
+template <typename T, int RS>
+__global__ void __launch_bounds__(256 * RS, (sizeof(T) == 4 && RS == 1) ? 2 : 1)
+    sap_block_kernel(C<T> *__restrict__ r, C<T> *__restrict__ z, C<T> *e_out, const C<T> *__restrict__ U,
+                     SapGeom sg, T diag, int color, int iters, int nrhs, int fuse_in) {
   extern __shared__ unsigned char smem_raw[];
   const int sites = sg.sites;
-  C<T> *Us = reinterpret_cast<C<T> *>(smem_raw);  // [4][9][sites]
-  C<T> *rho = Us + sites * 36;                      // [12][sites]
-  T *red = reinterpret_cast<T *>(rho + sites * 12);  // reduction scratch [3 * warps]
+  const int slot = RS == 1 ? 0 : (int)threadIdx.x / sites;
+  const int ls = (int)threadIdx.x - slot * sites;
+  C<T> *Us = reinterpret_cast<C<T> *>(smem_raw);     // [4][9][sites]
+  C<T> *rho = Us + sites * 36 + slot * sites * 12;    // [slot][12][sites]
+  T *red = reinterpret_cast<T *>(Us + sites * 36 + RS * sites * 12) + slot * 100;  // per slot
   T *out3 = red + 96;
   const int64_t n = sg.g.n();
-  // the right-hand side varies fastest over the grid: the CTAs of one block
-  // run together and read its links from L2 after the first of them
-  const int rr = (int)(blockIdx.x % (unsigned)nrhs);
+  // the right-hand-side group varies fastest over the grid: the CTAs of one
+  // block run together and read its links from L2 after the first of them
+  const int ngr = (nrhs + RS - 1) / RS;
+  const int rq = (int)(blockIdx.x % (unsigned)ngr) * RS + slot;
+  const bool live = rq < nrhs;  // a slot past the last right-hand side computes on zeros
+  const int rr = live ? rq : nrhs - 1;
   C<T> *rv = r + rr * n;
   C<T> *zv = z + rr * n;
   C<T> *ev = e_out + rr * n;
   int bc[4];
-  active_block(sg, (int)(blockIdx.x / (unsigned)nrhs), color, bc);
-  const int ls = threadIdx.x;
+  active_block(sg, (int)(blockIdx.x / (unsigned)ngr), color, bc);
   int lc[4];
   {
     int t = ls;
@@ -244,23 +282,23 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sap_block_kernel(
 #pragma unroll
   for (int i = 0; i < 4; ++i) gc[i] = bc[i] * sg.b[i] + lc[i];
   const int s = sg.g.index(gc);
-  // stage links and the residual of the block
+  // stage links (once for all slots) and the residual of the block
   const int64_t V = sg.g.V;
-  for (int i = 0; i < 36; ++i) Us[i * sites + ls] = kSoa<T> ? U[(int64_t)i * V + s] : U[(int64_t)s * 36 + i];
+  for (int i = slot; i < 36; i += RS) Us[i * sites + ls] = kSoa<T> ? U[(int64_t)i * V + s] : U[(int64_t)s * 36 + i];
+  C<T> rh[12];  // this site's residual, kept in registers (its slot in rho is for the neighbours)
   {
-    C<T> p[12];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) p[i] = rv[fidx<kSoa<T>>(s, i, V)];
-    if (fuse_in) {
+    for (int i = 0; i < 12; ++i) rh[i] = live ? rv[fidx<kSoa<T>>(s, i, V)] : mk<T>((T)0, (T)0);
+    if (fuse_in && live) {
       // the other colour's blocks are the face neighbours: their fresh
       // corrections e enter this block's residual, r -= hops of e
-      cross_pair<0, T>(ev, U, sg, s, gc, p, (T)-1);
-      cross_pair<1, T>(ev, U, sg, s, gc, p, (T)-1);
-      cross_pair<2, T>(ev, U, sg, s, gc, p, (T)-1);
-      cross_pair<3, T>(ev, U, sg, s, gc, p, (T)-1);
+      cross_pair<0, T>(ev, U, sg, s, gc, rh, (T)-1);
+      cross_pair<1, T>(ev, U, sg, s, gc, rh, (T)-1);
+      cross_pair<2, T>(ev, U, sg, s, gc, rh, (T)-1);
+      cross_pair<3, T>(ev, U, sg, s, gc, rh, (T)-1);
     }
 #pragma unroll
-    for (int i = 0; i < 12; ++i) rho[i * sites + ls] = p[i];
+    for (int i = 0; i < 12; ++i) rho[i * sites + ls] = rh[i];
   }
   C<T> e[12];
 #pragma unroll
@@ -269,7 +307,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sap_block_kernel(
   for (int it = 0; it < iters; ++it) {
     C<T> q[12];
 #pragma unroll
-    for (int i = 0; i < 12; ++i) q[i] = cscale(rho[i * sites + ls], diag);
+    for (int i = 0; i < 12; ++i) q[i] = cscale(rh[i], diag);
     local_hops<T, 0>(rho, Us, lc, sg.b, ls, sites, q);
     local_hops<T, 1>(rho, Us, lc, sg.b, ls, sites, q);
     local_hops<T, 2>(rho, Us, lc, sg.b, ls, sites, q);
@@ -277,29 +315,32 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) sap_block_kernel(
     T qr_re = 0, qr_im = 0, qq = 0;
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
-      const C<T> p = rho[i * sites + ls];
+      const C<T> p = rh[i];
       qr_re = fma(q[i].x, p.x, fma(q[i].y, p.y, qr_re));
       qr_im = fma(q[i].x, p.y, fma(-q[i].y, p.x, qr_im));
       qq = fma(q[i].x, q[i].x, fma(q[i].y, q[i].y, qq));
     }
-    block_reduce3<T>(qr_re, qr_im, qq, red, out3);
+    if (RS == 1) block_reduce3<T>(qr_re, qr_im, qq, red, out3);
+    else slot_reduce3<T>(qr_re, qr_im, qq, red, out3, ls, sites >> 5);
     const T den = out3[2];
     const T tiny = sizeof(T) == 4 ? (T)1e-30 : (T)1e-280;
     const C<T> al = den > tiny ? mk<T>(out3[0] / den, out3[1] / den) : mk<T>((T)0, (T)0);
 #pragma unroll
     for (int i = 0; i < 12; ++i) {
-      const C<T> p = rho[i * sites + ls];
+      const C<T> p = rh[i];
       e[i] = cfma(al, p, e[i]);
-      rho[i * sites + ls] = cfma(cneg(al), q[i], p);
+      rh[i] = cfma(cneg(al), q[i], p);
+      rho[i * sites + ls] = rh[i];
     }
     __syncthreads();
   }
+  if (!live) return;
 #pragma unroll
   for (int i = 0; i < 12; ++i) {
     const int64_t o = fidx<kSoa<T>>(s, i, V);
     zv[o] = cadd(zv[o], e[i]);
     ev[o] = e[i];
-    rv[o] = rho[i * sites + ls];
+    rv[o] = rh[i];
   }
 }
 
@@ -345,9 +386,9 @@ bool sap_feasible(const Geom &g, const int b[4]) {
 }
 
 template <typename T>
-size_t sap_smem_bytes(const int b[4]) {
+size_t sap_smem_bytes(const int b[4], int rs) {
   const int sites = b[0] * b[1] * b[2] * b[3];
-  return (size_t)sites * 48 * sizeof(C<T>) + 100 * sizeof(T);
+  return (size_t)sites * (36 + 12 * rs) * sizeof(C<T>) + (size_t)rs * 100 * sizeof(T);
 }
 
 template <typename T>
@@ -363,14 +404,30 @@ void sap_sweep(C<T> *r, C<T> *z, C<T> *e, const C<T> *U, Geom g, const int b[4],
     sg.sites *= b[i];
     nblocks *= sg.nb[i];
   }
-  const size_t sm = sap_smem_bytes<T>(b);
-  smem_optin((const void *)sap_block_kernel<T>, (int)(220 * 1024));
+  // two right-hand sides per CTA share the block's staged links where the
+  // shared memory allows it (FP32, whole warps per right-hand side)
+  const bool two = sizeof(T) == 4 && nrhs >= 2 && sg.sites % 32 == 0 && sg.sites <= 256;
+  const int rs = two ? 2 : 1;
+  const size_t sm = sap_smem_bytes<T>(b, rs);
   if (sm > 220 * 1024) throw Error(1, "SAP block too large for shared memory");
+  const unsigned grid = (unsigned)(nblocks / 2) * (unsigned)((nrhs + rs - 1) / rs);
   // red blocks; black blocks, which first take the red corrections across
   // their faces; then the red sites take the black corrections (r exact again)
   for (int color = 0; color < 2; ++color) {
-    sap_block_kernel<T><<<(unsigned)(nblocks / 2) * (unsigned)nrhs, sg.sites, sm, s>>>(
-        r, z, e, U, sg, (T)(4.0 + m0), color, block_iters, nrhs, color);
+    if constexpr (sizeof(T) == 4) {
+      if (two) {
+        smem_optin((const void *)sap_block_kernel<T, 2>, (int)sm);
+        sap_block_kernel<T, 2><<<grid, 2 * sg.sites, sm, s>>>(r, z, e, U, sg, (T)(4.0 + m0), color,
+                                                              block_iters, nrhs, color);
+        MG_LAUNCH_CHECK();
+        continue;
+      }
+    }
+    {
+      smem_optin((const void *)sap_block_kernel<T, 1>, (int)sm);
+      sap_block_kernel<T, 1><<<grid, sg.sites, sm, s>>>(r, z, e, U, sg, (T)(4.0 + m0), color, block_iters,
+                                                        nrhs, color);
+    }
     MG_LAUNCH_CHECK();
   }
   sap_boundary_kernel<T><<<(unsigned)div_up(g.V, 128) * (unsigned)nrhs, 128, 0, s>>>(r, e, U, sg, 1, nrhs);
@@ -381,7 +438,7 @@ template void sap_sweep<double>(C<double> *, C<double> *, C<double> *, const C<d
                                 const int *, double, int, int, cudaStream_t);
 template void sap_sweep<float>(C<float> *, C<float> *, C<float> *, const C<float> *, Geom,
                                const int *, double, int, int, cudaStream_t);
-template size_t sap_smem_bytes<double>(const int *);
-template size_t sap_smem_bytes<float>(const int *);
+template size_t sap_smem_bytes<double>(const int *, int);
+template size_t sap_smem_bytes<float>(const int *, int);
 
 }  // namespace mg

@@ -220,7 +220,7 @@ def mgmlmc_set_mass(ctx, m0):
     _check(ctx, lib().mgmlmc_set_mass(ctx, float(m0)))
 
 
-SMOOTHER_MR, SMOOTHER_SAP, SMOOTHER_LEARNED = 0, 1, 2
+SMOOTHER_MR, SMOOTHER_SAP, SMOOTHER_LEARNED, SMOOTHER_NET = 0, 1, 2, 3
 
 
 def solver_params(tol=1e-12, max_iter=2000, restart=16, smoother_steps=4, coarse_iters=8,

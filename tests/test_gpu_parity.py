@@ -161,10 +161,12 @@ def test_dslash_bf16(dims):
 
 def test_dslash_variant_bad_args():
     nv = M.mgmlmc_kernel_variants(M.VARIANT_DSLASH_FP32)
-    assert M.mgmlmc_kernel_variants(1) == -1
+    ns = M.mgmlmc_kernel_variants(M.VARIANT_STENCIL_FP32)
+    assert nv == 7 and ns == 4
+    assert M.mgmlmc_kernel_variants(2) == -1
     ctx = M.mgmlmc_create((4, 4, 4, 4), torch.cuda.current_stream())
     try:
-        for kern, v in ((0, nv), (0, -1), (0, -3), (1, 0)):
+        for kern, v in ((0, nv), (0, -1), (0, -3), (1, ns), (1, -1), (2, 0)):
             with pytest.raises(M.MgmlmcError):
                 M.mgmlmc_set_kernel_variant(ctx, kern, v)
     finally:
