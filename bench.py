@@ -679,6 +679,52 @@ def validate_allocation(M, ctx, det, kinds_n, est, B, val_s, eps_scale):
                 se_over_eps=se / eps, trace=[tr.real, tr.imag])
 
 
+def kernel_probe(M, torch, args):
+    """One kernel class on a lattice small enough for a profiler capture (a
+    few GB on the device) whose launches still move more than the L2 holds:
+    `sap` (one smoothing call: smoother_steps SAP sweeps on level 0), `stencil`
+    (the FP32 coarse stencil D_1 in its selected variant), `dslash` (the FP32
+    Wilson operator).  Prints the mean event-timed milliseconds per call."""
+    from paper_2509_11424_gb300 import synth
+    dims = tuple(int(x) for x in args.probe_dims.split(','))
+    nrhs = args.probe_nrhs
+    stream = torch.cuda.current_stream()
+    ctx = M.mgmlmc_create(dims, stream)
+    try:
+        M.mgmlmc_gen_gauge(ctx, 0.4, 1005)
+        M.mgmlmc_set_mass(ctx, -0.40)
+        M.mgmlmc_set_solver(ctx, precision=M.FP32, smoother=M.SMOOTHER_SAP, smoother_steps=1, sap_iters=4)
+        level, op = 0, M.OP_D
+        if args.kernel_probe == 'sap':
+            op = M.OP_SMOOTH
+        elif args.kernel_probe == 'stencil':
+            # Z4 test vectors (no setup iterations): the stencil's cost does
+            # not depend on their quality
+            M.mgmlmc_build_hierarchy(ctx, M.mg_params([(4, 4, 4, 4), (2, 2, 2, 2)], [16, 16], setup_rounds=0,
+                                                      seed=3005))
+            M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_STENCIL_FP32, args.probe_variant)
+            level = 1
+        n = M.mgmlmc_level_info(ctx, level)[2]
+        x = torch.randn((nrhs, n), dtype=torch.complex64, device='cuda')
+        y = torch.empty_like(x)
+        if level == 0:  # operands already in the internal order: the call is the kernel alone
+            op |= M.LAYOUT_INTERNAL
+        for _ in range(3):
+            M.mgmlmc_apply(ctx, op, level, M.FP32, x, y, nrhs)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.probe_reps):
+            M.mgmlmc_apply(ctx, op, level, M.FP32, x, y, nrhs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.probe_reps
+        print(json.dumps({'kernel_probe': args.kernel_probe, 'dims': list(dims), 'level': level, 'nrhs': nrhs,
+                          'variant': args.probe_variant, 'ms_per_call': ms}))
+    finally:
+        M.mgmlmc_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
@@ -706,6 +752,12 @@ def main():
                     help='host threads of the CPU oracle timing (0: every core of this host)')
     ap.add_argument('--refine-iters', type=int, default=30,
                     help='cap on the test-vector refinement steps of the "refined" arm')
+    ap.add_argument('--kernel-probe', default=None, choices=['sap', 'stencil', 'dslash'],
+                    help='time one kernel class on a small lattice (profiler captures) and exit')
+    ap.add_argument('--probe-dims', default='32,32,32,64')
+    ap.add_argument('--probe-nrhs', type=int, default=4)
+    ap.add_argument('--probe-variant', type=int, default=0, help='stencil variant of the stencil probe')
+    ap.add_argument('--probe-reps', type=int, default=5)
     ap.add_argument('--detail-out', default=os.environ.get('MGMLMC_BENCH_DETAIL'),
                     help='file for the full per-term and per-arm detail (the JSON line keeps a summary)')
     args = ap.parse_args()
@@ -735,6 +787,9 @@ def main():
     from paper_2509_11424_gb300 import mgmlmc as M, synth
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
+    if args.kernel_probe:
+        kernel_probe(M, torch, args)
+        return
     U16 = synth.gauge_field(DIMS, EPS_GAUGE, GAUGE_SEED)
     if args.dslash_only:
         print(json.dumps({'dslash_hbm': dslash_hbm(M, torch, U16, mass['m0'])}))

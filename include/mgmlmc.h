@@ -124,9 +124,10 @@ typedef struct {
   int coarse_smoother_steps; /* MR steps of the smoother on levels >= 1 */
   int coarse_restart;  /* FGMRES restart length of the solves on levels >= 1
                           (their vectors are small), 1 .. 64; 0 = restart */
-  int post_smoothing_only; /* 1: the multigrid cycle smooths after the
-                          coarse-grid correction only (no pre-smoothing);
-                          0 (default): before and after */
+  int post_smoothing_only; /* 1: on the fine level the multigrid cycle
+                          smooths after the coarse-grid correction only (no
+                          pre-smoothing; coarser levels keep both);
+                          0 (default): before and after on every level */
   int fine_batch;      /* memory bound of the fine level: mgmlmc_estimate_trace
                           solves level-0 systems (the O_0, F_0, M_0 and plain
                           terms) in blocks of at most fine_batch right-hand
@@ -530,10 +531,12 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
  * same numbers, twice the tensor work); 3 = the blocks stored as BF16 pairs
  * (half the bytes, relative rounding <= 2^-9 per entry) with FP32
  * arithmetic, for up to 8 right-hand sides at 32 dofs per site (variant 0
- * otherwise).  Variant 0 runs up to 8 right-hand sides at 32 dofs per site in
+ * otherwise); 4 = the tensor cores with BF16 operands (tcgen05.mma
+ * kind::f16, relative rounding <= 2^-9 per operand, FP32 accumulation, half
+ * the bytes of variant 1).  Variant 0 runs up to 8 right-hand sides at 32 dofs per site in
  * a pipelined kernel (persistent blocks, a two-stage ring of bulk copies
  * over sites) with results identical to the one-site-per-block kernels.
- * -2 = autotune among 0, 1 and 3 per (level, nrhs) on the first call
+ * -2 = autotune among 0, 1, 3 and 4 per (level, nrhs) on the first call
  * outside graph capture (opt-in,
  * since the choice changes the rounding).  Inside a solve the variant applies
  * to the multigrid preconditioner only (smoothers, coarse-grid corrections);

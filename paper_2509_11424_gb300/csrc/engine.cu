@@ -374,6 +374,8 @@ void Engine::free_hierarchy() {
       dfree(L.AT64);
       dfree(L.AT32);
       dfree(L.ATC);
+      if (L.ATCB) cudaFree(L.ATCB);
+      L.ATCB = nullptr;
       dfree(L.ATB16);
     }
     L.has_next = false;
@@ -400,7 +402,7 @@ int Engine::dslash_variant(int nrhs) const {
   return it == dslash_tuned_.end() ? -2 : it->second;
 }
 
-int Engine::stencil_variants() { return 4; }
+int Engine::stencil_variants() { return 5; }
 
 void Engine::set_stencil_variant(int v) {
   if (v < -2 || v == -1 || v >= stencil_variants()) throw Error(MGMLMC_ERR_ARG, "stencil variant out of range");
@@ -417,11 +419,13 @@ int Engine::stencil_variant(int l, int nrhs) const {
 
 // 0: FP32 (the pipelined kernel where it applies, same sums as the
 // one-site-per-CTA kernels); 1, 2: tensor cores (TF32); 3: BF16-stored
-// blocks, FP32 arithmetic (pipelined kernel, up to 8 right-hand sides)
+// blocks, FP32 arithmetic (pipelined kernel, up to 8 right-hand sides);
+// 4: tensor cores with BF16 operands
 void Engine::stencil_run(int l, int v, const float2 *in, float2 *out, int nrhs) {
   const Level &L = levels_[l];
   const bool pipe = stencil_pipe_supported(L.g) && nrhs <= 8;
   if ((v == 1 || v == 2) && L.ATC) stencil_apply_tc(in, out, L.ATC, L.g, nrhs, flag_dev_ + 1, v - 1, stream);
+  else if (v == 4 && L.ATCB) stencil_apply_tc(in, out, L.ATCB, L.g, nrhs, flag_dev_ + 1, 2, stream);
   else if (v == 3 && L.ATB16 && pipe) stencil_apply_pipe(in, out, L.ATB16, true, L.g, nrhs, flag_dev_ + 1, stream);
   else if (pipe) stencil_apply_pipe(in, out, L.AT32, false, L.g, nrhs, flag_dev_ + 1, stream);
   else stencil_apply<float>(in, out, L.AT32, L.g, nrhs, flag_dev_ + 1, stream);
@@ -443,7 +447,7 @@ int Engine::stencil_pick(int l, int nrhs, const float2 *in, float2 *out) {
   int pick = 0;
   float best = 1e30f;
   // variant 2 is variant 1 with twice the tensor work: not a candidate
-  for (int v : {0, 1, 3}) {
+  for (int v : {0, 1, 3, 4}) {
     if (v == 3 && !(levels_[l].ATB16 && nrhs <= 8)) continue;
     stencil_run(l, v, in, out, nrhs);
     MG_CUDA(cudaEventRecord(ev.a, stream));
@@ -661,7 +665,7 @@ template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nr
   C<T> *ec = ws<T>("mgec", l + 1, (size_t)nc * nrhs);
   MG_CUDA(cudaMemsetAsync(z, 0, sizeof(C<T>) * n * nrhs, stream));
   MG_CUDA(cudaMemcpyAsync(res, r, sizeof(C<T>) * n * nrhs, cudaMemcpyDeviceToDevice, stream));
-  if (!sp_.post_smoothing_only) smooth<T>(l, z, res, nrhs);
+  if (!(sp_.post_smoothing_only && l == 0)) smooth<T>(l, z, res, nrhs);
   cudaEvent_t pr = prof_begin();
   restrict_op<T>(res, rc, Pmat<T>(l), agg_of<T>(l), nrhs, stream);
   prof_end(pr, K_TRANSFER, 0.0, 0.0);
@@ -1002,8 +1006,10 @@ void Engine::galerkin(int l) {
   stencil_transpose<double>(c.A64, c.AT64, (int64_t)c.g.V * 9, dofc, stream);
   stencil_transpose<float>(c.A64, c.AT32, (int64_t)c.g.V * 9, dofc, stream);
   if (stencil_tc_supported(c.g)) {
-    c.ATC = dalloc<float>(stencil_tc_floats(c.g));
-    stencil_tile_tc(c.A64, c.ATC, c.g, stream);
+    c.ATC = dalloc<float>(stencil_tc_elems(c.g));
+    stencil_tile_tc(c.A64, c.ATC, false, c.g, stream);
+    c.ATCB = dalloc<float>((stencil_tc_elems(c.g) + 1) / 2);  // BF16 elements, two per float slot
+    stencil_tile_tc(c.A64, c.ATCB, true, c.g, stream);
   }
   if (stencil_pipe_supported(c.g)) {
     c.ATB16 = dalloc<float>(acnt);  // one bf16 pair (4 bytes) per complex entry

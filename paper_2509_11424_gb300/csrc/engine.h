@@ -24,6 +24,7 @@ struct Level {
   double2 *AT64 = nullptr;  // the same blocks transposed [V][9][j][i] (apply)
   float2 *AT32 = nullptr;
   float *ATC = nullptr;     // tensor-core tiles (32 dofs per site only), see stencil_tile_tc
+  void *ATCB = nullptr;     // the same tiles in BF16 (kind::f16 MMAs)
   float *ATB16 = nullptr;   // AT32 as bf16 pairs (32 dofs per site only), preconditioner variant
   bool has_next = false;
   AggMap agg{};            // to level + 1
@@ -183,8 +184,8 @@ class Engine {
   int dslash_variant(int nrhs) const;
   // FP32 coarse stencil per rhs count: 0 = FP32 CUDA cores, 1 = tcgen05
   // TF32 with M = 64 MMAs, 2 = the same with M = 128 MMAs, 3 = BF16-stored
-  // blocks with FP32 arithmetic, -2 = the fastest of 0, 1, 3 on the first call
-  // outside capture
+  // blocks with FP32 arithmetic, 4 = tcgen05 with BF16 operands, -2 = the
+  // fastest of 0, 1, 3, 4 on the first call outside capture
   void set_stencil_variant(int v);
   int stencil_variant(int l, int nrhs) const;
   static int stencil_variants();

@@ -131,12 +131,13 @@ void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, 
 // ATC holds each site's nine stacked [Re A_d; Im A_d] tiles in the MMA's
 // shared-memory image (stencil_tile_tc builds it from the canonical A);
 // FP32 vectors, TF32 products, FP32 accumulation.  layout 0: M = 64 MMAs,
-// 1: M = 128 MMAs with half the rows discarded (see kernels_tc.cu).  err[0] =
-// 3 if a bounded wait runs out.
+// 1: M = 128 MMAs with half the rows discarded, 2: BF16 operands (kind::f16,
+// M = 64) (see kernels_tc.cu).  err[0] = 3 if a bounded wait runs out.
+// With bf16 the tiles hold BF16 values (kind::f16 MMAs, layout 2).
 bool stencil_tc_supported(const Geom &g);
-size_t stencil_tc_floats(const Geom &g);
-void stencil_tile_tc(const double2 *A, float *ATC, const Geom &g, cudaStream_t s);
-void stencil_apply_tc(const float2 *in, float2 *out, const float *ATC, Geom g, int nrhs, int *err, int layout,
+size_t stencil_tc_elems(const Geom &g);
+void stencil_tile_tc(const double2 *A, void *ATC, bool bf16, const Geom &g, cudaStream_t s);
+void stencil_apply_tc(const float2 *in, float2 *out, const void *ATC, Geom g, int nrhs, int *err, int layout,
                       cudaStream_t s);
 // Pipelined FP32 coarse stencil for 32 dofs per site and 1 .. 8 right-hand
 // sides: persistent CTAs with a two-stage ring of bulk copies over sites.

@@ -20,21 +20,37 @@
 // every wait is bounded and a timeout sets the error flag, waits (bounded)
 // for the work in flight, releases the tensor memory and leaves.
 //
-// Precision: the tensor cores read the FP32 operands as TF32 (10-bit
-// mantissa) and accumulate in FP32.  The result is therefore not the FP32
-// stencil; it is used inside the FP32 inner solves of the FP64 defect
-// correction, where the true FP64 residual still decides convergence.
+// Precision: kind::tf32 reads FP32 operands as TF32 (10-bit mantissa);
+// kind::f16 takes BF16 operands (8-bit mantissa, half the bytes and twice the
+// tensor rate); both accumulate in FP32.  Neither is the FP32 stencil: the
+// library uses them inside the multigrid preconditioner of the FP32 inner
+// solves of the FP64 defect correction, where the true FP64 residual still
+// decides convergence.
 #include "kernels.h"
+
+#include <cuda_bf16.h>
 
 namespace mg {
 
 namespace {
 
 constexpr int kTcM = 32;                          // dofs per coarse site this path serves
-constexpr int kTcTileFloats = 64 * kTcM;          // one stacked [Ar; Ai] tile
-constexpr int kTcSiteBytes = 9 * kTcTileFloats * 4;  // 73728
+constexpr int kTcTileElems = 64 * kTcM;           // one stacked [Ar; Ai] tile
 constexpr int kTcMaxN = 32;                       // right-hand sides per MMA chunk
 constexpr int kTcThreads = 128;
+
+// operand element types: TF32 (FP32 storage, kind::tf32, K = 8 per MMA) and
+// BF16 (kind::f16, K = 16 per MMA); a core-matrix row is 16 bytes = KC
+// elements, each MMA spans two core matrices along K
+template <typename E> struct TcOp;
+template <> struct TcOp<float> {
+  static constexpr int KC = 4, KMMA = 8;
+  static constexpr uint32_t fmt = 2;  // TF32
+};
+template <> struct TcOp<__nv_bfloat16> {
+  static constexpr int KC = 8, KMMA = 16;
+  static constexpr uint32_t fmt = 1;  // BF16
+};
 
 __device__ __forceinline__ unsigned saddr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -81,19 +97,29 @@ __device__ __forceinline__ uint64_t smem_desc(unsigned addr, unsigned lbo, unsig
   d |= (uint64_t)1 << 46;
   return d;
 }
-// instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both
-// K-major, N >> 3 at bit 17, M >> 4 at bit 24
-__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// instruction descriptor: FP32 accumulator (bits 4-5 = 1), A and B format
+// (bits 7-9, 10-12: TF32 = 2 under kind::tf32, BF16 = 1 under kind::f16),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t mma_idesc(uint32_t fmt, int M, int N) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(unsigned tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         unsigned accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
+template <typename E>
+__device__ __forceinline__ void mma_op(unsigned tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                       unsigned accumulate) {
+  if constexpr (sizeof(E) == 4) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
 }
 __device__ __forceinline__ void mma_commit(uint64_t *mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(saddr(mbar))
@@ -127,19 +153,29 @@ template <int LAYOUT> __device__ __forceinline__ int acc_row_of_lane(int warp, i
   return warp < 2 ? 32 * warp + lane : -1;
 }
 
-// smem: [A tiles 9 x 8 KB][B: 9 dirs x {re, im} x (N x 32 floats)][acc staging]
-template <int LAYOUT>
+// four complex values (re, im) as the quad of real parts and the quad of
+// imaginary parts in the operand element type
+__device__ __forceinline__ void split_store(float *re_dst, float *im_dst, float2 a, float2 b, float2 c, float2 d) {
+  *reinterpret_cast<float4 *>(re_dst) = make_float4(a.x, b.x, c.x, d.x);
+  *reinterpret_cast<float4 *>(im_dst) = make_float4(a.y, b.y, c.y, d.y);
+}
+
+// smem: [A tiles 9 x 64 x 32 E][B: 9 dirs x {re, im} x (N x 32 E)][acc staging 2 x 64 x 32 FP32]
+template <typename E, int LAYOUT>
 __global__ void __launch_bounds__(kTcThreads) stencil_tc_kernel(const float2 *__restrict__ in,
                                                                float2 *__restrict__ out,
-                                                               const float *__restrict__ ATC, Geom g,
+                                                               const E *__restrict__ ATC, Geom g,
                                                                int nrhs, int *err, unsigned extra_tx) {
+  using Op = TcOp<E>;
+  constexpr int KC = Op::KC;
+  constexpr unsigned kSiteBytes = 9u * kTcTileElems * sizeof(E);
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t bar_a, bar_mma;
   __shared__ unsigned tmem_slot;
   __shared__ int fail;
-  float *As = reinterpret_cast<float *>(smem_raw);
-  float *Bs = As + 9 * kTcTileFloats;          // [d][part][N x 32]
-  float *St = Bs + 9 * 2 * kTcMaxN * kTcM;       // [2 acc][64 rows][kTcMaxN]
+  E *As = reinterpret_cast<E *>(smem_raw);
+  E *Bs = As + 9 * kTcTileElems;                                           // [d][part][N x 32]
+  float *St = reinterpret_cast<float *>(Bs + 9 * 2 * kTcMaxN * kTcM);      // [2 acc][64 rows][kTcMaxN]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int X = blockIdx.x;
   const int64_t n = g.n();
@@ -161,8 +197,8 @@ __global__ void __launch_bounds__(kTcThreads) stencil_tc_kernel(const float2 *__
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const unsigned tmem = tmem_slot;
   if (tid == 0) {
-    tc_expect_tx(&bar_a, (unsigned)kTcSiteBytes + extra_tx);  // extra_tx: failure-injection tests only
-    tc_bulk_g2s(As, ATC + (int64_t)X * (kTcSiteBytes / 4), (unsigned)kTcSiteBytes, &bar_a);
+    tc_expect_tx(&bar_a, kSiteBytes + extra_tx);  // extra_tx: failure-injection tests only
+    tc_bulk_g2s(As, ATC + (int64_t)X * 9 * kTcTileElems, kSiteBytes, &bar_a);
   }
   int nbr[9];
 #pragma unroll
@@ -172,22 +208,32 @@ __global__ void __launch_bounds__(kTcThreads) stencil_tc_kernel(const float2 *__
   bool a_ready = false;
   for (int r0 = 0; r0 < nrhs; r0 += kTcMaxN) {
     const int rc = nrhs - r0 < kTcMaxN ? nrhs - r0 : kTcMaxN;
-    const int N = LAYOUT == 2 ? (rc + 15) & ~15 : (rc + 7) & ~7;  // MMA N (M = 128 needs N % 16 == 0)
+    const int N = LAYOUT == 1 ? (rc + 15) & ~15 : (rc + 7) & ~7;  // MMA N (M = 128 needs N % 16 == 0)
     // gather B: element (n, k) of part p of direction d at
-    // ((k/4) * N + n) * 4 + k%4 floats (core matrices of 8 rows x 16 bytes)
-    for (int t = tid; t < 9 * 8 * N; t += kTcThreads) {
-      const int nn = t % N, c = (t / N) & 7, d = t / (8 * N);
-      float4 re = make_float4(0.f, 0.f, 0.f, 0.f), im = re;
-      if (nn < rc) {
-        const float4 *src = reinterpret_cast<const float4 *>(in + (int64_t)(r0 + nn) * n +
-                                                             (int64_t)nbr[d] * kTcM + 4 * c);
-        const float4 a = __ldg(src), b = __ldg(src + 1);  // 4 complex: (re, im) pairs
-        re = make_float4(a.x, a.z, b.x, b.z);
-        im = make_float4(a.y, a.w, b.y, b.w);
+    // ((k / KC) * N + n) * KC + k % KC (core matrices of 8 rows x 16 bytes)
+    for (int t = tid; t < 9 * (kTcM / KC) * N; t += kTcThreads) {
+      const int nn = t % N, c = (t / N) % (kTcM / KC), d = t / ((kTcM / KC) * N);
+      E *base = Bs + (size_t)(d * 2) * kTcMaxN * kTcM;
+      E *re_dst = base + ((size_t)c * N + nn) * KC;
+      E *im_dst = base + kTcMaxN * kTcM + ((size_t)c * N + nn) * KC;
+      const float2 *src = in + (int64_t)(r0 + (nn < rc ? nn : 0)) * n + (int64_t)nbr[d] * kTcM + KC * c;
+      if constexpr (sizeof(E) == 4) {
+        float2 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = nn < rc ? __ldg(src + q) : make_float2(0.f, 0.f);
+        split_store(reinterpret_cast<float *>(re_dst), reinterpret_cast<float *>(im_dst), v[0], v[1], v[2], v[3]);
+      } else {
+        __nv_bfloat162 re[4], im[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 a = nn < rc ? __ldg(src + 2 * q) : make_float2(0.f, 0.f);
+          const float2 b = nn < rc ? __ldg(src + 2 * q + 1) : make_float2(0.f, 0.f);
+          re[q] = __floats2bfloat162_rn(a.x, b.x);
+          im[q] = __floats2bfloat162_rn(a.y, b.y);
+        }
+        *reinterpret_cast<uint4 *>(re_dst) = *reinterpret_cast<const uint4 *>(re);
+        *reinterpret_cast<uint4 *>(im_dst) = *reinterpret_cast<const uint4 *>(im);
       }
-      float *base = Bs + (size_t)(d * 2) * kTcMaxN * kTcM;
-      reinterpret_cast<float4 *>(base)[c * N + nn] = re;
-      reinterpret_cast<float4 *>(base + kTcMaxN * kTcM)[c * N + nn] = im;
     }
     // make the generic-proxy stores visible to the tensor cores
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -201,18 +247,18 @@ __global__ void __launch_bounds__(kTcThreads) stencil_tc_kernel(const float2 *__
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (bad) break;
     if (tid == 0) {
-      const uint32_t idesc = tf32_idesc(LAYOUT == 2 ? 128 : 64, N);
+      const uint32_t idesc = mma_idesc(Op::fmt, LAYOUT == 1 ? 128 : 64, N);
       const unsigned a0 = saddr(As), b0 = saddr(Bs);
       for (int d = 0; d < 9; ++d) {
-        for (int kc = 0; kc < 4; ++kc) {
+        for (int kc = 0; kc < kTcM / Op::KMMA; ++kc) {
           // A: core matrix (row group gr, K chunk c) at c * 1024 + gr * 128
-          const uint64_t ad = smem_desc(a0 + d * kTcTileFloats * 4 + kc * 2 * 1024, 1024, 128);
+          const uint64_t ad = smem_desc(a0 + d * kTcTileElems * (unsigned)sizeof(E) + kc * 2 * 1024, 1024, 128);
           // B: (n group, K chunk c) at c * N * 16 + ng * 128
-          const unsigned bre = b0 + (unsigned)(d * 2) * kTcMaxN * kTcM * 4 + kc * 2 * N * 16;
-          const unsigned bim = bre + kTcMaxN * kTcM * 4;
+          const unsigned bre = b0 + (unsigned)(d * 2) * kTcMaxN * kTcM * (unsigned)sizeof(E) + kc * 2 * N * 16;
+          const unsigned bim = bre + kTcMaxN * kTcM * (unsigned)sizeof(E);
           const unsigned acc = (d > 0 || kc > 0) ? 1u : 0u;
-          mma_tf32(tmem, ad, smem_desc(bre, N * 16, 128), idesc, acc);
-          mma_tf32(tmem + kTcMaxN, ad, smem_desc(bim, N * 16, 128), idesc, acc);
+          mma_op<E>(tmem, ad, smem_desc(bre, N * 16, 128), idesc, acc);
+          mma_op<E>(tmem + kTcMaxN, ad, smem_desc(bim, N * 16, 128), idesc, acc);
         }
       }
       mma_commit(&bar_mma);
@@ -236,7 +282,7 @@ __global__ void __launch_bounds__(kTcThreads) stencil_tc_kernel(const float2 *__
       const unsigned lane_base = (unsigned)(32 * warp) << 16;
       tmem_ld32(tmem + lane_base, v1);
       tmem_ld32(tmem + lane_base + kTcMaxN, v2);
-      const int row = acc_row_of_lane<LAYOUT>(warp, lane);
+      const int row = acc_row_of_lane<LAYOUT == 1 ? 2 : 0>(warp, lane);
       if (row >= 0) {
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
@@ -270,18 +316,23 @@ __global__ void __launch_bounds__(kTcThreads) stencil_tc_kernel(const float2 *__
   if (tid == 0 && fail && err) atomicExch(err, 3);
 }
 
-// ATC[X][d][c][gr][r][q] = element (row 8 gr + r, k = 4 c + q) of the stacked
-// tile [Re A; Im A] of block d of site X (A canonical [X][d][i][j])
-__global__ void stencil_tile_tc_kernel(const double2 *__restrict__ A, float *__restrict__ ATC, int64_t nsites) {
-  const int64_t total = nsites * 9 * kTcTileFloats;
+// ATC[X][d][c][gr][r][q] = element (row 8 gr + r, k = KC c + q) of the
+// stacked tile [Re A; Im A] of block d of site X (A canonical [X][d][i][j]),
+// in the operand type E
+template <typename E>
+__global__ void stencil_tile_tc_kernel(const double2 *__restrict__ A, E *__restrict__ ATC, int64_t nsites) {
+  constexpr int KC = TcOp<E>::KC;
+  const int64_t total = nsites * 9 * kTcTileElems;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t blk = e / kTcTileFloats;  // X * 9 + d
-    const int w = (int)(e - blk * kTcTileFloats);
-    const int q = w & 3, r = (w >> 2) & 7, gr = (w >> 5) & 7, c = w >> 8;
-    const int row = 8 * gr + r, k = 4 * c + q;
+    const int64_t blk = e / kTcTileElems;  // X * 9 + d
+    const int w = (int)(e - blk * kTcTileElems);
+    const int q = w % KC, r = (w / KC) & 7, gr = (w / (8 * KC)) & 7, c = w / (64 * KC);
+    const int row = 8 * gr + r, k = KC * c + q;
     const double2 a = A[blk * kTcM * kTcM + (int64_t)(row & 31) * kTcM + k];
-    ATC[e] = (float)(row < 32 ? a.x : a.y);
+    const float v = (float)(row < 32 ? a.x : a.y);
+    if constexpr (sizeof(E) == 4) ATC[e] = v;
+    else ATC[e] = __float2bfloat16_rn(v);
   }
 }
 
@@ -289,32 +340,35 @@ __global__ void stencil_tile_tc_kernel(const double2 *__restrict__ A, float *__r
 
 bool stencil_tc_supported(const Geom &g) { return g.dof == kTcM; }
 
-size_t stencil_tc_floats(const Geom &g) { return (size_t)g.V * 9 * kTcTileFloats; }
+size_t stencil_tc_elems(const Geom &g) { return (size_t)g.V * 9 * kTcTileElems; }
 
-void stencil_tile_tc(const double2 *A, float *ATC, const Geom &g, cudaStream_t s) {
+void stencil_tile_tc(const double2 *A, void *ATC, bool bf16, const Geom &g, cudaStream_t s) {
   if (!stencil_tc_supported(g)) throw Error(1, "tensor-core stencil: needs 32 dofs per coarse site");
-  const int64_t total = (int64_t)g.V * 9 * kTcTileFloats;
+  const int64_t total = (int64_t)g.V * 9 * kTcTileElems;
   const int64_t blocks = (total + 255) / 256;
-  stencil_tile_tc_kernel<<<(int)(blocks < 152 * 16 ? blocks : 152 * 16), 256, 0, s>>>(A, ATC, g.V);
+  const int grid = (int)(blocks < 152 * 16 ? blocks : 152 * 16);
+  if (bf16) stencil_tile_tc_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(A, (__nv_bfloat16 *)ATC, g.V);
+  else stencil_tile_tc_kernel<float><<<grid, 256, 0, s>>>(A, (float *)ATC, g.V);
   MG_LAUNCH_CHECK();
 }
 
-void stencil_apply_tc(const float2 *in, float2 *out, const float *ATC, Geom g, int nrhs, int *err, int layout,
+template <typename E, int LAYOUT>
+static void launch_tc(const float2 *in, float2 *out, const E *ATC, Geom g, int nrhs, int *err, cudaStream_t s) {
+  const size_t sm = (size_t)(9 * kTcTileElems + 9 * 2 * kTcMaxN * kTcM) * sizeof(E) +
+                    (size_t)2 * 64 * kTcMaxN * sizeof(float);
+  smem_optin((const void *)stencil_tc_kernel<E, LAYOUT>, (int)sm);
+  stencil_tc_kernel<E, LAYOUT><<<g.V, kTcThreads, sm, s>>>(in, out, ATC, g, nrhs, err, staging_extra_bytes());
+  MG_LAUNCH_CHECK();
+}
+
+void stencil_apply_tc(const float2 *in, float2 *out, const void *ATC, Geom g, int nrhs, int *err, int layout,
                       cudaStream_t s) {
   if (!stencil_tc_supported(g)) throw Error(1, "tensor-core stencil: needs 32 dofs per coarse site");
   if ((((uintptr_t)in | (uintptr_t)out | (uintptr_t)ATC) & 15) != 0)
     throw Error(1, "tensor-core stencil: operands must be 16-byte aligned");
-  const size_t sm = (size_t)(9 * kTcTileFloats + 9 * 2 * kTcMaxN * kTcM + 2 * 64 * kTcMaxN) * sizeof(float);
-  if (layout == 1) {
-    smem_optin((const void *)stencil_tc_kernel<2>, (int)sm);
-    stencil_tc_kernel<2><<<g.V, kTcThreads, sm, s>>>(in, out, ATC, g, nrhs, err,
-                                                             staging_extra_bytes());
-  } else {
-    smem_optin((const void *)stencil_tc_kernel<0>, (int)sm);
-    stencil_tc_kernel<0><<<g.V, kTcThreads, sm, s>>>(in, out, ATC, g, nrhs, err,
-                                                             staging_extra_bytes());
-  }
-  MG_LAUNCH_CHECK();
+  if (layout == 2) launch_tc<__nv_bfloat16, 0>(in, out, (const __nv_bfloat16 *)ATC, g, nrhs, err, s);
+  else if (layout == 1) launch_tc<float, 1>(in, out, (const float *)ATC, g, nrhs, err, s);
+  else launch_tc<float, 0>(in, out, (const float *)ATC, g, nrhs, err, s);
 }
 
 }  // namespace mg

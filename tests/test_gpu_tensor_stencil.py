@@ -39,19 +39,21 @@ def tc():
     s.close()
 
 
-def bound_check(got, x32, A1):
-    """|got - A1 x| within the TF32 bound, entry by entry (real and imaginary
-    parts separately)."""
+def bound_check(got, x32, A1, u=U_TF32):
+    """|got - A1 x| within the bound for operands rounded with relative error
+    u, entry by entry (real and imaginary parts separately)."""
     want = A1 @ x32
     Aabs = abs(A1.real) + abs(A1.imag)
     xabs = np.abs(x32.real) + np.abs(x32.imag)
-    bnd = (2.1 * U_TF32 + K_FP32) * (Aabs @ xabs) + 1e-30
+    bnd = (2.1 * u + K_FP32) * (Aabs @ xabs) + 1e-30
     ok_re = np.abs(got.real - want.real) <= bnd
     ok_im = np.abs(got.imag - want.imag) <= bnd
     return bool(ok_re.all() and ok_im.all()), float(np.max(np.abs(got - want) / bnd))
 
 
-@pytest.mark.parametrize('variant', [1, 2])
+# variant 4: BF16 operands (kind::f16), both rounded to nearest: relative
+# error <= 2^-9 per operand, the same bound with u = 2^-9
+@pytest.mark.parametrize('variant', [1, 2, 4])
 @pytest.mark.parametrize('nrhs', [1, 8, 32, 37])
 def test_tensor_stencil_matches_oracle(tc, variant, nrhs):
     M = tc.M
@@ -66,8 +68,9 @@ def test_tensor_stencil_matches_oracle(tc, variant, nrhs):
         got = host(y).astype(np.complex128)
     finally:
         M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, 0)
+    u = 2.0 ** -9 if variant == 4 else U_TF32
     for r in range(nrhs):
-        ok, worst = bound_check(got[r], x32[r], A1)
+        ok, worst = bound_check(got[r], x32[r], A1, u)
         assert ok, (variant, nrhs, r, worst)
 
 
@@ -133,7 +136,7 @@ def test_solve_with_preconditioner_variants(tc):
     M.mgmlmc_set_solver(tc.ctx, precision=M.FP32, restart=8, coarse_restart=16, smoother=1, smoother_steps=1,
                         coarse_iters=4, inner_tol=1e-6)
     try:
-        for v in (1, 3, -2):
+        for v in (1, 3, 4, -2):
             M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, v)
             x = torch.empty((3, n), dtype=torch.complex128, device='cuda')
             M.mgmlmc_apply(tc.ctx, M.OP_SOLVE, 0, M.FP64, dev(b), x, 3)
