@@ -97,6 +97,39 @@ __host__ __device__ __forceinline__ int64_t fidx(int64_t s, int i, int64_t V) {
   return SOA ? soa_index(s, i, V) : s * 12 + i;
 }
 
+// the 12 components of site s of a fine vector: FP32 structure-of-arrays
+// vectors as six 16-byte chunks (two components each, one load per chunk, so
+// a warp's access covers whole sectors), FP64 ones canonical
+template <typename T>
+__device__ __forceinline__ void load_fine_site(const C<T> *v, int64_t s, int64_t V, C<T> (&p)[12]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 *c = reinterpret_cast<const float4 *>(v);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float4 q = c[(int64_t)k * V + s];
+      p[2 * k] = mk<T>(q.x, q.y);
+      p[2 * k + 1] = mk<T>(q.z, q.w);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) p[i] = v[s * 12 + i];
+  }
+}
+template <typename T>
+__device__ __forceinline__ void store_fine_site(C<T> *v, int64_t s, int64_t V, const C<T> (&p)[12]) {
+  if constexpr (sizeof(T) == 4) {
+    float4 *c = reinterpret_cast<float4 *>(v);
+#pragma unroll
+    for (int k = 0; k < 6; ++k)
+      c[(int64_t)k * V + s] = make_float4(p[2 * k].x, p[2 * k].y, p[2 * k + 1].x, p[2 * k + 1].y);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 12; ++i) v[s * 12 + i] = p[i];
+  }
+}
+
+
+
 // Block aggregation of a level (Sec. 2.2): aggregates are blocks of extent
 // b[4]; rows of an (aggregate, chirality) pair are site_in_block * half + d.
 struct AggMap {

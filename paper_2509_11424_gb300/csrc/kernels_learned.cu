@@ -30,8 +30,7 @@ __device__ __forceinline__ void transported(const C<T> *__restrict__ psi, const 
                                             C<T> (&t)[12]) {
   const int64_t V = g.V;
   if (h == 0) {
-#pragma unroll
-    for (int i = 0; i < 12; ++i) t[i] = psi[fidx<kSoa<T>>(s, i, V)];
+    load_fine_site<T>(psi, s, V, t);
     return;
   }
   const int mu = (h - 1) >> 1;
@@ -51,16 +50,16 @@ __device__ __forceinline__ void transported(const C<T> *__restrict__ psi, const 
 #pragma unroll
   for (int i = 0; i < 9; ++i)
     uu[i] = kSoa<T> ? __ldg(U + (int64_t)(mu * 9 + i) * V + ls) : __ldg(U + ((int64_t)ls * 4 + mu) * 9 + i);
+  C<T> v[12];
+  load_fine_site<T>(psi, sn, V, v);
 #pragma unroll
   for (int sp = 0; sp < 4; ++sp) {
-    C<T> v[3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) v[b] = psi[fidx<kSoa<T>>(sn, sp * 3 + b, V)];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
       C<T> z = mk<T>((T)0, (T)0);
 #pragma unroll
-      for (int b = 0; b < 3; ++b) z = fwd ? cfma(uu[3 * a + b], v[b], z) : cfmac(uu[3 * b + a], v[b], z);
+      for (int b = 0; b < 3; ++b)
+        z = fwd ? cfma(uu[3 * a + b], v[sp * 3 + b], z) : cfmac(uu[3 * b + a], v[sp * 3 + b], z);
       t[sp * 3 + a] = cscale(z, sign);
     }
   }
@@ -117,9 +116,7 @@ __global__ void __launch_bounds__(128) glayer_forward_kernel(const C<T> *__restr
 #pragma unroll
   for (int k = 0; k < OG; ++k) {
     if (k < og) {
-      C<T> *o_ = out + ((int64_t)b * Cout + o0 + k) * n;
-#pragma unroll
-      for (int i = 0; i < 12; ++i) o_[fidx<kSoa<T>>(s, i, g.V)] = acc[k][i];
+      store_fine_site<T>(out + ((int64_t)b * Cout + o0 + k) * n, s, g.V, acc[k]);
     }
   }
 }

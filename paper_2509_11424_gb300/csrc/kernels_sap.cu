@@ -41,37 +41,6 @@ __device__ __forceinline__ void link_at(const C<T> *__restrict__ U, int64_t V, i
     u[k] = kSoa<T> ? U[(int64_t)(mu * 9 + k) * V + site] : U[(site * 4 + mu) * 9 + k];
 }
 
-// the 12 components of site s of a fine vector: FP32 structure-of-arrays
-// vectors as six 16-byte chunks (two components each, one load per chunk, so
-// a warp's access covers whole sectors), FP64 ones canonical
-template <typename T>
-__device__ __forceinline__ void load_site(const C<T> *v, int64_t s, int64_t V, C<T> (&p)[12]) {
-  if constexpr (kSoa<T>) {
-    const float4 *c = reinterpret_cast<const float4 *>(v);
-#pragma unroll
-    for (int k = 0; k < 6; ++k) {
-      const float4 q = c[(int64_t)k * V + s];
-      p[2 * k] = mk<T>(q.x, q.y);
-      p[2 * k + 1] = mk<T>(q.z, q.w);
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 12; ++i) p[i] = v[s * 12 + i];
-  }
-}
-template <typename T>
-__device__ __forceinline__ void store_site(C<T> *v, int64_t s, int64_t V, const C<T> (&p)[12]) {
-  if constexpr (kSoa<T>) {
-    float4 *c = reinterpret_cast<float4 *>(v);
-#pragma unroll
-    for (int k = 0; k < 6; ++k)
-      c[(int64_t)k * V + s] = make_float4(p[2 * k].x, p[2 * k].y, p[2 * k + 1].x, p[2 * k + 1].y);
-  } else {
-#pragma unroll
-    for (int i = 0; i < 12; ++i) v[s * 12 + i] = p[i];
-  }
-}
-
 struct SapGeom {
   Geom g;
   int b[4];   // block extents
@@ -246,7 +215,7 @@ __device__ __forceinline__ void cross_pair(const C<T> *__restrict__ ev, const C<
       const int sn = g.index(cn);
       const T k = sign * ((MU == 3 && cn[3] == 0) ? (T)0.5 : (T)-0.5);
       C<T> p[12], u[9];
-      load_site<T>(ev, sn, g.V, p);
+      load_fine_site<T>(ev, sn, g.V, p);
       link_at<T>(U, g.V, s, MU, u);
       shop<MU, true, T>(p, u, k, acc);
     }
@@ -258,7 +227,7 @@ __device__ __forceinline__ void cross_pair(const C<T> *__restrict__ ev, const C<
       const int sn = g.index(cn);
       const T k = sign * ((MU == 3 && c[3] == 0) ? (T)0.5 : (T)-0.5);
       C<T> p[12], u[9];
-      load_site<T>(ev, sn, g.V, p);
+      load_fine_site<T>(ev, sn, g.V, p);
       link_at<T>(U, g.V, sn, MU, u);
       shop<MU, false, T>(p, u, k, acc);
     }
@@ -317,7 +286,7 @@ __global__ void __launch_bounds__(256 * RS, (sizeof(T) == 4 && RS == 1) ? 2 : 1)
   C<T> rh[12];  // this site's residual, kept in registers (its slot in rho is for the neighbours)
   {
     if (live) {
-      load_site<T>(rv, s, V, rh);
+      load_fine_site<T>(rv, s, V, rh);
     } else {
 #pragma unroll
       for (int i = 0; i < 12; ++i) rh[i] = mk<T>((T)0, (T)0);
@@ -370,13 +339,13 @@ __global__ void __launch_bounds__(256 * RS, (sizeof(T) == 4 && RS == 1) ? 2 : 1)
   if (!live) return;
   {
     C<T> zz[12];
-    load_site<T>(zv, s, V, zz);
+    load_fine_site<T>(zv, s, V, zz);
 #pragma unroll
     for (int i = 0; i < 12; ++i) zz[i] = cadd(zz[i], e[i]);
-    store_site<T>(zv, s, V, zz);
+    store_fine_site<T>(zv, s, V, zz);
   }
-  store_site<T>(ev, s, V, e);
-  store_site<T>(rv, s, V, rh);
+  store_fine_site<T>(ev, s, V, e);
+  store_fine_site<T>(rv, s, V, rh);
 }
 
 template <typename T>
@@ -402,10 +371,10 @@ __global__ void sap_boundary_kernel(C<T> *__restrict__ r, const C<T> *__restrict
   cross_pair<2, T>(ev, U, sg, s, c, acc);
   cross_pair<3, T>(ev, U, sg, s, c, acc);
   C<T> res[12];
-  load_site<T>(rv, s, sg.g.V, res);
+  load_fine_site<T>(rv, s, sg.g.V, res);
 #pragma unroll
   for (int i = 0; i < 12; ++i) res[i] = csub(res[i], acc[i]);
-  store_site<T>(rv, s, sg.g.V, res);
+  store_fine_site<T>(rv, s, sg.g.V, res);
 }
 
 }  // namespace
