@@ -118,8 +118,9 @@ typedef struct {
   int smoother;        /* fine level: MGMLMC_SMOOTHER_SAP (red/black Schwarz
                           blocks, MR inside each block) or MGMLMC_SMOOTHER_MR;
                           coarse levels always use MR.  SAP needs an even
-                          number of blocks in every direction (blocks of 4^4,
-                          else 2^4); otherwise MR is used. */
+                          number of blocks in every direction (blocks of
+                          8 x 4 x 4 x 2, else 4^4, else 2^4); otherwise MR is
+                          used. */
   int sap_iters;       /* MR iterations inside each SAP block */
   int coarse_smoother_steps; /* MR steps of the smoother on levels >= 1 */
   int coarse_restart;  /* FGMRES restart length of the solves on levels >= 1

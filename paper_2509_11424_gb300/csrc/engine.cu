@@ -88,11 +88,16 @@ Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
   sp_.smoother = MGMLMC_SMOOTHER_MR;
   sp_.sap_iters = 4;
   sp_.coarse_smoother_steps = 4;
-  // SAP blocks: 4^4 when every direction holds an even number of them, else 2^4
-  for (int bsz : {4, 2}) {
-    int b[4] = {bsz, bsz, bsz, bsz};
+  // SAP blocks of 256 sites, 8 x 4 x 4 x 2, when every direction holds an
+  // even number of them: a block's x rows are then 128 bytes per FP32
+  // structure-of-arrays chunk and 64 bytes per link plane, whole memory
+  // bursts (the 4-site rows of 4^4 blocks use half of each burst, the other
+  // half belonging to the neighbouring block of the other colour); else 4^4,
+  // else 2^4
+  const int shapes[3][4] = {{8, 4, 4, 2}, {4, 4, 4, 4}, {2, 2, 2, 2}};
+  for (const auto &b : shapes) {
     if (sap_feasible(fine_, b)) {
-      for (int i = 0; i < 4; ++i) sap_b_[i] = bsz;
+      for (int i = 0; i < 4; ++i) sap_b_[i] = b[i];
       break;
     }
   }

@@ -29,10 +29,13 @@ if not torch.cuda.is_available():
 from gpu_util import Setup, dev, host, rel  # noqa: E402
 
 
-@pytest.mark.parametrize('dims,bsz,blocks', [((4, 4, 4, 8), 2, [(2, 2, 2, 2)]),
-                                             ((8, 8, 8, 8), 4, [(4, 4, 4, 4)])])
+# the library picks SAP blocks of 8x4x4x2 where every direction holds an even
+# number of them (16x8x8x4 here), else 4^4, else 2^4
+@pytest.mark.parametrize('dims,bshape,blocks', [((4, 4, 4, 8), (2, 2, 2, 2), [(2, 2, 2, 2)]),
+                                                ((8, 8, 8, 8), (4, 4, 4, 4), [(4, 4, 4, 4)]),
+                                                ((16, 8, 8, 4), (8, 4, 4, 2), [(4, 4, 4, 4)])])
 @pytest.mark.parametrize('prec,tol', [(0, 1e-11), (1, 1e-4)])
-def test_sap_smoother_matches_oracle(dims, bsz, blocks, prec, tol):
+def test_sap_smoother_matches_oracle(dims, bshape, blocks, prec, tol):
     s = Setup(dims, blocks, [4], eps=0.4, m0=0.1, gseed=91, oracle=False,
               solver=dict(smoother=1, sap_iters=4, smoother_steps=2))
     try:
@@ -45,7 +48,7 @@ def test_sap_smoother_matches_oracle(dims, bsz, blocks, prec, tol):
         M.mgmlmc_apply(s.ctx, M.OP_SMOOTH, 0, prec, dev(b, ct), out, 2)
         got = host(out)
         for r in range(2):
-            want = osm.sap_smooth(Mx, dims, (bsz,) * 4, b[r], sweeps=2, iters=4)
+            want = osm.sap_smooth(Mx, dims, bshape, b[r], sweeps=2, iters=4)
             assert rel(got[r], want) < tol
     finally:
         s.close()
