@@ -509,7 +509,8 @@ mgmlmc_status mgmlmc_profile(mgmlmc_ctx *ctx, int enable);
 /* Counters of one kernel class since the last mgmlmc_profile: launches,
  * summed device milliseconds, summed algorithmic bytes (unique data: for the
  * Wilson operator nrhs input and output spinors plus 4 links per site; for a
- * coarse stencil the 9 blocks plus input and output per site) and summed
+ * coarse stencil the 9 blocks, at their stored size, plus input and output
+ * per site) and summed
  * algorithmic flops (1368 per site and rhs for Wilson; 72 m^2 per coarse
  * site and rhs for a stencil with m dofs per site).  Synchronises the
  * stream. */

@@ -517,13 +517,17 @@ template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int
     flops = 1368.0 * L.g.V * nrhs;
     cls = sizeof(T) == 8 ? K_WILSON64 : K_WILSON32;
   } else {
+    // bytes of one complex block entry as stored (BF16 variants: 4)
+    double bs = cs;
     if constexpr (sizeof(T) == 8) {
       stencil_apply<T>(in, out, L.AT64, L.g, nrhs, flag_dev_ + 1, stream);
     } else {
-      stencil_run(l, stencil_pick(l, nrhs, in, out), in, out, nrhs);
+      const int v = stencil_pick(l, nrhs, in, out);
+      stencil_run(l, v, in, out, nrhs);
+      if ((v == 3 && L.ATB16 && nrhs <= 8) || (v == 4 && L.ATCB)) bs = 4.0;
     }
     const double m = L.g.dof;
-    bytes = (double)L.g.V * (9.0 * m * m + 2.0 * m * nrhs) * cs;
+    bytes = (double)L.g.V * (9.0 * m * m * bs + 2.0 * m * nrhs * cs);
     flops = 8.0 * 9.0 * m * m * L.g.V * nrhs;
     cls = sizeof(T) == 8 ? K_STENCIL64 : K_STENCIL32;
   }
