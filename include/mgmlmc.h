@@ -129,6 +129,9 @@ typedef struct {
                           smooths after the coarse-grid correction only (no
                           pre-smoothing; coarser levels keep both);
                           0 (default): before and after on every level */
+  int gram_schmidt_passes; /* classical Gram-Schmidt passes of the FP32
+                          FGMRES Arnoldi step: 1, or 2 (0 = 2, the default);
+                          FP64 solves always run 2 */
   int fine_batch;      /* memory bound of the fine level: mgmlmc_estimate_trace
                           solves level-0 systems (the O_0, F_0, M_0 and plain
                           terms) in blocks of at most fine_batch right-hand

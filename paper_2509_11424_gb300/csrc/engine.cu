@@ -343,6 +343,7 @@ int Engine::restart_of(int l) const {
 void Engine::set_solver(const mgmlmc_solver_params &p) {
   if (!(p.tol > 0.0) || p.max_iter < 1 || p.restart < 1 || p.restart > 64 || p.smoother_steps < 0 ||
       p.coarse_restart < 0 || p.coarse_restart > 64 || (p.post_smoothing_only != 0 && p.post_smoothing_only != 1) ||
+      p.gram_schmidt_passes < 0 || p.gram_schmidt_passes > 2 ||
       p.coarse_iters < 1 || p.coarse_iters > 64 ||
       (p.precision != MGMLMC_FP64 && p.precision != MGMLMC_FP32) ||
       (p.precision == MGMLMC_FP32 && !(p.inner_tol > 0.0 && p.inner_tol < 1.0)) ||
@@ -774,6 +775,10 @@ SolveInfo Engine::fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, in
   auto part = [&](int k) { return partials((size_t)reduce_blocks(n) * nrhs * k); };
   (void)part_k;
 
+  // classical Gram-Schmidt twice, or once for FP32 solves when the solver
+  // parameters ask for it (the second coefficients then stay zero)
+  const bool two_pass = sizeof(T) == 8 || sp_.gram_schmidt_passes != 1;
+  if (!two_pass) MG_CUDA(cudaMemsetAsync(st.h2, 0, sizeof(double2) * nrhs * (m + 1), stream));
   dot<T>(b, b, n, nrhs, st.nrm, part(1), stream);
   target_kernel<<<(nrhs + 63) / 64, 64, 0, stream>>>(st.target, st.nrm, tol, nrhs);
   MG_LAUNCH_CHECK();
@@ -809,12 +814,15 @@ SolveInfo Engine::fgmres(int l, const C<T> *b, C<T> *x, int nrhs, double tol, in
       cudaEvent_t po = prof_begin();
       multi_dot<T>(V, vs, i + 1, w, n, nrhs, st.h1, m + 1, part(i + 1), stream);
       multi_axpy<T>(V, vs, i + 1, w, n, nrhs, st.h1, m + 1, -1.0, stream);
-      multi_dot<T>(V, vs, i + 1, w, n, nrhs, st.h2, m + 1, part(i + 1), stream);
-      multi_axpy<T>(V, vs, i + 1, w, n, nrhs, st.h2, m + 1, -1.0, stream);
+      if (two_pass) {
+        multi_dot<T>(V, vs, i + 1, w, n, nrhs, st.h2, m + 1, part(i + 1), stream);
+        multi_axpy<T>(V, vs, i + 1, w, n, nrhs, st.h2, m + 1, -1.0, stream);
+      }
       dot<T>(w, w, n, nrhs, st.nrm, part(1), stream);
-      // unique data of CGS2: the i+1 basis vectors twice for the dots and
-      // twice for the updates, w read/written four times
-      prof_end(po, K_ORTHO, (double)vs * sizeof(C<T>) * (4.0 * (i + 1) + 9.0), 0.0);
+      // unique data of CGS2 (CGS1): the i+1 basis vectors twice (once) for the
+      // dots and twice (once) for the updates, w read/written 9 (5) times
+      prof_end(po, K_ORTHO,
+               (double)vs * sizeof(C<T>) * (two_pass ? 4.0 * (i + 1) + 9.0 : 2.0 * (i + 1) + 5.0), 0.0);
       gmres_arnoldi(st, i, stream);
       scale_rhs<T>(w, w, st.inv, n, nrhs, stream);
       ++it;

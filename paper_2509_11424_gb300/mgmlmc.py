@@ -48,6 +48,7 @@ class SolverParams(ctypes.Structure):
                 ('coarse_smoother_steps', ctypes.c_int),
                 ('coarse_restart', ctypes.c_int),
                 ('post_smoothing_only', ctypes.c_int),
+                ('gram_schmidt_passes', ctypes.c_int),
                 ('fine_batch', ctypes.c_int)]
 
 
@@ -225,10 +226,11 @@ SMOOTHER_MR, SMOOTHER_SAP, SMOOTHER_LEARNED, SMOOTHER_NET = 0, 1, 2, 3
 
 def solver_params(tol=1e-12, max_iter=2000, restart=16, smoother_steps=4, coarse_iters=8,
                   precision=FP64, inner_tol=1e-6, smoother=SMOOTHER_MR, sap_iters=4,
-                  coarse_smoother_steps=4, coarse_restart=0, post_smoothing_only=0, fine_batch=0):
+                  coarse_smoother_steps=4, coarse_restart=0, post_smoothing_only=0, gram_schmidt_passes=0,
+                  fine_batch=0):
     return SolverParams(tol, max_iter, restart, smoother_steps, coarse_iters, precision, inner_tol,
                         smoother, sap_iters, coarse_smoother_steps, coarse_restart, post_smoothing_only,
-                        fine_batch)
+                        gram_schmidt_passes, fine_batch)
 
 
 def mgmlmc_set_solver(ctx, params=None, **kw):

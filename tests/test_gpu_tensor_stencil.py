@@ -125,16 +125,19 @@ def test_bf16_stencil_matches_oracle(tc, nrhs):
         assert np.max(np.abs(got[r] - want[r])) > 0  # it is not the FP32 result
 
 
-def test_solve_with_preconditioner_variants(tc):
+@pytest.mark.parametrize('gs', [2, 1])
+def test_solve_with_preconditioner_variants(tc, gs):
     """The tensor-core and BF16 stencils inside the multigrid preconditioner
-    of FP32 inner solves: every level-0 solve still reaches the 1e-12 true
-    residual measured with the oracle's D (the FP64 defect correction)."""
+    of FP32 inner solves, with two or one Gram-Schmidt passes and
+    post-smoothing only on the fine level: every level-0 solve still reaches
+    the 1e-12 true residual measured with the oracle's D (the FP64 defect
+    correction decides)."""
     M = tc.M
     A0 = tc.hier.matrix(0).tocsr()
     n = A0.shape[0]
     b = synth.complex_normal((3, n), 801)
     M.mgmlmc_set_solver(tc.ctx, precision=M.FP32, restart=8, coarse_restart=16, smoother=1, smoother_steps=1,
-                        coarse_iters=4, inner_tol=1e-6)
+                        coarse_iters=4, inner_tol=1e-6, gram_schmidt_passes=gs, post_smoothing_only=gs % 2)
     try:
         for v in (1, 3, 4, -2):
             M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, v)
