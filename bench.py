@@ -697,6 +697,7 @@ def kernel_probe(M, torch, args):
         level, op = 0, M.OP_D
         if args.kernel_probe == 'sap':
             op = M.OP_SMOOTH
+            M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_SAP_FP32, args.probe_variant)
         elif args.kernel_probe == 'stencil':
             # Z4 test vectors (no setup iterations): the stencil's cost does
             # not depend on their quality
@@ -756,7 +757,7 @@ def main():
                     help='time one kernel class on a small lattice (profiler captures) and exit')
     ap.add_argument('--probe-dims', default='32,32,32,64')
     ap.add_argument('--probe-nrhs', type=int, default=4)
-    ap.add_argument('--probe-variant', type=int, default=0, help='stencil variant of the stencil probe')
+    ap.add_argument('--probe-variant', type=int, default=0, help='kernel variant of the sap or stencil probe')
     ap.add_argument('--probe-reps', type=int, default=5)
     ap.add_argument('--detail-out', default=os.environ.get('MGMLMC_BENCH_DETAIL'),
                     help='file for the full per-term and per-arm detail (the JSON line keeps a summary)')

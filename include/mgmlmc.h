@@ -513,9 +513,11 @@ mgmlmc_status mgmlmc_profile(mgmlmc_ctx *ctx, int enable);
  * summed device milliseconds, summed algorithmic bytes (unique data: for the
  * Wilson operator nrhs input and output spinors plus 4 links per site; for a
  * coarse stencil the 9 blocks, at their stored size, plus input and output
- * per site) and summed
- * algorithmic flops (1368 per site and rhs for Wilson; 72 m^2 per coarse
- * site and rhs for a stencil with m dofs per site).  Synchronises the
+ * per site; for a SAP sweep the 4 links once, and per right-hand side the
+ * residual, z and e read or written by the block and face passes, 8 spinors
+ * per site) and summed algorithmic flops (1368 per site and rhs for Wilson;
+ * 72 m^2 per coarse site and rhs for a stencil with m dofs per site;
+ * 1368 sap_iters + 684 per site and rhs for a SAP sweep).  Synchronises the
  * stream. */
 mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *launches,
                                    double *ms, double *bytes, double *flops);
@@ -549,6 +551,17 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
  * solves reach their tolerance as with FP32 throughout, and the FP64 defect
  * correction decides convergence with the true residual either way. */
 #define MGMLMC_VARIANT_STENCIL_FP32 1
+/* The FP32 SAP sweep on the fine level (the smoother of Sec. 4's
+ * DD-alpha-AMG solver).  With two or more right-hand sides and blocks of
+ * 8 x 4 x 4 x 2 or 4^4 sites, one block and two right-hand sides per thread
+ * block: 0 (default) = one thread per site and right-hand side, the block's
+ * links and the solution it updates staged in shared memory by asynchronous
+ * copies that overlap the residual load; 1 = one thread per site carrying
+ * both right-hand sides in packed FP32 pairs (.f32x2 instructions).  Other
+ * cases, and 2 = throughout, the general kernels.  Every variant updates the
+ * faces of each colour in a separate pass over that colour's sites, and all
+ * compute the same sums in the same order: identical results. */
+#define MGMLMC_VARIANT_SAP_FP32 2
 /* Choose the variant of a kernel for later calls: for the FP32 fine Wilson
  * operator -2 = autotune (default: the first call per right-hand-side count
  * outside graph capture times every variant on that call's operands and

@@ -492,6 +492,7 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
 int mgmlmc_kernel_variants(int kernel) {
   if (kernel == MGMLMC_VARIANT_DSLASH_FP32) return mg::wilson_fp32_variants();
   if (kernel == MGMLMC_VARIANT_STENCIL_FP32) return mg::Engine::stencil_variants();
+  if (kernel == MGMLMC_VARIANT_SAP_FP32) return mg::sap_variants();
   return -1;
 }
 
@@ -499,6 +500,7 @@ mgmlmc_status mgmlmc_set_kernel_variant(mgmlmc_ctx *ctx, int kernel, int variant
   return guard(ctx, [&] {
     if (kernel == MGMLMC_VARIANT_DSLASH_FP32) E(ctx).set_dslash_variant(variant);
     else if (kernel == MGMLMC_VARIANT_STENCIL_FP32) E(ctx).set_stencil_variant(variant);
+    else if (kernel == MGMLMC_VARIANT_SAP_FP32) E(ctx).set_sap_variant(variant);
     else throw mg::Error(MGMLMC_ERR_ARG, "unknown kernel");
   });
 }
@@ -510,6 +512,7 @@ mgmlmc_status mgmlmc_get_kernel_variant(const mgmlmc_ctx *cctx, int kernel, int 
     if (!variant) throw mg::Error(MGMLMC_ERR_ARG, "variant is null");
     if (kernel == MGMLMC_VARIANT_DSLASH_FP32) *variant = E(ctx).dslash_variant(nrhs);
     else if (kernel == MGMLMC_VARIANT_STENCIL_FP32) *variant = E(ctx).stencil_variant(1, nrhs);
+    else if (kernel == MGMLMC_VARIANT_SAP_FP32) *variant = E(ctx).sap_variant();
     else throw mg::Error(MGMLMC_ERR_ARG, "unknown kernel");
   });
 }

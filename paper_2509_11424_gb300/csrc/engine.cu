@@ -410,6 +410,12 @@ int Engine::dslash_variant(int nrhs) const {
 
 int Engine::stencil_variants() { return 5; }
 
+void Engine::set_sap_variant(int v) {
+  if (v < 0 || v >= sap_variants()) throw Error(MGMLMC_ERR_ARG, "SAP variant out of range");
+  sap_variant_ = v;
+  drop_graphs();
+}
+
 void Engine::set_stencil_variant(int v) {
   if (v < -2 || v == -1 || v >= stencil_variants()) throw Error(MGMLMC_ERR_ARG, "stencil variant out of range");
   stencil_force_ = v;
@@ -602,15 +608,16 @@ template <typename T> void Engine::smooth(int l, C<T> *z, C<T> *res, int nrhs) {
     const C<T> *U;
     if constexpr (sizeof(T) == 8) U = levels_[0].U64; else U = levels_[0].UD32;
     const Geom &g = levels_[0].g;
-    // per sweep: both colours read links + residual, write z, e and the
-    // residual (block kernels), then the boundary pass reads e and the
-    // residual and writes the residual: 36 + 12 * (1 + 3 + 3) complex per site;
-    // flops: sap_iters block operators (1368 per site) + the boundary hops
-    const double bytes = (double)g.V * (36.0 + 84.0 * nrhs) * sizeof(C<T>);
+    // per sweep: the block kernels read the links (once, shared by the
+    // right-hand sides), the residual and z and write z, e and the residual;
+    // the face passes read e and the residual and write the residual, each
+    // site once: 36 + 12 * (5 + 3) complex per site and right-hand side;
+    // flops: sap_iters block operators (1368 per site) + the face hops
+    const double bytes = (double)g.V * (36.0 + 96.0 * nrhs) * sizeof(C<T>);
     const double flops = (double)g.V * nrhs * (1368.0 * sp_.sap_iters + 684.0);
     for (int s = 0; s < sp_.smoother_steps; ++s) {
       cudaEvent_t a = prof_begin();
-      sap_sweep<T>(res, z, e, U, g, sap_b_, m0_, sp_.sap_iters, nrhs, stream);
+      sap_sweep<T>(res, z, e, U, g, sap_b_, m0_, sp_.sap_iters, nrhs, stream, sap_variant_);
       prof_end(a, sizeof(T) == 8 ? K_SAP64 : K_SAP32, bytes, flops);
     }
     // training pairs: the residuals the learned step will see -- after SAP,

@@ -189,6 +189,10 @@ class Engine {
   void set_stencil_variant(int v);
   int stencil_variant(int l, int nrhs) const;
   static int stencil_variants();
+  // FP32 SAP sweep: 0 = the staged block kernels where they apply, 1 = the
+  // paired ones, 2 = the general ones (identical results)
+  void set_sap_variant(int v);
+  int sap_variant() const { return sap_variant_; }
 
  private:
   template <typename T> C<T> *ws(const std::string &name, int l, size_t count);
@@ -279,6 +283,7 @@ class Engine {
   void orthonormalise_cols(double2 *V, int k, int64_t n);
   std::map<int, int> dslash_tuned_;
   int stencil_force_ = 0;
+  int sap_variant_ = 0;
   int precond_depth_ = 0;  // > 0 while the multigrid preconditioner runs
   int solving_ = 0;        // > 0 inside solve()
   std::map<std::pair<int, int>, int> stencil_tuned_;  // (level, nrhs) -> variant

@@ -166,12 +166,16 @@ void gamma5_apply(const C<T> *in, C<T> *out, int64_t nsites, int dof, int nrhs, 
 // ------------------------------------------------------------------ SAP
 // blocks b tile the lattice with an even block count in every direction
 bool sap_feasible(const Geom &g, const int b[4]);
-template <typename T> size_t sap_smem_bytes(const int b[4]);
+template <typename T> size_t sap_smem_bytes(const int b[4], int rs);
 // one red/black sweep: r (residual, exact on exit), z += correction, e scratch;
-// FP32: structure-of-arrays vectors and links (UDs), FP64: canonical
+// FP32: structure-of-arrays vectors and links (UDs), FP64: canonical.
+// variant 0: the staged FP32 block kernels where they apply (two or more
+// right-hand sides, blocks 8 x 4 x 4 x 2 or 4^4), 1: the paired ones there,
+// 2: the general kernels throughout; all give identical results
+int sap_variants();
 template <typename T>
 void sap_sweep(C<T> *r, C<T> *z, C<T> *e, const C<T> *U, Geom g, const int b[4], double m0,
-               int block_iters, int nrhs, cudaStream_t s);
+               int block_iters, int nrhs, cudaStream_t s, int variant = 0);
 
 // ------------------------------------------------------------------ learned smoother
 // gauge-covariant layer phi[o] = sum_c sum_h W[h][o][c] T_h psi[c]; activations

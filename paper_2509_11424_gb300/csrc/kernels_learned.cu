@@ -67,16 +67,18 @@ __device__ __forceinline__ void transported(const C<T> *__restrict__ psi, const 
 
 // forward: one thread per site computing OG output channels at once, so each
 // transported input T_h psi[c] is formed once for the whole group;
-// blockIdx.y = output group, blockIdx.z = sample
+// blockIdx.x = (site range, sample) with the sample fastest, so the blocks
+// of one site range run together and read its links from L2 after the
+// first; blockIdx.y = output group
 template <typename T, int OG>
 __global__ void __launch_bounds__(128) glayer_forward_kernel(const C<T> *__restrict__ in,
                                                              C<T> *__restrict__ out,
                                                              const C<T> *__restrict__ W,
                                                              const C<T> *__restrict__ U, Geom g,
-                                                             int Cin, int Cout) {
+                                                             int Cin, int Cout, int nb) {
   extern __shared__ unsigned char smem_raw[];
   C<T> *Ws = reinterpret_cast<C<T> *>(smem_raw);  // [h][c][og][16] for this group
-  const int o0 = blockIdx.y * OG, b = blockIdx.z;
+  const int o0 = blockIdx.y * OG, b = (int)(blockIdx.x % (unsigned)nb);
   const int og = Cout - o0 < OG ? Cout - o0 : OG;
   for (int e = threadIdx.x; e < 9 * Cin * OG * 16; e += blockDim.x) {
     const int h = e / (Cin * OG * 16), rem = e - h * Cin * OG * 16;
@@ -84,7 +86,7 @@ __global__ void __launch_bounds__(128) glayer_forward_kernel(const C<T> *__restr
     Ws[e] = k < og ? W[(((int64_t)h * Cout + o0 + k) * Cin + c) * 16 + q] : mk<T>((T)0, (T)0);
   }
   __syncthreads();
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = (int)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   const int64_t n = g.n();
   int cc[4];
@@ -127,16 +129,17 @@ __global__ void __launch_bounds__(128) glayer_adjoint_kernel(const C<T> *__restr
                                                              C<T> *__restrict__ out,
                                                              const C<T> *__restrict__ W,
                                                              const C<T> *__restrict__ U, Geom g,
-                                                             int Cin, int Cout) {
+                                                             int Cin, int Cout, int nb) {
   extern __shared__ unsigned char smem_raw[];
   C<T> *Ws = reinterpret_cast<C<T> *>(smem_raw);  // [h][o][16] for this c
-  const int c = blockIdx.y, b = blockIdx.z;
+  // blockIdx.x = (site range, sample), the sample fastest (as the forward)
+  const int c = blockIdx.y, b = (int)(blockIdx.x % (unsigned)nb);
   for (int e = threadIdx.x; e < 9 * Cout * 16; e += blockDim.x) {
     const int h = e / (Cout * 16), rem = e - h * Cout * 16, o = rem / 16, k = rem % 16;
     Ws[e] = W[(((int64_t)h * Cout + o) * Cin + c) * 16 + k];
   }
   __syncthreads();
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = (int)(blockIdx.x / (unsigned)nb) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   const int64_t n = g.n();
   int cc[4];
@@ -272,8 +275,8 @@ static void glayer_forward_og(const C<T> *in, C<T> *out, const C<T> *W, const C<
                               int Cout, int B, cudaStream_t s) {
   const size_t sm = (size_t)9 * Cin * OG * 16 * sizeof(C<T>);
   smem_optin((const void *)glayer_forward_kernel<T, OG>, 160 * 1024);
-  glayer_forward_kernel<T, OG><<<dim3(div_up(g.V, 128), div_up(Cout, OG), B), 128, sm, s>>>(in, out, W, U,
-                                                                                          g, Cin, Cout);
+  glayer_forward_kernel<T, OG><<<dim3((unsigned)div_up(g.V, 128) * (unsigned)B, div_up(Cout, OG), 1), 128, sm,
+                                 s>>>(in, out, W, U, g, Cin, Cout, B);
   MG_LAUNCH_CHECK();
 }
 
@@ -290,7 +293,8 @@ void glayer_adjoint(const C<T> *gin, C<T> *out, const C<T> *W, const C<T> *U, Ge
                     int Cout, int B, cudaStream_t s) {
   const size_t sm = (size_t)9 * Cout * 16 * sizeof(C<T>);
   smem_optin((const void *)glayer_adjoint_kernel<T>, 100 * 1024);
-  glayer_adjoint_kernel<T><<<dim3(div_up(g.V, 128), Cin, B), 128, sm, s>>>(gin, out, W, U, g, Cin, Cout);
+  glayer_adjoint_kernel<T><<<dim3((unsigned)div_up(g.V, 128) * (unsigned)B, Cin, 1), 128, sm, s>>>(gin, out, W, U,
+                                                                                                  g, Cin, Cout, B);
   MG_LAUNCH_CHECK();
 }
 

@@ -216,20 +216,21 @@ __global__ void __launch_bounds__(kTcThreads) stencil_tc_kernel(const float2 *__
       E *base = Bs + (size_t)(d * 2) * kTcMaxN * kTcM;
       E *re_dst = base + ((size_t)c * N + nn) * KC;
       E *im_dst = base + kTcMaxN * kTcM + ((size_t)c * N + nn) * KC;
-      const float2 *src = in + (int64_t)(r0 + (nn < rc ? nn : 0)) * n + (int64_t)nbr[d] * kTcM + KC * c;
+      // KC consecutive complex values, two per 16-byte load
+      const float4 *src = reinterpret_cast<const float4 *>(in + (int64_t)(r0 + (nn < rc ? nn : 0)) * n +
+                                                           (int64_t)nbr[d] * kTcM + KC * c);
       if constexpr (sizeof(E) == 4) {
-        float2 v[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = nn < rc ? __ldg(src + q) : make_float2(0.f, 0.f);
-        split_store(reinterpret_cast<float *>(re_dst), reinterpret_cast<float *>(im_dst), v[0], v[1], v[2], v[3]);
+        const float4 a = nn < rc ? __ldg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 b = nn < rc ? __ldg(src + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+        split_store(reinterpret_cast<float *>(re_dst), reinterpret_cast<float *>(im_dst), make_float2(a.x, a.y),
+                    make_float2(a.z, a.w), make_float2(b.x, b.y), make_float2(b.z, b.w));
       } else {
         __nv_bfloat162 re[4], im[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const float2 a = nn < rc ? __ldg(src + 2 * q) : make_float2(0.f, 0.f);
-          const float2 b = nn < rc ? __ldg(src + 2 * q + 1) : make_float2(0.f, 0.f);
-          re[q] = __floats2bfloat162_rn(a.x, b.x);
-          im[q] = __floats2bfloat162_rn(a.y, b.y);
+          const float4 a = nn < rc ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+          re[q] = __floats2bfloat162_rn(a.x, a.z);
+          im[q] = __floats2bfloat162_rn(a.y, a.w);
         }
         *reinterpret_cast<uint4 *>(re_dst) = *reinterpret_cast<const uint4 *>(re);
         *reinterpret_cast<uint4 *>(im_dst) = *reinterpret_cast<const uint4 *>(im);

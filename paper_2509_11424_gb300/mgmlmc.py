@@ -389,6 +389,8 @@ def mgmlmc_kernel_launches():
 
 VARIANT_DSLASH_FP32 = 0
 VARIANT_STENCIL_FP32 = 1
+VARIANT_SAP_FP32 = 2
+VARIANT_AUTOTUNE = -2
 LAYOUT_INTERNAL = 0x100
 
 
@@ -396,7 +398,6 @@ def mgmlmc_reorder(ctx, inp, out, nrhs, to_internal):
     """Level-0 complex-float vectors: canonical <-> the library's internal
     structure-of-arrays order."""
     _check(ctx, lib().mgmlmc_reorder(ctx, ptr(inp), ptr(out), nrhs, int(bool(to_internal))))
-VARIANT_AUTOTUNE = -2
 
 
 def mgmlmc_reorder_bf16(ctx, inp, out, nrhs, to_internal):

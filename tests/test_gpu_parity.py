@@ -162,11 +162,12 @@ def test_dslash_bf16(dims):
 def test_dslash_variant_bad_args():
     nv = M.mgmlmc_kernel_variants(M.VARIANT_DSLASH_FP32)
     ns = M.mgmlmc_kernel_variants(M.VARIANT_STENCIL_FP32)
-    assert nv == 7 and ns == 4
-    assert M.mgmlmc_kernel_variants(2) == -1
+    nsap = M.mgmlmc_kernel_variants(M.VARIANT_SAP_FP32)
+    assert nv == 7 and ns == 5 and nsap == 3
+    assert M.mgmlmc_kernel_variants(3) == -1
     ctx = M.mgmlmc_create((4, 4, 4, 4), torch.cuda.current_stream())
     try:
-        for kern, v in ((0, nv), (0, -1), (0, -3), (1, ns), (1, -1), (2, 0)):
+        for kern, v in ((0, nv), (0, -1), (0, -3), (1, ns), (1, -1), (2, nsap), (2, -1), (2, -2), (3, 0)):
             with pytest.raises(M.MgmlmcError):
                 M.mgmlmc_set_kernel_variant(ctx, kern, v)
     finally:

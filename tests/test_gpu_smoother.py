@@ -54,6 +54,36 @@ def test_sap_smoother_matches_oracle(dims, bshape, blocks, prec, tol):
         s.close()
 
 
+@pytest.mark.parametrize('dims', [(16, 8, 8, 4), (8, 8, 8, 8)])
+@pytest.mark.parametrize('nrhs', [1, 2, 3, 4])
+def test_sap_variants_identical(dims, nrhs):
+    """The staged (variant 0) and paired (variant 1) FP32 SAP kernels
+    (8x4x4x2 blocks on 16x8x8x4, 4^4 on 8^4; two right-hand sides per thread
+    block, an odd count leaving one idle) against the general ones (variant
+    2), two sweeps so that the fused face terms and the face pass both run:
+    the same sums in the same order, so the results agree bit for bit; the
+    default variant is held to the oracle above."""
+    s = Setup(dims, [(4, 4, 4, 4)], [4], eps=0.4, m0=0.1, gseed=97, oracle=False,
+              solver=dict(smoother=1, sap_iters=4, smoother_steps=2))
+    try:
+        M = s.M
+        assert M.mgmlmc_kernel_variants(M.VARIANT_SAP_FP32) == 3
+        n = M.mgmlmc_level_info(s.ctx, 0)[2]
+        b = dev(synth.complex_normal((nrhs, n), 98), torch.complex64)
+        outs = []
+        for v in (0, 1, 2):
+            M.mgmlmc_set_kernel_variant(s.ctx, M.VARIANT_SAP_FP32, v)
+            assert M.mgmlmc_get_kernel_variant(s.ctx, M.VARIANT_SAP_FP32, nrhs) == v
+            out = torch.empty((nrhs, n), dtype=torch.complex64, device='cuda')
+            M.mgmlmc_apply(s.ctx, M.OP_SMOOTH, 0, 1, b, out, nrhs)
+            outs.append(out)
+        assert torch.equal(outs[0], outs[2])
+        assert torch.equal(outs[1], outs[2])
+        assert float(outs[0].abs().max()) > 0
+    finally:
+        s.close()
+
+
 def test_mr_smoother_matches_oracle():
     dims = (4, 4, 4, 8)
     s = Setup(dims, [(2, 2, 2, 2)], [4], eps=0.4, m0=0.1, gseed=93, solver=dict(smoother_steps=3, coarse_smoother_steps=3))
