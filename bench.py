@@ -683,11 +683,13 @@ def kernel_probe(M, torch, args):
     """One kernel class on a lattice small enough for a profiler capture (a
     few GB on the device) whose launches still move more than the L2 holds:
     `sap` (one smoothing call: smoother_steps SAP sweeps on level 0), `stencil`
-    (the FP32 coarse stencil D_1 in its selected variant), `dslash` (the FP32
-    Wilson operator).  Prints the mean event-timed milliseconds per call."""
-    from paper_2509_11424_gb300 import synth
+    (the FP32 coarse stencil D_l of --probe-level in its selected variant),
+    `dslash` (the FP32 Wilson operator).  --probe-variant and --probe-nrhs
+    take comma lists; prints one line per (variant, nrhs) with the mean
+    event-timed milliseconds per call."""
     dims = tuple(int(x) for x in args.probe_dims.split(','))
-    nrhs = args.probe_nrhs
+    variants = [int(v) for v in str(args.probe_variant).split(',')]
+    nrhs_list = [int(v) for v in str(args.probe_nrhs).split(',')]
     stream = torch.cuda.current_stream()
     ctx = M.mgmlmc_create(dims, stream)
     try:
@@ -697,31 +699,44 @@ def kernel_probe(M, torch, args):
         level, op = 0, M.OP_D
         if args.kernel_probe == 'sap':
             op = M.OP_SMOOTH
-            M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_SAP_FP32, args.probe_variant)
         elif args.kernel_probe == 'stencil':
             # Z4 test vectors (no setup iterations): the stencil's cost does
             # not depend on their quality
-            M.mgmlmc_build_hierarchy(ctx, M.mg_params([(4, 4, 4, 4), (2, 2, 2, 2)], [16, 16], setup_rounds=0,
-                                                      seed=3005))
-            M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_STENCIL_FP32, args.probe_variant)
-            level = 1
-        n = M.mgmlmc_level_info(ctx, level)[2]
-        x = torch.randn((nrhs, n), dtype=torch.complex64, device='cuda')
-        y = torch.empty_like(x)
-        if level == 0:  # operands already in the internal order: the call is the kernel alone
-            op |= M.LAYOUT_INTERNAL
-        for _ in range(3):
-            M.mgmlmc_apply(ctx, op, level, M.FP32, x, y, nrhs)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.probe_reps):
-            M.mgmlmc_apply(ctx, op, level, M.FP32, x, y, nrhs)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.probe_reps
-        print(json.dumps({'kernel_probe': args.kernel_probe, 'dims': list(dims), 'level': level, 'nrhs': nrhs,
-                          'variant': args.probe_variant, 'ms_per_call': ms}))
+            level = args.probe_level
+            # 2^4 aggregates below the first level until the probed level
+            # exists and the coarsest is small enough for its dense inverse
+            blocks, ext = [(4, 4, 4, 4)], [d // 4 for d in dims]
+            while len(blocks) <= level or (np.prod(ext) > 1000 and all(e % 2 == 0 for e in ext)):
+                blocks.append((2, 2, 2, 2))
+                ext = [e // 2 for e in ext]
+            M.mgmlmc_build_hierarchy(ctx, M.mg_params(blocks, [16] * len(blocks), setup_rounds=0, seed=3005))
+        for v in variants:
+            if args.kernel_probe == 'sap':
+                M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_SAP_FP32, v)
+            elif args.kernel_probe == 'stencil':
+                M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_STENCIL_FP32, v)
+            else:
+                M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_DSLASH_FP32, v)
+            for nrhs in nrhs_list:
+                info = M.mgmlmc_level_info(ctx, level)
+                n = info[2]
+                x = torch.randn((nrhs, n), dtype=torch.complex64, device='cuda')
+                y = torch.empty_like(x)
+                lop = op | M.LAYOUT_INTERNAL if level == 0 else op  # internal order: the call is the kernel alone
+                for _ in range(3):
+                    M.mgmlmc_apply(ctx, lop, level, M.FP32, x, y, nrhs)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                for _ in range(args.probe_reps):
+                    M.mgmlmc_apply(ctx, lop, level, M.FP32, x, y, nrhs)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.probe_reps
+                print(json.dumps({'kernel_probe': args.kernel_probe, 'dims': list(dims), 'level': level,
+                                  'sites': n // info[1], 'nrhs': nrhs,
+                                  'variant': v, 'ms_per_call': ms}))
+                del x, y
     finally:
         M.mgmlmc_destroy(ctx)
 
@@ -756,8 +771,9 @@ def main():
     ap.add_argument('--kernel-probe', default=None, choices=['sap', 'stencil', 'dslash'],
                     help='time one kernel class on a small lattice (profiler captures) and exit')
     ap.add_argument('--probe-dims', default='32,32,32,64')
-    ap.add_argument('--probe-nrhs', type=int, default=4)
-    ap.add_argument('--probe-variant', type=int, default=0, help='kernel variant of the sap or stencil probe')
+    ap.add_argument('--probe-nrhs', default='4', help='right-hand sides of the probe, comma-separated')
+    ap.add_argument('--probe-variant', default='0', help='kernel variant(s) of the probe, comma-separated')
+    ap.add_argument('--probe-level', type=int, default=1, help='level of the stencil probe (1 or 2)')
     ap.add_argument('--probe-reps', type=int, default=5)
     ap.add_argument('--detail-out', default=os.environ.get('MGMLMC_BENCH_DETAIL'),
                     help='file for the full per-term and per-arm detail (the JSON line keeps a summary)')
