@@ -540,10 +540,14 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
  * arithmetic, for up to 8 right-hand sides at 32 dofs per site (variant 0
  * otherwise); 4 = the tensor cores with BF16 operands (tcgen05.mma
  * kind::f16, relative rounding <= 2^-9 per operand, FP32 accumulation, half
- * the bytes of variant 1).  Variant 0 runs up to 8 right-hand sides at 32 dofs per site in
+ * the bytes of variant 1); 5 = variant 4 as a persistent kernel (one thread
+ * block per SM walking the sites with two shared-memory stages and two
+ * tensor-memory accumulators, so one site's MMAs and tile copy overlap the
+ * gathers and epilogue of others; identical results; up to 32 right-hand
+ * sides, variant 4 beyond).  Variant 0 runs up to 8 right-hand sides at 32 dofs per site in
  * a pipelined kernel (persistent blocks, a two-stage ring of bulk copies
  * over sites) with results identical to the one-site-per-block kernels.
- * -2 = autotune among 0, 1, 3 and 4 per (level, nrhs) on the first call
+ * -2 = autotune among 0, 1, 3, 4 and 5 per (level, nrhs) on the first call
  * outside graph capture (opt-in,
  * since the choice changes the rounding).  Inside a solve the variant applies
  * to the multigrid preconditioner only (smoothers, coarse-grid corrections);

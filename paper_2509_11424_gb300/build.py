@@ -52,7 +52,7 @@ def build(verbose=False, extra=()):
             if err.strip():
                 print(err, file=sys.stderr)
     tmp = LIB + '.tmp'
-    cmd = [nvcc()] + ARCH + ['-shared', '-Xlinker', '--no-undefined', '-o', tmp] + objs
+    cmd = [nvcc()] + ARCH + ['-shared', '-Xlinker', '--no-undefined', '-o', tmp] + objs + ['-lcublas']
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError('link failed:\n%s\n%s' % (r.stdout, r.stderr))

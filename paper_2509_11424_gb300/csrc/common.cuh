@@ -218,4 +218,7 @@ unsigned staging_extra_bytes();
 // host threads and devices.
 void smem_optin(const void *func, int bytes);
 
+// streaming multiprocessors of the current device (cached per device)
+int sm_count();
+
 }  // namespace mg

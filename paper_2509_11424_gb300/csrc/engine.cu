@@ -6,6 +6,8 @@
 #include "engine.h"
 #include "herm_eig.h"
 
+#include <cublas_v2.h>
+
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -107,6 +109,15 @@ Engine::Engine(const int dims[4], cudaStream_t s) : user_stream(s) {
   // a throwing constructor runs no destructor: release what was acquired
   try {
     MG_CUDA(cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking));
+    {
+      cublasHandle_t h = nullptr;
+      if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) throw Error(MGMLMC_ERR_CUDA, "cublasCreate failed");
+      blas_ = h;
+      MG_CUDA(cudaMalloc(&blas_ws_, kBlasWorkspace));
+      if (cublasSetStream(h, stream) != CUBLAS_STATUS_SUCCESS ||
+          cublasSetWorkspace(h, blas_ws_, kBlasWorkspace) != CUBLAS_STATUS_SUCCESS)
+        throw Error(MGMLMC_ERR_CUDA, "cuBLAS stream or workspace setup failed");
+    }
     MG_CUDA(cudaEventCreateWithFlags(&ev_enter_, cudaEventDisableTiming));
     MG_CUDA(cudaEventCreateWithFlags(&ev_leave_, cudaEventDisableTiming));
     levels_[0].U64 = dalloc<double2>((size_t)V * 36);
@@ -127,6 +138,10 @@ Engine::~Engine() { release(); }
 
 void Engine::release() {
   if (stream) cudaStreamSynchronize(stream);
+  if (blas_) cublasDestroy(static_cast<cublasHandle_t>(blas_));
+  blas_ = nullptr;
+  if (blas_ws_) cudaFree(blas_ws_);
+  blas_ws_ = nullptr;
   free_hierarchy();
   net_free();
   if (pool_) cudaFree(pool_);
@@ -408,7 +423,7 @@ int Engine::dslash_variant(int nrhs) const {
   return it == dslash_tuned_.end() ? -2 : it->second;
 }
 
-int Engine::stencil_variants() { return 5; }
+int Engine::stencil_variants() { return 6; }
 
 void Engine::set_sap_variant(int v) {
   if (v < 0 || v >= sap_variants()) throw Error(MGMLMC_ERR_ARG, "SAP variant out of range");
@@ -438,6 +453,7 @@ void Engine::stencil_run(int l, int v, const float2 *in, float2 *out, int nrhs) 
   const bool pipe = stencil_pipe_supported(L.g) && nrhs <= 8;
   if ((v == 1 || v == 2) && L.ATC) stencil_apply_tc(in, out, L.ATC, L.g, nrhs, flag_dev_ + 1, v - 1, stream);
   else if (v == 4 && L.ATCB) stencil_apply_tc(in, out, L.ATCB, L.g, nrhs, flag_dev_ + 1, 2, stream);
+  else if (v == 5 && L.ATCB) stencil_apply_tc(in, out, L.ATCB, L.g, nrhs, flag_dev_ + 1, 3, stream);
   else if (v == 3 && L.ATB16 && pipe) stencil_apply_pipe(in, out, L.ATB16, true, L.g, nrhs, flag_dev_ + 1, stream);
   else if (pipe) stencil_apply_pipe(in, out, L.AT32, false, L.g, nrhs, flag_dev_ + 1, stream);
   else stencil_apply<float>(in, out, L.AT32, L.g, nrhs, flag_dev_ + 1, stream);
@@ -459,7 +475,7 @@ int Engine::stencil_pick(int l, int nrhs, const float2 *in, float2 *out) {
   int pick = 0;
   float best = 1e30f;
   // variant 2 is variant 1 with twice the tensor work: not a candidate
-  for (int v : {0, 1, 3, 4}) {
+  for (int v : {0, 1, 3, 4, 5}) {
     if (v == 3 && !(levels_[l].ATB16 && nrhs <= 8)) continue;
     stencil_run(l, v, in, out, nrhs);
     MG_CUDA(cudaEventRecord(ev.a, stream));
@@ -531,7 +547,7 @@ template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int
     } else {
       const int v = stencil_pick(l, nrhs, in, out);
       stencil_run(l, v, in, out, nrhs);
-      if ((v == 3 && L.ATB16 && nrhs <= 8) || (v == 4 && L.ATCB)) bs = 4.0;
+      if ((v == 3 && L.ATB16 && nrhs <= 8) || ((v == 4 || v == 5) && L.ATCB)) bs = 4.0;
     }
     const double m = L.g.dof;
     bytes = (double)L.g.V * (9.0 * m * m * bs + 2.0 * m * nrhs * cs);
@@ -550,6 +566,27 @@ void Engine::apply_D_bf16(const void *in, void *out, int nrhs) {
   const Level &L = levels_[0];
   wilson_apply_bf16(in, out, L.Ub16, L.g, m0_, nrhs, stream);
 }
+
+// Minv is row-major, i.e. column-major Minv^T; the vectors are the columns
+// of a column-major n x nrhs matrix: out = (Minv^T)^T in
+template <typename T> void Engine::coarsest_apply(const C<T> *Minv, const C<T> *in, C<T> *out, int n, int nrhs) {
+  if (nrhs <= 0 || n <= 0) return;
+  cublasHandle_t h = static_cast<cublasHandle_t>(blas_);
+  cublasStatus_t st;
+  if constexpr (sizeof(T) == 4) {
+    const cuComplex one = make_cuComplex(1.f, 0.f), zero = make_cuComplex(0.f, 0.f);
+    st = cublasCgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, n, nrhs, n, &one, reinterpret_cast<const cuComplex *>(Minv), n,
+                     reinterpret_cast<const cuComplex *>(in), n, &zero, reinterpret_cast<cuComplex *>(out), n);
+  } else {
+    const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+    st = cublasZgemm(h, CUBLAS_OP_T, CUBLAS_OP_N, n, nrhs, n, &one,
+                     reinterpret_cast<const cuDoubleComplex *>(Minv), n, reinterpret_cast<const cuDoubleComplex *>(in),
+                     n, &zero, reinterpret_cast<cuDoubleComplex *>(out), n);
+  }
+  if (st != CUBLAS_STATUS_SUCCESS) throw Error(MGMLMC_ERR_CUDA, "cuBLAS GEMM of the coarsest level failed");
+}
+template void Engine::coarsest_apply<float>(const float2 *, const float2 *, float2 *, int, int);
+template void Engine::coarsest_apply<double>(const double2 *, const double2 *, double2 *, int, int);
 
 template <typename T> AggMap Engine::agg_of(int l) const {
   AggMap m = levels_.at(l).agg;
@@ -670,7 +707,7 @@ template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nr
   const Level &L = levels_[l];
   const int64_t n = L.g.n();
   if (l == n_levels() - 1) {
-    dense_apply<T>(Dinv<T>(l), r, z, (int)n, nrhs, stream);
+    coarsest_apply<T>(Dinv<T>(l), r, z, (int)n, nrhs);
     return;
   }
   const int64_t nc = levels_[l + 1].g.n();
@@ -688,7 +725,7 @@ template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nr
   prof_end(pr, K_TRANSFER, 0.0, 0.0);
   if (l + 1 == n_levels() - 1) {
     cudaEvent_t pd = prof_begin();
-    dense_apply<T>(Dinv<T>(l + 1), rc, ec, (int)nc, nrhs, stream);
+    coarsest_apply<T>(Dinv<T>(l + 1), rc, ec, (int)nc, nrhs);
     prof_end(pd, K_COARSEST, 0.0, 0.0);
   } else {
     fgmres<T>(l + 1, rc, ec, nrhs, 0.0, sp_.coarse_iters, sp_.coarse_iters, true, true);
@@ -953,7 +990,7 @@ SolveInfo Engine::solve(int l, const double2 *b, double2 *x, int nrhs) {
   const int64_t n = levels_.at(l).g.n();
   SolveInfo info;
   if (l == n_levels() - 1) {
-    dense_apply<double>(levels_[l].Dinv64, b, x, (int)n, nrhs, stream);
+    coarsest_apply<double>(levels_[l].Dinv64, b, x, (int)n, nrhs);
     info.iters = 0;
     info.residual = 0.0;
   } else if (l == 0 && (sp_.smoother == MGMLMC_SMOOTHER_LEARNED || sp_.smoother == MGMLMC_SMOOTHER_NET)) {
@@ -1354,7 +1391,7 @@ void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &ou
       } else {
         double2 *x = ws<double>("estx", l, (size_t)nb * n), *z = ws<double>("estz", l, (size_t)nb * n);
         noise(l, p.seed, s0, MGMLMC_TERM_COARSEST, 0, -1, x, nb);
-        dense_apply<double>(levels_[l].Dinv64, x, z, (int)n, nb, stream);
+        coarsest_apply<double>(levels_[l].Dinv64, x, z, (int)n, nb);
         dot<double>(x, z, n, nb, res, partials((size_t)reduce_blocks(n) * nb), stream);
       }
       MG_CUDA(cudaEventRecord(e1, stream));

@@ -159,6 +159,8 @@ class Engine {
 
   SolveInfo last_solve;
   cudaStream_t stream = nullptr;       // internal non-blocking stream: all work runs here
+  void *blas_ = nullptr;               // cuBLAS handle bound to `stream` (the coarsest-level GEMM)
+  void *blas_ws_ = nullptr;            // its fixed workspace, so that it can run under graph capture
   cudaStream_t user_stream = nullptr;  // the caller's stream given at creation
   // order the internal stream after the caller's earlier work / the caller's
   // stream after ours (every API call is bracketed by these)
@@ -185,7 +187,8 @@ class Engine {
   // FP32 coarse stencil per rhs count: 0 = FP32 CUDA cores, 1 = tcgen05
   // TF32 with M = 64 MMAs, 2 = the same with M = 128 MMAs, 3 = BF16-stored
   // blocks with FP32 arithmetic, 4 = tcgen05 with BF16 operands, -2 = the
-  // fastest of 0, 1, 3, 4 on the first call outside capture
+  // fastest of 0, 1, 3, 4, 5 on the first call outside capture; 5 = variant 4
+  // as a persistent pipelined kernel (up to 32 right-hand sides)
   void set_stencil_variant(int v);
   int stencil_variant(int l, int nrhs) const;
   static int stencil_variants();
@@ -207,6 +210,10 @@ class Engine {
 
   template <typename T> void smooth(int l, C<T> *z, C<T> *res, int nrhs);
   template <typename T> void precond(int l, const C<T> *r, C<T> *z, int nrhs);
+  // out = Minv in for the dense coarsest-level inverse (n x n, row-major) and
+  // nrhs vectors of n: one complex GEMM in cuBLAS (FP32 or FP64 arithmetic,
+  // no reduced-precision math mode)
+  template <typename T> void coarsest_apply(const C<T> *Minv, const C<T> *in, C<T> *out, int n, int nrhs);
   // the preconditioner of an outer solve: replayed from a CUDA graph captured
   // once per (level, nrhs, precision, operand addresses) unless profiling or
   // graphs are off
@@ -244,6 +251,7 @@ class Engine {
   size_t partial_cap_ = 0;
   int *flag_dev_ = nullptr;
   static constexpr size_t kPinnedBytes = 1 << 20;
+  static constexpr size_t kBlasWorkspace = 32u << 20;
   void *pinned_ = nullptr;
   size_t pinned_cap_ = 0;
   void *pinned(size_t bytes);

@@ -107,7 +107,7 @@ void Engine::contraction_vectors(int kind, int nb, double2 *x, double2 *B, doubl
     const int l = L - 1;
     const int64_t n = levels_[l].g.n();
     d[l] = ws<double>("cvd", l, (size_t)nb * n);
-    dense_apply<double>(levels_[l].Dinv64, u[l], d[l], (int)n, nb, stream);
+    coarsest_apply<double>(levels_[l].Dinv64, u[l], d[l], (int)n, nb);
   }
   // level-l vector -> fine vector (Phat_l) into dst
   auto to_fine = [&](int l, double2 *v, double2 *dst) {

@@ -232,8 +232,6 @@ void dense_from_stencil(const double2 *A, double2 *M, Geom g, cudaStream_t s);
 // in-place Gauss-Jordan inverse with partial pivoting of the n x n row-major
 // M (work: 2 n^2 complex + n); status[0] = 1 on a zero pivot
 void dense_invert(double2 *M, double2 *work, int n, int *status, cudaStream_t s);
-template <typename T>
-void dense_apply(const C<T> *Minv, const C<T> *in, C<T> *out, int n, int nrhs, cudaStream_t s);
 void dense_trace(const double2 *M, int n, double2 *out, cudaStream_t s);
 
 // ------------------------------------------------------------------ checks

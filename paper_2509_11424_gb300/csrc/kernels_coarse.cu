@@ -358,18 +358,6 @@ __global__ void stencil_bf16_kernel(const float2 *__restrict__ AT32, __nv_bfloat
     ATB[e] = __float22bfloat162_rn(AT32[e]);
 }
 
-int sm_count() {
-  static std::mutex mu;
-  static int cached[64] = {0};
-  int dev = 0;
-  MG_CUDA(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lock(mu);
-  if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
-  int n = 0;
-  MG_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
-  if (dev >= 0 && dev < 64) cached[dev] = n;
-  return n;
-}
 
 template <typename S, int RG>
 void launch_pipe(const float2 *in, float2 *out, const S *AT, Geom g, int nrhs, int *err, cudaStream_t s) {
@@ -711,31 +699,6 @@ __global__ void eye_kernel(double2 *__restrict__ M, int n) {
 
 // out_r = Minv in_r: warp per row, lanes over columns, RG right-hand sides
 // per pass so each matrix entry is loaded once per RG of them.
-template <typename T, int RG>
-__global__ void dense_apply_kernel(const C<T> *__restrict__ Minv, const C<T> *__restrict__ in,
-                                   C<T> *__restrict__ out, int n, int nrhs) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= n) return;
-  const C<T> *row = Minv + (int64_t)warp * n;
-  for (int r0 = 0; r0 < nrhs; r0 += RG) {
-    const int rg = nrhs - r0 < RG ? nrhs - r0 : RG;
-    C<T> acc[RG];
-#pragma unroll
-    for (int r = 0; r < RG; ++r) acc[r] = mk<T>((T)0, (T)0);
-    for (int j = lane; j < n; j += 32) {
-      const C<T> a = __ldg(row + j);
-#pragma unroll
-      for (int r = 0; r < RG; ++r)
-        if (r < rg) acc[r] = cfma(a, in[(int64_t)(r0 + r) * n + j], acc[r]);
-    }
-#pragma unroll
-    for (int r = 0; r < RG; ++r) {
-      const C<T> v = warp_csum(acc[r]);
-      if (lane == 0 && r < rg) out[(int64_t)(r0 + r) * n + warp] = v;
-    }
-  }
-}
-
 __global__ void dense_trace_kernel(const double2 *__restrict__ M, int n, double2 *out) {
   __shared__ double2 sh[33];
   double2 acc = make_double2(0.0, 0.0);
@@ -745,6 +708,19 @@ __global__ void dense_trace_kernel(const double2 *__restrict__ M, int n, double2
 }
 
 }  // namespace
+
+int sm_count() {
+  static std::mutex mu;
+  static int cached[64] = {0};
+  int dev = 0;
+  MG_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  if (dev >= 0 && dev < 64 && cached[dev]) return cached[dev];
+  int n = 0;
+  MG_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+  if (dev >= 0 && dev < 64) cached[dev] = n;
+  return n;
+}
 
 template <typename T>
 void stencil_apply(const C<T> *in, C<T> *out, const C<T> *AT, Geom g, int nrhs, int *err,
@@ -882,12 +858,6 @@ void dense_invert(double2 *M, double2 *work, int n, int *status, cudaStream_t s)
   MG_LAUNCH_CHECK();
 }
 
-template <typename T>
-void dense_apply(const C<T> *Minv, const C<T> *in, C<T> *out, int n, int nrhs, cudaStream_t s) {
-  dense_apply_kernel<T, 8><<<div_up((int64_t)n * 32, 256), 256, 0, s>>>(Minv, in, out, n, nrhs);
-  MG_LAUNCH_CHECK();
-}
-
 void dense_trace(const double2 *M, int n, double2 *out, cudaStream_t s) {
   dense_trace_kernel<<<1, 256, 0, s>>>(M, n, out);
   MG_LAUNCH_CHECK();
@@ -902,7 +872,7 @@ void dense_trace(const double2 *M, int n, double2 *out, cudaStream_t s) {
                                cudaStream_t);                                                   \
   template void prolong_op<T>(const C<T> *, C<T> *, const C<T> *, const AggMap &, int, double,  \
                               cudaStream_t);                                                    \
-  template void dense_apply<T>(const C<T> *, const C<T> *, C<T> *, int, int, cudaStream_t);
+
 INST(double)
 INST(float)
 

@@ -210,30 +210,49 @@ __global__ void __launch_bounds__(kTcThreads) stencil_tc_kernel(const float2 *__
     const int rc = nrhs - r0 < kTcMaxN ? nrhs - r0 : kTcMaxN;
     const int N = LAYOUT == 1 ? (rc + 15) & ~15 : (rc + 7) & ~7;  // MMA N (M = 128 needs N % 16 == 0)
     // gather B: element (n, k) of part p of direction d at
-    // ((k / KC) * N + n) * KC + k % KC (core matrices of 8 rows x 16 bytes)
-    for (int t = tid; t < 9 * (kTcM / KC) * N; t += kTcThreads) {
-      const int nn = t % N, c = (t / N) % (kTcM / KC), d = t / ((kTcM / KC) * N);
-      E *base = Bs + (size_t)(d * 2) * kTcMaxN * kTcM;
-      E *re_dst = base + ((size_t)c * N + nn) * KC;
-      E *im_dst = base + kTcMaxN * kTcM + ((size_t)c * N + nn) * KC;
-      // KC consecutive complex values, two per 16-byte load
-      const float4 *src = reinterpret_cast<const float4 *>(in + (int64_t)(r0 + (nn < rc ? nn : 0)) * n +
-                                                           (int64_t)nbr[d] * kTcM + KC * c);
-      if constexpr (sizeof(E) == 4) {
-        const float4 a = nn < rc ? __ldg(src) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 b = nn < rc ? __ldg(src + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-        split_store(reinterpret_cast<float *>(re_dst), reinterpret_cast<float *>(im_dst), make_float2(a.x, a.y),
-                    make_float2(a.z, a.w), make_float2(b.x, b.y), make_float2(b.z, b.w));
-      } else {
-        __nv_bfloat162 re[4], im[4];
+    // ((k / KC) * N + n) * KC + k % KC (core matrices of 8 rows x 16 bytes).
+    // A fixed trip count (the full chunk of 32 right-hand sides), all loads
+    // issued before the first conversion: one round trip to memory instead
+    // of one per item.
+    {
+      constexpr int kItems = 9 * (kTcM / KC) * kTcMaxN;
+      constexpr int kIters = (kItems + kTcThreads - 1) / kTcThreads;
+      constexpr int kLd = KC / 2;  // 16-byte loads per item (two complex values each)
+      const int total = 9 * (kTcM / KC) * N;
+      float4 v[kIters][kLd];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float4 a = nn < rc ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-          re[q] = __floats2bfloat162_rn(a.x, a.z);
-          im[q] = __floats2bfloat162_rn(a.y, a.w);
+      for (int it = 0; it < kIters; ++it) {
+        const int t = tid + it * kTcThreads;
+        const int nn = t % N, c = (t / N) % (kTcM / KC), d = t / ((kTcM / KC) * N);
+        const bool ok = t < total && nn < rc;
+        const float4 *src = reinterpret_cast<const float4 *>(in + (int64_t)(r0 + (ok ? nn : 0)) * n +
+                                                             (int64_t)nbr[ok ? d : 0] * kTcM + KC * c);
+#pragma unroll
+        for (int q = 0; q < kLd; ++q) v[it][q] = ok ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int it = 0; it < kIters; ++it) {
+        const int t = tid + it * kTcThreads;
+        if (t < total) {
+          const int nn = t % N, c = (t / N) % (kTcM / KC), d = t / ((kTcM / KC) * N);
+          E *base = Bs + (size_t)(d * 2) * kTcMaxN * kTcM;
+          E *re_dst = base + ((size_t)c * N + nn) * KC;
+          E *im_dst = base + kTcMaxN * kTcM + ((size_t)c * N + nn) * KC;
+          if constexpr (sizeof(E) == 4) {
+            split_store(reinterpret_cast<float *>(re_dst), reinterpret_cast<float *>(im_dst),
+                        make_float2(v[it][0].x, v[it][0].y), make_float2(v[it][0].z, v[it][0].w),
+                        make_float2(v[it][1].x, v[it][1].y), make_float2(v[it][1].z, v[it][1].w));
+          } else {
+            __nv_bfloat162 re[4], im[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              re[q] = __floats2bfloat162_rn(v[it][q].x, v[it][q].z);
+              im[q] = __floats2bfloat162_rn(v[it][q].y, v[it][q].w);
+            }
+            *reinterpret_cast<uint4 *>(re_dst) = *reinterpret_cast<const uint4 *>(re);
+            *reinterpret_cast<uint4 *>(im_dst) = *reinterpret_cast<const uint4 *>(im);
+          }
         }
-        *reinterpret_cast<uint4 *>(re_dst) = *reinterpret_cast<const uint4 *>(re);
-        *reinterpret_cast<uint4 *>(im_dst) = *reinterpret_cast<const uint4 *>(im);
       }
     }
     // make the generic-proxy stores visible to the tensor cores
@@ -317,6 +336,201 @@ __global__ void __launch_bounds__(kTcThreads) stencil_tc_kernel(const float2 *__
   if (tid == 0 && fail && err) atomicExch(err, 3);
 }
 
+// Persistent pipelined form of the BF16 kernel for up to 32 right-hand
+// sides: one CTA per SM walks the sites X = blockIdx.x + i gridDim.x with two
+// shared-memory stages and two TMEM accumulator sets.  Iteration i issues the
+// neighbour loads of site i, writes out site i - 1 (its MMAs ran meanwhile),
+// stores site i's operands, and has one thread start site i's MMAs and the
+// bulk copy of site i + 1's tiles, so the tensor work and the tile copy of
+// one site overlap the gathers and the epilogue of its neighbours in the
+// walk.  The MMAs and their order per site are those of stencil_tc_kernel:
+// identical results.  Every wait is bounded; on a timeout the CTA sets the
+// error flag, waits (bounded) for its MMAs and copies in flight, releases its
+// tensor memory and leaves.
+// smem: [2 stages][A tiles 9 x 64 x 32][B 9 x {re, im} x 32 x 32] BF16, then
+// [64 x 32 x 2] FP32 accumulator staging
+__global__ void __launch_bounds__(kTcThreads, 1)
+    stencil_tc_pipe_kernel(const float2 *__restrict__ in, float2 *__restrict__ out,
+                           const __nv_bfloat16 *__restrict__ ATC, Geom g, int nrhs, int *err,
+                           unsigned extra_tx) {
+  using E = __nv_bfloat16;
+  using Op = TcOp<E>;
+  constexpr int KC = Op::KC;
+  constexpr unsigned kSiteBytes = 9u * kTcTileElems * sizeof(E);
+  constexpr int kStageElems = 9 * kTcTileElems + 9 * 2 * kTcMaxN * kTcM;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar_a[2], bar_mma[2];
+  __shared__ unsigned tmem_slot;
+  E *stage0 = reinterpret_cast<E *>(smem_raw);
+  float *St = reinterpret_cast<float *>(stage0 + 2 * kStageElems);  // [2 acc][64 rows][kTcMaxN]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t n = g.n();
+  const int count = g.V > (int)blockIdx.x ? (g.V - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int N = (nrhs + 7) & ~7;
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q) {
+      tc_mbar_init(&bar_a[q], 1);
+      tc_mbar_init(&bar_mma[q], 1);
+    }
+  }
+  if (warp == 0) {
+    // two stages x two accumulators of 32 columns
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(saddr(&tmem_slot)),
+                 "r"(128)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tmem_slot;
+  // work in flight per stage and the parity of the phase that will end it
+  bool a_pending[2] = {false, false}, mma_pending[2] = {false, false};
+  unsigned a_par[2] = {0u, 0u}, mma_par[2] = {0u, 0u};
+  if (count > 0) {
+    if (tid == 0) {
+      tc_expect_tx(&bar_a[0], kSiteBytes + extra_tx);  // extra_tx: failure-injection tests only
+      tc_bulk_g2s(stage0, ATC + (int64_t)blockIdx.x * 9 * kTcTileElems, kSiteBytes, &bar_a[0]);
+    }
+    a_pending[0] = true;
+  }
+  bool failed = false;
+  constexpr int kItems = 9 * (kTcM / KC) * kTcMaxN;
+  constexpr int kIters = (kItems + kTcThreads - 1) / kTcThreads;
+  const int total = 9 * (kTcM / KC) * N;
+  for (int i = 0; i <= count && !failed; ++i) {
+    const int s = i & 1;
+    const int X = (int)blockIdx.x + i * (int)gridDim.x;
+    float4 v[kIters][4];
+    if (i < count) {
+      int nbr[9];
+#pragma unroll
+      for (int d = 0; d < 9; ++d) nbr[d] = g.neighbor(X, d);
+#pragma unroll
+      for (int it = 0; it < kIters; ++it) {
+        const int t = tid + it * kTcThreads;
+        const int nn = t % N, c = (t / N) % (kTcM / KC), d = t / ((kTcM / KC) * N);
+        const bool ok = t < total && nn < nrhs;
+        const float4 *src = reinterpret_cast<const float4 *>(in + (int64_t)(ok ? nn : 0) * n +
+                                                             (int64_t)nbr[ok ? d : 0] * kTcM + KC * c);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[it][q] = ok ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+    }
+    if (i > 0) {
+      // epilogue of site i - 1 (stage s ^ 1)
+      const int sp = s ^ 1;
+      const bool done = tc_wait(&bar_mma[sp], ((i - 1) >> 1) & 1);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      const int bad = __syncthreads_or(done ? 0 : 1);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (bad) {
+        failed = true;
+        break;
+      }
+      mma_pending[sp] = false;
+      {
+        float v1[32], v2[32];
+        const unsigned lane_base = (unsigned)(32 * warp) << 16;
+        tmem_ld32(tmem + lane_base + sp * 64, v1);
+        tmem_ld32(tmem + lane_base + sp * 64 + kTcMaxN, v2);
+        const int row = acc_row_of_lane<0>(warp, lane);
+        if (row >= 0) {
+#pragma unroll
+          for (int c = 0; c < 32; ++c) {
+            St[row * kTcMaxN + c] = v1[c];
+            St[64 * kTcMaxN + row * kTcMaxN + c] = v2[c];
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int Xp = X - (int)gridDim.x;
+      for (int t = tid; t < nrhs * kTcM; t += kTcThreads) {
+        const int r = t / kTcM, k = t % kTcM;
+        const float re = St[k * kTcMaxN + r] - St[64 * kTcMaxN + (32 + k) * kTcMaxN + r];
+        const float im = St[64 * kTcMaxN + k * kTcMaxN + r] + St[(32 + k) * kTcMaxN + r];
+        out[(int64_t)r * n + (int64_t)Xp * kTcM + k] = make_float2(re, im);
+      }
+    }
+    if (i == count) break;
+    // operands of site i into stage s (its previous MMAs, site i - 2, are done)
+    E *As = stage0 + s * kStageElems;
+    E *Bs = As + 9 * kTcTileElems;
+#pragma unroll
+    for (int it = 0; it < kIters; ++it) {
+      const int t = tid + it * kTcThreads;
+      if (t < total) {
+        const int nn = t % N, c = (t / N) % (kTcM / KC), d = t / ((kTcM / KC) * N);
+        E *base = Bs + (size_t)(d * 2) * kTcMaxN * kTcM;
+        E *re_dst = base + ((size_t)c * N + nn) * KC;
+        E *im_dst = base + kTcMaxN * kTcM + ((size_t)c * N + nn) * KC;
+        __nv_bfloat162 re[4], im[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          re[q] = __floats2bfloat162_rn(v[it][q].x, v[it][q].z);
+          im[q] = __floats2bfloat162_rn(v[it][q].y, v[it][q].w);
+        }
+        *reinterpret_cast<uint4 *>(re_dst) = *reinterpret_cast<const uint4 *>(re);
+        *reinterpret_cast<uint4 *>(im_dst) = *reinterpret_cast<const uint4 *>(im);
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const bool landed = tc_wait(&bar_a[s], (i >> 1) & 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    const int bad = __syncthreads_or(landed ? 0 : 1);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (bad) {
+      failed = true;
+      break;
+    }
+    a_pending[s] = false;
+    if (tid == 0) {
+      const uint32_t idesc = mma_idesc(Op::fmt, 64, N);
+      const unsigned a0 = saddr(As), b0 = saddr(Bs);
+      const unsigned acc0 = tmem + s * 64;
+      for (int d = 0; d < 9; ++d) {
+        for (int kc = 0; kc < kTcM / Op::KMMA; ++kc) {
+          const uint64_t ad = smem_desc(a0 + d * kTcTileElems * (unsigned)sizeof(E) + kc * 2 * 1024, 1024, 128);
+          const unsigned bre = b0 + (unsigned)(d * 2) * kTcMaxN * kTcM * (unsigned)sizeof(E) + kc * 2 * N * 16;
+          const unsigned bim = bre + kTcMaxN * kTcM * (unsigned)sizeof(E);
+          const unsigned acc = (d > 0 || kc > 0) ? 1u : 0u;
+          mma_op<E>(acc0, ad, smem_desc(bre, N * 16, 128), idesc, acc);
+          mma_op<E>(acc0 + kTcMaxN, ad, smem_desc(bim, N * 16, 128), idesc, acc);
+        }
+      }
+      mma_commit(&bar_mma[s]);
+      if (i + 1 < count) {
+        // stage s ^ 1's tiles were read by site i - 1's MMAs, complete above
+        tc_expect_tx(&bar_a[s ^ 1], kSiteBytes + extra_tx);
+        tc_bulk_g2s(stage0 + (s ^ 1) * kStageElems, ATC + (int64_t)(X + (int)gridDim.x) * 9 * kTcTileElems,
+                    kSiteBytes, &bar_a[s ^ 1]);
+      }
+    }
+    mma_pending[s] = true;
+    mma_par[s] = (i >> 1) & 1;
+    if (i + 1 < count) {
+      a_pending[s ^ 1] = true;
+      a_par[s ^ 1] = ((i + 1) >> 1) & 1;
+    }
+    __syncwarp();
+  }
+  if (failed) {
+    // copies and MMAs still in flight: bounded waits before the memory goes
+    for (int q = 0; q < 2; ++q) {
+      if (a_pending[q]) tc_wait(&bar_a[q], a_par[q]);
+      if (mma_pending[q]) tc_wait(&bar_mma[q], mma_par[q]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+  if (tid == 0 && failed && err) atomicExch(err, 3);
+}
+
 // ATC[X][d][c][gr][r][q] = element (row 8 gr + r, k = KC c + q) of the
 // stacked tile [Re A; Im A] of block d of site X (A canonical [X][d][i][j]),
 // in the operand type E
@@ -367,7 +581,17 @@ void stencil_apply_tc(const float2 *in, float2 *out, const void *ATC, Geom g, in
   if (!stencil_tc_supported(g)) throw Error(1, "tensor-core stencil: needs 32 dofs per coarse site");
   if ((((uintptr_t)in | (uintptr_t)out | (uintptr_t)ATC) & 15) != 0)
     throw Error(1, "tensor-core stencil: operands must be 16-byte aligned");
-  if (layout == 2) launch_tc<__nv_bfloat16, 0>(in, out, (const __nv_bfloat16 *)ATC, g, nrhs, err, s);
+  if (layout == 3 && nrhs >= 1 && nrhs <= kTcMaxN) {
+    const size_t sm = (size_t)2 * (9 * kTcTileElems + 9 * 2 * kTcMaxN * kTcM) * sizeof(__nv_bfloat16) +
+                      (size_t)2 * 64 * kTcMaxN * sizeof(float);
+    smem_optin((const void *)stencil_tc_pipe_kernel, (int)sm);
+    const int grid = g.V < sm_count() ? g.V : sm_count();
+    stencil_tc_pipe_kernel<<<grid, kTcThreads, sm, s>>>(in, out, (const __nv_bfloat16 *)ATC, g, nrhs, err,
+                                                       staging_extra_bytes());
+    MG_LAUNCH_CHECK();
+    return;
+  }
+  if (layout == 2 || layout == 3) launch_tc<__nv_bfloat16, 0>(in, out, (const __nv_bfloat16 *)ATC, g, nrhs, err, s);
   else if (layout == 1) launch_tc<float, 1>(in, out, (const float *)ATC, g, nrhs, err, s);
   else launch_tc<float, 0>(in, out, (const float *)ATC, g, nrhs, err, s);
 }

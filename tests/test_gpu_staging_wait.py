@@ -20,8 +20,11 @@ from gpu_util import Setup, dev, host, rel  # noqa: E402
 
 
 # variant 0 with 9 right-hand sides: the one-site-per-block kernel (more
-# than the 8 of the pipelined one); variant 1: the tensor-core kernel
-@pytest.mark.parametrize('variant,nr', [(0, 9), (1, 2)])
+# than the 8 of the pipelined one); variant 1: the tensor-core kernel;
+# variant 5: the persistent tensor-core kernel (its bulk copy of the first
+# site runs out; the CTA then waits, bounded, for it once more and for
+# nothing else in flight)
+@pytest.mark.parametrize('variant,nr', [(0, 9), (1, 2), (5, 2)])
 def test_staging_wait_runs_out_and_context_survives(variant, nr):
     # a 2^4 coarse lattice of 16 sites: one wave of blocks waits its 2 x 1 s
     s = Setup((4, 4, 4, 4), [(2, 2, 2, 2)], [16], eps=0.3, m0=-0.2, gseed=81)
@@ -44,7 +47,7 @@ def test_staging_wait_runs_out_and_context_survives(variant, nr):
         M.mgmlmc_apply(s.ctx, M.OP_D, 1, M.FP32, dev(x, torch.complex64), y, nr)
         got = host(y)
         want = np.array([A1 @ v.astype(np.complex64).astype(np.complex128) for v in x])
-        assert rel(got, want) < (1e-5 if variant == 0 else 3e-3)
+        assert rel(got, want) < {0: 1e-5, 1: 3e-3, 5: 1e-2}[variant]
     finally:
         M.mgmlmc_set_kernel_variant(s.ctx, M.VARIANT_STENCIL_FP32, 0)
         s.close()

@@ -51,9 +51,9 @@ def bound_check(got, x32, A1, u=U_TF32):
     return bool(ok_re.all() and ok_im.all()), float(np.max(np.abs(got - want) / bnd))
 
 
-# variant 4: BF16 operands (kind::f16), both rounded to nearest: relative
-# error <= 2^-9 per operand, the same bound with u = 2^-9
-@pytest.mark.parametrize('variant', [1, 2, 4])
+# variants 4 and 5: BF16 operands (kind::f16), both rounded to nearest:
+# relative error <= 2^-9 per operand, the same bound with u = 2^-9
+@pytest.mark.parametrize('variant', [1, 2, 4, 5])
 @pytest.mark.parametrize('nrhs', [1, 8, 32, 37])
 def test_tensor_stencil_matches_oracle(tc, variant, nrhs):
     M = tc.M
@@ -68,10 +68,32 @@ def test_tensor_stencil_matches_oracle(tc, variant, nrhs):
         got = host(y).astype(np.complex128)
     finally:
         M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, 0)
-    u = 2.0 ** -9 if variant == 4 else U_TF32
+    u = 2.0 ** -9 if variant in (4, 5) else U_TF32
     for r in range(nrhs):
         ok, worst = bound_check(got[r], x32[r], A1, u)
         assert ok, (variant, nrhs, r, worst)
+
+
+@pytest.mark.parametrize('nrhs', [1, 8, 32, 37])
+def test_persistent_tensor_stencil_identical(tc, nrhs):
+    """Variant 5, the persistent two-stage form of the BF16 tensor-core
+    stencil (152 thread blocks walking the 256 sites of the 4^4 level, so
+    most walk two), bit-identical to variant 4: the same MMAs in the same
+    order per site.  37 right-hand sides exceed its 32 and run variant 4."""
+    M = tc.M
+    n1 = tc.hier.matrix(1).shape[0]
+    xd = dev(synth.complex_normal((nrhs, n1), 550 + nrhs), torch.complex64)
+    outs = []
+    try:
+        for v in (4, 5):
+            M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, v)
+            y = torch.empty((nrhs, n1), dtype=torch.complex64, device='cuda')
+            M.mgmlmc_apply(tc.ctx, M.OP_D, 1, M.FP32, xd, y, nrhs)
+            outs.append(y)
+    finally:
+        M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, 0)
+    assert torch.equal(outs[0], outs[1])
+    assert float(outs[0].abs().max()) > 0
 
 
 @pytest.mark.parametrize('nrhs', [1, 4, 5, 8])
@@ -139,7 +161,7 @@ def test_solve_with_preconditioner_variants(tc, gs):
     M.mgmlmc_set_solver(tc.ctx, precision=M.FP32, restart=8, coarse_restart=16, smoother=1, smoother_steps=1,
                         coarse_iters=4, inner_tol=1e-6, gram_schmidt_passes=gs, post_smoothing_only=gs % 2)
     try:
-        for v in (1, 3, 4, -2):
+        for v in (1, 3, 4, 5, -2):
             M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, v)
             x = torch.empty((3, n), dtype=torch.complex128, device='cuda')
             M.mgmlmc_apply(tc.ctx, M.OP_SOLVE, 0, M.FP64, dev(b), x, 3)
