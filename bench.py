@@ -761,6 +761,8 @@ def main():
     ap.add_argument('--validate-s', type=float, default=20.0,
                     help='device seconds the allocation check may take (0: skip)')
     ap.add_argument('--m0', type=float, default=None, help='override the mass (exploration)')
+    ap.add_argument('--solver', action='append', default=None, metavar='KEY=VALUE',
+                    help='override one solver parameter of the workload (repeatable)')
     ap.add_argument('--gram-schmidt', type=int, default=None, choices=[1, 2],
                     help='classical Gram-Schmidt passes of the FP32 FGMRES (default: the workload\'s)')
     ap.add_argument('--learned', type=int, default=1, help='channels of the learned smoother (0: off)')
@@ -788,6 +790,12 @@ def main():
     wl = dict(WORKLOADS[args.workload])
     if args.gram_schmidt is not None:
         wl['solver'] = dict(wl['solver'], gram_schmidt_passes=args.gram_schmidt)
+    for kv in args.solver or []:
+        key, val = kv.split('=')
+        if key not in wl['solver'] and key not in ('coarse_iters', 'coarse_smoother_steps', 'smoother_steps',
+                                                    'restart', 'coarse_restart', 'sap_iters', 'inner_tol'):
+            raise SystemExit('unknown solver parameter %s' % key)
+        wl['solver'] = dict(wl['solver'], **{key: float(val) if key == 'inner_tol' else int(val)})
     if args.impl == 'reference':
         reference_arm(args, rank, world, wl)
         if dist:

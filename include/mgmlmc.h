@@ -566,6 +566,13 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
  * faces of each colour in a separate pass over that colour's sites, and all
  * compute the same sums in the same order: identical results. */
 #define MGMLMC_VARIANT_SAP_FP32 2
+/* FP32 restriction P_l^H and prolongation P_l (Sec. 2.2): 0 (default) = P in
+ * FP32; 1 = P stored as BF16 (round to nearest, relative error <= 2^-9 per
+ * entry; FP32 arithmetic; half the bytes of the dominant operand), for the
+ * transfers inside the multigrid preconditioner and for MGMLMC_OP_RESTRICT /
+ * MGMLMC_OP_PROLONG on FP32 vectors.  The orthogonal projector
+ * I - P_l P_l^H of the estimators always uses the exact P. */
+#define MGMLMC_VARIANT_TRANSFER_FP32 3
 /* Choose the variant of a kernel for later calls: for the FP32 fine Wilson
  * operator -2 = autotune (default: the first call per right-hand-side count
  * outside graph capture times every variant on that call's operands and

@@ -493,6 +493,7 @@ int mgmlmc_kernel_variants(int kernel) {
   if (kernel == MGMLMC_VARIANT_DSLASH_FP32) return mg::wilson_fp32_variants();
   if (kernel == MGMLMC_VARIANT_STENCIL_FP32) return mg::Engine::stencil_variants();
   if (kernel == MGMLMC_VARIANT_SAP_FP32) return mg::sap_variants();
+  if (kernel == MGMLMC_VARIANT_TRANSFER_FP32) return 2;
   return -1;
 }
 
@@ -501,6 +502,7 @@ mgmlmc_status mgmlmc_set_kernel_variant(mgmlmc_ctx *ctx, int kernel, int variant
     if (kernel == MGMLMC_VARIANT_DSLASH_FP32) E(ctx).set_dslash_variant(variant);
     else if (kernel == MGMLMC_VARIANT_STENCIL_FP32) E(ctx).set_stencil_variant(variant);
     else if (kernel == MGMLMC_VARIANT_SAP_FP32) E(ctx).set_sap_variant(variant);
+    else if (kernel == MGMLMC_VARIANT_TRANSFER_FP32) E(ctx).set_transfer_variant(variant);
     else throw mg::Error(MGMLMC_ERR_ARG, "unknown kernel");
   });
 }
@@ -513,6 +515,7 @@ mgmlmc_status mgmlmc_get_kernel_variant(const mgmlmc_ctx *cctx, int kernel, int 
     if (kernel == MGMLMC_VARIANT_DSLASH_FP32) *variant = E(ctx).dslash_variant(nrhs);
     else if (kernel == MGMLMC_VARIANT_STENCIL_FP32) *variant = E(ctx).stencil_variant(1, nrhs);
     else if (kernel == MGMLMC_VARIANT_SAP_FP32) *variant = E(ctx).sap_variant();
+    else if (kernel == MGMLMC_VARIANT_TRANSFER_FP32) *variant = E(ctx).transfer_variant();
     else throw mg::Error(MGMLMC_ERR_ARG, "unknown kernel");
   });
 }

@@ -388,6 +388,7 @@ void Engine::free_hierarchy() {
     Level &L = levels_[l];
     dfree(L.P64);
     dfree(L.P32);
+    dfree(L.PB16);
     dfree(L.Dinv64);
     dfree(L.Dinv32);
     if (l > 0) {
@@ -424,6 +425,12 @@ int Engine::dslash_variant(int nrhs) const {
 }
 
 int Engine::stencil_variants() { return 6; }
+
+void Engine::set_transfer_variant(int v) {
+  if (v < 0 || v > 1) throw Error(MGMLMC_ERR_ARG, "transfer variant out of range");
+  transfer_variant_ = v;
+  drop_graphs();
+}
 
 void Engine::set_sap_variant(int v) {
   if (v < 0 || v >= sap_variants()) throw Error(MGMLMC_ERR_ARG, "SAP variant out of range");
@@ -594,10 +601,22 @@ template <typename T> AggMap Engine::agg_of(int l) const {
   return m;
 }
 template <typename T> void Engine::restrict_to(int l, const C<T> *in, C<T> *out, int nrhs) {
+  if constexpr (sizeof(T) == 4) {
+    if (transfer_variant_ == 1 && levels_[l].PB16) {
+      restrict_op_bf16(in, out, levels_[l].PB16, agg_of<T>(l), nrhs, stream);
+      return;
+    }
+  }
   restrict_op<T>(in, out, Pmat<T>(l), agg_of<T>(l), nrhs, stream);
 }
 template <typename T>
 void Engine::prolong_from(int l, const C<T> *in, C<T> *out, int nrhs, double beta) {
+  if constexpr (sizeof(T) == 4) {
+    if (transfer_variant_ == 1 && levels_[l].PB16) {
+      prolong_op_bf16(in, out, levels_[l].PB16, agg_of<T>(l), nrhs, beta, stream);
+      return;
+    }
+  }
   prolong_op<T>(in, out, Pmat<T>(l), agg_of<T>(l), nrhs, beta, stream);
 }
 template <typename T> void Engine::project_out(int l, const C<T> *in, C<T> *out, int nrhs) {
@@ -721,7 +740,7 @@ template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nr
   MG_CUDA(cudaMemcpyAsync(res, r, sizeof(C<T>) * n * nrhs, cudaMemcpyDeviceToDevice, stream));
   if (!(sp_.post_smoothing_only && l == 0)) smooth<T>(l, z, res, nrhs);
   cudaEvent_t pr = prof_begin();
-  restrict_op<T>(res, rc, Pmat<T>(l), agg_of<T>(l), nrhs, stream);
+  restrict_to<T>(l, res, rc, nrhs);
   prof_end(pr, K_TRANSFER, 0.0, 0.0);
   if (l + 1 == n_levels() - 1) {
     cudaEvent_t pd = prof_begin();
@@ -731,7 +750,7 @@ template <typename T> void Engine::precond(int l, const C<T> *r, C<T> *z, int nr
     fgmres<T>(l + 1, rc, ec, nrhs, 0.0, sp_.coarse_iters, sp_.coarse_iters, true, true);
   }
   cudaEvent_t pp = prof_begin();
-  prolong_op<T>(ec, z, Pmat<T>(l), agg_of<T>(l), nrhs, 1.0, stream);
+  prolong_from<T>(l, ec, z, nrhs, 1.0);
   prof_end(pp, K_TRANSFER, 0.0, 0.0);
   if ((l == 0 ? sp_.smoother_steps : sp_.coarse_smoother_steps) > 0) {
     apply_D<T>(l, z, q, nrhs);
@@ -1140,9 +1159,11 @@ void Engine::build_hierarchy(const mgmlmc_mg_params &p) {
     }
     f.P64 = dalloc<double2>((size_t)ntv * n);
     f.P32 = dalloc<float2>((size_t)ntv * n);
+    f.PB16 = dalloc<float>((size_t)ntv * n);
     MG_CUDA(cudaMemsetAsync(flag_dev_, 0, sizeof(int), stream));
     build_prolongator(V, f.P64, f.agg, flag_dev_, stream);
     convert<float, double>(f.P64, f.P32, (int64_t)ntv * n, stream);
+    stencil_to_bf16(f.P32, f.PB16, (int64_t)ntv * n, stream);
     int flag = 0;
     MG_CUDA(cudaMemcpyAsync(&flag, flag_dev_, sizeof(int), cudaMemcpyDeviceToHost, stream));
     sync();

@@ -30,6 +30,7 @@ struct Level {
   AggMap agg{};            // to level + 1
   double2 *P64 = nullptr;  // [X][c][k][row]
   float2 *P32 = nullptr;
+  float *PB16 = nullptr;   // P32 as bf16 pairs (transfer variant 1)
   double2 *Dinv64 = nullptr;  // coarsest: dense inverse, row-major
   float2 *Dinv32 = nullptr;
 };
@@ -196,6 +197,10 @@ class Engine {
   // paired ones, 2 = the general ones (identical results)
   void set_sap_variant(int v);
   int sap_variant() const { return sap_variant_; }
+  // FP32 restriction / prolongation (mgmlmc_apply and the multigrid
+  // preconditioner; never the projector): 0 = P in FP32, 1 = P stored as BF16
+  void set_transfer_variant(int v);
+  int transfer_variant() const { return transfer_variant_; }
 
  private:
   template <typename T> C<T> *ws(const std::string &name, int l, size_t count);
@@ -292,6 +297,7 @@ class Engine {
   std::map<int, int> dslash_tuned_;
   int stencil_force_ = 0;
   int sap_variant_ = 0;
+  int transfer_variant_ = 0;
   int precond_depth_ = 0;  // > 0 while the multigrid preconditioner runs
   int solving_ = 0;        // > 0 inside solve()
   std::map<std::pair<int, int>, int> stencil_tuned_;  // (level, nrhs) -> variant

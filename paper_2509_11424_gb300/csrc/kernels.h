@@ -206,6 +206,12 @@ void restrict_op(const C<T> *in, C<T> *out, const C<T> *P, const AggMap &m, int 
 template <typename T>
 void prolong_op(const C<T> *in, C<T> *out, const C<T> *P, const AggMap &m, int nrhs, double beta,
                 cudaStream_t s);
+// the same with P stored as BF16 pairs (from stencil_to_bf16; relative
+// rounding <= 2^-9 per entry, FP32 arithmetic): the transfers inside the
+// multigrid preconditioner of FP32 solves
+void restrict_op_bf16(const float2 *in, float2 *out, const void *P, const AggMap &m, int nrhs, cudaStream_t s);
+void prolong_op_bf16(const float2 *in, float2 *out, const void *P, const AggMap &m, int nrhs, double beta,
+                     cudaStream_t s);
 // out = P e_col: column `col` of every aggregate's block (col = c * ntv + k)
 void probe_column(double2 *out, const double2 *P, const AggMap &m, int col, cudaStream_t s);
 // P from ntv test vectors V[k][n]: per (aggregate, chirality) modified

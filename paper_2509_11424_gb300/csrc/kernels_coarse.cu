@@ -297,12 +297,25 @@ __global__ void __launch_bounds__(32 * 9, 1) stencil_pipe_kernel(const float2 *_
   bool pending[2] = {blockIdx.x < (unsigned)g.V, blockIdx.x + gridDim.x < (unsigned)g.V};
   int k = 0;
   bool failed = false;
-  for (int X = blockIdx.x; X < g.V; X += gridDim.x, ++k) {
-    const int st = k & 1;
-    const int nb = g.neighbor(X, d);
+  // the neighbour values of the next site are loaded into registers while
+  // the current one computes (one site ahead, like the block copies)
+  float2 xn[RG];
+  if ((int)blockIdx.x < g.V) {
+    const int nb = g.neighbor(blockIdx.x, d);
 #pragma unroll
     for (int r = 0; r < RG; ++r)
-      xs[(d * RG + r) * m + i] = r < nrhs ? in[(int64_t)r * n + (int64_t)nb * m + i] : make_float2(0.f, 0.f);
+      xn[r] = r < nrhs ? __ldg(in + (int64_t)r * n + (int64_t)nb * m + i) : make_float2(0.f, 0.f);
+  }
+  for (int X = blockIdx.x; X < g.V; X += gridDim.x, ++k) {
+    const int st = k & 1;
+#pragma unroll
+    for (int r = 0; r < RG; ++r) xs[(d * RG + r) * m + i] = xn[r];
+    if (X + (int)gridDim.x < g.V) {
+      const int nb = g.neighbor(X + (int)gridDim.x, d);
+#pragma unroll
+      for (int r = 0; r < RG; ++r)
+        xn[r] = r < nrhs ? __ldg(in + (int64_t)r * n + (int64_t)nb * m + i) : make_float2(0.f, 0.f);
+    }
     const bool ready = mbar_wait_bounded(&bar[st], phase[st], err);
     if (__syncthreads_or(ready ? 0 : 1)) {
       failed = true;
@@ -433,15 +446,23 @@ __global__ void stencil_split_kernel(const C<T> *__restrict__ in, C<T> *__restri
 // out[r][X][c*ntv + k] = sum_row conj(P[X][c][k][row]) in_r[fine(X, c, row)]
 // One block per (aggregate, chirality); RG right-hand sides are staged in
 // shared memory per pass so each P entry is read once per RG of them.
-template <typename T, int RG>
+// entries of P as stored: FP64 / FP32 complex, or BF16 pairs (FP32 arithmetic)
+__device__ __forceinline__ double2 ldp(const double2 *p) { return __ldg(p); }
+__device__ __forceinline__ float2 ldp(const float2 *p) { return __ldg(p); }
+__device__ __forceinline__ float2 ldp(const __nv_bfloat162 *p) {
+  const unsigned u = __ldg(reinterpret_cast<const unsigned *>(p));
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u));
+}
+
+template <typename T, int RG, typename PS = C<T>>
 __global__ void restrict_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ out,
-                                const C<T> *__restrict__ P, AggMap m, int nrhs) {
+                                const PS *__restrict__ P, AggMap m, int nrhs) {
   extern __shared__ unsigned char smem_raw[];
   C<T> *xs = reinterpret_cast<C<T> *>(smem_raw);  // [RG][rows]
   const int X = blockIdx.x >> 1, c = blockIdx.x & 1;
   const int64_t nf = m.fine.n(), nc = m.coarse.n();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const C<T> *PX = P + ((int64_t)(X * 2 + c) * m.ntv) * m.rows;
+  const PS *PX = P + ((int64_t)(X * 2 + c) * m.ntv) * m.rows;
   for (int r0 = 0; r0 < nrhs; r0 += RG) {
     const int rg = nrhs - r0 < RG ? nrhs - r0 : RG;
     __syncthreads();
@@ -453,12 +474,12 @@ __global__ void restrict_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ 
     }
     __syncthreads();
     for (int k = warp; k < m.ntv; k += nw) {
-      const C<T> *Pk = PX + (int64_t)k * m.rows;
+      const PS *Pk = PX + (int64_t)k * m.rows;
       C<T> acc[RG];
 #pragma unroll
       for (int r = 0; r < RG; ++r) acc[r] = mk<T>((T)0, (T)0);
       for (int row = lane; row < m.rows; row += 32) {
-        const C<T> a = __ldg(Pk + row);
+        const C<T> a = ldp(Pk + row);
 #pragma unroll
         for (int r = 0; r < RG; ++r) acc[r] = cfmac(a, xs[r * m.rows + row], acc[r]);
       }
@@ -474,9 +495,9 @@ __global__ void restrict_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ 
 // out_r[fine(X, c, row)] = beta out + sum_k P[X][c][k][row] in_r[X][c*ntv + k]
 // One block per (aggregate, chirality); each thread owns rows and applies the
 // column segment of P to RG right-hand sides at a time.
-template <typename T, int RG>
+template <typename T, int RG, typename PS = C<T>>
 __global__ void prolong_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ out,
-                               const C<T> *__restrict__ P, AggMap m, int nrhs, T beta) {
+                               const PS *__restrict__ P, AggMap m, int nrhs, T beta) {
   extern __shared__ unsigned char smem_raw[];
   C<T> *cs = reinterpret_cast<C<T> *>(smem_raw);  // [nrhs][ntv]
   const int X = blockIdx.x >> 1, c = blockIdx.x & 1;
@@ -486,7 +507,7 @@ __global__ void prolong_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ o
     cs[e] = in[(int64_t)r * nc + (int64_t)X * m.coarse.dof + c * m.ntv + k];
   }
   __syncthreads();
-  const C<T> *PX = P + ((int64_t)(X * 2 + c) * m.ntv) * m.rows;
+  const PS *PX = P + ((int64_t)(X * 2 + c) * m.ntv) * m.rows;
   for (int row = threadIdx.x; row < m.rows; row += blockDim.x) {
     const int64_t fi = m.fine_index(X, c, row);
     for (int r0 = 0; r0 < nrhs; r0 += RG) {
@@ -495,7 +516,7 @@ __global__ void prolong_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ o
 #pragma unroll
       for (int r = 0; r < RG; ++r) acc[r] = mk<T>((T)0, (T)0);
       for (int k = 0; k < m.ntv; ++k) {
-        const C<T> a = __ldg(PX + (int64_t)k * m.rows + row);
+        const C<T> a = ldp(PX + (int64_t)k * m.rows + row);
 #pragma unroll
         for (int r = 0; r < RG; ++r)
           if (r < rg) acc[r] = cfma(a, cs[(r0 + r) * m.ntv + k], acc[r]);
@@ -812,6 +833,30 @@ void prolong_op(const C<T> *in, C<T> *out, const C<T> *P, const AggMap &m, int n
     const size_t sm = (size_t)rg * m.ntv * sizeof(C<T>);
     prolong_kernel<T, 4><<<m.coarse.V * 2, 256, sm, s>>>(in + (int64_t)r0 * nc, out + (int64_t)r0 * nf, P, m,
                                                          rg, (T)beta);
+    MG_LAUNCH_CHECK();
+  }
+}
+
+void restrict_op_bf16(const float2 *in, float2 *out, const void *P, const AggMap &m, int nrhs, cudaStream_t s) {
+  constexpr int RG = 4;
+  const size_t sm = (size_t)RG * m.rows * sizeof(float2);
+  if (sm > 200 * 1024) throw Error(1, "restrict: aggregate too large for shared memory");
+  smem_optin((const void *)restrict_kernel<float, RG, __nv_bfloat162>, 200 * 1024);
+  restrict_kernel<float, RG, __nv_bfloat162>
+      <<<m.coarse.V * 2, 256, sm, s>>>(in, out, static_cast<const __nv_bfloat162 *>(P), m, nrhs);
+  MG_LAUNCH_CHECK();
+}
+
+void prolong_op_bf16(const float2 *in, float2 *out, const void *P, const AggMap &m, int nrhs, double beta,
+                     cudaStream_t s) {
+  const int per = (int)((48 * 1024) / ((size_t)m.ntv * sizeof(float2)));
+  if (per < 1) throw Error(1, "prolong: too many test vectors");
+  const int64_t nf = m.fine.n(), nc = m.coarse.n();
+  for (int r0 = 0; r0 < nrhs; r0 += per) {
+    const int rg = nrhs - r0 < per ? nrhs - r0 : per;
+    const size_t sm = (size_t)rg * m.ntv * sizeof(float2);
+    prolong_kernel<float, 4, __nv_bfloat162><<<m.coarse.V * 2, 256, sm, s>>>(
+        in + (int64_t)r0 * nc, out + (int64_t)r0 * nf, static_cast<const __nv_bfloat162 *>(P), m, rg, (float)beta);
     MG_LAUNCH_CHECK();
   }
 }

@@ -390,6 +390,7 @@ def mgmlmc_kernel_launches():
 VARIANT_DSLASH_FP32 = 0
 VARIANT_STENCIL_FP32 = 1
 VARIANT_SAP_FP32 = 2
+VARIANT_TRANSFER_FP32 = 3
 VARIANT_AUTOTUNE = -2
 LAYOUT_INTERNAL = 0x100
 

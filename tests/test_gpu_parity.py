@@ -164,10 +164,12 @@ def test_dslash_variant_bad_args():
     ns = M.mgmlmc_kernel_variants(M.VARIANT_STENCIL_FP32)
     nsap = M.mgmlmc_kernel_variants(M.VARIANT_SAP_FP32)
     assert nv == 7 and ns == 6 and nsap == 3
-    assert M.mgmlmc_kernel_variants(3) == -1
+    assert M.mgmlmc_kernel_variants(M.VARIANT_TRANSFER_FP32) == 2
+    assert M.mgmlmc_kernel_variants(4) == -1
     ctx = M.mgmlmc_create((4, 4, 4, 4), torch.cuda.current_stream())
     try:
-        for kern, v in ((0, nv), (0, -1), (0, -3), (1, ns), (1, -1), (2, nsap), (2, -1), (2, -2), (3, 0)):
+        for kern, v in ((0, nv), (0, -1), (0, -3), (1, ns), (1, -1), (2, nsap), (2, -1), (2, -2), (3, 2), (3, -1),
+                        (4, 0)):
             with pytest.raises(M.MgmlmcError):
                 M.mgmlmc_set_kernel_variant(ctx, kern, v)
     finally:
@@ -261,6 +263,50 @@ def test_transfer_and_coarse_ops(three, prec):
         y = host(out)
         for r in range(2):
             assert rel(y[r], dirac.apply_stencil(h.A[l], x[r], h.dims[l])) < tol
+
+
+def test_transfer_bf16_storage(three):
+    """Transfer variant 1: P stored as BF16 pairs (round to nearest, relative
+    error <= 2^-9 per real entry), FP32 products and sums.  Every entry of
+    P^H x or P x_c is a sum of products p_k x_k, so per output entry, real and
+    imaginary parts: |got - exact| <= 2^-9 sum_k |p_k|_1 |x_k|_1 (storage)
+    plus the FP32 accumulation, K 2^-24 of the same sum (K <= 2 x 192 here),
+    with |z|_1 = |Re z| + |Im z|; asserted against the oracle's P applied to
+    the FP32-rounded input.  The projector keeps the exact P: OP_PROJECT
+    equals variant 0 bit for bit."""
+    h = three.hier
+    u = 2.0 ** -9 + 400 * 2.0 ** -24
+    try:
+        for l in range(2):
+            Pm = h.P[l].matrix()
+            Pabs = abs(Pm.real) + abs(Pm.imag)
+            n, nc = h.size(l), h.size(l + 1)
+            x = synth.complex_normal((2, n), 120 + l).astype(np.complex64).astype(np.complex128)
+            xc = synth.complex_normal((2, nc), 130 + l).astype(np.complex64).astype(np.complex128)
+            out_c = torch.empty((2, nc), dtype=torch.complex64, device='cuda')
+            out_f = torch.empty((2, n), dtype=torch.complex64, device='cuda')
+            pj = []
+            for v in (0, 1):
+                M.mgmlmc_set_kernel_variant(three.ctx, M.VARIANT_TRANSFER_FP32, v)
+                M.mgmlmc_apply(three.ctx, M.OP_PROJECT, l, 1, dev(x, torch.complex64), out_f, 2)
+                pj.append(out_f.clone())
+            assert torch.equal(pj[0], pj[1])
+            assert M.mgmlmc_get_kernel_variant(three.ctx, M.VARIANT_TRANSFER_FP32, 2) == 1
+            M.mgmlmc_apply(three.ctx, M.OP_RESTRICT, l, 1, dev(x, torch.complex64), out_c, 2)
+            M.mgmlmc_apply(three.ctx, M.OP_PROLONG, l, 1, dev(xc, torch.complex64), out_f, 2)
+            rc, pf = host(out_c).astype(np.complex128), host(out_f).astype(np.complex128)
+            for r in range(2):
+                want = h.P[l].restrict(x[r])
+                bnd = u * (Pabs.T @ (np.abs(x[r].real) + np.abs(x[r].imag))) + 1e-30
+                assert np.all(np.abs(rc[r].real - want.real) <= bnd), (l, r)
+                assert np.all(np.abs(rc[r].imag - want.imag) <= bnd), (l, r)
+                assert np.max(np.abs(rc[r] - want)) > 1e-6 * np.max(np.abs(want))  # not the FP32 P
+                want = h.P[l].prolong(xc[r])
+                bnd = u * (Pabs @ (np.abs(xc[r].real) + np.abs(xc[r].imag))) + 1e-30
+                assert np.all(np.abs(pf[r].real - want.real) <= bnd), (l, r)
+                assert np.all(np.abs(pf[r].imag - want.imag) <= bnd), (l, r)
+    finally:
+        M.mgmlmc_set_kernel_variant(three.ctx, M.VARIANT_TRANSFER_FP32, 0)
 
 
 def test_coarsest_trace(three):

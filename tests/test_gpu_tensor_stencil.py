@@ -163,6 +163,8 @@ def test_solve_with_preconditioner_variants(tc, gs):
     try:
         for v in (1, 3, 4, 5, -2):
             M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, v)
+            # with the BF16 stencils, BF16-stored P in the preconditioner too
+            M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_TRANSFER_FP32, 1 if v in (3, 4, 5) else 0)
             x = torch.empty((3, n), dtype=torch.complex128, device='cuda')
             M.mgmlmc_apply(tc.ctx, M.OP_SOLVE, 0, M.FP64, dev(b), x, 3)
             xs = host(x)
@@ -170,4 +172,5 @@ def test_solve_with_preconditioner_variants(tc, gs):
                 assert np.linalg.norm(b[r] - A0 @ xs[r]) / np.linalg.norm(b[r]) < 1.5e-12, v
     finally:
         M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, 0)
+        M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_TRANSFER_FP32, 0)
         M.mgmlmc_set_solver(tc.ctx)
