@@ -602,13 +602,13 @@ def build_context(M, torch, wl, stream, U=None, dims=None, blocks=None, ntv=None
     return ctx, time.time() - t0
 
 
-def train_network(M, torch, wl, ctx, stream, channels, steps):
+def train_network(M, torch, wl, ctx, stream, channels, steps, source=0):
     """The gauge-covariant network trained on the solver's own residuals
     (mgmlmc_learned_train).  Workloads with a `train` entry train on that
     smaller lattice of the same generator and carry the weights over to ctx
     (the layers act the same way on any lattice); returns (train result,
     wall seconds including the side context's setup)."""
-    kw = dict(channels=channels, steps=steps, batch=8, pool=2000, lr=1e-3, seed=5002)
+    kw = dict(channels=channels, steps=steps, batch=8, pool=2000, lr=1e-3, seed=5002, source=source)
     t0 = time.time()
     if not wl['train']:
         res = M.mgmlmc_learned_train(ctx, **kw)
@@ -766,8 +766,9 @@ def main():
     ap.add_argument('--gram-schmidt', type=int, default=None, choices=[1, 2],
                     help='classical Gram-Schmidt passes of the FP32 FGMRES (default: the workload\'s)')
     ap.add_argument('--learned', type=int, default=1, help='channels of the learned smoother (0: off)')
-    ap.add_argument('--net-mode', default='after-sap', choices=['after-sap', 'replace-sap'],
-                    help='the network as one step after the SAP sweeps, or in place of SAP')
+    ap.add_argument('--net-mode', default='after-sap', choices=['after-sap', 'replace-sap', 'guess'],
+                    help='the network as one step after the SAP sweeps, in place of SAP, or as the initial '
+                         'guess of the fine-level solves (SAP smoother)')
     ap.add_argument('--train-steps', type=int, default=200)
     ap.add_argument('--dslash-only', action='store_true', help='only the 32^4 FP32 Dslash measurement')
     ap.add_argument('--arms', default=None, help='comparison arms to run (comma list of %s)' % ', '.join(ARMS))
@@ -838,8 +839,13 @@ def main():
     train, t_train = None, 0.0
     main_solver = dict(wl['solver'])
     if args.learned > 0:
-        train, t_train = train_network(M, torch, wl, ctx, stream, args.learned, args.train_steps)
-        main_solver['smoother'] = M.SMOOTHER_LEARNED if args.net_mode == 'after-sap' else M.SMOOTHER_NET
+        guess = args.net_mode == 'guess'
+        train, t_train = train_network(M, torch, wl, ctx, stream, args.learned, args.train_steps,
+                                       source=1 if guess else 0)
+        if guess:
+            main_solver['learned_guess'] = 1
+        else:
+            main_solver['smoother'] = M.SMOOTHER_LEARNED if args.net_mode == 'after-sap' else M.SMOOTHER_NET
         M.mgmlmc_set_solver(ctx, precision=prec, **main_solver)
     print('kernel launches after setup: %d' % M.mgmlmc_kernel_launches(), file=sys.stderr)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device='cuda')  # 256 MB > L2
@@ -1130,7 +1136,8 @@ def compact_line(args, wl, world, value, ms_per_step, launches, clk, det, compar
                                   ', '.join('%d^4' % b[0] for b in wl['blocks']), '/'.join(map(str, wl['ntv'])),
                                   ('' if not args.learned else ' + learned(%d ch)' % args.learned
                                    if args.net_mode == 'after-sap' else ' -> learned(%d ch) in place of SAP'
-                                   % args.learned),
+                                   % args.learned if args.net_mode == 'replace-sap'
+                                   else ' + learned(%d ch) initial guess' % args.learned),
                                   wl['solver']['restart'], wl['fine_n'], wl['coarse_n'],
                                   wl['solver'].get('fine_batch') or wl['batch']),
                    'global_batch': sum(v['n'] for v in det['terms'].values()) // max(1, args.steps) * world,

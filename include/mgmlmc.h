@@ -137,6 +137,15 @@ typedef struct {
                           terms) in blocks of at most fine_batch right-hand
                           sides; 0 = the estimator's batch.  Samples, noise
                           counters and results do not depend on it. */
+  int learned_guess;   /* 1: FP32 solves on the fine level start from the
+                          trained network's guess instead of zero: with
+                          c = b / ||b||, x0 = ||b|| alpha N(c), alpha =
+                          <D N(c), c> / ||D N(c)||^2 (the residual-minimising
+                          step), and the FP32 residual c - alpha D N(c),
+                          scaled back, as the first defect; every later defect
+                          is the true FP64 residual, which alone decides
+                          convergence (needs mgmlmc_learned_init or _train;
+                          any smoother).  0 (default): x0 = 0. */
 } mgmlmc_solver_params;
 
 #define MGMLMC_SMOOTHER_MR 0
@@ -459,6 +468,13 @@ typedef struct {
   double lr;      /* Adam learning rate */
   uint64_t seed;  /* seed of the weight initialisation and of the noise of the
                      solves that produce the pairs */
+  int source;     /* 0: the residuals the SAP post-smoother leaves during solves
+                     of Z4 right-hand sides (the network as a smoothing step);
+                     1: the right-hand sides of the estimator's fine-level
+                     solves, half projected Z4 noise (I - P_0 P_0^H) x (term
+                     O_0), half prolonged coarse Z4 noise P_0 x (term F_0),
+                     for the network as the initial guess (learned_guess);
+                     no solves are needed to collect them */
 } mgmlmc_train_params;
 
 typedef struct {
@@ -544,10 +560,14 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
  * block per SM walking the sites with two shared-memory stages and two
  * tensor-memory accumulators, so one site's MMAs and tile copy overlap the
  * gathers and epilogue of others; identical results; up to 32 right-hand
- * sides, variant 4 beyond).  Variant 0 runs up to 8 right-hand sides at 32 dofs per site in
+ * sides, variant 4 beyond); 6 = variant 3's BF16 blocks and sums with one
+ * warp per coarse site streaming its blocks from memory in 16-byte row
+ * chunks (a second BF16 copy of the blocks in that layout; results
+ * identical to variant 3; up to 8 right-hand sides at 32 dofs per site,
+ * variant 0 otherwise).  Variant 0 runs up to 8 right-hand sides at 32 dofs per site in
  * a pipelined kernel (persistent blocks, a two-stage ring of bulk copies
  * over sites) with results identical to the one-site-per-block kernels.
- * -2 = autotune among 0, 1, 3, 4 and 5 per (level, nrhs) on the first call
+ * -2 = autotune among 0, 1, 3, 4, 5 and 6 per (level, nrhs) on the first call
  * outside graph capture (opt-in,
  * since the choice changes the rounding).  Inside a solve the variant applies
  * to the multigrid preconditioner only (smoothers, coarse-grid corrections);

@@ -55,6 +55,45 @@ template <typename To, typename From> __host__ __device__ __forceinline__ C<To> 
   C<To> r; r.x = (To)a.x; r.y = (To)a.y; return r;
 }
 
+// ---- packed FP32 pairs: two values in the lanes of a 64-bit register pair,
+// advanced by one .f32x2 instruction; each lane rounds exactly as the scalar
+// instruction would, so a paired computation reproduces the scalar one bit
+// for bit
+struct P2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ P2 p2(float lo, float hi) {
+  P2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ float2 p2split(P2 a) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a.v));
+  return r;
+}
+__device__ __forceinline__ P2 p2fma(P2 a, P2 b, P2 c) {
+  P2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ P2 p2add(P2 a, P2 b) {
+  P2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ P2 p2sub(P2 a, P2 b) {
+  P2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ P2 p2mul(P2 a, P2 b) {
+  P2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ P2 p2neg(P2 a) { return p2mul(a, p2(-1.f, -1.f)); }
+
 // ----------------------------------------------------------------- geometry
 // A 4-D periodic lattice with `dof` complex entries per site.  Site index
 // s = x + L0 (y + L1 (z + L2 t)).

@@ -365,7 +365,7 @@ void Engine::set_solver(const mgmlmc_solver_params &p) {
       (p.smoother != MGMLMC_SMOOTHER_MR && p.smoother != MGMLMC_SMOOTHER_SAP &&
        p.smoother != MGMLMC_SMOOTHER_LEARNED && p.smoother != MGMLMC_SMOOTHER_NET) || p.sap_iters < 1 ||
       p.coarse_smoother_steps < 0 ||
-      p.sap_iters > 64 || p.fine_batch < 0)
+      p.sap_iters > 64 || p.fine_batch < 0 || (p.learned_guess != 0 && p.learned_guess != 1))
     throw Error(MGMLMC_ERR_ARG, "invalid solver parameters");
   drop_graphs();  // captured preconditioners bake in smoother / inner iteration counts
   sp_ = p;
@@ -399,6 +399,7 @@ void Engine::free_hierarchy() {
       if (L.ATCB) cudaFree(L.ATCB);
       L.ATCB = nullptr;
       dfree(L.ATB16);
+      dfree(L.ATS);
     }
     L.has_next = false;
   }
@@ -424,7 +425,7 @@ int Engine::dslash_variant(int nrhs) const {
   return it == dslash_tuned_.end() ? -2 : it->second;
 }
 
-int Engine::stencil_variants() { return 6; }
+int Engine::stencil_variants() { return 7; }
 
 void Engine::set_transfer_variant(int v) {
   if (v < 0 || v > 1) throw Error(MGMLMC_ERR_ARG, "transfer variant out of range");
@@ -454,7 +455,8 @@ int Engine::stencil_variant(int l, int nrhs) const {
 // 0: FP32 (the pipelined kernel where it applies, same sums as the
 // one-site-per-CTA kernels); 1, 2: tensor cores (TF32); 3: BF16-stored
 // blocks, FP32 arithmetic (pipelined kernel, up to 8 right-hand sides);
-// 4: tensor cores with BF16 operands
+// 4: tensor cores with BF16 operands; 5: 4 as a persistent pipelined kernel;
+// 6: 3's sums with one warp per site streaming the row-chunked blocks
 void Engine::stencil_run(int l, int v, const float2 *in, float2 *out, int nrhs) {
   const Level &L = levels_[l];
   const bool pipe = stencil_pipe_supported(L.g) && nrhs <= 8;
@@ -462,6 +464,7 @@ void Engine::stencil_run(int l, int v, const float2 *in, float2 *out, int nrhs) 
   else if (v == 4 && L.ATCB) stencil_apply_tc(in, out, L.ATCB, L.g, nrhs, flag_dev_ + 1, 2, stream);
   else if (v == 5 && L.ATCB) stencil_apply_tc(in, out, L.ATCB, L.g, nrhs, flag_dev_ + 1, 3, stream);
   else if (v == 3 && L.ATB16 && pipe) stencil_apply_pipe(in, out, L.ATB16, true, L.g, nrhs, flag_dev_ + 1, stream);
+  else if (v == 6 && L.ATS && nrhs <= 8) stencil_apply_stream(in, out, L.ATS, L.g, nrhs, stream);
   else if (pipe) stencil_apply_pipe(in, out, L.AT32, false, L.g, nrhs, flag_dev_ + 1, stream);
   else stencil_apply<float>(in, out, L.AT32, L.g, nrhs, flag_dev_ + 1, stream);
 }
@@ -482,8 +485,9 @@ int Engine::stencil_pick(int l, int nrhs, const float2 *in, float2 *out) {
   int pick = 0;
   float best = 1e30f;
   // variant 2 is variant 1 with twice the tensor work: not a candidate
-  for (int v : {0, 1, 3, 4, 5}) {
+  for (int v : {0, 1, 3, 4, 5, 6}) {
     if (v == 3 && !(levels_[l].ATB16 && nrhs <= 8)) continue;
+    if (v == 6 && !(levels_[l].ATS && nrhs <= 8)) continue;
     stencil_run(l, v, in, out, nrhs);
     MG_CUDA(cudaEventRecord(ev.a, stream));
     for (int rep = 0; rep < 3; ++rep) stencil_run(l, v, in, out, nrhs);
@@ -554,7 +558,8 @@ template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int
     } else {
       const int v = stencil_pick(l, nrhs, in, out);
       stencil_run(l, v, in, out, nrhs);
-      if ((v == 3 && L.ATB16 && nrhs <= 8) || ((v == 4 || v == 5) && L.ATCB)) bs = 4.0;
+      if ((v == 3 && L.ATB16 && nrhs <= 8) || (v == 6 && L.ATS && nrhs <= 8) || ((v == 4 || v == 5) && L.ATCB))
+        bs = 4.0;
     }
     const double m = L.g.dof;
     bytes = (double)L.g.V * (9.0 * m * m * bs + 2.0 * m * nrhs * cs);
@@ -964,6 +969,29 @@ SolveInfo Engine::solve_mixed(int l, const double2 *b, double2 *x, int nrhs) {
   for (int q = 0; q < nrhs; ++q) bn[q] = std::sqrt(std::max(h[q].x, 0.0));
   MG_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * vs, stream));
   const double2 *r = b;  // residual of x = 0
+  if (l == 0 && sp_.learned_guess) {
+    // the network's guess: with c = b / ||b|| (FP32 fine layout), e = N(c)
+    // and q = D e, x0 = ||b|| alpha e and c - alpha q is the first defect
+    // (its FP32 rounding is corrected by the true FP64 residual after the
+    // first inner solve)
+    if (!net_.C) throw Error(MGMLMC_ERR_STATE, "learned guess selected but the network is not initialised");
+    float2 *q32 = ws<float>("smq", 0, (size_t)vs);
+    float2 *z32 = ws<float>("sape", 0, (size_t)vs);
+    double2 *dq = ws<double>("netd", 0, 2 * (size_t)nrhs);
+    inv_norm_kernel<<<(nrhs + 63) / 64, 64, 0, stream>>>(inv, rn, nr, nrhs);
+    MG_LAUNCH_CHECK();
+    relayout<float, double>(b, r32, inv, levels_[0].g.V, nrhs, true, stream);
+    cudaEvent_t pa = prof_begin();
+    net_forward<float>(r32, e32, nrhs);
+    prof_end(pa, K_NET, 0.0, 0.0);
+    apply_D<float>(0, e32, q32, nrhs);
+    dot_qr<float>(q32, r32, n, nrhs, dq, dq + nrhs, partials((size_t)reduce_blocks(n) * nrhs * 2), stream);
+    MG_CUDA(cudaMemsetAsync(z32, 0, sizeof(float2) * vs, stream));
+    mr_dir_update<float>(z32, r32, e32, q32, dq, dq + nrhs, n, nrhs, stream);
+    relayout<double, float>(z32, x, rn, levels_[0].g.V, nrhs, false, stream);
+    relayout<double, float>(r32, t, rn, levels_[0].g.V, nrhs, false, stream);
+    r = t;
+  }
   SolveInfo info;
   int total = 0;
   for (int outer = 0;; ++outer) {
@@ -1094,6 +1122,8 @@ void Engine::galerkin(int l) {
   if (stencil_pipe_supported(c.g)) {
     c.ATB16 = dalloc<float>(acnt);  // one bf16 pair (4 bytes) per complex entry
     stencil_to_bf16(c.AT32, c.ATB16, (int64_t)acnt, stream);
+    c.ATS = dalloc<float>(acnt);
+    stencil_to_stream(c.AT32, c.ATS, (int64_t)acnt, stream);
   }
 }
 

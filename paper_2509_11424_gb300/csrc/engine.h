@@ -26,6 +26,7 @@ struct Level {
   float *ATC = nullptr;     // tensor-core tiles (32 dofs per site only), see stencil_tile_tc
   void *ATCB = nullptr;     // the same tiles in BF16 (kind::f16 MMAs)
   float *ATB16 = nullptr;   // AT32 as bf16 pairs (32 dofs per site only), preconditioner variant
+  float *ATS = nullptr;     // the same BF16 pairs row-chunked for the streaming kernel (variant 6)
   bool has_next = false;
   AggMap agg{};            // to level + 1
   double2 *P64 = nullptr;  // [X][c][k][row]
@@ -188,8 +189,10 @@ class Engine {
   // FP32 coarse stencil per rhs count: 0 = FP32 CUDA cores, 1 = tcgen05
   // TF32 with M = 64 MMAs, 2 = the same with M = 128 MMAs, 3 = BF16-stored
   // blocks with FP32 arithmetic, 4 = tcgen05 with BF16 operands, -2 = the
-  // fastest of 0, 1, 3, 4, 5 on the first call outside capture; 5 = variant 4
-  // as a persistent pipelined kernel (up to 32 right-hand sides)
+  // fastest of 0, 1, 3, 4, 5, 6 on the first call outside capture; 5 =
+  // variant 4 as a persistent pipelined kernel (up to 32 right-hand sides);
+  // 6 = variant 3's arithmetic with one warp per site streaming the blocks
+  // (up to 8 right-hand sides; identical results to 3)
   void set_stencil_variant(int v);
   int stencil_variant(int l, int nrhs) const;
   static int stencil_variants();

@@ -182,17 +182,20 @@ template <typename T> void Engine::record(const C<T> *res, int nrhs) {
 
 void Engine::net_train(const mgmlmc_train_params &p, mgmlmc_train_result &out) {
   if (!ready_) throw Error(MGMLMC_ERR_STATE, "hierarchy not built");
-  if (p.steps < 1 || p.batch < 1 || p.batch > 64 || p.pool < p.batch || !(p.lr > 0.0))
+  if (p.steps < 1 || p.batch < 1 || p.batch > 64 || p.pool < p.batch || !(p.lr > 0.0) ||
+      (p.source != 0 && p.source != 1))
     throw Error(MGMLMC_ERR_ARG, "invalid training parameters");
   const auto t0 = std::chrono::steady_clock::now();
   if (net_.C != p.channels) net_init(p.channels, p.seed);
   const int64_t n = levels_[0].g.n();
   // 1. residual / error pairs from the solver: the inputs of its fine-level
   //    smoother during solves of Z4 right-hand sides (SAP when the learned
-  //    smoother is selected, so the pairs never depend on the network)
-  const int saved = sp_.smoother;
+  //    smoother is selected, so the pairs never depend on the network), or
+  //    (source 1) the right-hand sides its fine-level solves start from
+  const int saved = sp_.smoother, saved_guess = sp_.learned_guess;
   if (sp_.smoother == MGMLMC_SMOOTHER_LEARNED || sp_.smoother == MGMLMC_SMOOTHER_NET)
     sp_.smoother = MGMLMC_SMOOTHER_SAP;
+  sp_.learned_guess = 0;
   drop_graphs();
   if (pool_) cudaFree(pool_);
   pool_ = nullptr;
@@ -207,17 +210,36 @@ void Engine::net_train(const mgmlmc_train_params &p, mgmlmc_train_result &out) {
   double2 *b = ws<double>("trb", 0, (size_t)nb * n), *x = ws<double>("trx", 0, (size_t)nb * n);
   recording_ = true;
   try {
-    for (int k = 0; pool_n_ < pool_cap_ && k < 400; ++k) {
-      z4_noise<double>(b, levels_[0].g, p.seed, (uint64_t)k * nb, 113, 0, -1, nb, stream);
-      solve(0, b, x, nb);
+    if (p.source == 1) {
+      // the right-hand sides of the estimator's fine-level solves, O_0 and
+      // F_0 alternately: (I - P P^H) x for fine Z4 noise x, P x for coarse
+      // Z4 noise x (noise streams 113 and 114 of the training seed)
+      double2 *xc = ws<double>("trxc", 1, (size_t)nb * levels_[1].g.n());
+      for (int k = 0; pool_n_ < pool_cap_ && k < 400; ++k) {
+        if (k % 2 == 0) {
+          z4_noise<double>(b, levels_[0].g, p.seed, (uint64_t)k * nb, 113, 0, -1, nb, stream);
+          project_out<double>(0, b, x, nb);
+        } else {
+          z4_noise<double>(xc, levels_[1].g, p.seed, (uint64_t)k * nb, 114, 0, -1, nb, stream);
+          prolong_from<double>(0, xc, x, nb, 0.0);
+        }
+        record<double>(x, nb);
+      }
+    } else {
+      for (int k = 0; pool_n_ < pool_cap_ && k < 400; ++k) {
+        z4_noise<double>(b, levels_[0].g, p.seed, (uint64_t)k * nb, 113, 0, -1, nb, stream);
+        solve(0, b, x, nb);
+      }
     }
   } catch (...) {
     recording_ = false;
     sp_.smoother = saved;
+    sp_.learned_guess = saved_guess;
     throw;
   }
   recording_ = false;
   sp_.smoother = saved;
+  sp_.learned_guess = saved_guess;
   drop_graphs();
   const int P = pool_n_;
   if (P < p.batch) throw Error(MGMLMC_ERR_STATE, "too few training pairs collected");

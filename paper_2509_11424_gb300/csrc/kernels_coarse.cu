@@ -372,6 +372,140 @@ __global__ void stencil_bf16_kernel(const float2 *__restrict__ AT32, __nv_bfloat
 }
 
 
+// ---- streaming BF16 coarse stencil for 32 dofs per site and up to 8
+// right-hand sides: one warp per coarse site, lane i forming row i.
+//
+// The blocks are stored row-chunked, AS[X][d][c][i][q] = A(X, d)[i][4c + q]
+// as BF16 pairs (real part in the low half), so lane i's four entries of a
+// chunk are one 16-byte load and a warp's load is 512 contiguous bytes: the
+// blocks stream from HBM straight into registers, with no shared-memory
+// staging and no barrier.  A warp walks its items (site, direction) in
+// order and loads item t + 1 (eight chunks and the neighbour's vector
+// entries) while it computes item t.  The neighbour's 32 entries reach every
+// lane through a per-warp shared-memory buffer (two buffers, one __syncwarp
+// per item), packed as right-hand-side pairs (re_a, re_b, im_a, im_b) so
+// that one broadcast load feeds four paired .f32x2 FMAs.
+//
+// Per direction each lane accumulates over j in order, from zero, with the
+// same fused multiply-adds as cfma; the nine direction sums are added in
+// direction order.  This is the order of stencil_pipe_kernel on the same
+// BF16 values, so the two give identical results.
+// neighbour of site X in direction d (Geom::neighbor without a local
+// coordinate array: selects instead of a dynamically indexed one)
+__device__ __forceinline__ int stream_neighbor(const Geom &g, int X, int d) {
+  if (d == 0) return X;
+  const int mu = (d - 1) >> 1;
+  const int L0 = g.L[0], L1 = g.L[1], L2 = g.L[2], L3 = g.L[3];
+  int s = X;
+  const int x0 = s % L0;
+  s /= L0;
+  const int x1 = s % L1;
+  s /= L1;
+  const int x2 = s % L2, x3 = s / L2;
+  const int c = mu == 0 ? x0 : mu == 1 ? x1 : mu == 2 ? x2 : x3;
+  const int ext = mu == 0 ? L0 : mu == 1 ? L1 : mu == 2 ? L2 : L3;
+  const int stride = mu == 0 ? 1 : mu == 1 ? L0 : mu == 2 ? L0 * L1 : L0 * L1 * L2;
+  if (d & 1) return c + 1 == ext ? X - c * stride : X + stride;
+  return c == 0 ? X + (ext - 1) * stride : X - stride;
+}
+
+template <int RP>
+__device__ __forceinline__ void stream_load(const uint4 *__restrict__ AS, const float2 *__restrict__ in, int64_t n,
+                                            const Geom &g, int X, int d, int nrhs, int lane, uint4 (&a)[8],
+                                            float2 (&xv)[2 * RP]) {
+  const uint4 *src = AS + ((int64_t)X * 9 + d) * 256 + lane;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) a[c] = __ldg(src + c * 32);
+  const int nb = stream_neighbor(g, X, d);
+#pragma unroll
+  for (int r = 0; r < 2 * RP; ++r)
+    xv[r] = r < nrhs ? __ldg(in + (int64_t)r * n + (int64_t)nb * 32 + lane) : make_float2(0.f, 0.f);
+}
+
+template <int RP>
+__global__ void __launch_bounds__(256, 2) stencil_stream_kernel(const float2 *__restrict__ in,
+                                                                float2 *__restrict__ out,
+                                                                const uint4 *__restrict__ AS, Geom g, int nrhs) {
+  __shared__ __align__(16) float4 xbuf[8][2][32 * RP];  // per warp: two buffers [j][rhs pair]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t n = g.n();
+  const int gw = (int)blockIdx.x * 8 + w, nw = (int)gridDim.x * 8;
+  const int nsites = gw < g.V ? (g.V - 1 - gw) / nw + 1 : 0;
+  const int items = nsites * 9;
+  if (items == 0) return;
+  uint4 a[8];
+  float2 xv[2 * RP];
+  stream_load<RP>(AS, in, n, g, gw, 0, nrhs, lane, a, xv);
+  P2 totR[RP], totI[RP];
+#pragma unroll
+  for (int rp = 0; rp < RP; ++rp) totR[rp] = totI[rp] = p2(0.f, 0.f);
+  for (int t = 0; t < items; ++t) {
+    const int d = t % 9;
+    const int X = gw + (t / 9) * nw;
+    float4 *xs = xbuf[w][t & 1];
+#pragma unroll
+    for (int rp = 0; rp < RP; ++rp)
+      xs[lane * RP + rp] = make_float4(xv[2 * rp].x, xv[2 * rp + 1].x, xv[2 * rp].y, xv[2 * rp + 1].y);
+    __syncwarp();
+    uint4 ac[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) ac[c] = a[c];
+    if (t + 1 < items) {
+      const int t1 = t + 1;
+      stream_load<RP>(AS, in, n, g, gw + (t1 / 9) * nw, t1 % 9, nrhs, lane, a, xv);
+    }
+    P2 accR[RP], accI[RP];
+#pragma unroll
+    for (int rp = 0; rp < RP; ++rp) accR[rp] = accI[rp] = p2(0.f, 0.f);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const unsigned wd[4] = {ac[c].x, ac[c].y, ac[c].z, ac[c].w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float ar = __uint_as_float(wd[q] << 16), ai = __uint_as_float(wd[q] & 0xffff0000u);
+        const P2 AX = p2(ar, ar), NAY = p2(-ai, -ai), AY = p2(ai, ai);
+        const float4 *xj = xs + (4 * c + q) * RP;
+#pragma unroll
+        for (int rp = 0; rp < RP; ++rp) {
+          const float4 x4 = xj[rp];
+          const P2 XR = p2(x4.x, x4.y), XI = p2(x4.z, x4.w);
+          // cfma: re += ar xr, re += -ai xi; im += ar xi, im += ai xr
+          accR[rp] = p2fma(AX, XR, accR[rp]);
+          accR[rp] = p2fma(NAY, XI, accR[rp]);
+          accI[rp] = p2fma(AX, XI, accI[rp]);
+          accI[rp] = p2fma(AY, XR, accI[rp]);
+        }
+      }
+    }
+#pragma unroll
+    for (int rp = 0; rp < RP; ++rp) {
+      totR[rp] = d == 0 ? accR[rp] : p2add(totR[rp], accR[rp]);
+      totI[rp] = d == 0 ? accI[rp] : p2add(totI[rp], accI[rp]);
+    }
+    if (d == 8) {
+#pragma unroll
+      for (int rp = 0; rp < RP; ++rp) {
+        const float2 re = p2split(totR[rp]), im = p2split(totI[rp]);
+        if (2 * rp < nrhs) out[(int64_t)(2 * rp) * n + (int64_t)X * 32 + lane] = make_float2(re.x, im.x);
+        if (2 * rp + 1 < nrhs) out[(int64_t)(2 * rp + 1) * n + (int64_t)X * 32 + lane] = make_float2(re.y, im.y);
+      }
+    }
+  }
+}
+
+// AS[blk][c][i][q] = AT32[blk][4c + q][i] as a BF16 pair (round to nearest),
+// blk = 9 X + d
+__global__ void stencil_stream_layout_kernel(const float2 *__restrict__ AT32, __nv_bfloat162 *__restrict__ AS,
+                                             int64_t total) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t blk = e >> 10;
+    const int w = (int)(e & 1023);
+    const int q = w & 3, i = (w >> 2) & 31, c = w >> 7;
+    AS[e] = __float22bfloat162_rn(AT32[(blk << 10) + (4 * c + q) * 32 + i]);
+  }
+}
+
 template <typename S, int RG>
 void launch_pipe(const float2 *in, float2 *out, const S *AT, Geom g, int nrhs, int *err, cudaStream_t s) {
   const size_t sm = (size_t)2 * 9 * 32 * 32 * sizeof(S) + (size_t)2 * 9 * RG * 32 * sizeof(float2);
@@ -787,6 +921,26 @@ void stencil_apply_pipe(const float2 *in, float2 *out, const void *AT, bool bf16
     if (nrhs <= 4) launch_pipe<float2, 4>(in, out, (const float2 *)AT, g, nrhs, err, s);
     else launch_pipe<float2, 8>(in, out, (const float2 *)AT, g, nrhs, err, s);
   }
+}
+
+void stencil_apply_stream(const float2 *in, float2 *out, const void *AS, Geom g, int nrhs, cudaStream_t s) {
+  if (!stencil_pipe_supported(g) || nrhs > 8 || nrhs < 1)
+    throw Error(1, "streaming stencil: 32 dofs per site and 1 .. 8 right-hand sides");
+  if ((((uintptr_t)in | (uintptr_t)out | (uintptr_t)AS) & 15) != 0)
+    throw Error(1, "streaming stencil: operands must be 16-byte aligned");
+  // one warp per site, eight per block, at most two resident blocks per SM
+  // worth of warps: each warp walks its share of the sites
+  const int grid = (int)std::min<int64_t>((g.V + 7) / 8, (int64_t)sm_count() * 2);
+  const uint4 *a = static_cast<const uint4 *>(AS);
+  if (nrhs <= 2) stencil_stream_kernel<1><<<grid, 256, 0, s>>>(in, out, a, g, nrhs);
+  else if (nrhs <= 4) stencil_stream_kernel<2><<<grid, 256, 0, s>>>(in, out, a, g, nrhs);
+  else stencil_stream_kernel<4><<<grid, 256, 0, s>>>(in, out, a, g, nrhs);
+  MG_LAUNCH_CHECK();
+}
+
+void stencil_to_stream(const float2 *AT32, void *AS, int64_t count, cudaStream_t s) {
+  stencil_stream_layout_kernel<<<grid_for(count), 256, 0, s>>>(AT32, (__nv_bfloat162 *)AS, count);
+  MG_LAUNCH_CHECK();
 }
 
 void stencil_to_bf16(const float2 *AT32, void *ATB, int64_t count, cudaStream_t s) {

@@ -461,44 +461,8 @@ __global__ void __launch_bounds__(2 * B0 * B1 * B2 * B3, 1)
   store_fine_site<float>(rv, s, V, rh);
 }
 
-// ---- paired FP32 arithmetic: the same component of two right-hand sides in
-// the two lanes of a 64-bit register pair, computed by the packed .f32x2
-// instructions (one instruction for both; each lane rounds exactly as the
-// scalar instruction would, so the sums below equal the scalar kernel's)
-struct P2 {
-  unsigned long long v;
-};
-__device__ __forceinline__ P2 p2(float lo, float hi) {
-  P2 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ float2 p2split(P2 a) {
-  float2 r;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a.v));
-  return r;
-}
-__device__ __forceinline__ P2 p2fma(P2 a, P2 b, P2 c) {
-  P2 r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
-  return r;
-}
-__device__ __forceinline__ P2 p2add(P2 a, P2 b) {
-  P2 r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-  return r;
-}
-__device__ __forceinline__ P2 p2sub(P2 a, P2 b) {
-  P2 r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-  return r;
-}
-__device__ __forceinline__ P2 p2mul(P2 a, P2 b) {
-  P2 r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-  return r;
-}
-__device__ __forceinline__ P2 p2neg(P2 a) { return p2mul(a, p2(-1.f, -1.f)); }
+// ---- paired FP32 arithmetic (P2 and the p2* helpers of common.cuh): the
+// same component of two right-hand sides in the two lanes of a register pair
 
 // the spin-projection and reconstruction rules of sBl / sBh as data: the
 // result's real (imaginary) part is sign * (real or imaginary part) of one

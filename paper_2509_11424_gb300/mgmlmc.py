@@ -49,7 +49,8 @@ class SolverParams(ctypes.Structure):
                 ('coarse_restart', ctypes.c_int),
                 ('post_smoothing_only', ctypes.c_int),
                 ('gram_schmidt_passes', ctypes.c_int),
-                ('fine_batch', ctypes.c_int)]
+                ('fine_batch', ctypes.c_int),
+                ('learned_guess', ctypes.c_int)]
 
 
 class EstParams(ctypes.Structure):
@@ -75,7 +76,8 @@ class TermResult(ctypes.Structure):
 
 class TrainParams(ctypes.Structure):
     _fields_ = [('channels', ctypes.c_int), ('steps', ctypes.c_int), ('batch', ctypes.c_int),
-                ('pool', ctypes.c_int), ('lr', ctypes.c_double), ('seed', ctypes.c_uint64)]
+                ('pool', ctypes.c_int), ('lr', ctypes.c_double), ('seed', ctypes.c_uint64),
+                ('source', ctypes.c_int)]
 
 
 class TrainResult(ctypes.Structure):
@@ -227,10 +229,10 @@ SMOOTHER_MR, SMOOTHER_SAP, SMOOTHER_LEARNED, SMOOTHER_NET = 0, 1, 2, 3
 def solver_params(tol=1e-12, max_iter=2000, restart=16, smoother_steps=4, coarse_iters=8,
                   precision=FP64, inner_tol=1e-6, smoother=SMOOTHER_MR, sap_iters=4,
                   coarse_smoother_steps=4, coarse_restart=0, post_smoothing_only=0, gram_schmidt_passes=0,
-                  fine_batch=0):
+                  fine_batch=0, learned_guess=0):
     return SolverParams(tol, max_iter, restart, smoother_steps, coarse_iters, precision, inner_tol,
                         smoother, sap_iters, coarse_smoother_steps, coarse_restart, post_smoothing_only,
-                        gram_schmidt_passes, fine_batch)
+                        gram_schmidt_passes, fine_batch, learned_guess)
 
 
 def mgmlmc_set_solver(ctx, params=None, **kw):
@@ -474,8 +476,8 @@ def mgmlmc_learned_loss_grad(ctx, r, nrhs, grad_host):
     return loss.value
 
 
-def mgmlmc_learned_train(ctx, channels=16, steps=200, batch=8, pool=2000, lr=1e-3, seed=5000):
-    p = TrainParams(channels, steps, batch, pool, lr, seed)
+def mgmlmc_learned_train(ctx, channels=16, steps=200, batch=8, pool=2000, lr=1e-3, seed=5000, source=0):
+    p = TrainParams(channels, steps, batch, pool, lr, seed, source)
     out = TrainResult()
     _check(ctx, lib().mgmlmc_learned_train(ctx, ctypes.byref(p), ctypes.byref(out)))
     return out.as_dict()

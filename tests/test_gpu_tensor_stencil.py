@@ -120,19 +120,21 @@ def test_fp32_stencil_pipelined_matches_oracle_and_staged_kernel(tc, nrhs):
         assert rel(got[r], A1 @ x32[r]) < 1e-5
 
 
+@pytest.mark.parametrize('variant', [3, 6])
 @pytest.mark.parametrize('nrhs', [1, 4, 7])
-def test_bf16_stencil_matches_oracle(tc, nrhs):
-    """Variant 3: the blocks stored as BF16 pairs (round to nearest, relative
-    error <= 2^-9 per real entry), FP32 products and sums.  Bound per output
-    entry, real and imaginary parts: 2^-9 sum_k |a_k| |b_k| from the storage
-    rounding, plus FP32 accumulation (300 x 2^-24 of the same sum)."""
+def test_bf16_stencil_matches_oracle(tc, variant, nrhs):
+    """Variants 3 and 6: the blocks stored as BF16 pairs (round to nearest,
+    relative error <= 2^-9 per real entry), FP32 products and sums (6 streams
+    them with one warp per site).  Bound per output entry, real and imaginary
+    parts: 2^-9 sum_k |a_k| |b_k| from the storage rounding, plus FP32
+    accumulation (300 x 2^-24 of the same sum)."""
     M = tc.M
     A1 = tc.hier.matrix(1).tocsr()
     n1 = A1.shape[0]
     x = synth.complex_normal((nrhs, n1), 700 + nrhs)
     x32 = x.astype(np.complex64).astype(np.complex128)
     y = torch.empty((nrhs, n1), dtype=torch.complex64, device='cuda')
-    M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, 3)
+    M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, variant)
     try:
         M.mgmlmc_apply(tc.ctx, M.OP_D, 1, M.FP32, dev(x, torch.complex64), y, nrhs)
         got = host(y).astype(np.complex128)
@@ -145,6 +147,48 @@ def test_bf16_stencil_matches_oracle(tc, nrhs):
         assert np.all(np.abs(got[r].real - want[r].real) <= bnd), r
         assert np.all(np.abs(got[r].imag - want[r].imag) <= bnd), r
         assert np.max(np.abs(got[r] - want[r])) > 0  # it is not the FP32 result
+
+
+@pytest.fixture(scope='module')
+def walk():
+    """16^3 x 32 lattice with 2^4 aggregates twice (16 test vectors each,
+    device gauge field, no setup iterations): level 1 is 8^3 x 16 (8192
+    sites) and level 2 4^3 x 8 (512 sites), both with 32 dofs per site.  At
+    level 1 every warp of the streaming kernel walks several sites, so the
+    prefetch of the next (site, direction) item crosses site boundaries."""
+    from gpu_util import require_lib
+    M = require_lib()
+    ctx = M.mgmlmc_create((16, 16, 16, 32), torch.cuda.current_stream())
+    M.mgmlmc_gen_gauge(ctx, 0.4, 91)
+    M.mgmlmc_set_mass(ctx, -0.3)
+    M.mgmlmc_build_hierarchy(ctx, M.mg_params([(2, 2, 2, 2), (2, 2, 2, 2)], [16, 16], setup_rounds=0, seed=92))
+    yield M, ctx
+    M.mgmlmc_destroy(ctx)
+
+
+@pytest.mark.parametrize('level', [1, 2])
+@pytest.mark.parametrize('nrhs', [1, 2, 3, 4, 5, 8])
+def test_streaming_stencil_identical_to_pipelined(walk, level, nrhs):
+    """Variant 6 (one warp per site, row-chunked BF16 blocks streamed into
+    registers, packed FP32 pair arithmetic) bit-identical to variant 3 (the
+    pipelined kernel on the same BF16 values): the same fused multiply-adds
+    per direction in the same order, the nine direction sums added in the
+    same order.  Odd counts leave the last packed lane unused."""
+    M, ctx = walk
+    _, dof, n = M.mgmlmc_level_info(ctx, level)
+    assert dof == 32
+    xd = dev(synth.complex_normal((nrhs, n), 900 + 10 * level + nrhs), torch.complex64)
+    outs = []
+    try:
+        for v in (3, 6):
+            M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_STENCIL_FP32, v)
+            y = torch.full((nrhs, n), float('nan'), dtype=torch.complex64, device='cuda')
+            M.mgmlmc_apply(ctx, M.OP_D, level, M.FP32, xd, y, nrhs)
+            outs.append(y)
+    finally:
+        M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_STENCIL_FP32, 0)
+    assert torch.equal(outs[0], outs[1])
+    assert bool(torch.isfinite(outs[1]).all()) and float(outs[1].abs().max()) > 0
 
 
 @pytest.mark.parametrize('gs', [2, 1])
@@ -161,10 +205,10 @@ def test_solve_with_preconditioner_variants(tc, gs):
     M.mgmlmc_set_solver(tc.ctx, precision=M.FP32, restart=8, coarse_restart=16, smoother=1, smoother_steps=1,
                         coarse_iters=4, inner_tol=1e-6, gram_schmidt_passes=gs, post_smoothing_only=gs % 2)
     try:
-        for v in (1, 3, 4, 5, -2):
+        for v in (1, 3, 4, 5, 6, -2):
             M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, v)
             # with the BF16 stencils, BF16-stored P in the preconditioner too
-            M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_TRANSFER_FP32, 1 if v in (3, 4, 5) else 0)
+            M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_TRANSFER_FP32, 1 if v in (3, 4, 5, 6) else 0)
             x = torch.empty((3, n), dtype=torch.complex128, device='cuda')
             M.mgmlmc_apply(tc.ctx, M.OP_SOLVE, 0, M.FP64, dev(b), x, 3)
             xs = host(x)
