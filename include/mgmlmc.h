@@ -103,9 +103,12 @@ typedef struct {
 
 /* Level solver: FGMRES(restart) preconditioned by a multigrid K-cycle that
  * starts at the level being solved (Sec. 4: all levels to 1e-12).  With
- * MGMLMC_FP32 each inner FP32 solve of the FP64 defect correction also ends
- * when a restart cycle fails to halve its true residual (the precision floor
- * of FP32 on an ill-conditioned level); the outer loop continues from it. */
+ * MGMLMC_FP32 each inner FP32 solve of the FP64 defect correction reduces its
+ * residual by inner_tol, or by the smaller factor 2 tol / r that is left to
+ * do (r the largest relative true residual over the right-hand sides), and
+ * also ends when a restart cycle fails to halve its true residual (the
+ * precision floor of FP32 on an ill-conditioned level); the outer loop
+ * continues from it until the true FP64 residual meets tol. */
 typedef struct {
   double tol;          /* relative residual target ||b - D x|| / ||b|| */
   int max_iter;        /* cap on outer FGMRES iterations per solve */
@@ -145,7 +148,11 @@ typedef struct {
                           scaled back, as the first defect; every later defect
                           is the true FP64 residual, which alone decides
                           convergence (needs mgmlmc_learned_init or _train;
-                          any smoother).  0 (default): x0 = 0. */
+                          any smoother).  mgmlmc_estimate_trace does not use
+                          it for the fine solve of F_0, whose right-hand side
+                          P_0 x lies in the range of P_0 (the coarse-grid
+                          correction already covers it; measured, the guess
+                          cost iterations there).  0 (default): x0 = 0. */
 } mgmlmc_solver_params;
 
 #define MGMLMC_SMOOTHER_MR 0
@@ -470,11 +477,10 @@ typedef struct {
                      solves that produce the pairs */
   int source;     /* 0: the residuals the SAP post-smoother leaves during solves
                      of Z4 right-hand sides (the network as a smoothing step);
-                     1: the right-hand sides of the estimator's fine-level
-                     solves, half projected Z4 noise (I - P_0 P_0^H) x (term
-                     O_0), half prolonged coarse Z4 noise P_0 x (term F_0),
-                     for the network as the initial guess (learned_guess);
-                     no solves are needed to collect them */
+                     1: the right-hand sides of the estimator's O_0
+                     solves, projected Z4 noise (I - P_0 P_0^H) x, for the
+                     network as the initial guess (learned_guess); no solves
+                     are needed to collect them */
 } mgmlmc_train_params;
 
 typedef struct {
@@ -564,10 +570,12 @@ mgmlmc_status mgmlmc_profile_stats(mgmlmc_ctx *ctx, int kernel_class, int64_t *l
  * warp per coarse site streaming its blocks from memory in 16-byte row
  * chunks (a second BF16 copy of the blocks in that layout; results
  * identical to variant 3; up to 8 right-hand sides at 32 dofs per site,
- * variant 0 otherwise).  Variant 0 runs up to 8 right-hand sides at 32 dofs per site in
+ * variant 0 otherwise); 7 = variant 6 with one thread block per coarse site
+ * and a warp per direction (more parallel work on coarse lattices with few
+ * sites; identical results).  Variant 0 runs up to 8 right-hand sides at 32 dofs per site in
  * a pipelined kernel (persistent blocks, a two-stage ring of bulk copies
  * over sites) with results identical to the one-site-per-block kernels.
- * -2 = autotune among 0, 1, 3, 4, 5 and 6 per (level, nrhs) on the first call
+ * -2 = autotune among 0, 1, 3, 4, 5, 6 and 7 per (level, nrhs) on the first call
  * outside graph capture (opt-in,
  * since the choice changes the rounding).  Inside a solve the variant applies
  * to the multigrid preconditioner only (smoothers, coarse-grid corrections);

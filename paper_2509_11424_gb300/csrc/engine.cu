@@ -425,7 +425,7 @@ int Engine::dslash_variant(int nrhs) const {
   return it == dslash_tuned_.end() ? -2 : it->second;
 }
 
-int Engine::stencil_variants() { return 7; }
+int Engine::stencil_variants() { return 8; }
 
 void Engine::set_transfer_variant(int v) {
   if (v < 0 || v > 1) throw Error(MGMLMC_ERR_ARG, "transfer variant out of range");
@@ -456,7 +456,8 @@ int Engine::stencil_variant(int l, int nrhs) const {
 // one-site-per-CTA kernels); 1, 2: tensor cores (TF32); 3: BF16-stored
 // blocks, FP32 arithmetic (pipelined kernel, up to 8 right-hand sides);
 // 4: tensor cores with BF16 operands; 5: 4 as a persistent pipelined kernel;
-// 6: 3's sums with one warp per site streaming the row-chunked blocks
+// 6: 3's sums with one warp per site streaming the row-chunked blocks;
+// 7: 6 with one thread block per site (a warp per direction)
 void Engine::stencil_run(int l, int v, const float2 *in, float2 *out, int nrhs) {
   const Level &L = levels_[l];
   const bool pipe = stencil_pipe_supported(L.g) && nrhs <= 8;
@@ -464,7 +465,7 @@ void Engine::stencil_run(int l, int v, const float2 *in, float2 *out, int nrhs) 
   else if (v == 4 && L.ATCB) stencil_apply_tc(in, out, L.ATCB, L.g, nrhs, flag_dev_ + 1, 2, stream);
   else if (v == 5 && L.ATCB) stencil_apply_tc(in, out, L.ATCB, L.g, nrhs, flag_dev_ + 1, 3, stream);
   else if (v == 3 && L.ATB16 && pipe) stencil_apply_pipe(in, out, L.ATB16, true, L.g, nrhs, flag_dev_ + 1, stream);
-  else if (v == 6 && L.ATS && nrhs <= 8) stencil_apply_stream(in, out, L.ATS, L.g, nrhs, stream);
+  else if ((v == 6 || v == 7) && L.ATS && nrhs <= 8) stencil_apply_stream(in, out, L.ATS, L.g, nrhs, v == 7, stream);
   else if (pipe) stencil_apply_pipe(in, out, L.AT32, false, L.g, nrhs, flag_dev_ + 1, stream);
   else stencil_apply<float>(in, out, L.AT32, L.g, nrhs, flag_dev_ + 1, stream);
 }
@@ -485,9 +486,9 @@ int Engine::stencil_pick(int l, int nrhs, const float2 *in, float2 *out) {
   int pick = 0;
   float best = 1e30f;
   // variant 2 is variant 1 with twice the tensor work: not a candidate
-  for (int v : {0, 1, 3, 4, 5, 6}) {
+  for (int v : {0, 1, 3, 4, 5, 6, 7}) {
     if (v == 3 && !(levels_[l].ATB16 && nrhs <= 8)) continue;
-    if (v == 6 && !(levels_[l].ATS && nrhs <= 8)) continue;
+    if ((v == 6 || v == 7) && !(levels_[l].ATS && nrhs <= 8)) continue;
     stencil_run(l, v, in, out, nrhs);
     MG_CUDA(cudaEventRecord(ev.a, stream));
     for (int rep = 0; rep < 3; ++rep) stencil_run(l, v, in, out, nrhs);
@@ -558,7 +559,7 @@ template <typename T> void Engine::apply_D(int l, const C<T> *in, C<T> *out, int
     } else {
       const int v = stencil_pick(l, nrhs, in, out);
       stencil_run(l, v, in, out, nrhs);
-      if ((v == 3 && L.ATB16 && nrhs <= 8) || (v == 6 && L.ATS && nrhs <= 8) || ((v == 4 || v == 5) && L.ATCB))
+      if ((v == 3 && L.ATB16 && nrhs <= 8) || ((v == 6 || v == 7) && L.ATS && nrhs <= 8) || ((v == 4 || v == 5) && L.ATCB))
         bs = 4.0;
     }
     const double m = L.g.dof;
@@ -969,7 +970,7 @@ SolveInfo Engine::solve_mixed(int l, const double2 *b, double2 *x, int nrhs) {
   for (int q = 0; q < nrhs; ++q) bn[q] = std::sqrt(std::max(h[q].x, 0.0));
   MG_CUDA(cudaMemsetAsync(x, 0, sizeof(double2) * vs, stream));
   const double2 *r = b;  // residual of x = 0
-  if (l == 0 && sp_.learned_guess) {
+  if (l == 0 && sp_.learned_guess && !guess_off_) {
     // the network's guess: with c = b / ||b|| (FP32 fine layout), e = N(c)
     // and q = D e, x0 = ||b|| alpha e and c - alpha q is the first defect
     // (its FP32 rounding is corrected by the true FP64 residual after the
@@ -1013,8 +1014,11 @@ SolveInfo Engine::solve_mixed(int l, const double2 *b, double2 *x, int nrhs) {
     MG_LAUNCH_CHECK();
     if (l == 0) relayout<float, double>(r, r32, inv, levels_[0].g.V, nrhs, true, stream);
     else convert_scale<float, double>(r, r32, inv, n, nrhs, stream);
-    SolveInfo in = fgmres<float>(l, r32, e32, nrhs, sp_.inner_tol, sp_.max_iter - total, restart_of(l),
-                                 true, false, true);
+    // the inner solve reduces its residual by inner_tol, or by only what is
+    // left to reach tol (with a factor 2 of margin) when that is less: the
+    // least converged right-hand side sets it, so it suffices for all
+    const double itol = std::max(sp_.inner_tol, std::min(0.5, 0.5 * sp_.tol / std::max(worst, 1e-300)));
+    SolveInfo in = fgmres<float>(l, r32, e32, nrhs, itol, sp_.max_iter - total, restart_of(l), true, false, true);
     total += in.iters;
     if (l == 0) relayout<double, float>(e32, t, rn, levels_[0].g.V, nrhs, false, stream);
     else convert_scale<double, float>(e32, t, rn, n, nrhs, stream);
@@ -1386,7 +1390,17 @@ void Engine::estimate_trace(const mgmlmc_est_params &p, std::vector<TermAcc> &ou
         double2 *z1 = ws<double>("estz", l, (size_t)nb * n), *z2 = ws<double>("estzc", l + 1, (size_t)nb * nc);
         noise(l + 1, p.seed, s0, MGMLMC_TERM_F + l, 0, -1, x, nb);
         prolong_from<double>(l, x, y, nb, 0.0);
-        SolveInfo s1 = solve(l, y, z1, nb);
+        // y = P x lies in the range of P, which the coarse-grid correction
+        // covers: the learned guess is not used for it
+        guess_off_ = true;
+        SolveInfo s1;
+        try {
+          s1 = solve(l, y, z1, nb);
+        } catch (...) {
+          guess_off_ = false;
+          throw;
+        }
+        guess_off_ = false;
         SolveInfo s2 = solve(l + 1, x, z2, nb);
         acc.iters_sum += s1.iters + s2.iters;
         acc.solves += 2;

@@ -189,10 +189,11 @@ class Engine {
   // FP32 coarse stencil per rhs count: 0 = FP32 CUDA cores, 1 = tcgen05
   // TF32 with M = 64 MMAs, 2 = the same with M = 128 MMAs, 3 = BF16-stored
   // blocks with FP32 arithmetic, 4 = tcgen05 with BF16 operands, -2 = the
-  // fastest of 0, 1, 3, 4, 5, 6 on the first call outside capture; 5 =
+  // fastest of 0, 1, 3, 4, 5, 6, 7 on the first call outside capture; 5 =
   // variant 4 as a persistent pipelined kernel (up to 32 right-hand sides);
   // 6 = variant 3's arithmetic with one warp per site streaming the blocks
-  // (up to 8 right-hand sides; identical results to 3)
+  // (up to 8 right-hand sides; identical results to 3); 7 = 6 with one
+  // thread block per site, a warp per direction (small coarse lattices)
   void set_stencil_variant(int v);
   int stencil_variant(int l, int nrhs) const;
   static int stencil_variants();
@@ -249,6 +250,7 @@ class Engine {
   bool have_gauge_ = false;
   bool ready_ = false;
   mgmlmc_solver_params sp_{};
+  bool guess_off_ = false;  // the learned guess skips the solve in progress (F_l fine solves)
   std::vector<Level> levels_;
   std::map<int, std::vector<double>> imported_host_;  // level -> ntv * n complex
   mgmlmc_mg_params mgp_{};  // parameters of the last successful build

@@ -211,18 +211,11 @@ void Engine::net_train(const mgmlmc_train_params &p, mgmlmc_train_result &out) {
   recording_ = true;
   try {
     if (p.source == 1) {
-      // the right-hand sides of the estimator's fine-level solves, O_0 and
-      // F_0 alternately: (I - P P^H) x for fine Z4 noise x, P x for coarse
-      // Z4 noise x (noise streams 113 and 114 of the training seed)
-      double2 *xc = ws<double>("trxc", 1, (size_t)nb * levels_[1].g.n());
+      // the right-hand sides of the estimator's O_0 solves, (I - P P^H) x
+      // for fine Z4 noise x (noise stream 113 of the training seed)
       for (int k = 0; pool_n_ < pool_cap_ && k < 400; ++k) {
-        if (k % 2 == 0) {
-          z4_noise<double>(b, levels_[0].g, p.seed, (uint64_t)k * nb, 113, 0, -1, nb, stream);
-          project_out<double>(0, b, x, nb);
-        } else {
-          z4_noise<double>(xc, levels_[1].g, p.seed, (uint64_t)k * nb, 114, 0, -1, nb, stream);
-          prolong_from<double>(0, xc, x, nb, 0.0);
-        }
+        z4_noise<double>(b, levels_[0].g, p.seed, (uint64_t)k * nb, 113, 0, -1, nb, stream);
+        project_out<double>(0, b, x, nb);
         record<double>(x, nb);
       }
     } else {

@@ -149,10 +149,12 @@ void stencil_apply_pipe(const float2 *in, float2 *out, const void *AT, bool bf16
                         cudaStream_t s);
 void stencil_to_bf16(const float2 *AT32, void *ATB, int64_t count, cudaStream_t s);
 // Streaming BF16 coarse stencil for 32 dofs per site and 1 .. 8 right-hand
-// sides: one warp per site, the blocks in the row-chunked BF16 layout that
+// sides: one warp per site (per_site: one thread block per site, a warp per
+// direction), the blocks in the row-chunked BF16 layout that
 // stencil_to_stream builds from the transposed FP32 blocks (count complex
 // entries); the same results as the BF16 pipelined kernel.
-void stencil_apply_stream(const float2 *in, float2 *out, const void *AS, Geom g, int nrhs, cudaStream_t s);
+void stencil_apply_stream(const float2 *in, float2 *out, const void *AS, Geom g, int nrhs, bool per_site,
+                          cudaStream_t s);
 void stencil_to_stream(const float2 *AT32, void *AS, int64_t count, cudaStream_t s);
 // AT = blockwise transpose of the canonical A[X][d][i][j] (nblocks = 9 V)
 template <typename To>

@@ -422,6 +422,37 @@ __device__ __forceinline__ void stream_load(const uint4 *__restrict__ AS, const 
     xv[r] = r < nrhs ? __ldg(in + (int64_t)r * n + (int64_t)nb * 32 + lane) : make_float2(0.f, 0.f);
 }
 
+// one item (site, direction) of a lane: row `lane` of the block, whose
+// four-entry chunks are ac[c], times the neighbour's entries xs[j][rhs pair];
+// per right-hand side the fused multiply-adds of cfma, over j in order, from
+// zero
+template <int RP>
+__device__ __forceinline__ void stream_item(const uint4 (&ac)[8], const float4 *xs, P2 (&accR)[RP],
+                                            P2 (&accI)[RP]) {
+#pragma unroll
+  for (int rp = 0; rp < RP; ++rp) accR[rp] = accI[rp] = p2(0.f, 0.f);
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const unsigned wd[4] = {ac[c].x, ac[c].y, ac[c].z, ac[c].w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float ar = __uint_as_float(wd[q] << 16), ai = __uint_as_float(wd[q] & 0xffff0000u);
+      const P2 AX = p2(ar, ar), NAY = p2(-ai, -ai), AY = p2(ai, ai);
+      const float4 *xj = xs + (4 * c + q) * RP;
+#pragma unroll
+      for (int rp = 0; rp < RP; ++rp) {
+        const float4 x4 = xj[rp];
+        const P2 XR = p2(x4.x, x4.y), XI = p2(x4.z, x4.w);
+        // cfma: re += ar xr, re += -ai xi; im += ar xi, im += ai xr
+        accR[rp] = p2fma(AX, XR, accR[rp]);
+        accR[rp] = p2fma(NAY, XI, accR[rp]);
+        accI[rp] = p2fma(AX, XI, accI[rp]);
+        accI[rp] = p2fma(AY, XR, accI[rp]);
+      }
+    }
+  }
+}
+
 template <int RP>
 __global__ void __launch_bounds__(256, 2) stencil_stream_kernel(const float2 *__restrict__ in,
                                                                 float2 *__restrict__ out,
@@ -455,28 +486,7 @@ __global__ void __launch_bounds__(256, 2) stencil_stream_kernel(const float2 *__
       stream_load<RP>(AS, in, n, g, gw + (t1 / 9) * nw, t1 % 9, nrhs, lane, a, xv);
     }
     P2 accR[RP], accI[RP];
-#pragma unroll
-    for (int rp = 0; rp < RP; ++rp) accR[rp] = accI[rp] = p2(0.f, 0.f);
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-      const unsigned wd[4] = {ac[c].x, ac[c].y, ac[c].z, ac[c].w};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float ar = __uint_as_float(wd[q] << 16), ai = __uint_as_float(wd[q] & 0xffff0000u);
-        const P2 AX = p2(ar, ar), NAY = p2(-ai, -ai), AY = p2(ai, ai);
-        const float4 *xj = xs + (4 * c + q) * RP;
-#pragma unroll
-        for (int rp = 0; rp < RP; ++rp) {
-          const float4 x4 = xj[rp];
-          const P2 XR = p2(x4.x, x4.y), XI = p2(x4.z, x4.w);
-          // cfma: re += ar xr, re += -ai xi; im += ar xi, im += ai xr
-          accR[rp] = p2fma(AX, XR, accR[rp]);
-          accR[rp] = p2fma(NAY, XI, accR[rp]);
-          accI[rp] = p2fma(AX, XI, accI[rp]);
-          accI[rp] = p2fma(AY, XR, accI[rp]);
-        }
-      }
-    }
+    stream_item<RP>(ac, xs, accR, accI);
 #pragma unroll
     for (int rp = 0; rp < RP; ++rp) {
       totR[rp] = d == 0 ? accR[rp] : p2add(totR[rp], accR[rp]);
@@ -490,6 +500,53 @@ __global__ void __launch_bounds__(256, 2) stencil_stream_kernel(const float2 *__
         if (2 * rp + 1 < nrhs) out[(int64_t)(2 * rp + 1) * n + (int64_t)X * 32 + lane] = make_float2(re.y, im.y);
       }
     }
+  }
+}
+
+// The same items with one thread block per coarse site and one warp per
+// direction (for coarse lattices with fewer sites than the walking kernel
+// has warps): warp d forms direction d's partial rows, warp 0 adds the nine
+// partials in direction order.  Identical results to stencil_stream_kernel.
+template <int RP>
+__global__ void __launch_bounds__(288) stencil_stream_site_kernel(const float2 *__restrict__ in,
+                                                                 float2 *__restrict__ out,
+                                                                 const uint4 *__restrict__ AS, Geom g,
+                                                                 int nrhs) {
+  __shared__ __align__(16) float4 xbuf[9][32 * RP];
+  __shared__ __align__(16) float4 part[9][RP][32];  // (re_a, re_b, im_a, im_b) per lane
+  const int lane = threadIdx.x & 31, d = threadIdx.x >> 5;
+  const int X = blockIdx.x;
+  const int64_t n = g.n();
+  uint4 a[8];
+  float2 xv[2 * RP];
+  stream_load<RP>(AS, in, n, g, X, d, nrhs, lane, a, xv);
+  float4 *xs = xbuf[d];
+#pragma unroll
+  for (int rp = 0; rp < RP; ++rp)
+    xs[lane * RP + rp] = make_float4(xv[2 * rp].x, xv[2 * rp + 1].x, xv[2 * rp].y, xv[2 * rp + 1].y);
+  __syncwarp();
+  P2 accR[RP], accI[RP];
+  stream_item<RP>(a, xs, accR, accI);
+#pragma unroll
+  for (int rp = 0; rp < RP; ++rp) {
+    const float2 re = p2split(accR[rp]), im = p2split(accI[rp]);
+    part[d][rp][lane] = make_float4(re.x, re.y, im.x, im.y);
+  }
+  __syncthreads();
+  if (d != 0) return;
+#pragma unroll
+  for (int rp = 0; rp < RP; ++rp) {
+    float4 v = part[0][rp][lane];
+    P2 totR = p2(v.x, v.y), totI = p2(v.z, v.w);
+#pragma unroll
+    for (int dd = 1; dd < 9; ++dd) {
+      v = part[dd][rp][lane];
+      totR = p2add(totR, p2(v.x, v.y));
+      totI = p2add(totI, p2(v.z, v.w));
+    }
+    const float2 re = p2split(totR), im = p2split(totI);
+    if (2 * rp < nrhs) out[(int64_t)(2 * rp) * n + (int64_t)X * 32 + lane] = make_float2(re.x, im.x);
+    if (2 * rp + 1 < nrhs) out[(int64_t)(2 * rp + 1) * n + (int64_t)X * 32 + lane] = make_float2(re.y, im.y);
   }
 }
 
@@ -923,11 +980,20 @@ void stencil_apply_pipe(const float2 *in, float2 *out, const void *AT, bool bf16
   }
 }
 
-void stencil_apply_stream(const float2 *in, float2 *out, const void *AS, Geom g, int nrhs, cudaStream_t s) {
+void stencil_apply_stream(const float2 *in, float2 *out, const void *AS, Geom g, int nrhs, bool per_site,
+                          cudaStream_t s) {
   if (!stencil_pipe_supported(g) || nrhs > 8 || nrhs < 1)
     throw Error(1, "streaming stencil: 32 dofs per site and 1 .. 8 right-hand sides");
   if ((((uintptr_t)in | (uintptr_t)out | (uintptr_t)AS) & 15) != 0)
     throw Error(1, "streaming stencil: operands must be 16-byte aligned");
+  if (per_site) {
+    const uint4 *a = static_cast<const uint4 *>(AS);
+    if (nrhs <= 2) stencil_stream_site_kernel<1><<<g.V, 288, 0, s>>>(in, out, a, g, nrhs);
+    else if (nrhs <= 4) stencil_stream_site_kernel<2><<<g.V, 288, 0, s>>>(in, out, a, g, nrhs);
+    else stencil_stream_site_kernel<4><<<g.V, 288, 0, s>>>(in, out, a, g, nrhs);
+    MG_LAUNCH_CHECK();
+    return;
+  }
   // one warp per site, eight per block, at most two resident blocks per SM
   // worth of warps: each warp walks its share of the sites
   const int grid = (int)std::min<int64_t>((g.V + 7) / 8, (int64_t)sm_count() * 2);

@@ -110,8 +110,7 @@ def test_training_lowers_loss_and_trained_solves_converge():
 def test_learned_initial_guess():
     """The network as the initial guess of the fine-level solves (solver
     option learned_guess), trained on the right-hand sides the estimator's
-    fine solves start from (training source 1: projected Z4 noise and
-    prolonged coarse Z4 noise).  Training lowers the loss; on a projected
+    O_0 solves start from (training source 1: projected Z4 noise).  Training lowers the loss; on a projected
     right-hand side c (unit norm) the trained network's guess leaves a
     smaller residual ||c - alpha D N(c)|| (alpha residual-minimising) than
     the untrained one, i.e. what training gains; solves that start from the

@@ -163,7 +163,7 @@ def test_dslash_variant_bad_args():
     nv = M.mgmlmc_kernel_variants(M.VARIANT_DSLASH_FP32)
     ns = M.mgmlmc_kernel_variants(M.VARIANT_STENCIL_FP32)
     nsap = M.mgmlmc_kernel_variants(M.VARIANT_SAP_FP32)
-    assert nv == 7 and ns == 7 and nsap == 3
+    assert nv == 7 and ns == 8 and nsap == 3
     assert M.mgmlmc_kernel_variants(M.VARIANT_TRANSFER_FP32) == 2
     assert M.mgmlmc_kernel_variants(4) == -1
     ctx = M.mgmlmc_create((4, 4, 4, 4), torch.cuda.current_stream())

@@ -120,12 +120,12 @@ def test_fp32_stencil_pipelined_matches_oracle_and_staged_kernel(tc, nrhs):
         assert rel(got[r], A1 @ x32[r]) < 1e-5
 
 
-@pytest.mark.parametrize('variant', [3, 6])
+@pytest.mark.parametrize('variant', [3, 6, 7])
 @pytest.mark.parametrize('nrhs', [1, 4, 7])
 def test_bf16_stencil_matches_oracle(tc, variant, nrhs):
-    """Variants 3 and 6: the blocks stored as BF16 pairs (round to nearest,
-    relative error <= 2^-9 per real entry), FP32 products and sums (6 streams
-    them with one warp per site).  Bound per output entry, real and imaginary
+    """Variants 3, 6 and 7: the blocks stored as BF16 pairs (round to nearest,
+    relative error <= 2^-9 per real entry), FP32 products and sums (6 and 7
+    stream them with one warp per site or per direction).  Bound per output entry, real and imaginary
     parts: 2^-9 sum_k |a_k| |b_k| from the storage rounding, plus FP32
     accumulation (300 x 2^-24 of the same sum)."""
     M = tc.M
@@ -169,25 +169,26 @@ def walk():
 @pytest.mark.parametrize('level', [1, 2])
 @pytest.mark.parametrize('nrhs', [1, 2, 3, 4, 5, 8])
 def test_streaming_stencil_identical_to_pipelined(walk, level, nrhs):
-    """Variant 6 (one warp per site, row-chunked BF16 blocks streamed into
-    registers, packed FP32 pair arithmetic) bit-identical to variant 3 (the
-    pipelined kernel on the same BF16 values): the same fused multiply-adds
-    per direction in the same order, the nine direction sums added in the
-    same order.  Odd counts leave the last packed lane unused."""
+    """Variants 6 (one warp per site, row-chunked BF16 blocks streamed into
+    registers, packed FP32 pair arithmetic) and 7 (one thread block per site,
+    a warp per direction) bit-identical to variant 3 (the pipelined kernel on
+    the same BF16 values): the same fused multiply-adds per direction in the
+    same order, the nine direction sums added in the same order.  Odd counts
+    leave the last packed lane unused."""
     M, ctx = walk
     _, dof, n = M.mgmlmc_level_info(ctx, level)
     assert dof == 32
     xd = dev(synth.complex_normal((nrhs, n), 900 + 10 * level + nrhs), torch.complex64)
     outs = []
     try:
-        for v in (3, 6):
+        for v in (3, 6, 7):
             M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_STENCIL_FP32, v)
             y = torch.full((nrhs, n), float('nan'), dtype=torch.complex64, device='cuda')
             M.mgmlmc_apply(ctx, M.OP_D, level, M.FP32, xd, y, nrhs)
             outs.append(y)
     finally:
         M.mgmlmc_set_kernel_variant(ctx, M.VARIANT_STENCIL_FP32, 0)
-    assert torch.equal(outs[0], outs[1])
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
     assert bool(torch.isfinite(outs[1]).all()) and float(outs[1].abs().max()) > 0
 
 
@@ -205,10 +206,10 @@ def test_solve_with_preconditioner_variants(tc, gs):
     M.mgmlmc_set_solver(tc.ctx, precision=M.FP32, restart=8, coarse_restart=16, smoother=1, smoother_steps=1,
                         coarse_iters=4, inner_tol=1e-6, gram_schmidt_passes=gs, post_smoothing_only=gs % 2)
     try:
-        for v in (1, 3, 4, 5, 6, -2):
+        for v in (1, 3, 4, 5, 6, 7, -2):
             M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_STENCIL_FP32, v)
             # with the BF16 stencils, BF16-stored P in the preconditioner too
-            M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_TRANSFER_FP32, 1 if v in (3, 4, 5, 6) else 0)
+            M.mgmlmc_set_kernel_variant(tc.ctx, M.VARIANT_TRANSFER_FP32, 1 if v in (3, 4, 5, 6, 7) else 0)
             x = torch.empty((3, n), dtype=torch.complex128, device='cuda')
             M.mgmlmc_apply(tc.ctx, M.OP_SOLVE, 0, M.FP64, dev(b), x, 3)
             xs = host(x)
