@@ -669,6 +669,9 @@ __global__ void restrict_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ 
       C<T> acc[RG];
 #pragma unroll
       for (int r = 0; r < RG; ++r) acc[r] = mk<T>((T)0, (T)0);
+      // unrolled so that several rows' loads of P are in flight per lane
+      // (the sums keep their order)
+#pragma unroll 4
       for (int row = lane; row < m.rows; row += 32) {
         const C<T> a = ldp(Pk + row);
 #pragma unroll
@@ -706,6 +709,9 @@ __global__ void prolong_kernel(const C<T> *__restrict__ in, C<T> *__restrict__ o
       C<T> acc[RG];
 #pragma unroll
       for (int r = 0; r < RG; ++r) acc[r] = mk<T>((T)0, (T)0);
+      // unrolled so that several test vectors' loads of P are in flight
+      // (the sums keep their order)
+#pragma unroll 4
       for (int k = 0; k < m.ntv; ++k) {
         const C<T> a = ldp(PX + (int64_t)k * m.rows + row);
 #pragma unroll
