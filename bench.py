@@ -15,11 +15,14 @@ Default workload (`--workload 48x48x48x96`): a 48^3 x 96 lattice, synthetic
 SU(3) links U = exp(i 0.4 H) drawn on the device (seed 1005), m0 = -0.40,
 four-level hierarchy (4^4, 2^4, 2^4 aggregates, 16 test vectors per level,
 coarsest level 3^3 x 6 inverted densely), every solve to a relative
-residual of 1e-12: FP32 MG-preconditioned FGMRES(8) with SAP and a learned
-one-channel post-smoothing step inside FP64 defect correction.  The network
-is trained on the GPU on 2000 residual / error pairs of the solver on a
-16^4 field of the same generator (seed 1006) and its weights carried over
-(the layers are translation and gauge covariant).  A step is one call of
+residual of 1e-12: FP32 MG-preconditioned FGMRES(8) with SAP inside FP64
+defect correction, the fine-level solves of the O_0 term starting from the
+guess of a learned one-channel network (--net-mode guess; after-sap and
+replace-sap put the network into the smoother instead).  The network is
+trained on the GPU on 2000 projected Z4 right-hand sides drawn on a 16^4
+field of the same generator (seed 1006; the smoother roles train on the
+solver's post-SAP residuals), and its weights are carried over: the layers
+are translation and gauge covariant.  A step is one call of
 mgmlmc_estimate_trace with 4 Z4 samples for each fine-level term (O_0,
 F_0; one right-hand-side block, the fine level's memory bound) and 32 for
 each coarse term (O_1, O_2, F_1, F_2, coarsest).  Inputs are resident in HBM
