@@ -185,6 +185,8 @@ void Engine::net_train(const mgmlmc_train_params &p, mgmlmc_train_result &out) {
   if (p.steps < 1 || p.batch < 1 || p.batch > 64 || p.pool < p.batch || !(p.lr > 0.0) ||
       (p.source != 0 && p.source != 1))
     throw Error(MGMLMC_ERR_ARG, "invalid training parameters");
+  if (p.source == 1 && n_levels() < 2)
+    throw Error(MGMLMC_ERR_ARG, "training source 1 needs a coarse level (the projector of the O_0 term)");
   const auto t0 = std::chrono::steady_clock::now();
   if (net_.C != p.channels) net_init(p.channels, p.seed);
   const int64_t n = levels_[0].g.n();
