@@ -69,3 +69,24 @@ def test_oracle_threads_bounded_by_memory(monkeypatch):
     monkeypatch.setattr(bench, 'host_memory_available', lambda: 1e9)
     assert bench.oracle_threads(0) == 1
     assert bench.host_cores() == 16
+
+
+def test_roofline_class_and_traffic_lookup():
+    """The roofline object: the class with the largest event time is the
+    dominant kernel; achieved = algorithmic bytes / event seconds against the
+    HBM peak; traffic is the recorded ncu figure only while the kernel's
+    source hash and the workload match (null otherwise)."""
+    names = {v: k for k, v in bench.KERNELS.items()}
+    kst = {c: dict(launches=0, ms=0.0, bytes=0.0, flops=0.0) for c in bench.KERNELS}
+    kst[names['sap_sweep_fp32']] = dict(launches=10, ms=150.0, bytes=10 * 35.67e9, flops=10 * 2.614e11)
+    kst[names['coarse_stencil_fp32']] = dict(launches=100, ms=100.0, bytes=100 * 1.5e9, flops=1e12)
+    roof = bench.roofline_of(kst, 600.0, 4, '48x48x48x96', None)
+    assert roof['kernel'] == 'sap_sweep_fp32' and roof['bound'] == 'hbm'
+    assert abs(roof['achieved'] - 35.67e9 / 15e-3 / 1e9) < 1e-6 * roof['achieved']
+    assert abs(roof['frac'] - roof['achieved'] / roof['peak']) < 1e-12
+    assert abs(roof['share_of_profiled_step'] - 0.25) < 1e-12
+    key = ('sap_sweep_fp32', bench.kernel_source_hash('sap_sweep_fp32'), 4, '48x48x48x96')
+    assert roof['traffic'] == bench.TRAFFIC.get(key)
+    # another lattice or batch has no recorded traffic
+    assert bench.roofline_of(kst, 600.0, 4, '16x16x16x16', None)['traffic'] is None
+    assert bench.roofline_of(kst, 600.0, 8, '48x48x48x96', None)['traffic'] is None
