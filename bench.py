@@ -117,8 +117,8 @@ VALIDATE_FIRST = 500000  # sample counters of the allocation check (fresh sample
 # dram bytes per launch of a kernel from an ncu capture, keyed by (kernel,
 # sha1 of the kernel sources it was measured on, right-hand sides per
 # launch, lattice); a stale or missing key gives null.  SAP sweep: dram
-# read + write of its four kernels on 32^3 x 64 with 4 rhs (8.240 GB,
-# profiles/sap_sweep_fp32_32x32x32x64.md), scaled by the site count to
+# read + write of its four kernels on 32^3 x 64 with 4 rhs (8.240 GB, one
+# ncu capture of `--kernel-probe sap`), scaled by the site count to
 # 48^3 x 96 (traffic per site does not depend on the lattice size)
 TRAFFIC = {('sap_sweep_fp32', 'a4045b474347', 4, '48x48x48x96'): 41716159920.0}
 
